@@ -1,0 +1,322 @@
+"""Pins of the FP64 oracle against facts fixed outside its own code.
+
+Each test names the paper passage it follows and the independent fact it
+checks (a closed form, an invariant, brute force or a library routine), so
+that a dropped term, a wrong sign or index, or a transposed operand in the
+oracle fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2512_18863_gb300 import synth as S
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _phantom(shape, spacing, hu_fn=None, iso_index=None):
+    nz, ny, nx = shape
+    sx, sy, sz = spacing
+    ci = iso_index or (nx // 2, ny // 2, nz // 2)
+    origin = (-ci[0] * sx, -ci[1] * sy, -ci[2] * sz)
+    hu = np.zeros(shape, np.float32)
+    if hu_fn is not None:
+        Z, Y, X = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        hu = hu_fn(X, Y, Z).astype(np.float32)
+    return S.Phantom(hu=hu, spacing=tuple(spacing), origin=origin)
+
+
+def _depth_dose_np(machine, z):
+    return np.interp(z, np.arange(len(machine.t_table)) * machine.dz_t, machine.t_table)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2.2, fractional overlap equation: hand-derived values
+# --------------------------------------------------------------------------
+def test_overlap_golden_values():
+    rows = np.loadtxt(os.path.join(GOLDEN, "overlap_eq.txt"), comments="#")
+    for d, lo, hi, D, exp in rows:
+        assert O.overlap(d, lo, hi, D) == pytest.approx(exp, abs=1e-15)
+
+
+def test_overlap_partition_of_unity():
+    """T7: sum_a f(u_a; l, r) D = r - l for any l < r inside the lattice."""
+    rng = np.random.default_rng(0)
+    for D in (2.0, 2.5, 3.0):
+        u = (np.arange(-200, 201)) * D
+        for _ in range(20):
+            lo, hi = np.sort(rng.uniform(-150, 150, 2))
+            s = sum(O.overlap(x, lo, hi, D) for x in u) * D
+            assert s == pytest.approx(hi - lo, rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2 (HU -> relative electron density): piecewise-linear curve
+# --------------------------------------------------------------------------
+def test_hu_to_red_knots_and_clamps():
+    pts = S.HU_TO_RED
+    hu = np.array([-2000, -1000, -500, 0, 500, 1000, 2000, 3000, 5000], float)
+    exp = np.array([0.0, 0.0, 0.5, 1.0, 1.3, 1.6, 2.2, 2.8, 2.8])
+    np.testing.assert_allclose(O.hu_to_red(hu, pts), exp, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.2.4 (WEPL): slab closed forms, air pocket
+# --------------------------------------------------------------------------
+def _slab_profile(n):
+    # air | water | bone (HU 1000 -> RED 1.6) | air pocket | water
+    hu = np.full(n, -1000.0)
+    hu[6:14] = 0.0
+    hu[14:18] = 1000.0
+    hu[18:21] = -1000.0
+    hu[21:29] = 0.0
+    return hu
+
+
+@pytest.mark.parametrize("gantry,axis,sign", [(0.0, "y", +1), (180.0, "y", -1),
+                                              (90.0, "x", +1), (270.0, "x", -1)])
+def test_wepl_slab_closed_form(gantry, axis, sign):
+    n, s = 33, 2.0
+    prof = _slab_profile(n)
+    if axis == "y":
+        ph = _phantom((5, n, n), (s, s, s), lambda X, Y, Z: prof[Y])
+    else:
+        ph = _phantom((5, n, n), (s, s, s), lambda X, Y, Z: prof[X])
+    m = S.machine_model(3, r_px=2)
+    plan = S.static_field(m, gantry_deg=gantry)
+    mod = O.Model(ph, m, plan)
+    z = mod.wepl(0)
+    lat = mod.lattice
+    rho = np.interp(prof, S.HU_TO_RED[:, 0], S.HU_TO_RED[:, 1])
+    # exact integral of the piecewise-constant density from outside the grid
+    # to each voxel centre along the beam direction
+    edges = (np.arange(n + 1) - 0.5 - n // 2) * s          # voxel boundaries, mm from iso
+    for k in range(lat["nw"]):
+        w = (k - lat["cw"]) * lat["du"]
+        pos = sign * w                                      # coordinate along +axis
+        if sign > 0:
+            seg = np.clip(np.minimum(edges[1:], pos) - edges[:-1], 0, None)
+        else:
+            seg = np.clip(edges[1:] - np.maximum(edges[:-1], pos), 0, None)
+        exp = float((seg * rho).sum())
+        assert z[k] == pytest.approx(exp, abs=1e-12), (k, w)
+    # the air pocket (voxels 18..20) leaves the depth unchanged across it
+    kk = [int(round(lat["cw"] + sign * (i - n // 2))) for i in (18, 19, 20)]
+    assert z[kk[0]] == pytest.approx(z[kk[1]], abs=1e-12) == pytest.approx(z[kk[2]], abs=1e-12)
+
+
+# --------------------------------------------------------------------------
+# T1: open-field water depth dose = cal MU T(z) (SID/d)^2 on the central axis
+# (Sec. 2.2.3 inverse square, Sec. 2.2.4 depth, Sec. 2.2.6 kernel unit sum,
+#  Sec. 2.2.7 MU weighting)
+# --------------------------------------------------------------------------
+def test_open_field_depth_dose_closed_form():
+    w = S.water_static_64()
+    mod = O.Model(w.phantom, w.machine, w.plan)
+    D = mod.dose()
+    iy = np.arange(64)
+    depth = (iy + 0.5) * 2.5
+    d = 1000.0 + (iy - 32) * 2.5
+    exp = w.machine.cal * 100.0 * _depth_dose_np(w.machine, depth) * (1000.0 / d) ** 2
+    np.testing.assert_allclose(D[32, :, 32], exp, rtol=1e-12)
+
+
+def _pencil_model(gantry, jaws, sz=3.0, a=0.2, r_px=6):
+    n, s = 41, 2.0
+    ph = _phantom((41, n, n), (s, s, sz))
+    m = S.machine_model(5, r_px=r_px)
+    m.alpha = np.zeros((3, 3))
+    m.alpha[:, 0] = [a, 1.0, 1.0]
+    m.beta = np.zeros((3, 3))
+    m.beta[0, 0] = 1.0
+    plan = S.static_field(m, gantry_deg=gantry, leaf_half=60.0)
+    plan.jaws[0] = jaws
+    plan.mu[0] = 1.0
+    return O.Model(ph, m, plan), m
+
+
+def test_pencil_kernel_shape_and_unit_sum():
+    """Sec. 2.2.5/2.2.6: a one-pixel field at the isocentre plane (m = 1, C = 1)
+    gives D = cal MU T(z_iso) K(p,q); a single-exponential kernel must then fall
+    as exp(-a r) with r = sqrt((p sx)^2 + (q sz)^2) (sx != sz pins the axes)
+    and sum to cal MU T over the plane."""
+    a, R = 0.2, 6
+    mod, m = _pencil_model(0.0, [-1.0, 1.0, -1.5, 1.5], sz=3.0, a=a, r_px=R)
+    D = mod.dose()
+    plane = D[:, 20, :]                       # iso plane (y index 20), [iz][ix]
+    peak = plane[20, 20]
+    dz, dx = np.meshgrid(np.arange(41) - 20, np.arange(41) - 20, indexing="ij")
+    r = np.sqrt((dx * 2.0) ** 2 + (dz * 3.0) ** 2)
+    inside = (np.abs(dx) <= R) & (np.abs(dz) <= R)
+    np.testing.assert_allclose(plane[inside] / peak, np.exp(-a * r[inside]), rtol=1e-12)
+    assert np.abs(plane[~inside]).max() <= 1e-14 * peak
+    T_iso = _depth_dose_np(m, 20.5 * 2.0)
+    assert plane.sum() == pytest.approx(m.cal * T_iso, rel=1e-12)
+
+
+@pytest.mark.parametrize("gantry,peak_at", [(0.0, ("x", 21)), (90.0, ("y", 19)),
+                                            (180.0, ("x", 19)), (270.0, ("y", 21))])
+def test_beam_axis_orientation(gantry, peak_at):
+    """Reading of the geometry (e_u = (cos g, -sin g, 0)): a pixel at u = +2 mm
+    lands at x = +2 mm for gantry 0, y = -2 mm for 90, x = -2 mm for 180."""
+    mod, _ = _pencil_model(gantry, [1.0, 3.0, -1.5, 1.5])
+    D = mod.dose()
+    if peak_at[0] == "x":
+        line = D[20, 20, :]
+    else:
+        line = D[20, :, 20]
+    assert int(np.argmax(line)) == peak_at[1]
+
+
+def test_magnification_of_sharp_field_edge():
+    """Sec. 2.2.3: with an impulse kernel the dose is cal MU T(z) C(d)
+    F_bilinear((SID/d) x_perp): the field appears wider beyond the
+    isocentre and narrower before it, scaled by the inverse square."""
+    ny = 161
+    ph = _phantom((9, ny, 41), (2.5, 2.5, 2.5))
+    m = S.machine_model(11, r_px=3, delta_kernel=True)
+    plan = S.static_field(m, 0.0, half_x=20.0, half_y=20.0, leaf_half=50.0, mu=1.0)
+    mod = O.Model(ph, m, plan)
+    D = mod.dose()
+    lat = mod.lattice
+    nu, cu = lat["nu"], lat["cu"]
+    a = np.arange(nu)
+    fx_nodes = np.clip(8.5 - np.abs(a - cu), 0.0, 1.0)      # 20 mm edge = half of pixel 8
+    for iy in (0, 30, 80, 130, 160):
+        w = (iy - 80) * 2.5
+        mk = 1000.0 / (1000.0 + w)
+        depth = (iy + 0.5) * 2.5
+        ix = np.arange(41)
+        i = ix - 20 + cu
+        exp = m.cal * _depth_dose_np(m, depth) * mk ** 2 * np.interp(mk * (i - cu) + cu, a, fx_nodes)
+        np.testing.assert_allclose(D[4, iy, :], exp, rtol=1e-12, atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# T3-T6: linearity, superposition, leakage, rotation
+# --------------------------------------------------------------------------
+def test_mu_linearity_and_cp_superposition():
+    w = S.small_pelvis(n=(16, 28, 28), n_cp=4, r_px=3)
+    mod = O.Model(w.phantom, w.machine, w.plan)
+    D = mod.dose()
+    np.testing.assert_allclose(mod.dose(mu=2.5 * w.plan.mu), 2.5 * D, rtol=1e-13, atol=1e-15 * D.max())
+    acc = np.zeros_like(D)
+    for b in range(w.plan.n_cp):
+        mu = np.zeros(w.plan.n_cp)
+        mu[b] = w.plan.mu[b]
+        m2 = S.Machine(**{**w.machine.__dict__, "eps_mu": 0.0})
+        acc += O.Model(w.phantom, m2, w.plan).dose(mu=mu)
+    np.testing.assert_allclose(acc, D, rtol=0, atol=1e-13 * D.max())
+
+
+def _water_model(plan_jaws, plan_leaves, gantry=30.0, wmin_leaf=0.5):
+    ph = _phantom((21, 33, 33), (2.5, 2.5, 2.5))
+    m = S.machine_model(13, r_px=4)
+    m.wmin_leaf = wmin_leaf
+    plan = S.static_field(m, gantry_deg=gantry)
+    plan.jaws[0] = plan_jaws
+    plan.leaves[0, :, 0] = plan_leaves[0]
+    plan.leaves[0, :, 1] = plan_leaves[1]
+    plan.mu[0] = 1.0
+    return O.Model(ph, m, plan).dose(), m
+
+
+def test_abutting_half_fields():
+    """T4: f is additive over adjoining intervals, so jaw-made halves sum to
+    the full field exactly; leaf-made halves add one extra leakage term
+    tau * D(jaw-only field)."""
+    full, _ = _water_model([-50, 50, -40, 40], (-60, 60))
+    h1, _ = _water_model([-50, 0, -40, 40], (-60, 60))
+    h2, _ = _water_model([0, 50, -40, 40], (-60, 60))
+    np.testing.assert_allclose(h1 + h2, full, rtol=0, atol=1e-13 * full.max())
+    lfull, m = _water_model([-50, 50, -40, 40], (-50, 50))
+    l1, _ = _water_model([-50, 50, -40, 40], (-50, 0))
+    l2, _ = _water_model([-50, 50, -40, 40], (0, 50))
+    np.testing.assert_allclose(l1 + l2 - lfull, m.tau * full, rtol=0, atol=1e-13 * full.max())
+
+
+def test_closed_mlc_leaves_only_leakage():
+    """T5: l = r with w_min = 0 gives f_leaf = 0, so D = tau D(jaw-only)."""
+    jaw_only, m = _water_model([-30, 40, -20, 30], (-80, 80), wmin_leaf=0.0)
+    closed, _ = _water_model([-30, 40, -20, 30], (10, 10), wmin_leaf=0.0)
+    np.testing.assert_allclose(closed, m.tau * jaw_only, rtol=0, atol=1e-14 * jaw_only.max())
+
+
+def test_rotation_symmetry_90_degrees():
+    """T6: on a phantom invariant under 90-degree rotation about the
+    isocentre (odd grid, iso on a voxel centre), D_{g+90}(Q x) = D_g(x) with
+    Q(x, y) = (y, -x)."""
+    n, c = 33, 16
+
+    def hu(X, Y, Z):
+        dx, dy = X - c, Y - c
+        out = np.where(dx ** 2 + dy ** 2 <= 14 ** 2, 0.0, -1000.0)
+        for px, py in ((6, 0), (-6, 0), (0, 6), (0, -6)):
+            out = np.where((dx - px) ** 2 + (dy - py) ** 2 <= 4, 800.0, out)
+        return out
+
+    ph = _phantom((7, n, n), (2.5, 2.5, 2.5), hu)
+    m = S.machine_model(17, r_px=4)
+    rng = np.random.default_rng(3)
+    out = []
+    for g in (30.0, 120.0):
+        plan = S.static_field(m, gantry_deg=g)
+        plan.jaws[0] = [-10.0, 25.0, -15.0, 10.0]
+        plan.leaves[0, :, 0] = rng.uniform(-15, 0, m.n_pairs) if not out else plan_l0
+        plan.leaves[0, :, 1] = rng.uniform(2, 20, m.n_pairs) if not out else plan_l1
+        plan_l0, plan_l1 = plan.leaves[0, :, 0].copy(), plan.leaves[0, :, 1].copy()
+        plan.mu[0] = 1.0
+        out.append(O.Model(ph, m, plan).dose())
+    A, B = out
+    iy, ix = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    np.testing.assert_allclose(B[:, 2 * c - ix, iy], A[:, iy, ix], rtol=0, atol=1e-12 * A.max())
+
+
+def test_fluence_area_closed_forms():
+    """T7: jaws only: sum F dA = jaw area; leaves inside pixel-aligned jaws:
+    sum F dA = tau A_jaw + (1 - tau) sum_i (r_i - l_i) |strip_i within the y jaws|.
+    Rows: partition of unity of the leaf strips inside the MLC span."""
+    ph = _phantom((170, 9, 41), (2.5, 2.5, 2.5))   # u lattice reaches +-55 mm
+    m = S.machine_model(19, r_px=2)
+    plan = S.static_field(m)
+    mod = O.Model(ph, m, plan)
+    du, dv = mod.lattice["du"], mod.lattice["dv"]
+    lv_open = np.stack([np.full(m.n_pairs, -100.0), np.full(m.n_pairs, 100.0)], 1)
+    jw = np.array([-13.3, 7.9, -21.7, 34.1])
+    F = mod.fluence(lv_open, jw)
+    assert F.sum() * du * dv == pytest.approx((jw[1] - jw[0]) * (jw[3] - jw[2]), rel=1e-13)
+    # leaf-defined aperture, pixel-aligned jaws (edges at +-1.25 + 2.5 k)
+    jw2 = np.array([-26.25, 26.25, -31.25, 18.75])
+    rng = np.random.default_rng(5)
+    lv = np.stack([rng.uniform(-20, -1, m.n_pairs), rng.uniform(1, 20, m.n_pairs)], 1)
+    F2 = mod.fluence(lv, jw2)
+    lb = m.leaf_bounds
+    strip = np.clip(np.minimum(lb[1:], jw2[3]) - np.maximum(lb[:-1], jw2[2]), 0, None)
+    a_jaw = (jw2[1] - jw2[0]) * (jw2[3] - jw2[2])
+    exp = m.tau * a_jaw + (1 - m.tau) * ((lv[:, 1] - lv[:, 0]) * strip).sum()
+    assert F2.sum() * du * dv == pytest.approx(exp, rel=1e-13)
+    # leaf strips tile the MLC span: with tau = 0 and all leaves open, F = 1
+    # on every row inside +-200 mm and 0 outside it
+    m0 = S.Machine(**{**m.__dict__, "tau": 0.0})
+    mod0 = O.Model(ph, m0, plan)
+    F3 = mod0.fluence(lv_open, np.array([-50.0, 50.0, -300.0, 300.0]))
+    v = (np.arange(mod0.lattice["nv"]) - mod0.lattice["cv"]) * dv
+    col = F3[:, int(mod0.lattice["cu"])]
+    inside = np.abs(v) < 200.0 - dv / 2
+    outside = np.abs(v) > 200.0 + dv / 2
+    np.testing.assert_allclose(col[inside], 1.0, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(col[outside], 0.0, rtol=0, atol=0)
+
+
+# --------------------------------------------------------------------------
+# T8: brute force on a 16^3 grid
+# --------------------------------------------------------------------------
+def test_brute_force_16cube():
+    w = S.small_pelvis(n=(16, 16, 16), spacing=4.0, n_cp=3, r_px=3, ptv_radii=(12.0, 10.0, 12.0))
+    mod = O.Model(w.phantom, w.machine, w.plan)
+    fast = mod.dose()
+    brute = mod.dose(brute=True)
+    assert fast.max() > 0
+    np.testing.assert_allclose(fast, brute, rtol=0, atol=1e-12 * brute.max())
