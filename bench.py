@@ -1,0 +1,337 @@
+#!/usr/bin/env python
+"""Benchmark of the dose engine: arc dose evaluations per second, forward +
+adjoint, on a 256x256x160 pelvis-like grid at 2 mm with a two-arc VMAT plan
+(2 x 178 control points, kernel radius 4 cm by default).
+
+One step = pdrt_dose_forward + pdrt_dose_backward of the whole plan (all
+control points), with the dose gradient of a quadratic dose-volume objective
+resident in HBM.  value = arcs (178 CPs) evaluated per second, whole job.
+The L2 cache (129 MB) is flushed between steps by writing a 256 MB buffer.
+
+--impl reference times the FP64 CPU oracle (the method's plain definition)
+on the host cores on a bounded sample (one control point per step at full
+grid size), in the same metric.
+
+Multi-GPU: the method's control points are independent, but one plan fits a
+GPU; --gpus N runs N independent replicas (one process per GPU via
+torch.distributed.run), value = total arcs/s over ranks, no collective on the
+data path.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "arc dose evals/sec fwd+adjoint (256^3-class grid, 178 CPs) vs HBM roofline; warm vs plain"
+UNIT = "arc evals/s"
+CP_PER_ARC = 178
+SMS, FP32_LANES = 152, 128
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pdrt", choices=["pdrt", "reference"])
+    ap.add_argument("--r-cm", type=float, default=4.0)
+    ap.add_argument("--cpu-sample-cps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload(r_cm):
+    from paper_2512_18863_gb300 import synth
+    return synth.pelvis_two_arc_256(r_cm=r_cm)
+
+
+def _subplan(w, sel):
+    from paper_2512_18863_gb300 import synth
+    return synth.Workload(w.name, w.phantom, w.machine,
+                          synth.Plan(w.plan.gantry_deg[sel], w.plan.iso, w.plan.leaves[sel],
+                                     w.plan.jaws[sel], w.plan.mu[sel]))
+
+
+def _objective_grad(D, masks, torch):
+    """dL/dD of L = 100 mean_PTV (D - Dp)^2 + sum_s l_s mean_s max(D - d_s, 0)^2
+    (prescription Dp = 0.9 x median PTV dose; OAR thresholds 0.5 Dp)."""
+    ptv = masks["ptv"]
+    dp = 0.9 * float(D[ptv].median())
+    g = torch.zeros_like(D)
+    g[ptv] = 100.0 * 2.0 * (D[ptv] - dp) / ptv.sum()
+    for name, lam in (("bladder", 1.0), ("rectum", 10.0)):
+        m = masks[name]
+        ex = torch.clamp(D[m] - 0.5 * dp, min=0.0)
+        g[m] += lam * 2.0 * ex / m.sum()
+    return g.contiguous()
+
+
+class _Clocks:
+    """nvidia-smi sampling (200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = os.path.join(tempfile.gettempdir(), f"pdrt_clocks_{os.getpid()}.csv")
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(gpu_index), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _cpu_baseline(w, n_cps):
+    """FP64 oracle forward + adjoint on n_cps control points at full size."""
+    from oracle import oracle
+    sel = np.linspace(0, w.plan.n_cp - 1, n_cps).round().astype(int)
+    sub = _subplan(w, sel)
+    mod = oracle.Model(sub.phantom, sub.machine, sub.plan)
+    rng = np.random.default_rng(0)
+    g = rng.standard_normal(sub.phantom.shape)
+    t0 = time.perf_counter()
+    mod.dose()
+    mod.dose_grad(g)
+    dt = time.perf_counter() - t0
+    return {"value": (n_cps / CP_PER_ARC) / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n_cps} of {w.plan.n_cp} control points (fwd+adjoint) on the full "
+                      f"256x256x160 grid, FP64, OpenMP; {dt:.1f} s"}
+
+
+def _reference(args):
+    world, rank, _ = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+        if rank != 0:
+            dist.barrier()
+            dist.destroy_process_group()
+            return
+    from oracle import oracle
+    w = _workload(args.r_cm)
+    rng = np.random.default_rng(0)
+    times = []
+    for s in range(args.warmup + args.steps):
+        b = int(rng.integers(0, w.plan.n_cp))
+        sub = _subplan(w, np.array([b]))
+        mod = oracle.Model(sub.phantom, sub.machine, sub.plan)
+        g = rng.standard_normal(sub.phantom.shape)
+        t0 = time.perf_counter()
+        mod.dose()
+        mod.dose_grad(g)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    per_step = float(np.mean(times))
+    value = (1.0 / CP_PER_ARC) / per_step
+    nz, ny, nx = w.phantom.shape
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded pelvis phantom and VMAT arcs)",
+           "config": {"workload": w.name, "grid": [nx, ny, nz], "spacing_mm": 2.0,
+                      "n_cp": int(w.plan.n_cp), "kernel_radius_px": int(w.machine.r_px)},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                            "kind": "oracle",
+                            "sample": "one control point per step (fwd+adjoint), full grid"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2512_18863_gb300 import _lib
+    from paper_2512_18863_gb300.engine import DoseEngine
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = _workload(args.r_cm)
+    eng = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso)
+    dev = eng.device
+    leaves = torch.tensor(w.plan.leaves, dtype=torch.float32, device=dev)
+    jaws = torch.tensor(w.plan.jaws, dtype=torch.float32, device=dev)
+    mu = torch.tensor(w.plan.mu, dtype=torch.float32, device=dev)
+    masks = {k: torch.tensor(v, device=dev) for k, v in w.phantom.masks.items()}
+    dose = torch.empty(w.phantom.shape, dtype=torch.float32, device=dev)
+    eng.forward(leaves, jaws, mu, out=dose)
+    g = _objective_grad(dose, masks, torch)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        eng.forward(leaves, jaws, mu, out=dose)
+        eng.backward(leaves, jaws, mu, g)
+        flush.zero_()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    work = eng.work()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = _lib.pdrt_launch_count()
+    eng.profile(True)
+    clocks = _Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = eng.profile_read()
+    eng.profile(False)
+    launches = _lib.pdrt_launch_count() - launches0
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    arcs_per_step = w.plan.n_cp / CP_PER_ARC
+    value = arcs_per_step * args.steps * world / (ms_max / 1e3)
+
+    # roofline of the dominant kernel: the direct FP32 convolution (forward and adjoint)
+    conv_ms = prof["conv_forward"]["total_ms"] + prof["conv_adjoint"]["total_ms"]
+    conv_launches = prof["conv_forward"]["launches"] + prof["conv_adjoint"]["launches"]
+    flops_total = 2.0 * work["conv_flops"] * args.steps          # two convolution passes per step
+    achieved = flops_total / (conv_ms / 1e3) / 1e12
+    peak = SMS * FP32_LANES * 2 * 2070.0e6 / 1e12
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps}
+               for k, v in prof.items() if not k.startswith("_") and v["launches"]}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda t: t.cpu().pin_memory()
+        h_leaves, h_jaws, h_mu, h_g = pin(leaves), pin(jaws), pin(mu), pin(g)
+        h_dose = torch.empty(dose.shape, dtype=torch.float32).pin_memory()
+        h_dl, h_dj, h_dm = (torch.empty(t.shape, dtype=torch.float32).pin_memory()
+                            for t in (leaves, jaws, mu))
+        d_l, d_j, d_m, d_g = (torch.empty_like(t) for t in (leaves, jaws, mu, g))
+
+        def e2e_step():
+            d_l.copy_(h_leaves, non_blocking=True)
+            d_j.copy_(h_jaws, non_blocking=True)
+            d_m.copy_(h_mu, non_blocking=True)
+            d_g.copy_(h_g, non_blocking=True)
+            eng.forward(d_l, d_j, d_m, out=dose)
+            dl, dj, dm = eng.backward(d_l, d_j, d_m, d_g)
+            h_dose.copy_(dose, non_blocking=True)
+            h_dl.copy_(dl, non_blocking=True)
+            h_dj.copy_(dj, non_blocking=True)
+            h_dm.copy_(dm, non_blocking=True)
+            flush.zero_()
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        el = lambda ts: sum(t.numel() * 4 for t in ts)
+        e2e = {"value": arcs_per_step * args.steps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": el([h_leaves, h_jaws, h_mu, h_g]),
+               "d2h_bytes_per_step": el([h_dose, h_dl, h_dj, h_dm])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(w, args.cpu_sample_cps)
+
+    if rank == 0:
+        nz, ny, nx = w.phantom.shape
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (seeded pelvis phantom and VMAT arcs)",
+               "config": {"workload": w.name, "grid": [nx, ny, nz], "spacing_mm": 2.0,
+                          "n_cp": int(w.plan.n_cp), "kernel_radius_px": int(w.machine.r_px),
+                          "step": "forward + adjoint of all control points",
+                          "l2": "flushed between steps (256 MB write)",
+                          "parallelism": "replicas" if world > 1 else "single"},
+               "roofline": {"bound": "alu", "kernel": "conv_forward+conv_adjoint",
+                            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                            "frac": achieved / peak, "traffic": None,
+                            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                            "flops_per_launch": flops_total / max(conv_launches, 1),
+                            "ms_per_launch": conv_ms / max(conv_launches, 1)},
+               "kernels": kernels, "work": work, "gpu_launches": launches,
+               "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
+    eng.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        _reference(args)
+    else:
+        _gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * pdrt.h -- C ABI of the GB300 (sm_103a) pencil-beam VMAT dose engine.
+ *
+ * The engine maps delivery parameters (MLC leaf positions, jaws, MUs at each
+ * control point of a VMAT arc) to a 3-D dose on a CT grid, and back-propagates
+ * a dose gradient to those parameters.  It implements the layer chain of
+ * arXiv 2512.18863, Sec. 2.1-2.2.7:
+ *   hardware projection (Sec. 2.2.1) -> fluence map (Sec. 2.2.2, fractional
+ *   overlap, jaw masking, MLC transmission) -> divergent fluence volume
+ *   (Sec. 2.2.3, magnification SID/d and inverse square) -> radiological depth
+ *   on the central ray (Sec. 2.2.4) -> depth-dependent radial kernel
+ *   (Sec. 2.2.5) -> per-slice 2-D convolution (Sec. 2.2.6) -> rotation to the
+ *   patient grid and MU-weighted sum (Sec. 2.2.7, Eq. D_total).
+ *
+ * Conventions shared by every entry point
+ *   - Lengths in mm, angles in degrees, MU in monitor units.  Leaf and jaw
+ *     positions are given at the isocentre plane.
+ *   - Volumes are [nz][ny][nx] float32, x fastest.  Voxel (0,0,0) is centred
+ *     at origin_mm.  sx must equal sy (the beam frame uses one in-plane pitch).
+ *   - Leaves are [n_cp][n_pairs][2] float32: (left, right) edge of each pair.
+ *     Jaws are [n_cp][4] float32: (x-, x+, y-, y+).  MU is [n_cp] float32.
+ *   - Geometry: the gantry rotates about the patient z axis; the beam
+ *     direction is e_w = (sin g, cos g, 0), leaves travel along
+ *     e_u = (cos g, -sin g, 0), leaf pairs are stacked along e_v = +z, and the
+ *     source sits at iso - SID e_w.
+ *   - Pointers named *_dev are device pointers (cudaMalloc / PyTorch CUDA
+ *     tensors) on the device that was current at pdrt_grid_create; pointers
+ *     named *_host or passed by value are host memory read during the call.
+ *   - Streams: pdrt_stream_t is a cudaStream_t (NULL = legacy default stream).
+ *     pdrt_dose_forward / pdrt_dose_backward only enqueue work on that stream
+ *     and return; they allocate nothing (all scratch is owned by the plan and
+ *     is allocated in pdrt_plan_upload).  One plan must not be used by two
+ *     calls that can overlap on the GPU (they share the plan's scratch).
+ *   - Ownership: the caller owns every buffer passed in; the library owns the
+ *     grid and plan handles and frees them in pdrt_*_destroy.
+ *   - Errors: every call returns a pdrt_status; on failure pdrt_last_error()
+ *     gives a message (thread-local, valid until the next call on the same
+ *     thread).  Argument errors are detected on the host before any work is
+ *     enqueued.  Bad values inside device buffers (NaN leaves, jaws or MU) are
+ *     detected on the device and reported by pdrt_plan_status.
+ */
+#ifndef PDRT_H
+#define PDRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDRT_MAX_PAIRS 160        /* leaf pairs per bank */
+#define PDRT_MAX_RADIUS_PX 44     /* kernel half-window, pixels */
+#define PDRT_MAX_DEPTH_TABLE 4096 /* depth-dose table entries */
+#define PDRT_MAX_HU_POINTS 32     /* HU -> density calibration points */
+
+typedef struct pdrt_grid_s *pdrt_grid_t;
+typedef struct pdrt_plan_s *pdrt_plan_t;
+typedef void *pdrt_stream_t;
+
+typedef enum {
+    PDRT_OK = 0,
+    PDRT_EINVAL = 1,   /* invalid argument value (NULL pointer, NaN, out of range) */
+    PDRT_ESHAPE = 2,   /* inconsistent sizes */
+    PDRT_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    PDRT_ENOMEM = 4,   /* device or host allocation failed */
+    PDRT_EDEVICE = 5   /* the device does not support this build (needs sm_103a) */
+} pdrt_status;
+
+/* Device-detected input problems, reported by pdrt_plan_status. */
+#define PDRT_FLAG_NAN_INPUT 1u     /* a leaf, jaw or MU value was NaN/inf */
+#define PDRT_FLAG_CAPACITY 2u      /* internal: a slice's work exceeded the plan's scratch
+                                      bound and was dropped (dose incomplete) */
+
+/*
+ * Beam model (machine) constants, Sec. 2.2 and Sec. 2.4.
+ *   sid_mm          source-isocentre distance.
+ *   leaf_bounds_mm  n_pairs+1 ascending positions along e_v of the leaf-pair
+ *                   boundaries at the isocentre plane.
+ *   tau             MLC transmission (Sec. 2.2.2): F = f_jaw (tau + (1-tau) f_leaf).
+ *   wmin_*_mm, f_*_mm  minimum opening and half travel range of the aperture
+ *                   centre in the projection of Sec. 2.2.1 (jaw values apply
+ *                   to both jaw pairs).
+ *   eps_mu          lower MU bound of Sec. 2.2.1.
+ *   kernel_radius_px  half window R of the (2R+1)^2 lateral kernel (Sec. 2.2.5).
+ *   kernel_alpha[c][k], kernel_beta[c][k]  three radial exponentials
+ *                   K(r;z) = sum_c w_c(z) exp(-a_c(z) r) / S_c(z) with
+ *                   a_c = max(alpha_c0 + alpha_c1 z + alpha_c2 z^2, 1e-4) /mm,
+ *                   w_c = max(beta_c0 + beta_c1 z + beta_c2 z^2, 0), normalised
+ *                   to sum 1, S_c the sum of exp(-a_c r) over the window.
+ *   depth_dose[n_depth], depth_step_mm  depth-dose table T(z) at z = m step,
+ *                   linearly interpolated and clamped at both ends.
+ *   cal             output calibration factor (Sec. 2.4).
+ *   ste             1: the projection of Sec. 2.2.1 is the identity in the
+ *                   backward pass (straight-through estimator); 0: exact
+ *                   Jacobian (zero gradient through active clamps).
+ */
+typedef struct {
+    double sid_mm;
+    int32_t n_pairs;
+    double leaf_bounds_mm[PDRT_MAX_PAIRS + 1];
+    double tau;
+    double wmin_leaf_mm, wmin_jaw_mm;
+    double f_leaf_mm, f_jaw_mm;
+    double eps_mu;
+    int32_t kernel_radius_px;
+    double kernel_alpha[3][3];
+    double kernel_beta[3][3];
+    int32_t n_depth;
+    double depth_step_mm;
+    double depth_dose[PDRT_MAX_DEPTH_TABLE];
+    double cal;
+    int32_t ste;
+} pdrt_machine;
+
+/* Beam-frame lattice and scratch layout of a plan (host-side query). */
+typedef struct {
+    int32_t nu, nv, nw;          /* lattice size along e_u, e_v, e_w */
+    double cu, cv, cw;           /* lattice index of the isocentre */
+    int32_t n_cp;
+    int32_t chunk_cp;            /* control points processed per pass */
+    size_t scratch_bytes;        /* device scratch owned by the plan */
+} pdrt_plan_info;
+
+/* Work counters of the last forward/backward call (for roofline accounting). */
+typedef struct {
+    int64_t active_slices;       /* (control point, beam slice) pairs with work */
+    int64_t support_points;      /* beam-frame points with non-zero fluence input */
+    int64_t region_points;       /* beam-frame points where dose is produced */
+    int64_t taps;                /* (2R+1)^2 */
+    double conv_flops;           /* 2 * taps * support_points: one convolution pass */
+} pdrt_work;
+
+/* Per-kernel device time accumulated while profiling is enabled. */
+#define PDRT_NUM_KERNELS 8
+typedef struct {
+    const char *name[PDRT_NUM_KERNELS];
+    int64_t launches[PDRT_NUM_KERNELS];
+    double total_ms[PDRT_NUM_KERNELS];
+    int32_t overflow;            /* 1 if the event pool ran out (times incomplete) */
+} pdrt_profile;
+
+/*
+ * Create a CT grid on the current device.
+ *   out         receives the handle.
+ *   hu_dev      [nz][ny][nx] Hounsfield units (device, read once, not kept).
+ *   sx,sy,sz    voxel spacing (mm); sx == sy required.
+ *   origin_mm   centre of voxel (0,0,0) (host, 3 values).
+ *   hu_red_host n_pts (HU, relative electron density) pairs, ascending HU
+ *               (host); the commissioned piecewise-linear curve of Sec. 2.2,
+ *               clamped at both ends.
+ * Errors: EINVAL (NULL pointers, non-positive sizes or spacing, sx != sy,
+ * unsorted or too many points), EDEVICE (device is not sm_103), ENOMEM, ECUDA.
+ */
+pdrt_status pdrt_grid_create(pdrt_grid_t *out, const float *hu_dev, int32_t nx, int32_t ny,
+                             int32_t nz, double sx, double sy, double sz, const double origin_mm[3],
+                             const double *hu_red_host, int32_t n_pts, pdrt_stream_t stream);
+void pdrt_grid_destroy(pdrt_grid_t g);
+
+/*
+ * Upload a VMAT plan geometry (Sec. 2.2: beam sequence of control points).
+ *   gantry_deg_host  [n_cp] gantry angle of each control point (host).
+ *   iso_mm           isocentre, patient frame (host, 3 values).
+ *   m                beam model (host, copied).
+ *   scratch_budget_bytes  upper bound on the device scratch the plan may own
+ *                    (0 = library default); it sets how many control points
+ *                    one pass processes.
+ * The plan owns all device scratch the forward and backward passes need.
+ * Errors: EINVAL (bad values; kernel radius above PDRT_MAX_RADIUS_PX;
+ * SID not larger than the grid's reach from the isocentre), ENOMEM, ECUDA.
+ */
+pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
+                             const double *gantry_deg_host, const double iso_mm[3],
+                             const pdrt_machine *m, size_t scratch_budget_bytes,
+                             pdrt_stream_t stream);
+void pdrt_plan_destroy(pdrt_plan_t p);
+
+/*
+ * Forward dose (Eq. D_total):
+ *   dose(x) = cal sum_b MU^_b  Rot_b( T(z) (K(z) * Phi_b) )(x)
+ * with Phi_b the divergent fluence volume of control point b.
+ *   leaves_dev [n_cp][n_pairs][2], jaws_dev [n_cp][4], mu_dev [n_cp] (device, raw:
+ *   the projection of Sec. 2.2.1 is applied inside).
+ *   dose_dev   [nz][ny][nx] (device), overwritten.
+ * Errors: EINVAL (NULL pointers, handles from different grids), ECUDA.
+ */
+pdrt_status pdrt_dose_forward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_dev,
+                              const float *jaws_dev, const float *mu_dev, float *dose_dev,
+                              pdrt_stream_t stream);
+
+/*
+ * Adjoint of pdrt_dose_forward: given dL/d dose, writes dL/d leaves, dL/d jaws
+ * and dL/d MU (raw parameters; through the projection of Sec. 2.2.1 as set by
+ * machine.ste).  Radiological depths and kernels are recomputed, not stored.
+ *   dose_grad_dev [nz][ny][nx] (device, read).
+ *   dleaves_dev, djaws_dev, dmu_dev: same shapes as the inputs, overwritten.
+ * Leaf edges are differentiated as the piecewise-linear overlap of
+ * Sec. 2.2.2 (one-sided at pixel boundaries).
+ * Errors: as pdrt_dose_forward.
+ */
+pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_dev,
+                               const float *jaws_dev, const float *mu_dev,
+                               const float *dose_grad_dev, float *dleaves_dev, float *djaws_dev,
+                               float *dmu_dev, pdrt_stream_t stream);
+
+/* Lattice and scratch sizes of a plan (host only, no device work). */
+pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out);
+
+/*
+ * Synchronises `stream`, returns the device-detected input flags
+ * (PDRT_FLAG_*) raised since the previous call, and clears them.
+ */
+pdrt_status pdrt_plan_status(pdrt_plan_t p, pdrt_stream_t stream, uint32_t *flags_out);
+
+/* Synchronises `stream` and returns the work counters of the last call. */
+pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the launch stream around
+ * every kernel the plan launches.  enable != 0 starts (and clears) a
+ * measurement; pdrt_profile_read synchronises `stream` and returns the sums.
+ */
+pdrt_status pdrt_profile_enable(pdrt_plan_t p, int32_t enable);
+pdrt_status pdrt_profile_read(pdrt_plan_t p, pdrt_stream_t stream, pdrt_profile *out);
+
+/* Number of kernels this library has launched since it was loaded. */
+int64_t pdrt_launch_count(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pdrt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDRT_H */

@@ -1,0 +1,224 @@
+"""Thin ctypes binding of the C ABI in include/pdrt.h (argument marshalling only).
+
+The Python functions carry the C names.  Device buffers are passed as raw
+pointers (int), streams as cudaStream_t values; every non-OK status raises
+PdrtError with pdrt_last_error().  There is no fallback: if the library is not
+built, load() raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from . import build as _build
+
+MAX_PAIRS = 160
+MAX_RADIUS_PX = 44
+MAX_DEPTH_TABLE = 4096
+MAX_HU_POINTS = 32
+NUM_KERNELS = 8
+FLAG_NAN_INPUT = 1
+FLAG_CAPACITY = 2
+
+STATUS = {0: "PDRT_OK", 1: "PDRT_EINVAL", 2: "PDRT_ESHAPE", 3: "PDRT_ECUDA", 4: "PDRT_ENOMEM",
+          5: "PDRT_EDEVICE"}
+
+
+class PdrtError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class pdrt_machine(C.Structure):
+    _fields_ = [("sid_mm", C.c_double), ("n_pairs", C.c_int32),
+                ("leaf_bounds_mm", C.c_double * (MAX_PAIRS + 1)), ("tau", C.c_double),
+                ("wmin_leaf_mm", C.c_double), ("wmin_jaw_mm", C.c_double),
+                ("f_leaf_mm", C.c_double), ("f_jaw_mm", C.c_double), ("eps_mu", C.c_double),
+                ("kernel_radius_px", C.c_int32), ("kernel_alpha", (C.c_double * 3) * 3),
+                ("kernel_beta", (C.c_double * 3) * 3), ("n_depth", C.c_int32),
+                ("depth_step_mm", C.c_double), ("depth_dose", C.c_double * MAX_DEPTH_TABLE),
+                ("cal", C.c_double), ("ste", C.c_int32)]
+
+
+class pdrt_plan_info(C.Structure):
+    _fields_ = [("nu", C.c_int32), ("nv", C.c_int32), ("nw", C.c_int32),
+                ("cu", C.c_double), ("cv", C.c_double), ("cw", C.c_double),
+                ("n_cp", C.c_int32), ("chunk_cp", C.c_int32), ("scratch_bytes", C.c_size_t)]
+
+
+class pdrt_work(C.Structure):
+    _fields_ = [("active_slices", C.c_int64), ("support_points", C.c_int64),
+                ("region_points", C.c_int64), ("taps", C.c_int64), ("conv_flops", C.c_double)]
+
+
+class pdrt_profile(C.Structure):
+    _fields_ = [("name", C.c_char_p * NUM_KERNELS), ("launches", C.c_int64 * NUM_KERNELS),
+                ("total_ms", C.c_double * NUM_KERNELS), ("overflow", C.c_int32)]
+
+
+_VP = C.c_void_p
+_SIG = {
+    "pdrt_grid_create": (C.c_int, [C.POINTER(_VP), _VP, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                   C.c_double, C.c_double, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double), C.c_int32, _VP]),
+    "pdrt_grid_destroy": (None, [_VP]),
+    "pdrt_plan_upload": (C.c_int, [C.POINTER(_VP), _VP, C.c_int32, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double), C.POINTER(pdrt_machine), C.c_size_t, _VP]),
+    "pdrt_plan_destroy": (None, [_VP]),
+    "pdrt_dose_forward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "pdrt_dose_backward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "pdrt_plan_get_info": (C.c_int, [_VP, C.POINTER(pdrt_plan_info)]),
+    "pdrt_plan_status": (C.c_int, [_VP, _VP, C.POINTER(C.c_uint32)]),
+    "pdrt_plan_work": (C.c_int, [_VP, _VP, C.POINTER(pdrt_work)]),
+    "pdrt_profile_enable": (C.c_int, [_VP, C.c_int32]),
+    "pdrt_profile_read": (C.c_int, [_VP, _VP, C.POINTER(pdrt_profile)]),
+    "pdrt_launch_count": (C.c_int64, []),
+    "pdrt_last_error": (C.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_handle = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpdrt.so (building it first if needed and allowed)."""
+    global _handle
+    with _lock:
+        if _handle is None:
+            path = _build.LIB
+            if build_if_missing:
+                path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"dose-engine library not built: {path} (run build())")
+            h = C.CDLL(path)
+            for name, (res, args) in _SIG.items():
+                f = getattr(h, name)
+                f.restype = res
+                f.argtypes = args
+            _handle = h
+    return _handle
+
+
+def _check(st):
+    if st != 0:
+        raise PdrtError(st, load().pdrt_last_error().decode())
+
+
+def _dptr(a):
+    return C.c_double(0) if a is None else (C.c_double * len(a))(*[float(x) for x in a])
+
+
+def pdrt_last_error() -> str:
+    return load().pdrt_last_error().decode()
+
+
+def pdrt_launch_count() -> int:
+    return int(load().pdrt_launch_count())
+
+
+def pdrt_grid_create(hu_dev_ptr, nx, ny, nz, sx, sy, sz, origin_mm, hu_red_pairs, stream):
+    out = _VP()
+    pts = [float(x) for pair in hu_red_pairs for x in pair]
+    _check(load().pdrt_grid_create(C.byref(out), _VP(hu_dev_ptr), int(nx), int(ny), int(nz),
+                                   float(sx), float(sy), float(sz), _dptr(origin_mm), _dptr(pts),
+                                   len(pts) // 2, _VP(stream)))
+    return out.value
+
+
+def pdrt_grid_destroy(grid):
+    load().pdrt_grid_destroy(_VP(grid))
+
+
+def pdrt_plan_upload(grid, gantry_deg, iso_mm, machine: pdrt_machine, scratch_budget_bytes, stream):
+    out = _VP()
+    _check(load().pdrt_plan_upload(C.byref(out), _VP(grid), len(gantry_deg), _dptr(gantry_deg),
+                                   _dptr(iso_mm), C.byref(machine), int(scratch_budget_bytes),
+                                   _VP(stream)))
+    return out.value
+
+
+def pdrt_plan_destroy(plan):
+    load().pdrt_plan_destroy(_VP(plan))
+
+
+def pdrt_dose_forward(grid, plan, leaves_ptr, jaws_ptr, mu_ptr, dose_ptr, stream):
+    _check(load().pdrt_dose_forward(_VP(grid), _VP(plan), _VP(leaves_ptr), _VP(jaws_ptr),
+                                    _VP(mu_ptr), _VP(dose_ptr), _VP(stream)))
+
+
+def pdrt_dose_backward(grid, plan, leaves_ptr, jaws_ptr, mu_ptr, dose_grad_ptr, dleaves_ptr,
+                       djaws_ptr, dmu_ptr, stream):
+    _check(load().pdrt_dose_backward(_VP(grid), _VP(plan), _VP(leaves_ptr), _VP(jaws_ptr),
+                                     _VP(mu_ptr), _VP(dose_grad_ptr), _VP(dleaves_ptr),
+                                     _VP(djaws_ptr), _VP(dmu_ptr), _VP(stream)))
+
+
+def pdrt_plan_get_info(plan) -> dict:
+    info = pdrt_plan_info()
+    _check(load().pdrt_plan_get_info(_VP(plan), C.byref(info)))
+    return {k: getattr(info, k) for k, _ in pdrt_plan_info._fields_}
+
+
+def pdrt_plan_status(plan, stream) -> int:
+    f = C.c_uint32(0)
+    _check(load().pdrt_plan_status(_VP(plan), _VP(stream), C.byref(f)))
+    return int(f.value)
+
+
+def pdrt_plan_work(plan, stream) -> dict:
+    w = pdrt_work()
+    _check(load().pdrt_plan_work(_VP(plan), _VP(stream), C.byref(w)))
+    return {k: getattr(w, k) for k, _ in pdrt_work._fields_}
+
+
+def pdrt_profile_enable(plan, enable):
+    _check(load().pdrt_profile_enable(_VP(plan), 1 if enable else 0))
+
+
+def pdrt_profile_read(plan, stream) -> dict:
+    p = pdrt_profile()
+    _check(load().pdrt_profile_read(_VP(plan), _VP(stream), C.byref(p)))
+    out = {}
+    for k in range(NUM_KERNELS):
+        out[p.name[k].decode()] = {"launches": int(p.launches[k]), "total_ms": float(p.total_ms[k])}
+    out["_overflow"] = bool(p.overflow)
+    return out
+
+
+def machine_struct(machine) -> pdrt_machine:
+    """Fill pdrt_machine from a synth.Machine-like object."""
+    m = pdrt_machine()
+    lb = list(machine.leaf_bounds)
+    if len(lb) - 1 > MAX_PAIRS:
+        raise ValueError("too many leaf pairs")
+    tt = list(machine.t_table)
+    if len(tt) > MAX_DEPTH_TABLE:
+        raise ValueError("depth-dose table too long")
+    m.sid_mm = float(machine.sid)
+    m.n_pairs = len(lb) - 1
+    for i, x in enumerate(lb):
+        m.leaf_bounds_mm[i] = float(x)
+    m.tau = float(machine.tau)
+    m.wmin_leaf_mm = float(machine.wmin_leaf)
+    m.wmin_jaw_mm = float(machine.wmin_jaw)
+    m.f_leaf_mm = float(machine.f_leaf)
+    m.f_jaw_mm = float(machine.f_jaw)
+    m.eps_mu = float(machine.eps_mu)
+    m.kernel_radius_px = int(machine.r_px)
+    for c in range(3):
+        for k in range(3):
+            m.kernel_alpha[c][k] = float(machine.alpha[c][k])
+            m.kernel_beta[c][k] = float(machine.beta[c][k])
+    m.n_depth = len(tt)
+    m.depth_step_mm = float(machine.dz_t)
+    for i, x in enumerate(tt):
+        m.depth_dose[i] = float(x)
+    m.cal = float(machine.cal)
+    m.ste = int(machine.ste)
+    return m

@@ -1,0 +1,593 @@
+// C ABI of the dose engine (declared in include/pdrt.h): argument checks, the
+// beam-frame lattice and per-slice needed ranges (host, double precision),
+// scratch allocation at plan upload, and the launch sequence of the forward
+// and adjoint passes.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "pdrt_impl.cuh"
+
+using namespace pdrt;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<long long> g_launches{0};
+
+pdrt_status fail(pdrt_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+pdrt_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? PDRT_ENOMEM : PDRT_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CU_TRY(expr, what)                         \
+    do {                                           \
+        cudaError_t e_ = (expr);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+}  // namespace
+
+struct pdrt_grid_s {
+    int device;
+    int sm_count;
+    int nx, ny, nz;
+    double sx, sy, sz;
+    double origin[3];
+    float *red;
+};
+
+struct ProfileRec {
+    int kid;
+    int ev;
+};
+
+struct pdrt_plan_s {
+    pdrt_grid_t grid;
+    int n_cp;
+    int chunk;
+    int conv_blocks_fwd, conv_blocks_adj;
+    PlanDev dev;
+    size_t scratch_bytes;
+    std::vector<void *> allocs;
+    // profiling
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;
+    std::vector<ProfileRec> recs;
+    int next_ev = 0;
+    bool overflow = false;
+};
+
+static const char *kKernelNames[PDRT_NUM_KERNELS] = {
+    "hu_to_red", "project_raster", "wepl_tables", "conv_forward",
+    "gather_accumulate", "gather_transpose", "conv_adjoint", "mag_transpose_param_grad"};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(pdrt_plan_t p, T **ptr, size_t count)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    p->allocs.push_back(q);
+    p->scratch_bytes += std::max<size_t>(count, 1) * sizeof(T);
+    *ptr = static_cast<T *>(q);
+    return cudaSuccess;
+}
+
+// Launch with optional event timing on the launch stream.
+template <typename F>
+cudaError_t timed(pdrt_plan_t p, int kid, cudaStream_t s, F &&launch)
+{
+    int ev = -1;
+    if (p && p->profiling) {
+        if (p->next_ev + 2 <= (int)p->events.size()) {
+            ev = p->next_ev;
+            p->next_ev += 2;
+            cudaEventRecord(p->events[ev], s);
+        } else {
+            p->overflow = true;
+        }
+    }
+    cudaError_t e = launch();
+    g_launches.fetch_add(1);
+    if (ev >= 0) {
+        cudaEventRecord(p->events[ev + 1], s);
+        p->recs.push_back({kid, ev});
+    }
+    return e;
+}
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+// u-range [lo, hi) of the beam lattice points of slice k that some voxel's
+// bilinear stencil can touch: the rotated grid rectangle in (fu, fw) index
+// space clipped to the band fw in [k-1, k+1], widened by one point.
+void needed_range(const double fu[4], const double fw[4], int k, int nu, int &lo, int &hi)
+{
+    double umin = 1e300, umax = -1e300;
+    const double b0 = k - 1.0, b1 = k + 1.0;
+    for (int e = 0; e < 4; ++e) {
+        const int f = (e + 1) & 3;
+        const double w0 = fw[e], w1 = fw[f], u0 = fu[e], u1 = fu[f];
+        double tlo, thi;
+        if (fabs(w1 - w0) < 1e-12) {
+            if (w0 < b0 || w0 > b1) continue;
+            tlo = 0.0;
+            thi = 1.0;
+        } else {
+            double t0 = (b0 - w0) / (w1 - w0), t1 = (b1 - w0) / (w1 - w0);
+            tlo = std::max(0.0, std::min(t0, t1));
+            thi = std::min(1.0, std::max(t0, t1));
+            if (tlo > thi) continue;
+        }
+        for (double t : {tlo, thi}) {
+            const double u = u0 + t * (u1 - u0);
+            umin = std::min(umin, u);
+            umax = std::max(umax, u);
+        }
+    }
+    if (umin > umax) {
+        lo = hi = 0;
+        return;
+    }
+    lo = std::max((int)floor(umin) - 1, 0);
+    hi = std::min((int)floor(umax) + 3, nu);
+    if (hi < lo) hi = lo;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pdrt_last_error(void) { return g_last_error.c_str(); }
+
+int64_t pdrt_launch_count(void) { return g_launches.load(); }
+
+pdrt_status pdrt_grid_create(pdrt_grid_t *out, const float *hu_dev, int32_t nx, int32_t ny,
+                             int32_t nz, double sx, double sy, double sz, const double origin_mm[3],
+                             const double *hu_red_host, int32_t n_pts, pdrt_stream_t stream)
+{
+    g_last_error.clear();
+    if (!out || !hu_dev || !origin_mm || !hu_red_host) return fail(PDRT_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (nx <= 0 || ny <= 0 || nz <= 0) return fail(PDRT_ESHAPE, "grid dimensions must be positive");
+    if (!(sx > 0) || !(sy > 0) || !(sz > 0) || !is_fin(sx) || !is_fin(sy) || !is_fin(sz))
+        return fail(PDRT_EINVAL, "voxel spacing must be positive and finite");
+    if (fabs(sx - sy) > 1e-6 * sx) return fail(PDRT_EINVAL, "sx must equal sy (got %g, %g)", sx, sy);
+    for (int d = 0; d < 3; ++d)
+        if (!is_fin(origin_mm[d])) return fail(PDRT_EINVAL, "origin must be finite");
+    if (n_pts < 2 || n_pts > PDRT_MAX_HU_POINTS)
+        return fail(PDRT_EINVAL, "HU calibration needs 2..%d points", PDRT_MAX_HU_POINTS);
+    for (int i = 0; i < n_pts; ++i) {
+        if (!is_fin(hu_red_host[2 * i]) || !is_fin(hu_red_host[2 * i + 1]))
+            return fail(PDRT_EINVAL, "HU calibration point %d is not finite", i);
+        if (i > 0 && !(hu_red_host[2 * i] > hu_red_host[2 * i - 2]))
+            return fail(PDRT_EINVAL, "HU calibration points must be strictly ascending in HU");
+    }
+    int dev = 0;
+    CU_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    cudaDeviceProp prop;
+    CU_TRY(cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+    if (prop.major * 10 + prop.minor != 103)
+        return fail(PDRT_EDEVICE, "device %d is sm_%d%d; this library is built for sm_103a", dev,
+                    prop.major, prop.minor);
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, hu_dev) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(PDRT_EINVAL, "hu_dev is not a device pointer");
+    }
+    const long long n = (long long)nx * ny * nz;
+    pdrt_grid_t g = new pdrt_grid_s();
+    g->device = dev;
+    g->sm_count = prop.multiProcessorCount;
+    g->nx = nx; g->ny = ny; g->nz = nz;
+    g->sx = sx; g->sy = sy; g->sz = sz;
+    for (int d = 0; d < 3; ++d) g->origin[d] = origin_mm[d];
+    cudaError_t e = cudaMalloc(&g->red, n * sizeof(float));
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "cudaMalloc(density)");
+    }
+    float pts[2 * PDRT_MAX_HU_POINTS];
+    for (int i = 0; i < 2 * n_pts; ++i) pts[i] = (float)hu_red_host[i];
+    e = launch_hu_to_red(hu_dev, g->red, n, pts, n_pts, (cudaStream_t)stream);
+    g_launches.fetch_add(1);
+    if (e != cudaSuccess) {
+        cudaFree(g->red);
+        delete g;
+        return cuda_fail(e, "hu_to_red launch");
+    }
+    *out = g;
+    return PDRT_OK;
+}
+
+void pdrt_grid_destroy(pdrt_grid_t g)
+{
+    if (!g) return;
+    cudaFree(g->red);
+    delete g;
+}
+
+void pdrt_plan_destroy(pdrt_plan_t p)
+{
+    if (!p) return;
+    for (void *q : p->allocs) cudaFree(q);
+    for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+    delete p;
+}
+
+pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
+                             const double *gantry_deg_host, const double iso_mm[3],
+                             const pdrt_machine *m, size_t scratch_budget_bytes,
+                             pdrt_stream_t stream)
+{
+    g_last_error.clear();
+    if (!out || !g || !gantry_deg_host || !iso_mm || !m) return fail(PDRT_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n_cp <= 0) return fail(PDRT_ESHAPE, "n_cp must be positive");
+    for (int b = 0; b < n_cp; ++b)
+        if (!is_fin(gantry_deg_host[b])) return fail(PDRT_EINVAL, "gantry angle %d is not finite", b);
+    for (int d = 0; d < 3; ++d)
+        if (!is_fin(iso_mm[d])) return fail(PDRT_EINVAL, "isocentre must be finite");
+    if (m->n_pairs < 1 || m->n_pairs > PDRT_MAX_PAIRS)
+        return fail(PDRT_EINVAL, "n_pairs must be in 1..%d", PDRT_MAX_PAIRS);
+    for (int i = 0; i <= m->n_pairs; ++i) {
+        if (!is_fin(m->leaf_bounds_mm[i])) return fail(PDRT_EINVAL, "leaf bound %d not finite", i);
+        if (i > 0 && !(m->leaf_bounds_mm[i] > m->leaf_bounds_mm[i - 1]))
+            return fail(PDRT_EINVAL, "leaf bounds must be strictly ascending");
+    }
+    if (m->kernel_radius_px < 0 || m->kernel_radius_px > PDRT_MAX_RADIUS_PX)
+        return fail(PDRT_EINVAL, "kernel radius must be in 0..%d px", PDRT_MAX_RADIUS_PX);
+    if (m->n_depth < 2 || m->n_depth > PDRT_MAX_DEPTH_TABLE || !(m->depth_step_mm > 0))
+        return fail(PDRT_EINVAL, "depth-dose table needs 2..%d entries and a positive step",
+                    PDRT_MAX_DEPTH_TABLE);
+    if (!(m->tau >= 0 && m->tau <= 1)) return fail(PDRT_EINVAL, "tau must be in [0,1]");
+    if (!(m->wmin_leaf_mm >= 0) || !(m->wmin_jaw_mm >= 0) || !(m->f_leaf_mm >= 0) ||
+        !(m->f_jaw_mm >= 0) || !(m->eps_mu >= 0) || !is_fin(m->cal) || !is_fin(m->sid_mm))
+        return fail(PDRT_EINVAL, "machine limits must be non-negative and finite");
+    for (int c = 0; c < 3; ++c)
+        for (int q = 0; q < 3; ++q)
+            if (!is_fin(m->kernel_alpha[c][q]) || !is_fin(m->kernel_beta[c][q]))
+                return fail(PDRT_EINVAL, "kernel polynomial coefficients must be finite");
+    for (int i = 0; i < m->n_depth; ++i)
+        if (!is_fin(m->depth_dose[i])) return fail(PDRT_EINVAL, "depth-dose entry %d not finite", i);
+    int dev = 0;
+    CU_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != g->device) return fail(PDRT_EINVAL, "current device differs from the grid's device");
+
+    // ---- lattice (same definition as the model: +-H pixels, H covers every voxel)
+    double rmax = 0.0;
+    for (int cx = 0; cx < 2; ++cx)
+        for (int cy = 0; cy < 2; ++cy) {
+            double x = g->origin[0] + (cx ? g->nx - 1 : 0) * g->sx - iso_mm[0];
+            double y = g->origin[1] + (cy ? g->ny - 1 : 0) * g->sy - iso_mm[1];
+            rmax = std::max(rmax, sqrt(x * x + y * y));
+        }
+    const int H = (int)ceil(rmax / g->sx - 1e-9) + 1;
+    Lattice L;
+    L.nu = L.nw = 2 * H + 1;
+    L.nv = g->nz;
+    L.cu = L.cw = (float)H;
+    const double cv = (iso_mm[2] - g->origin[2]) / g->sz;
+    L.cv = (float)cv;
+    L.du = (float)g->sx;
+    L.dv = (float)g->sz;
+    if (!(m->sid_mm > (H + 2) * g->sx))
+        return fail(PDRT_EINVAL, "SID %.1f mm must exceed the grid's reach from the isocentre (%.1f mm)",
+                    m->sid_mm, (H + 2) * g->sx);
+
+    MachineDev M;
+    memset(&M, 0, sizeof(M));
+    M.sid = (float)m->sid_mm;
+    M.n_pairs = m->n_pairs;
+    M.tau = (float)m->tau;
+    M.wmin_leaf = (float)m->wmin_leaf_mm;
+    M.wmin_jaw = (float)m->wmin_jaw_mm;
+    M.f_leaf = (float)m->f_leaf_mm;
+    M.f_jaw = (float)m->f_jaw_mm;
+    M.eps_mu = (float)m->eps_mu;
+    M.R = m->kernel_radius_px;
+    M.nq4 = conv_nq4_for_radius(M.R);
+    if (M.nq4 < 0) return fail(PDRT_EINVAL, "no convolution variant for radius %d", M.R);
+    M.kstride = 4 * ((M.nq4 & 1) ? M.nq4 : M.nq4 + 1);
+    for (int c = 0; c < 3; ++c)
+        for (int q = 0; q < 3; ++q) {
+            M.alpha[c][q] = (float)m->kernel_alpha[c][q];
+            M.beta[c][q] = (float)m->kernel_beta[c][q];
+        }
+    M.n_depth = m->n_depth;
+    M.depth_step = (float)m->depth_step_mm;
+    M.cal = (float)m->cal;
+    M.ste = m->ste ? 1 : 0;
+
+    // ---- per-CP geometry and needed slice ranges
+    std::vector<CpGeo> geo(n_cp);
+    std::vector<int2> ukr((size_t)n_cp * L.nw);
+    const double px0 = (iso_mm[0] - g->origin[0]) / g->sx;
+    const double py0 = (iso_mm[1] - g->origin[1]) / g->sy;
+    const double pz0 = cv;
+    long long cap_o = 1, cap_a = 1;
+    const int R = M.R;
+    for (int b = 0; b < n_cp; ++b) {
+        const double phi = gantry_deg_host[b] * M_PI / 180.0;
+        const double cs = cos(phi), sn = sin(phi);
+        const double au = cs, bu = -sn, aw = sn, bw = cs;
+        CpGeo &G = geo[b];
+        G.au = (float)au; G.bu = (float)bu; G.aw = (float)aw; G.bw = (float)bw;
+        G.cu0 = (float)(H - au * px0 - bu * py0);
+        G.cw0 = (float)(H - aw * px0 - bw * py0);
+        G.sx_w = (float)sn;
+        G.sy_w = (float)cs;
+        G.px0 = (float)px0; G.py0 = (float)py0; G.pz0 = (float)pz0;
+        double fu[4], fw[4];
+        const int cxs[4] = {0, g->nx - 1, g->nx - 1, 0}, cys[4] = {0, 0, g->ny - 1, g->ny - 1};
+        for (int c = 0; c < 4; ++c) {
+            fu[c] = au * (cxs[c] - px0) + bu * (cys[c] - py0) + H;
+            fw[c] = aw * (cxs[c] - px0) + bw * (cys[c] - py0) + H;
+        }
+        long long so = 0, sa = 0;
+        for (int k = 0; k < L.nw; ++k) {
+            int lo, hi;
+            needed_range(fu, fw, k, L.nu, lo, hi);
+            ukr[(size_t)b * L.nw + k] = make_int2(lo, hi);
+            if (hi > lo) {
+                so += (long long)(hi - lo) * L.nv;
+                sa += (long long)std::min(hi - lo + 2 * R, L.nu) * L.nv;
+            }
+        }
+        cap_o = std::max(cap_o, so);
+        cap_a = std::max(cap_a, sa);
+    }
+
+    pdrt_plan_t p = new pdrt_plan_s();
+    p->grid = g;
+    p->n_cp = n_cp;
+    p->scratch_bytes = 0;
+    PlanDev &P = p->dev;
+    memset(&P, 0, sizeof(P));
+    P.lat = L;
+    P.mach = M;
+    P.n_cp = n_cp;
+    P.nx = g->nx; P.ny = g->ny; P.nz = g->nz;
+    P.red = g->red;
+    P.cap_o = cap_o;
+    P.cap_a = cap_a;
+
+    const size_t fixed = sizeof(float) * 2 * (size_t)n_cp * L.nu * L.nv +
+                         sizeof(SliceTab) * (size_t)n_cp * L.nw;
+    const size_t budget = scratch_budget_bytes ? scratch_budget_bytes : ((size_t)8 << 30);
+    const size_t per_cp = sizeof(float) * (size_t)(cap_o + cap_a);
+    long long chunk = budget > fixed ? (long long)((budget - fixed) / per_cp) : 1;
+    chunk = std::max(1LL, std::min<long long>(chunk, std::min(n_cp, kMaxCpPerChunk)));
+    p->chunk = (int)chunk;
+
+    cudaError_t e = cudaSuccess;
+    float *lb = nullptr, *dd = nullptr;
+    CpGeo *dgeo = nullptr;
+    int2 *dukr = nullptr;
+#define PLAN_TRY(expr, what)                      \
+    do {                                          \
+        e = (expr);                               \
+        if (e != cudaSuccess) {                   \
+            pdrt_status st_ = cuda_fail(e, what); \
+            pdrt_plan_destroy(p);                 \
+            return st_;                           \
+        }                                         \
+    } while (0)
+    PLAN_TRY(dalloc(p, &lb, m->n_pairs + 1), "cudaMalloc(leaf bounds)");
+    PLAN_TRY(dalloc(p, &dd, m->n_depth), "cudaMalloc(depth dose)");
+    PLAN_TRY(dalloc(p, &dgeo, n_cp), "cudaMalloc(cp geometry)");
+    PLAN_TRY(dalloc(p, &dukr, (size_t)n_cp * L.nw), "cudaMalloc(slice ranges)");
+    PLAN_TRY(dalloc(p, &P.cptab, n_cp), "cudaMalloc(cp table)");
+    PLAN_TRY(dalloc(p, &P.slices, (size_t)n_cp * L.nw), "cudaMalloc(slice table)");
+    PLAN_TRY(dalloc(p, &P.fbuf, (size_t)n_cp * L.nu * L.nv), "cudaMalloc(fluence)");
+    PLAN_TRY(dalloc(p, &P.gfbuf, (size_t)n_cp * L.nu * L.nv), "cudaMalloc(fluence adjoint)");
+    PLAN_TRY(dalloc(p, &P.region, (size_t)chunk * cap_o), "cudaMalloc(beam-frame region)");
+    PLAN_TRY(dalloc(p, &P.adjbuf, (size_t)chunk * cap_a), "cudaMalloc(adjoint region)");
+    PLAN_TRY(dalloc(p, &P.flags, 1), "cudaMalloc(flags)");
+    PLAN_TRY(dalloc(p, &P.counters, 2 * ((n_cp + chunk - 1) / chunk) + 2), "cudaMalloc(counters)");
+    P.leaf_bounds = lb;
+    P.depth_dose = dd;
+    P.cpgeo = dgeo;
+    P.ukr = dukr;
+
+    std::vector<float> hlb(m->n_pairs + 1), hdd(m->n_depth);
+    for (int i = 0; i <= m->n_pairs; ++i) hlb[i] = (float)m->leaf_bounds_mm[i];
+    for (int i = 0; i < m->n_depth; ++i) hdd[i] = (float)m->depth_dose[i];
+    cudaStream_t s = (cudaStream_t)stream;
+    PLAN_TRY(cudaMemcpyAsync(lb, hlb.data(), hlb.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+             "upload leaf bounds");
+    PLAN_TRY(cudaMemcpyAsync(dd, hdd.data(), hdd.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+             "upload depth dose");
+    PLAN_TRY(cudaMemcpyAsync(dgeo, geo.data(), geo.size() * sizeof(CpGeo), cudaMemcpyHostToDevice, s),
+             "upload geometry");
+    PLAN_TRY(cudaMemcpyAsync(dukr, ukr.data(), ukr.size() * sizeof(int2), cudaMemcpyHostToDevice, s),
+             "upload slice ranges");
+    PLAN_TRY(cudaMemsetAsync(P.flags, 0, sizeof(unsigned), s), "clear flags");
+    // host vectors go out of scope: wait for the copies
+    PLAN_TRY(cudaStreamSynchronize(s), "plan upload sync");
+
+    int bf = 1, ba = 1;
+    PLAN_TRY(conv_prepare(M, &bf, &ba), "convolution kernel set-up");
+    p->conv_blocks_fwd = std::max(1, bf) * g->sm_count;
+    p->conv_blocks_adj = std::max(1, ba) * g->sm_count;
+#undef PLAN_TRY
+    *out = p;
+    return PDRT_OK;
+}
+
+
+static pdrt_status check_call(pdrt_grid_t g, pdrt_plan_t p)
+{
+    g_last_error.clear();
+    if (!g || !p) return fail(PDRT_EINVAL, "NULL handle");
+    if (p->grid != g) return fail(PDRT_EINVAL, "plan was uploaded for a different grid");
+    int dev = 0;
+    CU_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != g->device) return fail(PDRT_EINVAL, "current device differs from the grid's device");
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_dose_forward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_dev,
+                              const float *jaws_dev, const float *mu_dev, float *dose_dev,
+                              pdrt_stream_t stream)
+{
+    pdrt_status st = check_call(g, p);
+    if (st != PDRT_OK) return st;
+    if (!leaves_dev || !jaws_dev || !mu_dev || !dose_dev) return fail(PDRT_EINVAL, "NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const PlanDev &P = p->dev;
+    CU_TRY(timed(p, K_RASTER, s, [&] { return launch_raster(P, leaves_dev, jaws_dev, mu_dev, s); }),
+           "project_raster launch");
+    CU_TRY(timed(p, K_TABLES, s, [&] { return launch_tables(P, s); }), "wepl_tables launch");
+    const int n_chunks = (p->n_cp + p->chunk - 1) / p->chunk;
+    CU_TRY(cudaMemsetAsync(P.counters, 0, sizeof(unsigned) * n_chunks, s), "clear counters");
+    for (int c = 0; c < n_chunks; ++c) {
+        const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
+        CU_TRY(timed(p, K_CONV_FWD, s,
+                     [&] { return launch_conv(P, b0, nb, false, P.counters + c, p->conv_blocks_fwd, s); }),
+               "conv_forward launch");
+        CU_TRY(timed(p, K_GATHER, s, [&] { return launch_gather(P, b0, nb, dose_dev, c == 0, s); }),
+               "gather launch");
+    }
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_dev,
+                               const float *jaws_dev, const float *mu_dev,
+                               const float *dose_grad_dev, float *dleaves_dev, float *djaws_dev,
+                               float *dmu_dev, pdrt_stream_t stream)
+{
+    pdrt_status st = check_call(g, p);
+    if (st != PDRT_OK) return st;
+    if (!leaves_dev || !jaws_dev || !mu_dev || !dose_grad_dev || !dleaves_dev || !djaws_dev ||
+        !dmu_dev)
+        return fail(PDRT_EINVAL, "NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const PlanDev &P = p->dev;
+    CU_TRY(timed(p, K_RASTER, s, [&] { return launch_raster(P, leaves_dev, jaws_dev, mu_dev, s); }),
+           "project_raster launch");
+    CU_TRY(timed(p, K_TABLES, s, [&] { return launch_tables(P, s); }), "wepl_tables launch");
+    const int n_chunks = (p->n_cp + p->chunk - 1) / p->chunk;
+    unsigned int *ctr = P.counters + n_chunks;
+    CU_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned) * n_chunks, s), "clear counters");
+    for (int c = 0; c < n_chunks; ++c) {
+        const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
+        CU_TRY(timed(p, K_GATHER_T, s, [&] { return launch_gather_T(P, b0, nb, dose_grad_dev, s); }),
+               "gather_transpose launch");
+        CU_TRY(timed(p, K_CONV_ADJ, s,
+                     [&] { return launch_conv(P, b0, nb, true, ctr + c, p->conv_blocks_adj, s); }),
+               "conv_adjoint launch");
+        CU_TRY(timed(p, K_MAG_T_GRAD, s, [&] { return launch_mag_T(P, b0, nb, s); }),
+               "mag_transpose launch");
+    }
+    CU_TRY(timed(p, K_MAG_T_GRAD, s,
+                 [&] {
+                     return launch_param_grad(P, leaves_dev, jaws_dev, mu_dev, dleaves_dev, djaws_dev,
+                                              dmu_dev, s);
+                 }),
+           "param_grad launch");
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out)
+{
+    g_last_error.clear();
+    if (!p || !out) return fail(PDRT_EINVAL, "NULL argument");
+    const Lattice &L = p->dev.lat;
+    out->nu = L.nu; out->nv = L.nv; out->nw = L.nw;
+    out->cu = L.cu; out->cv = L.cv; out->cw = L.cw;
+    out->n_cp = p->n_cp;
+    out->chunk_cp = p->chunk;
+    out->scratch_bytes = p->scratch_bytes;
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_plan_status(pdrt_plan_t p, pdrt_stream_t stream, uint32_t *flags_out)
+{
+    g_last_error.clear();
+    if (!p || !flags_out) return fail(PDRT_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned int f = 0;
+    CU_TRY(cudaStreamSynchronize(s), "stream sync");
+    CU_TRY(cudaMemcpy(&f, p->dev.flags, sizeof(f), cudaMemcpyDeviceToHost), "read flags");
+    CU_TRY(cudaMemset(p->dev.flags, 0, sizeof(f)), "clear flags");
+    *flags_out = f;
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
+{
+    g_last_error.clear();
+    if (!p || !out) return fail(PDRT_EINVAL, "NULL argument");
+    CU_TRY(cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
+    std::vector<CpTab> t(p->n_cp);
+    CU_TRY(cudaMemcpy(t.data(), p->dev.cptab, sizeof(CpTab) * p->n_cp, cudaMemcpyDeviceToHost),
+           "read work counters");
+    memset(out, 0, sizeof(*out));
+    for (const CpTab &c : t) {
+        out->active_slices += c.n_active;
+        out->support_points += c.n_support;
+        out->region_points += c.n_region;
+    }
+    const long long n = 2LL * p->dev.mach.R + 1;
+    out->taps = n * n;
+    out->conv_flops = 2.0 * (double)out->taps * (double)out->support_points;
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_profile_enable(pdrt_plan_t p, int32_t enable)
+{
+    g_last_error.clear();
+    if (!p) return fail(PDRT_EINVAL, "NULL plan");
+    if (enable && p->events.empty()) {
+        p->events.resize(16384);
+        for (auto &e : p->events) CU_TRY(cudaEventCreate(&e), "cudaEventCreate");
+    }
+    p->profiling = enable != 0;
+    if (enable) {
+        p->recs.clear();
+        p->next_ev = 0;
+        p->overflow = false;
+    }
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_profile_read(pdrt_plan_t p, pdrt_stream_t stream, pdrt_profile *out)
+{
+    g_last_error.clear();
+    if (!p || !out) return fail(PDRT_EINVAL, "NULL argument");
+    CU_TRY(cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
+    memset(out, 0, sizeof(*out));
+    for (int k = 0; k < PDRT_NUM_KERNELS; ++k) out->name[k] = kKernelNames[k];
+    for (const ProfileRec &r : p->recs) {
+        float ms = 0.f;
+        CU_TRY(cudaEventElapsedTime(&ms, p->events[r.ev], p->events[r.ev + 1]), "cudaEventElapsedTime");
+        out->launches[r.kid] += 1;
+        out->total_ms[r.kid] += ms;
+    }
+    out->overflow = p->overflow ? 1 : 0;
+    return PDRT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,259 @@
+// Adjoint tail of the dose engine.
+//
+// k_mag_T: transpose of the divergent fluence projection (Sec. 2.2.3): every
+//   fluence pixel of the support box pulls, over all beam slices, the adjoint
+//   convolution output h'_k at the lattice points whose magnified bilinear
+//   stencil contains the pixel (weights recomputed with mag_coord, the same
+//   expression the forward tile fill uses).  No atomics.
+// k_param_grad: chain rule of the fluence map (Sec. 2.2.2, piecewise-linear
+//   overlap, derivative taken one-sided at pixel boundaries) and of the
+//   hardware projection (Sec. 2.2.1: identity if ste, exact Jacobian
+//   otherwise) to leaves, jaws and MU:
+//     dL/dF_b   = cal MU^_b g_F,   dL/dMU^_b = cal <g_F, F_b>.
+#include <math.h>
+
+#include "pdrt_impl.cuh"
+
+namespace pdrt {
+
+__global__ void __launch_bounds__(256) k_mag_T(PlanDev P, int b0)
+{
+    const Lattice &L = P.lat;
+    const int bl = blockIdx.x, b = b0 + bl;
+    const CpTab ct = P.cptab[b];
+    const int Fa = ct.fa1 - ct.fa0, Fc = ct.fc1 - ct.fc0;
+    if (Fa <= 0 || Fc <= 0) return;
+    float *gF = P.gfbuf + (long long)b * L.nu * L.nv;
+    const float *hb = P.adjbuf + (long long)bl * P.cap_a;
+    const SliceTab *sl = P.slices + (long long)b * L.nw;
+    const int n = Fa * Fc;
+    for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n; t += gridDim.y * blockDim.x) {
+        const int a = ct.fa0 + t % Fa, c = ct.fc0 + t / Fa;   // consecutive threads: consecutive a
+        float s = 0.f;
+        for (int k = ct.k0; k < ct.k1; ++k) {
+            const SliceTab *sp = sl + k;
+            const int4 ab = *reinterpret_cast<const int4 *>(&sp->ai0);
+            if (ab.y <= ab.x || ab.w <= ab.z) continue;
+            const float m = sp->m;
+            // i with |mag_coord(m, i, cu) - a| < 1, widened by one for rounding
+            const int i_lo = max((int)floorf(L.cu + ((float)a - 1.f - L.cu) / m), ab.x);
+            const int i_hi = min((int)ceilf(L.cu + ((float)a + 1.f - L.cu) / m) + 1, ab.y);
+            const int j_lo = max((int)floorf(L.cv + ((float)c - 1.f - L.cv) / m), ab.z);
+            const int j_hi = min((int)ceilf(L.cv + ((float)c + 1.f - L.cv) / m) + 1, ab.w);
+            if (i_hi <= i_lo || j_hi <= j_lo) continue;
+            const float *h = hb + sp->off_a;
+            const int aw = ab.y - ab.x;
+            for (int j = j_lo; j < j_hi; ++j) {
+                const float fc = mag_coord(m, j, L.cv);
+                const float bc = floorf(fc);
+                const int c0 = (int)bc;
+                const float tc = fc - bc;
+                const float wc = (c == c0) ? 1.f - tc : ((c == c0 + 1) ? tc : 0.f);
+                if (wc == 0.f) continue;
+                for (int i = i_lo; i < i_hi; ++i) {
+                    const float fa = mag_coord(m, i, L.cu);
+                    const float ba = floorf(fa);
+                    const int a0 = (int)ba;
+                    const float ta = fa - ba;
+                    const float wa = (a == a0) ? 1.f - ta : ((a == a0 + 1) ? ta : 0.f);
+                    if (wa != 0.f) s = fmaf(wa * wc, h[(long long)(j - ab.z) * aw + (i - ab.x)], s);
+                }
+            }
+        }
+        gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)] = s;
+    }
+}
+
+cudaError_t launch_mag_T(const PlanDev &P, int b0, int nb, cudaStream_t s)
+{
+    dim3 grid(nb, 8);
+    k_mag_T<<<grid, 256, 0, s>>>(P, b0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void project_pair_grad(float pa, float pb, float wmin, float F, float &ah,
+                                                  float &bh, float &gc, float &gw)
+{
+    float c = 0.5f * (pa + pb);
+    float w = pb - pa;
+    float w2 = (w >= wmin) ? w : wmin;
+    float c1 = (c >= -F) ? c : -F;
+    float c2 = (c1 <= F) ? c1 : F;
+    ah = c2 - 0.5f * w2;
+    bh = c2 + 0.5f * w2;
+    gw = (w >= wmin) ? 1.f : 0.f;
+    gc = ((c >= -F) ? 1.f : 0.f) * ((c1 <= F) ? 1.f : 0.f);
+}
+
+// one-sided derivatives of the overlap w.r.t. its upper / lower edge
+__device__ __forceinline__ float overlap_dhi(float x, float lo, float hi, float d)
+{
+    float e = x + 0.5f * d, s = x - 0.5f * d;
+    float top = (hi <= e) ? hi : e;
+    float bot = (lo >= s) ? lo : s;
+    return (top - bot > 0.f && hi <= e) ? 1.f / d : 0.f;
+}
+
+__device__ __forceinline__ float overlap_dlo(float x, float lo, float hi, float d)
+{
+    float e = x + 0.5f * d, s = x - 0.5f * d;
+    float top = (hi <= e) ? hi : e;
+    float bot = (lo >= s) ? lo : s;
+    return (top - bot > 0.f && lo >= s) ? -1.f / d : 0.f;
+}
+
+template <int N>
+__device__ void block_sum(float (&v)[N], float *s_red)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        float x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s_red[wid * N + q] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        float x = 0.f;
+        for (int w = 0; w < nwarp; ++w) x += s_red[w * N + threadIdx.x];
+        s_red[32 * N + threadIdx.x] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < N; ++q) v[q] = s_red[32 * N + q];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_param_grad(PlanDev P, const float *__restrict__ leaves,
+                                                    const float *__restrict__ jaws,
+                                                    const float *__restrict__ mu,
+                                                    float *__restrict__ dleaves,
+                                                    float *__restrict__ djaws,
+                                                    float *__restrict__ dmu)
+{
+    const int b = blockIdx.x;
+    const Lattice &L = P.lat;
+    const MachineDev &M = P.mach;
+    const int np = M.n_pairs;
+    __shared__ float s_lo[PDRT_MAX_PAIRS], s_hi[PDRT_MAX_PAIRS], s_lb[PDRT_MAX_PAIRS + 1];
+    __shared__ float s_gc[PDRT_MAX_PAIRS], s_gw[PDRT_MAX_PAIRS];
+    __shared__ float s_j[4], s_jgc[2], s_jgw[2];
+    __shared__ float s_red[33 * 5];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const float pa = leaves[((long long)b * np + i) * 2], pb = leaves[((long long)b * np + i) * 2 + 1];
+        project_pair_grad(pa, pb, M.wmin_leaf, M.f_leaf, s_lo[i], s_hi[i], s_gc[i], s_gw[i]);
+    }
+    for (int i = threadIdx.x; i <= np; i += blockDim.x) s_lb[i] = P.leaf_bounds[i];
+    if (threadIdx.x == 0) {
+        project_pair_grad(jaws[4LL * b], jaws[4LL * b + 1], M.wmin_jaw, M.f_jaw, s_j[0], s_j[1],
+                          s_jgc[0], s_jgw[0]);
+        project_pair_grad(jaws[4LL * b + 2], jaws[4LL * b + 3], M.wmin_jaw, M.f_jaw, s_j[2], s_j[3],
+                          s_jgc[1], s_jgw[1]);
+    }
+    __syncthreads();
+    const CpTab ct = P.cptab[b];
+    const int Fa = ct.fa1 - ct.fa0, Fc = ct.fc1 - ct.fc0;
+    const float *gF = P.gfbuf + (long long)b * L.nu * L.nv;
+    const float *F = P.fbuf + (long long)b * L.nu * L.nv;
+    const float dscale = ct.cal_mu;   // dL/dF = cal MU^ g_F
+    const float hdv = 0.5f * L.dv;
+    // dMU^ and the four jaw edges: reduction over the support box
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (Fa > 0 && Fc > 0) {
+        for (int t = threadIdx.x; t < Fa * Fc; t += blockDim.x) {
+            const int a = ct.fa0 + t / Fc, c = ct.fc0 + t % Fc;
+            const float g = gF[t];
+            acc[0] = fmaf(g, F[t], acc[0]);
+            const float u = ((float)a - L.cu) * L.du, v = ((float)c - L.cv) * L.dv;
+            const float fx = overlap_f(u, s_j[0], s_j[1], L.du);
+            const float fy = overlap_f(v, s_j[2], s_j[3], L.dv);
+            const float dxl = overlap_dlo(u, s_j[0], s_j[1], L.du), dxh = overlap_dhi(u, s_j[0], s_j[1], L.du);
+            const float dyl = overlap_dlo(v, s_j[2], s_j[3], L.dv), dyh = overlap_dhi(v, s_j[2], s_j[3], L.dv);
+            if (dxl == 0.f && dxh == 0.f && dyl == 0.f && dyh == 0.f) continue;
+            // G = tau + (1 - tau) f_leaf
+            int lo = 0, hi = np;
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (s_lb[mid + 1] > v - hdv) hi = mid; else lo = mid + 1;
+            }
+            float fl = 0.f;
+            for (int i = lo; i < np && s_lb[i] < v + hdv; ++i) {
+                const float om = overlap_f(v, s_lb[i], s_lb[i + 1], L.dv);
+                if (om > 0.f) fl += om * overlap_f(u, s_lo[i], s_hi[i], L.du);
+            }
+            const float G = M.tau + (1.f - M.tau) * fl;
+            const float gd = g * dscale;
+            acc[1] = fmaf(gd, dxl * fy * G, acc[1]);
+            acc[2] = fmaf(gd, dxh * fy * G, acc[2]);
+            acc[3] = fmaf(gd, fx * dyl * G, acc[3]);
+            acc[4] = fmaf(gd, fx * dyh * G, acc[4]);
+        }
+    }
+    block_sum<5>(acc, s_red);
+    if (threadIdx.x == 0) {
+        const float dmuh = M.cal * acc[0];
+        const float m = mu[b];
+        dmu[b] = (M.ste || m >= M.eps_mu) ? dmuh : 0.f;
+        for (int pr = 0; pr < 2; ++pr) {
+            const float ga = acc[1 + 2 * pr], gb = acc[2 + 2 * pr];
+            if (M.ste) {
+                djaws[4LL * b + 2 * pr] = ga;
+                djaws[4LL * b + 2 * pr + 1] = gb;
+            } else {
+                const float sp = 0.5f * (s_jgc[pr] + s_jgw[pr]), dp = 0.5f * (s_jgc[pr] - s_jgw[pr]);
+                djaws[4LL * b + 2 * pr] = ga * sp + gb * dp;
+                djaws[4LL * b + 2 * pr + 1] = ga * dp + gb * sp;
+            }
+        }
+    }
+    // leaf edges: one thread per pair, over the rows its strip overlaps
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        float gl = 0.f, gr = 0.f;
+        if (Fa > 0 && Fc > 0) {
+            const float lb0 = s_lb[i], lb1 = s_lb[i + 1];
+            // rows c whose pixel [v - dv/2, v + dv/2] overlaps the strip
+            const int c_lo = max((int)floorf(L.cv + lb0 / L.dv - 0.5f), ct.fc0);
+            const int c_hi = min((int)ceilf(L.cv + lb1 / L.dv + 0.5f) + 1, ct.fc1);
+            for (int c = c_lo; c < c_hi; ++c) {
+                const float v = ((float)c - L.cv) * L.dv;
+                const float om = overlap_f(v, lb0, lb1, L.dv);
+                if (om <= 0.f) continue;
+                const float fy = overlap_f(v, s_j[2], s_j[3], L.dv);
+                if (fy <= 0.f) continue;
+                for (int a = ct.fa0; a < ct.fa1; ++a) {
+                    const float u = ((float)a - L.cu) * L.du;
+                    const float dl = overlap_dlo(u, s_lo[i], s_hi[i], L.du);
+                    const float dr = overlap_dhi(u, s_lo[i], s_hi[i], L.du);
+                    if (dl == 0.f && dr == 0.f) continue;
+                    const float fx = overlap_f(u, s_j[0], s_j[1], L.du);
+                    const float s = gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)] * dscale * fx * fy *
+                                    (1.f - M.tau) * om;
+                    gl = fmaf(s, dl, gl);
+                    gr = fmaf(s, dr, gr);
+                }
+            }
+        }
+        float ol, orr;
+        if (M.ste) {
+            ol = gl;
+            orr = gr;
+        } else {
+            const float sp = 0.5f * (s_gc[i] + s_gw[i]), dp = 0.5f * (s_gc[i] - s_gw[i]);
+            ol = gl * sp + gr * dp;
+            orr = gl * dp + gr * sp;
+        }
+        dleaves[((long long)b * np + i) * 2] = ol;
+        dleaves[((long long)b * np + i) * 2 + 1] = orr;
+    }
+}
+
+cudaError_t launch_param_grad(const PlanDev &P, const float *leaves, const float *jaws,
+                              const float *mu, float *dleaves, float *djaws, float *dmu,
+                              cudaStream_t s)
+{
+    k_param_grad<<<P.n_cp, 256, 0, s>>>(P, leaves, jaws, mu, dleaves, djaws, dmu);
+    return cudaGetLastError();
+}
+
+}  // namespace pdrt

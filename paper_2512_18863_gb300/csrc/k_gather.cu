@@ -1,0 +1,139 @@
+// Rotation back to the patient grid and MU-weighted accumulation
+// (Sec. 2.2.7, Eq. D_total), and its transpose.
+//
+// k_gather: one thread per voxel, looping over the control points of a chunk;
+//   the voxel samples the beam-frame dose D'_b bilinearly in (u, w) (its v
+//   coordinate is an exact lattice plane, so trilinear reduces to bilinear),
+//   sums cal * MU_b * sample in a register and writes the voxel once per chunk.
+//   No atomics; the CP order of the sum is fixed.  A CTA (32 x 8 voxels of one
+//   z plane) skips a control point when its footprint misses the CTA.
+// k_gather_T: pull form of the transpose: every beam-frame point (i, j, k) of
+//   the output box gathers the dose gradient of the (at most 3 x 3) voxels of
+//   plane j whose bilinear stencil contains it, with the weights recomputed by
+//   the same float expressions as k_gather (voxel_to_beam), so it is the exact
+//   transpose of the forward up to summation order.  No atomics.
+#include <math.h>
+
+#include "pdrt_impl.cuh"
+
+namespace pdrt {
+
+__device__ __forceinline__ float region_value(const float *__restrict__ base, const int4 ob,
+                                              long long off, int i, int j)
+{
+    if (i < ob.x || i >= ob.y || j < ob.z || j >= ob.w) return 0.f;
+    return __ldg(&base[off + (long long)(j - ob.z) * (ob.y - ob.x) + (i - ob.x)]);
+}
+
+__global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float *__restrict__ dose,
+                                                int first)
+{
+    const Lattice &L = P.lat;
+    const int ix = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int iy = blockIdx.y * 8 + (threadIdx.x >> 5);
+    const int iz = blockIdx.z;
+    const bool inside = ix < P.nx && iy < P.ny;
+    const float bx0 = (float)(blockIdx.x * 32), bx1 = (float)min((int)blockIdx.x * 32 + 31, P.nx - 1);
+    const float by0 = (float)(blockIdx.y * 8), by1 = (float)min((int)blockIdx.y * 8 + 7, P.ny - 1);
+    float acc = 0.f;
+    for (int bl = 0; bl < nb; ++bl) {
+        const int b = b0 + bl;
+        const CpTab &ct = P.cptab[b];
+        if (iz < ct.vj0 || iz >= ct.vj1) continue;
+        const CpGeo g = P.cpgeo[b];
+        // footprint test of the CTA: fu, fw are affine in (ix, iy)
+        const float u00 = fmaf(g.au, bx0, fmaf(g.bu, by0, g.cu0));
+        const float u10 = fmaf(g.au, bx1, fmaf(g.bu, by0, g.cu0));
+        const float u01 = fmaf(g.au, bx0, fmaf(g.bu, by1, g.cu0));
+        const float u11 = fmaf(g.au, bx1, fmaf(g.bu, by1, g.cu0));
+        const float umin = fminf(fminf(u00, u10), fminf(u01, u11));
+        const float umax = fmaxf(fmaxf(u00, u10), fmaxf(u01, u11));
+        if (umax < (float)ct.ui0 - 1.f || umin > (float)ct.ui1) continue;
+        const float w00 = fmaf(g.aw, bx0, fmaf(g.bw, by0, g.cw0));
+        const float w10 = fmaf(g.aw, bx1, fmaf(g.bw, by0, g.cw0));
+        const float w01 = fmaf(g.aw, bx0, fmaf(g.bw, by1, g.cw0));
+        const float w11 = fmaf(g.aw, bx1, fmaf(g.bw, by1, g.cw0));
+        const float wmin = fminf(fminf(w00, w10), fminf(w01, w11));
+        const float wmax = fmaxf(fmaxf(w00, w10), fmaxf(w01, w11));
+        if (wmax < (float)ct.k0 - 1.f || wmin > (float)ct.k1) continue;
+        if (!inside) continue;
+        float fu, fw;
+        voxel_to_beam(g, ix, iy, fu, fw);
+        const float bu = floorf(fu), bw = floorf(fw);
+        const int i0 = (int)bu, k0 = (int)bw;
+        const float tu = fu - bu, tw = fw - bw;
+        const float *base = P.region + (long long)bl * P.cap_o;
+        float val = 0.f;
+#pragma unroll
+        for (int dk = 0; dk < 2; ++dk) {
+            const int k = k0 + dk;
+            if (k < 0 || k >= L.nw) continue;
+            const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
+            const int4 ob = __ldg(reinterpret_cast<const int4 *>(&sp->oi0));
+            if (iz < ob.z || iz >= ob.w) continue;
+            const long long off = __ldg(&sp->off_o);
+            const float v0 = region_value(base, ob, off, i0, iz);
+            const float v1 = region_value(base, ob, off, i0 + 1, iz);
+            val += (dk ? tw : 1.f - tw) * ((1.f - tu) * v0 + tu * v1);
+        }
+        acc = fmaf(ct.cal_mu, val, acc);
+    }
+    if (inside) {
+        const long long idx = ((long long)iz * P.ny + iy) * P.nx + ix;
+        dose[idx] = first ? acc : dose[idx] + acc;
+    }
+}
+
+cudaError_t launch_gather(const PlanDev &P, int b0, int nb, float *dose, bool first, cudaStream_t s)
+{
+    dim3 grid((P.nx + 31) / 32, (P.ny + 7) / 8, P.nz);
+    k_gather<<<grid, 256, 0, s>>>(P, b0, nb, dose, first ? 1 : 0);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
+{
+    const Lattice &L = P.lat;
+    const int k = blockIdx.x, bl = blockIdx.y, b = b0 + bl;
+    const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
+    const int4 ob = *reinterpret_cast<const int4 *>(&sp->oi0);
+    const int ow = ob.y - ob.x, oh = ob.w - ob.z;
+    if (ow <= 0 || oh <= 0) return;
+    const CpGeo g = P.cpgeo[b];
+    float *out = P.region + (long long)bl * P.cap_o + sp->off_o;
+    const float dk = (float)k - L.cw;
+    for (int t = threadIdx.x; t < ow * oh; t += blockDim.x) {
+        const int i = ob.x + t % ow, j = ob.z + t / ow;
+        const float di = (float)i - L.cu;
+        // voxel-index position of lattice point (i, k): rotation transpose
+        const float fx = fmaf(di, g.au, fmaf(dk, g.aw, g.px0));
+        const float fy = fmaf(di, g.bu, fmaf(dk, g.bw, g.py0));
+        const int x0 = max((int)ceilf(fx - 1.45f), 0), x1 = min((int)floorf(fx + 1.45f), P.nx - 1);
+        const int y0 = max((int)ceilf(fy - 1.45f), 0), y1 = min((int)floorf(fy + 1.45f), P.ny - 1);
+        const float *gp = gd + (long long)j * P.ny * P.nx;
+        float s = 0.f;
+        for (int iy = y0; iy <= y1; ++iy) {
+            for (int ix = x0; ix <= x1; ++ix) {
+                float fu, fw;
+                voxel_to_beam(g, ix, iy, fu, fw);
+                const float bu = floorf(fu), bw = floorf(fw);
+                const int i0 = (int)bu, k0 = (int)bw;
+                const float tu = fu - bu, tw = fw - bw;
+                const float wu = (i == i0) ? 1.f - tu : ((i == i0 + 1) ? tu : 0.f);
+                const float ww = (k == k0) ? 1.f - tw : ((k == k0 + 1) ? tw : 0.f);
+                const float wgt = ww * wu;
+                if (wgt != 0.f) s = fmaf(wgt, __ldg(&gp[(long long)iy * P.nx + ix]), s);
+            }
+        }
+        out[t] = s;
+    }
+}
+
+cudaError_t launch_gather_T(const PlanDev &P, int b0, int nb, const float *g, cudaStream_t s)
+{
+    dim3 grid(P.lat.nw, nb);
+    k_gather_T<<<grid, 256, 0, s>>>(P, b0, g);
+    return cudaGetLastError();
+}
+
+}  // namespace pdrt

@@ -1,0 +1,149 @@
+// Internal declarations of the sm_103a dose engine (not part of the C ABI).
+//
+// Data layout in device memory (per plan):
+//   cpgeo  [n_cp]            static per-CP geometry (affine maps voxel -> beam lattice)
+//   ukr    [n_cp][nw]        static needed u-range of every beam slice (int2)
+//   cptab  [n_cp]            per-call CP state (projected MU, fluence support box, ...)
+//   slices [n_cp][nw]        per-call slice table (depth, kernel, boxes, offsets)
+//   fbuf   [n_cp][nu*nv]     fluence maps over their support boxes, [a][c] (c fastest)
+//   gfbuf  [n_cp][nu*nv]     adjoint of the fluence maps, same layout
+//   region [chunk][cap_o]    beam-frame dose D' (forward) or gathered gradient h
+//                            (adjoint) of one chunk of CPs; each slice's box is
+//                            stored [j][i] (i fastest) at slices[].off_o
+//   adjbuf [chunk][cap_a]    adjoint convolution output on the support boxes
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pdrt.h"
+
+namespace pdrt {
+
+constexpr int kMaxCpPerChunk = 256;
+constexpr int kConvThreads = 128;        // 4 warps: 32 output rows x (4 x 16) output columns
+constexpr int kConvTJ = 16;              // output columns per lane
+constexpr int kConvCols = 64;            // output columns per CTA
+constexpr int kConvRows = 32;            // output rows per CTA (one per lane)
+
+enum KernelId {
+    K_HU = 0, K_RASTER = 1, K_TABLES = 2, K_CONV_FWD = 3, K_GATHER = 4,
+    K_GATHER_T = 5, K_CONV_ADJ = 6, K_MAG_T_GRAD = 7
+};
+
+struct Lattice {
+    int nu, nv, nw;
+    float cu, cv, cw;     // isocentre lattice index (cu = cw integer)
+    float du, dv;         // pitch along u/w and along v
+};
+
+// Machine constants in the precision the kernels use.
+struct MachineDev {
+    float sid;
+    int n_pairs;
+    float tau, wmin_leaf, wmin_jaw, f_leaf, f_jaw, eps_mu;
+    int R;                // kernel half window
+    int nq4;              // taps per kernel row rounded up to 4, / 4
+    int kstride;          // smem row stride of the kernel table (4 * odd >= 4*nq4)
+    float alpha[3][3], beta[3][3];
+    int n_depth;
+    float depth_step;
+    float cal;
+    int ste;
+};
+
+struct CpGeo {
+    float au, bu, cu0;    // fu = au*ix + bu*iy + cu0   (beam lattice index along u)
+    float aw, bw, cw0;    // fw = aw*ix + bw*iy + cw0   (beam lattice index along w)
+    float sx_w, sy_w;     // beam direction e_w projected to voxel index units (x, y)
+    float px0, py0, pz0;  // isocentre in voxel index units
+};
+
+struct CpTab {
+    float mu_hat;         // projected MU
+    float cal_mu;         // cal * mu_hat
+    int fa0, fa1, fc0, fc1;  // fluence support box [fa0,fa1) x [fc0,fc1) (pixels)
+    int ui0, ui1, vj0, vj1;  // union over slices of the output boxes (gather culling)
+    int k0, k1;           // slices with work [k0,k1)
+    long long tot_o, tot_a;  // floats used in the region / adjoint buffers
+    long long n_support, n_region, n_active;  // work counters
+};
+
+struct alignas(16) SliceTab {
+    float z, tdd, m, c2;      // WEPL, depth dose T(z), magnification, inverse square
+    float a[3];               // kernel decays
+    float pad0;
+    float wn[3];              // kernel weights divided by their window sums
+    float pad1;
+    int pi0, pi1, pj0, pj1;   // conv input box (non-zero fluence volume)
+    int oi0, oi1, oj0, oj1;   // forward output box (where D' is produced)
+    int ai0, ai1, aj0, aj1;   // adjoint output box
+    long long off_o, off_a;   // offsets (floats) inside the CP's region / adjoint slot
+};
+static_assert(sizeof(SliceTab) % 16 == 0, "SliceTab rows are read as int4");
+static_assert(offsetof(SliceTab, oi0) % 16 == 0 && offsetof(SliceTab, ai0) % 16 == 0,
+              "box fields must be 16-byte aligned");
+
+struct PlanDev {
+    Lattice lat;
+    MachineDev mach;
+    int n_cp;
+    int nx, ny, nz;
+    const float *red;        // grid density
+    const float *leaf_bounds;  // [n_pairs+1] (device)
+    const float *depth_dose;   // [n_depth] (device)
+    const CpGeo *cpgeo;
+    const int2 *ukr;
+    CpTab *cptab;
+    SliceTab *slices;
+    float *fbuf, *gfbuf;
+    float *region, *adjbuf;
+    long long cap_o, cap_a;  // floats per CP slot
+    unsigned int *flags;
+    unsigned int *counters;  // work-queue counters (per chunk launch)
+};
+
+// Same float expression in every kernel that samples or transposes the
+// magnified fluence (forward tile fill and its adjoint).
+__device__ __forceinline__ float mag_coord(float m, int idx, float c)
+{
+    return fmaf(m, (float)idx - c, c);
+}
+
+// Beam lattice coordinates of voxel (ix, iy) for one control point; shared
+// by the gather and its transpose so both use bit-identical weights.
+__device__ __forceinline__ void voxel_to_beam(const CpGeo &g, int ix, int iy, float &fu, float &fw)
+{
+    fu = fmaf(g.au, (float)ix, fmaf(g.bu, (float)iy, g.cu0));
+    fw = fmaf(g.aw, (float)ix, fmaf(g.bw, (float)iy, g.cw0));
+}
+
+__device__ __forceinline__ float overlap_f(float x, float lo, float hi, float d)
+{
+    float e = x + 0.5f * d, s = x - 0.5f * d;
+    float top = (hi <= e) ? hi : e;
+    float bot = (lo >= s) ? lo : s;
+    float X = top - bot;
+    return X > 0.f ? X / d : 0.f;
+}
+
+// launchers (one per kernel); each returns cudaGetLastError() of its launch
+cudaError_t launch_hu_to_red(const float *hu, float *red, long long n, const float *pts, int npts,
+                             cudaStream_t s);
+cudaError_t launch_raster(const PlanDev &P, const float *leaves, const float *jaws,
+                          const float *mu, cudaStream_t s);
+cudaError_t launch_tables(const PlanDev &P, cudaStream_t s);
+cudaError_t launch_conv(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
+                        int grid_blocks, cudaStream_t s);
+cudaError_t launch_gather(const PlanDev &P, int b0, int nb, float *dose, bool first,
+                          cudaStream_t s);
+cudaError_t launch_gather_T(const PlanDev &P, int b0, int nb, const float *g, cudaStream_t s);
+cudaError_t launch_mag_T(const PlanDev &P, int b0, int nb, cudaStream_t s);
+cudaError_t launch_param_grad(const PlanDev &P, const float *leaves, const float *jaws,
+                              const float *mu, float *dleaves, float *djaws, float *dmu,
+                              cudaStream_t s);
+int conv_smem_bytes(const MachineDev &m);
+int conv_nq4_for_radius(int R);
+cudaError_t conv_prepare(const MachineDev &m, int *fwd_blocks_per_sm, int *adj_blocks_per_sm);
+
+}  // namespace pdrt

@@ -1,0 +1,66 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point that
+include/pdrt.h declares, and rejects bad arguments on the host before it
+touches the GPU (no compute calls here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2512_18863_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "pdrt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pdrt_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_entry_point():
+    lib = _lib.load()
+    names = _declared()
+    assert "pdrt_dose_forward" in names and "pdrt_dose_backward" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib._SIG), "binding and header disagree"
+
+
+def test_host_only_calls():
+    assert _lib.pdrt_last_error() == ""
+    assert _lib.pdrt_launch_count() >= 0
+
+
+def _grid_create(**kw):
+    args = dict(hu=1, nx=4, ny=4, nz=4, sx=2.0, sy=2.0, sz=2.0, origin=(0, 0, 0),
+                pts=((-1000.0, 0.0), (0.0, 1.0)))
+    args.update(kw)
+    return _lib.pdrt_grid_create(args["hu"], args["nx"], args["ny"], args["nz"], args["sx"],
+                                 args["sy"], args["sz"], args["origin"], args["pts"], 0)
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(nx=0), 2),
+    (dict(sx=2.0, sy=3.0), 1),
+    (dict(sz=-1.0), 1),
+    (dict(pts=((0.0, 1.0),)), 1),
+    (dict(pts=((0.0, 1.0), (-5.0, 0.0))), 1),
+    (dict(origin=(0.0, float("nan"), 0.0)), 1),
+])
+def test_grid_create_rejects_bad_arguments(kw, status):
+    with pytest.raises(_lib.PdrtError) as e:
+        _grid_create(**kw)
+    assert e.value.status == status
+    assert _lib.pdrt_last_error() != ""
+
+
+def test_null_handles_rejected():
+    lib = _lib.load()
+    assert lib.pdrt_dose_forward(None, None, None, None, None, None, None) == 1
+    assert lib.pdrt_dose_backward(None, None, None, None, None, None, None, None, None, None) == 1
+    out = C.c_void_p()
+    m = _lib.pdrt_machine()
+    assert lib.pdrt_plan_upload(C.byref(out), None, 1, None, None, C.byref(m), 0, None) == 1
+    info = _lib.pdrt_plan_info()
+    assert lib.pdrt_plan_get_info(None, C.byref(info)) == 1

@@ -1,0 +1,235 @@
+"""GPU (sm_103a, FP32) vs FP64 oracle parity, through the C ABI.
+
+Bars (FP32 path vs FP64 oracle): dose max |dD| <= 1e-4 * max D;
+gradients ||dg||_inf <= 1e-3 * ||g||_inf per parameter class (leaves, jaws, MU).
+Inputs are seeded synthetic workloads (paper_2512_18863_gb300.synth); no
+expected value comes from the CUDA path.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2512_18863_gb300 import synth as S
+from paper_2512_18863_gb300.engine import DoseEngine
+
+pytestmark = pytest.mark.gpu
+
+DOSE_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+def _engine(w, **kw):
+    return DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso, **kw)
+
+
+def _gpu_dose(w, leaves=None, jaws=None, mu=None, **kw):
+    eng = _engine(w, **kw)
+    d = eng.forward(w.plan.leaves if leaves is None else leaves,
+                    w.plan.jaws if jaws is None else jaws,
+                    w.plan.mu if mu is None else mu)
+    out = d.cpu().numpy().astype(np.float64)
+    eng.close()
+    return out
+
+
+def _assert_dose(gpu, ref, tol=DOSE_TOL):
+    err = np.abs(gpu - ref).max()
+    assert err <= tol * ref.max(), f"max |dD| = {err:.3e} vs {tol} * {ref.max():.4e}"
+
+
+def _assert_grad(gpu, ref, name):
+    scale = np.abs(ref).max()
+    err = np.abs(gpu - ref).max()
+    assert err <= GRAD_TOL * scale, f"{name}: |dg|_inf = {err:.3e} vs {GRAD_TOL} * {scale:.4e}"
+
+
+# ---------------------------------------------------------------------------
+# forward
+# ---------------------------------------------------------------------------
+def test_water_static_10x10_matches_oracle_and_closed_form():
+    w = S.water_static_64()
+    gpu = _gpu_dose(w)
+    ref = O.Model(w.phantom, w.machine, w.plan).dose()
+    _assert_dose(gpu, ref)
+    iy = np.arange(64)
+    T = np.interp((iy + 0.5) * 2.5, np.arange(len(w.machine.t_table)) * w.machine.dz_t,
+                  w.machine.t_table)
+    closed = w.machine.cal * 100.0 * T * (1000.0 / (1000.0 + (iy - 32) * 2.5)) ** 2
+    np.testing.assert_allclose(gpu[32, :, 32], closed, rtol=2e-5)
+
+
+@pytest.mark.parametrize("n,spacing,n_cp,r_px,seed", [
+    ((24, 40, 40), 3.0, 6, 4, 7),      # several CTA tiles per slice
+    ((23, 37, 41), 3.0, 5, 3, 8),      # ragged, odd grid, nx != ny
+    ((20, 33, 33), 4.0, 4, 10, 9),     # R = 10 px
+    ((18, 30, 30), 4.0, 3, 21, 10),    # R = 21 px
+    ((16, 28, 28), 5.0, 2, 44, 11),    # maximum radius
+    ((40, 48, 48), 2.0, 3, 13, 12),    # 2 mm grid, R = 13
+])
+def test_pelvis_forward_matches_oracle(n, spacing, n_cp, r_px, seed):
+    w = S.small_pelvis(seed=seed, n=n, spacing=spacing, n_cp=n_cp, r_px=r_px)
+    gpu = _gpu_dose(w)
+    ref = O.Model(w.phantom, w.machine, w.plan).dose()
+    assert ref.max() > 0
+    _assert_dose(gpu, ref)
+
+
+def test_pelvis_128_arc_subset_matches_oracle():
+    """128x128x96 at 3 mm (kernel radius 4 cm): 8 control points spread
+    around the 178-CP arc."""
+    w = S.pelvis_arc_128()
+    sel = np.arange(0, 178, 22)[:8]
+    sub = S.Workload(w.name, w.phantom, w.machine,
+                     S.Plan(w.plan.gantry_deg[sel], w.plan.iso, w.plan.leaves[sel],
+                            w.plan.jaws[sel], w.plan.mu[sel]))
+    gpu = _gpu_dose(sub)
+    ref = O.Model(sub.phantom, sub.machine, sub.plan).dose()
+    _assert_dose(gpu, ref)
+
+
+def test_chunking_does_not_change_the_dose():
+    """One CP per pass (tiny scratch budget) vs all CPs in one pass."""
+    w = S.small_pelvis(n=(20, 36, 36), n_cp=7, r_px=5)
+    a = _gpu_dose(w, scratch_budget_bytes=1)
+    b = _gpu_dose(w)
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-6 * b.max())
+
+
+# ---------------------------------------------------------------------------
+# gradients
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("ste", [1, 0])
+def test_gradients_match_oracle(ste):
+    w = S.small_pelvis(seed=21, n=(20, 36, 36), n_cp=5, r_px=6)
+    w.machine.ste = ste
+    w.plan.leaves[1, 30] = (2.1, 2.4)          # a pair under w_min: clamp active
+    w.plan.mu[2] = 0.004                       # below eps_mu
+    rng = np.random.default_rng(5)
+    g = rng.standard_normal(w.phantom.shape)
+    eng = _engine(w)
+    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
+                  for t in eng.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g))
+    rl, rj, rm = O.Model(w.phantom, w.machine, w.plan).dose_grad(g)
+    _assert_grad(dl, rl, "leaves")
+    _assert_grad(dj, rj, "jaws")
+    _assert_grad(dm, rm, "mu")
+    eng.close()
+
+
+def test_autograd_function_matches_oracle():
+    """DoseFn inside a torch graph: quadratic objective on the PTV and an OAR."""
+    w = S.small_pelvis(seed=22, n=(20, 36, 36), n_cp=4, r_px=5)
+    eng = _engine(w)
+    dev = eng.device
+    leaves = torch.tensor(w.plan.leaves, dtype=torch.float32, device=dev, requires_grad=True)
+    jaws = torch.tensor(w.plan.jaws, dtype=torch.float32, device=dev, requires_grad=True)
+    mu = torch.tensor(w.plan.mu, dtype=torch.float32, device=dev, requires_grad=True)
+    ptv = torch.tensor(w.phantom.masks["ptv"], device=dev, dtype=torch.float32)
+    D = eng(leaves, jaws, mu)
+    loss = ((D - 2.0) ** 2 * ptv).sum() + 0.1 * (D ** 2 * (1 - ptv)).sum()
+    loss.backward()
+    mod = O.Model(w.phantom, w.machine, w.plan)
+    Dr = mod.dose()
+    pm = w.phantom.masks["ptv"].astype(np.float64)
+    g = 2 * (Dr - 2.0) * pm + 0.2 * Dr * (1 - pm)      # dL/dD from the oracle's own dose
+    rl, rj, rm = mod.dose_grad(g)
+    _assert_grad(leaves.grad.cpu().numpy(), rl, "leaves")
+    _assert_grad(jaws.grad.cpu().numpy(), rj, "jaws")
+    _assert_grad(mu.grad.cpu().numpy(), rm, "mu")
+    eng.close()
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_closed_jaws_give_zero_dose_and_gradient():
+    w = S.small_pelvis(n=(16, 24, 24), n_cp=3, r_px=3)
+    w.machine.wmin_jaw = 0.0
+    jaws = w.plan.jaws.copy()
+    jaws[:] = (5.0, 5.0, -3.0, -3.0)
+    eng = _engine(w)
+    d = eng.forward(w.plan.leaves, jaws, w.plan.mu)
+    assert float(d.abs().max()) == 0.0
+    g = np.ones(w.phantom.shape)
+    dl, dj, dm = eng.backward(w.plan.leaves, jaws, w.plan.mu, g)
+    assert float(dl.abs().max()) == 0.0 and float(dm.abs().max()) == 0.0
+    eng.close()
+
+
+def test_field_larger_than_lattice_and_single_cp():
+    w = S.small_pelvis(n=(16, 24, 24), n_cp=1, r_px=4)
+    w.plan.jaws[0] = (-300.0, 300.0, -300.0, 300.0)
+    w.plan.leaves[0, :, 0] = -250.0
+    w.plan.leaves[0, :, 1] = 250.0
+    gpu = _gpu_dose(w)
+    ref = O.Model(w.phantom, w.machine, w.plan).dose()
+    _assert_dose(gpu, ref)
+
+
+def test_nan_input_is_flagged():
+    w = S.small_pelvis(n=(16, 24, 24), n_cp=2, r_px=3)
+    eng = _engine(w)
+    leaves = w.plan.leaves.copy()
+    leaves[1, 5, 0] = np.nan
+    eng.forward(leaves, w.plan.jaws, w.plan.mu)
+    assert eng.status_flags() & 1
+    eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu)
+    assert eng.status_flags() == 0
+    eng.close()
+
+
+def test_forward_and_backward_are_deterministic():
+    w = S.small_pelvis(n=(20, 32, 32), n_cp=4, r_px=5)
+    eng = _engine(w)
+    a = eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).clone()
+    b = eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).clone()
+    assert torch.equal(a, b)
+    g = torch.rand(w.phantom.shape, device=eng.device)
+    r1 = [t.clone() for t in eng.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g)]
+    r2 = eng.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g)
+    assert all(torch.equal(x, y) for x, y in zip(r1, r2))
+    eng.close()
+
+
+# ---------------------------------------------------------------------------
+# full size (256x256x160, 2 x 178 CPs) in the benchmark's launch configuration
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c3():
+    return S.pelvis_two_arc_256(r_cm=4.0)
+
+
+def _subplan(w, sel):
+    return S.Workload(w.name, w.phantom, w.machine,
+                      S.Plan(w.plan.gantry_deg[sel], w.plan.iso, w.plan.leaves[sel],
+                             w.plan.jaws[sel], w.plan.mu[sel]))
+
+
+def test_full_size_forward_sampled_against_oracle(c3):
+    """Oracle on 2 control points at full grid size vs the GPU on the same two;
+    the full 356-CP dose equals the sum of its two arcs (linearity, any size)."""
+    sel = np.array([45, 250])
+    sub = _subplan(c3, sel)
+    gpu = _gpu_dose(sub)
+    ref = O.Model(sub.phantom, sub.machine, sub.plan).dose()
+    _assert_dose(gpu, ref)
+    full = _gpu_dose(c3)
+    a = _gpu_dose(_subplan(c3, np.arange(178)))
+    b = _gpu_dose(_subplan(c3, np.arange(178, 356)))
+    np.testing.assert_allclose(full, a + b, rtol=0, atol=1e-5 * full.max())
+
+
+def test_full_size_gradient_sampled_against_oracle(c3):
+    sel = np.array([100])
+    sub = _subplan(c3, sel)
+    rng = np.random.default_rng(9)
+    g = rng.standard_normal(sub.phantom.shape).astype(np.float32)
+    eng = _engine(sub)
+    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
+                  for t in eng.backward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu, g))
+    rl, rj, rm = O.Model(sub.phantom, sub.machine, sub.plan).dose_grad(g.astype(np.float64))
+    _assert_grad(dl, rl, "leaves")
+    _assert_grad(dj, rj, "jaws")
+    _assert_grad(dm, rm, "mu")
+    eng.close()
