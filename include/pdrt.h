@@ -223,6 +223,42 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out);
 pdrt_status pdrt_profile_enable(pdrt_plan_t p, int32_t enable);
 pdrt_status pdrt_profile_read(pdrt_plan_t p, pdrt_stream_t stream, pdrt_profile *out);
 
+/*
+ * Allocation-free forward dose of ONE control point.  The paper has no
+ * counterpart: this is an integration variant of pdrt_dose_forward for
+ * callers that cannot call cudaMalloc -- for example a plug-in hosted by a
+ * framework that owns all device memory and hands it only input and output
+ * buffers, or a latency-critical loop that must never enter the CUDA
+ * allocator (cudaMalloc/cudaFree can synchronise the device and can fail on
+ * fragmented memory).  pdrt_grid_create and pdrt_plan_upload allocate, so this
+ * entry point takes the density grid and the beam model directly and uses
+ * no handle.
+ *   red_dev     [nz][ny][nx] relative electron density (device; the HU curve
+ *               of pdrt_grid_create already applied by the caller).
+ *   nx..origin_mm  grid as in pdrt_grid_create; iso_mm, gantry_deg, m as in
+ *               pdrt_plan_upload for a one-point plan.
+ *   leaves_dev [n_pairs][2], jaws_dev [4], mu_dev [1] (device, raw).
+ *   dose_dev   [nz][ny][nx] (device), overwritten with this point's dose.
+ * Scratch: all intermediate data lives in one static device array of
+ * PDRT_STATIC_SCRATCH_BYTES inside the library, held by every GPU that loads
+ * the library until the process exits.  The first call made with a device
+ * current looks up that array's device address (cudaGetSymbolAddress) and
+ * prepares the kernels for that device; make that first call before any
+ * stream capture.  Every call shares the array, which keeps the last call's
+ * contents (counters are cleared at the start of each call); calls that can
+ * overlap on the GPU (other streams, other host threads) race on it.
+ * Synchronous: returns once the dose is written (the stream is synchronised).
+ * Errors: EINVAL (bad arguments; a grid whose scratch would exceed
+ * PDRT_STATIC_SCRATCH_BYTES, with the needed size in the message), EDEVICE,
+ * ECUDA.  Calls no cudaMalloc/cudaFree.
+ */
+#define PDRT_STATIC_SCRATCH_BYTES (64u << 20)
+pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int32_t ny, int32_t nz,
+                                double sx, double sy, double sz, const double origin_mm[3],
+                                const double iso_mm[3], double gantry_deg, const pdrt_machine *m,
+                                const float *leaves_dev, const float *jaws_dev,
+                                const float *mu_dev, float *dose_dev, pdrt_stream_t stream);
+
 /* Number of kernels this library has launched since it was loaded. */
 int64_t pdrt_launch_count(void);
 

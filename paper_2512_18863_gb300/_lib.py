@@ -74,6 +74,9 @@ _SIG = {
     "pdrt_plan_work": (C.c_int, [_VP, _VP, C.POINTER(pdrt_work)]),
     "pdrt_profile_enable": (C.c_int, [_VP, C.c_int32]),
     "pdrt_profile_read": (C.c_int, [_VP, _VP, C.POINTER(pdrt_profile)]),
+    "pdrt_cp_dose_static": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                      C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.c_double, C.POINTER(pdrt_machine), _VP, _VP, _VP, _VP, _VP]),
     "pdrt_launch_count": (C.c_int64, []),
     "pdrt_last_error": (C.c_char_p, []),
 }
@@ -189,6 +192,18 @@ def pdrt_profile_read(plan, stream) -> dict:
         out[p.name[k].decode()] = {"launches": int(p.launches[k]), "total_ms": float(p.total_ms[k])}
     out["_overflow"] = bool(p.overflow)
     return out
+
+
+STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def pdrt_cp_dose_static(red_dev_ptr, nx, ny, nz, sx, sy, sz, origin_mm, iso_mm, gantry_deg,
+                        machine: pdrt_machine, leaves_ptr, jaws_ptr, mu_ptr, dose_ptr, stream):
+    """One control point's dose using the library's static scratch (no allocation)."""
+    _check(load().pdrt_cp_dose_static(_VP(red_dev_ptr), int(nx), int(ny), int(nz), float(sx),
+                                      float(sy), float(sz), _dptr(origin_mm), _dptr(iso_mm),
+                                      float(gantry_deg), C.byref(machine), _VP(leaves_ptr),
+                                      _VP(jaws_ptr), _VP(mu_ptr), _VP(dose_ptr), _VP(stream)))
 
 
 def machine_struct(machine) -> pdrt_machine:

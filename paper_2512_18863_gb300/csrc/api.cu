@@ -157,6 +157,10 @@ void needed_range(const double fu[4], const double fw[4], int k, int nu, int &lo
 
 }  // namespace
 
+// Hooks for entry points defined in other translation units.
+void pdrt::internal_set_error(const char *msg) { g_last_error = msg ? msg : ""; }
+void pdrt::internal_count_launch() { g_launches.fetch_add(1); }
+
 extern "C" {
 
 const char *pdrt_last_error(void) { return g_last_error.c_str(); }

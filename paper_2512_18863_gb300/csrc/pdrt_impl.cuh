@@ -145,5 +145,7 @@ cudaError_t launch_param_grad(const PlanDev &P, const float *leaves, const float
 int conv_smem_bytes(const MachineDev &m);
 int conv_nq4_for_radius(int R);
 cudaError_t conv_prepare(const MachineDev &m, int *fwd_blocks_per_sm, int *adj_blocks_per_sm);
+void internal_set_error(const char *msg);   // sets pdrt_last_error() for this thread
+void internal_count_launch();                // counts one launch in pdrt_launch_count()
 
 }  // namespace pdrt
