@@ -47,6 +47,11 @@ def _args():
     ap.add_argument("--cpu-sample-cps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="pelvis256", choices=["pelvis256", "pelvis128"],
+                    help="pelvis256: 256x256x160 @ 2 mm, 2 x 178 CPs (headline); "
+                         "pelvis128: 128x128x96 @ 3 mm, 178 CPs (smaller case for profiler captures)")
+    ap.add_argument("--scratch-gb", type=float, default=0.0,
+                    help="plan scratch budget in GB (0 = library default)")
     return ap.parse_args()
 
 
@@ -57,8 +62,10 @@ def _dist():
     return world, rank, local
 
 
-def _workload(r_cm):
+def _workload(r_cm, name="pelvis256"):
     from paper_2512_18863_gb300 import synth
+    if name == "pelvis128":
+        return synth.pelvis_arc_128(r_cm=r_cm)
     return synth.pelvis_two_arc_256(r_cm=r_cm)
 
 
@@ -145,7 +152,8 @@ def _cpu_baseline(w, n_cps):
     return {"value": (n_cps / CP_PER_ARC) / dt, "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"{n_cps} of {w.plan.n_cp} control points (fwd+adjoint) on the full "
-                      f"256x256x160 grid, FP64, OpenMP; {dt:.1f} s"}
+                      f"{'x'.join(str(s) for s in w.phantom.shape[::-1])} grid, FP64, OpenMP; "
+                      f"{dt:.1f} s"}
 
 
 def _reference(args):
@@ -158,7 +166,7 @@ def _reference(args):
             dist.destroy_process_group()
             return
     from oracle import oracle
-    w = _workload(args.r_cm)
+    w = _workload(args.r_cm, args.workload)
     rng = np.random.default_rng(0)
     times = []
     for s in range(args.warmup + args.steps):
@@ -202,8 +210,9 @@ def _gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = _workload(args.r_cm)
-    eng = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso)
+    w = _workload(args.r_cm, args.workload)
+    eng = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso,
+                     scratch_budget_bytes=int(args.scratch_gb * 1e9))
     dev = eng.device
     leaves = torch.tensor(w.plan.leaves, dtype=torch.float32, device=dev)
     jaws = torch.tensor(w.plan.jaws, dtype=torch.float32, device=dev)
@@ -302,11 +311,12 @@ def _gpu(args):
 
     if rank == 0:
         nz, ny, nx = w.phantom.shape
+        sp = float(w.phantom.spacing[0])
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded pelvis phantom and VMAT arcs)",
-               "config": {"workload": w.name, "grid": [nx, ny, nz], "spacing_mm": 2.0,
+               "config": {"workload": w.name, "grid": [nx, ny, nz], "spacing_mm": sp,
                           "n_cp": int(w.plan.n_cp), "kernel_radius_px": int(w.machine.r_px),
                           "step": "forward + adjoint of all control points",
                           "l2": "flushed between steps (256 MB write)",

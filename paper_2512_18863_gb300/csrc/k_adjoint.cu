@@ -16,6 +16,25 @@
 
 namespace pdrt {
 
+constexpr int kMagStage = 1024;   // slices staged in shared memory per pass
+
+struct MagSlice {
+    float m;
+    int ai0, ai1, aj0, aj1;
+    int pad;
+    long long off_a;
+};
+
+// candidate lattice indices idx with |mag_coord(m, idx, c) - p| < 1, widened
+// by a small margin (the exact weights decide)
+__device__ __forceinline__ void mag_candidates(int p, float c, float m, int lo_box, int hi_box,
+                                               int &lo, int &hi)
+{
+    const float inv = 1.f / m;
+    lo = max((int)floorf(c + ((float)p - 1.f - c) * inv - 1e-3f) + 1, lo_box);
+    hi = min((int)ceilf(c + ((float)p + 1.f - c) * inv + 1e-3f), hi_box);   // exclusive
+}
+
 __global__ void __launch_bounds__(256) k_mag_T(PlanDev P, int b0)
 {
     const Lattice &L = P.lat;
@@ -23,50 +42,71 @@ __global__ void __launch_bounds__(256) k_mag_T(PlanDev P, int b0)
     const CpTab ct = P.cptab[b];
     const int Fa = ct.fa1 - ct.fa0, Fc = ct.fc1 - ct.fc0;
     if (Fa <= 0 || Fc <= 0) return;
+    __shared__ MagSlice s_sl[kMagStage];
     float *gF = P.gfbuf + (long long)b * L.nu * L.nv;
     const float *hb = P.adjbuf + (long long)bl * P.cap_a;
     const SliceTab *sl = P.slices + (long long)b * L.nw;
     const int n = Fa * Fc;
-    for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n; t += gridDim.y * blockDim.x) {
-        const int a = ct.fa0 + t % Fa, c = ct.fc0 + t / Fa;   // consecutive threads: consecutive a
-        float s = 0.f;
-        for (int k = ct.k0; k < ct.k1; ++k) {
-            const SliceTab *sp = sl + k;
-            const int4 ab = *reinterpret_cast<const int4 *>(&sp->ai0);
-            if (ab.y <= ab.x || ab.w <= ab.z) continue;
-            const float m = sp->m;
-            // i with |mag_coord(m, i, cu) - a| < 1, widened by one for rounding
-            const int i_lo = max((int)floorf(L.cu + ((float)a - 1.f - L.cu) / m), ab.x);
-            const int i_hi = min((int)ceilf(L.cu + ((float)a + 1.f - L.cu) / m) + 1, ab.y);
-            const int j_lo = max((int)floorf(L.cv + ((float)c - 1.f - L.cv) / m), ab.z);
-            const int j_hi = min((int)ceilf(L.cv + ((float)c + 1.f - L.cv) / m) + 1, ab.w);
-            if (i_hi <= i_lo || j_hi <= j_lo) continue;
-            const float *h = hb + sp->off_a;
-            const int aw = ab.y - ab.x;
-            for (int j = j_lo; j < j_hi; ++j) {
-                const float fc = mag_coord(m, j, L.cv);
-                const float bc = floorf(fc);
-                const int c0 = (int)bc;
-                const float tc = fc - bc;
-                const float wc = (c == c0) ? 1.f - tc : ((c == c0 + 1) ? tc : 0.f);
-                if (wc == 0.f) continue;
-                for (int i = i_lo; i < i_hi; ++i) {
-                    const float fa = mag_coord(m, i, L.cu);
-                    const float ba = floorf(fa);
-                    const int a0 = (int)ba;
-                    const float ta = fa - ba;
-                    const float wa = (a == a0) ? 1.f - ta : ((a == a0 + 1) ? ta : 0.f);
-                    if (wa != 0.f) s = fmaf(wa * wc, h[(long long)(j - ab.z) * aw + (i - ab.x)], s);
+    for (int kc = ct.k0; kc < ct.k1; kc += kMagStage) {
+        const int kn = min(kMagStage, ct.k1 - kc);
+        __syncthreads();
+        for (int q = threadIdx.x; q < kn; q += blockDim.x) {
+            const SliceTab *sp = sl + kc + q;
+            MagSlice e;
+            e.m = sp->m;
+            e.ai0 = sp->ai0; e.ai1 = sp->ai1; e.aj0 = sp->aj0; e.aj1 = sp->aj1;
+            e.pad = 0;
+            e.off_a = sp->off_a;
+            s_sl[q] = e;
+        }
+        __syncthreads();
+        for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n; t += gridDim.y * blockDim.x) {
+            const int a = ct.fa0 + t % Fa, c = ct.fc0 + t / Fa;   // consecutive threads: consecutive a
+            float s = 0.f;
+            for (int q = 0; q < kn; ++q) {
+                const MagSlice e = s_sl[q];
+                if (e.ai1 <= e.ai0 || e.aj1 <= e.aj0) continue;
+                int i_lo, i_hi, j_lo, j_hi;
+                mag_candidates(a, L.cu, e.m, e.ai0, e.ai1, i_lo, i_hi);
+                mag_candidates(c, L.cv, e.m, e.aj0, e.aj1, j_lo, j_hi);
+                if (i_hi <= i_lo || j_hi <= j_lo) continue;
+                const float *h = hb + e.off_a;
+                const int aw = e.ai1 - e.ai0;
+                for (int j = j_lo; j < j_hi; ++j) {
+                    const float fc = mag_coord(e.m, j, L.cv);
+                    const float bc = floorf(fc);
+                    const int c0 = (int)bc;
+                    const float tc = fc - bc;
+                    const float wc = (c == c0) ? 1.f - tc : ((c == c0 + 1) ? tc : 0.f);
+                    if (wc == 0.f) continue;
+                    float sr = 0.f;
+                    for (int i = i_lo; i < i_hi; ++i) {
+                        const float fa = mag_coord(e.m, i, L.cu);
+                        const float ba = floorf(fa);
+                        const int a0 = (int)ba;
+                        const float ta = fa - ba;
+                        const float wa = (a == a0) ? 1.f - ta : ((a == a0 + 1) ? ta : 0.f);
+                        if (wa != 0.f) sr = fmaf(wa, h[(long long)(j - e.aj0) * aw + (i - e.ai0)], sr);
+                    }
+                    s = fmaf(wc, sr, s);
                 }
             }
+            float *dstp = &gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)];
+            *dstp = (kc == ct.k0) ? s : *dstp + s;
         }
-        gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)] = s;
+    }
+    if (ct.k1 <= ct.k0) {
+        // no slice with work: the adjoint of the fluence map is zero
+        for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n; t += gridDim.y * blockDim.x) {
+            const int a = ct.fa0 + t % Fa, c = ct.fc0 + t / Fa;
+            gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)] = 0.f;
+        }
     }
 }
 
 cudaError_t launch_mag_T(const PlanDev &P, int b0, int nb, cudaStream_t s)
 {
-    dim3 grid(nb, 8);
+    dim3 grid(nb, 16);
     k_mag_T<<<grid, 256, 0, s>>>(P, b0);
     return cudaGetLastError();
 }

@@ -24,11 +24,17 @@ namespace pdrt {
 
 __host__ __device__ constexpr int conv_tile_width(int nq4) { return kConvCols + 4 * nq4; }
 
+// Output rows per warp: the forward (large halo output box, small input box)
+// keeps 32 rows per warp; the adjoint (small output box) uses 8 rows x 4
+// column blocks, which wastes fewer lanes on rows outside the box.
+constexpr int kFwdRowsPerWarp = 32;
+constexpr int kAdjRowsPerWarp = 8;
+
 __host__ __device__ inline int kstride_for(int nq4) { return 4 * ((nq4 & 1) ? nq4 : nq4 + 1); }
 
 template <int NQ4>
 __device__ __forceinline__ void conv_row(float (&acc)[kConvTJ], const float *__restrict__ seg,
-                                         const float *__restrict__ kr)
+                                         const float *__restrict__ kr, int c_lo, int c_hi)
 {
     float win[kConvTJ + 4];
 #pragma unroll
@@ -38,12 +44,14 @@ __device__ __forceinline__ void conv_row(float (&acc)[kConvTJ], const float *__r
     }
 #pragma unroll
     for (int c = 0; c < NQ4; ++c) {
-        const float4 w4 = *reinterpret_cast<const float4 *>(kr + 4 * c);
-        const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
+        if (c >= c_lo && c < c_hi) {   // warp-uniform: chunk touches non-zero input columns
+            const float4 w4 = *reinterpret_cast<const float4 *>(kr + 4 * c);
+            const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
+            for (int qq = 0; qq < 4; ++qq) {
 #pragma unroll
-            for (int t = 0; t < kConvTJ; ++t) acc[t] = fmaf(wq[qq], win[t + qq], acc[t]);
+                for (int t = 0; t < kConvTJ; ++t) acc[t] = fmaf(wq[qq], win[t + qq], acc[t]);
+            }
         }
         if (c + 1 < NQ4) {
 #pragma unroll
@@ -80,10 +88,15 @@ __device__ __forceinline__ float fluence_sample(const float *__restrict__ F, int
     return s;
 }
 
-template <int NQ4, bool ADJ>
+// G = output rows per warp (32, 16 or 8); a warp's lanes cover G rows x 32/G
+// blocks of 16 columns, the CTA's 4 warps tile 32 rows x 64 columns.
+template <int NQ4, bool ADJ, int G>
 __global__ void __launch_bounds__(kConvThreads) k_conv(PlanDev P, int b0, int nb,
                                                        unsigned int *__restrict__ counter)
 {
+    static_assert(G == 8 || G == 16 || G == 32, "rows per warp");
+    constexpr int NB = 32 / G;                 // column blocks per warp
+    constexpr int WPR = 32 / G;                // warps stacked along rows
     extern __shared__ float4 smem4[];
     float *smem = reinterpret_cast<float *>(smem4);
     constexpr int W = conv_tile_width(NQ4);
@@ -143,6 +156,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(PlanDev P, int b0, int nb
         const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
         const int h_w = st.oi1 - st.oi0;
 
+        const int rsub = warp % WPR, csub = warp / WPR;
+        const int lr = lane % G, lg = lane / G;
         for (int unit = 0; unit < n_ug * n_vg; ++unit) {
             const int ug = unit / n_vg, vg = unit - ug * n_vg;
             const int ibase = out_i0 + kConvRows * ug;
@@ -151,41 +166,64 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(PlanDev P, int b0, int nb
             const int r1 = min(ibase + kConvRows + R, in_i1);
             const int cbase = jbase - R;
             __syncthreads();   // previous unit finished reading the tile; krow written
-            for (int idx = threadIdx.x; idx < (r1 - r0) * W; idx += blockDim.x) {
-                const int rr = idx / W, cc = idx - rr * W;
-                const int u = r0 + rr, jj = cbase + cc;
-                float v = 0.f;
-                if (jj >= in_j0 && jj < in_j1) {
-                    if (ADJ) {
-                        v = hsrc[(long long)(jj - st.oj0) * h_w + (u - st.oi0)];
-                    } else {
+            if (ADJ) {
+                // rows fastest: coalesced reads of the [j][i] input box
+                const int nr = r1 - r0;
+                for (int idx = threadIdx.x; idx < nr * W; idx += blockDim.x) {
+                    const int cc = idx / nr, rr = idx - cc * nr;
+                    const int u = r0 + rr, jj = cbase + cc;
+                    float v = 0.f;
+                    if (jj >= in_j0 && jj < in_j1) v = hsrc[(long long)(jj - st.oj0) * h_w + (u - st.oi0)];
+                    tile[rr * W + cc] = v;
+                }
+            } else {
+                for (int idx = threadIdx.x; idx < (r1 - r0) * W; idx += blockDim.x) {
+                    const int rr = idx / W, cc = idx - rr * W;
+                    const int u = r0 + rr, jj = cbase + cc;
+                    float v = 0.f;
+                    if (jj >= in_j0 && jj < in_j1)
                         v = fluence_sample(fmap, fa0, fa1, fc0, fc1, mag_coord(st.m, u, L.cu),
                                            mag_coord(st.m, jj, L.cv));
-                    }
+                    tile[idx] = v;
                 }
-                tile[idx] = v;
             }
             __syncthreads();
 
+            // this warp: rows [wi0, wi0 + G), column blocks [cb0, cb0 + NB)
+            const int wi0 = ibase + rsub * G;
+            const int wi_last = min(wi0 + G, out_i1) - 1;
+            const int cb0 = csub * NB;
+            const int wj0 = jbase + kConvTJ * cb0;
+            const int wj_end = min(jbase + kConvTJ * (cb0 + NB), out_j1);
+            if (wi_last < wi0 || wj0 >= out_j1) continue;   // warp-uniform
+            // input rows within R of the warp's rows
+            const int ur0 = max(r0, wi0 - R), ur1 = min(r1, wi_last + R + 1);
+            // 4-tap chunks that touch non-zero input columns for some block of the
+            // warp: chunk c of the block starting at column jw reads input columns
+            // jw - R + [4c, 4c + TJ + 3); the union over the warp's blocks takes its
+            // lower bound from the last block and its upper bound from the first.
+            const int wj_last = wj0 + kConvTJ * (NB - 1);
+            const int lo_num = in_j0 - wj_last + R - (kConvTJ + 2);   // need 4c >= lo_num
+            const int hi_num = in_j1 - 1 - wj0 + R;                    // need 4c <= hi_num
+            const int c_lo = lo_num > 0 ? (lo_num + 3) / 4 : 0;
+            const int c_hi = hi_num >= 0 ? min(NQ4, hi_num / 4 + 1) : 0;
             float acc[kConvTJ];
 #pragma unroll
             for (int t = 0; t < kConvTJ; ++t) acc[t] = 0.f;
-            const int i = ibase + lane;
-            const int jw0 = jbase + kConvTJ * warp;
-            if (jw0 < out_j1) {
-                const float *segbase = tile + kConvTJ * warp;
-                for (int u = r0; u < r1; ++u) {
-                    int row = abs(i - u);
-                    row = row > R ? R + 1 : row;
-                    conv_row<NQ4>(acc, segbase + (u - r0) * W, krow + row * S);
-                }
-                if (i < out_i1) {
-                    float *o = dst + (i - out_i0);
+            const int i = wi0 + lr;
+            const int jw0 = wj0 + kConvTJ * lg;
+            const float *segbase = tile + (jw0 - jbase);
+            for (int u = ur0; c_lo < c_hi && u < ur1; ++u) {
+                int row = abs(i - u);
+                row = row > R ? R + 1 : row;
+                conv_row<NQ4>(acc, segbase + (u - r0) * W, krow + row * S, c_lo, c_hi);
+            }
+            if (i < out_i1 && jw0 < wj_end) {
+                float *o = dst + (i - out_i0);
 #pragma unroll
-                    for (int t = 0; t < kConvTJ; ++t) {
-                        const int j = jw0 + t;
-                        if (j < out_j1) o[(long long)(j - out_j0) * out_w] = acc[t] * scale;
-                    }
+                for (int t = 0; t < kConvTJ; ++t) {
+                    const int j = jw0 + t;
+                    if (j < out_j1) o[(long long)(j - out_j0) * out_w] = acc[t] * scale;
                 }
             }
         }
@@ -217,7 +255,8 @@ template <int NQ4, bool ADJ>
 static cudaError_t launch_one(const PlanDev &P, int b0, int nb, unsigned int *counter, int blocks,
                               cudaStream_t s)
 {
-    k_conv<NQ4, ADJ><<<blocks, kConvThreads, conv_smem_bytes(P.mach), s>>>(P, b0, nb, counter);
+    k_conv<NQ4, ADJ, ADJ ? kAdjRowsPerWarp : kFwdRowsPerWarp>
+        <<<blocks, kConvThreads, conv_smem_bytes(P.mach), s>>>(P, b0, nb, counter);
     return cudaGetLastError();
 }
 
@@ -239,11 +278,10 @@ cudaError_t launch_conv(const PlanDev &P, int b0, int nb, bool adjoint, unsigned
 template <int NQ4, bool ADJ>
 static cudaError_t prepare_one(int smem, int *blocks_per_sm)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_conv<NQ4, ADJ>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = k_conv<NQ4, ADJ, ADJ ? kAdjRowsPerWarp : kFwdRowsPerWarp>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_conv<NQ4, ADJ>,
-                                                         kConvThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, kConvThreads, smem);
 }
 
 // Sets the dynamic shared-memory limit of the instantiation a machine model

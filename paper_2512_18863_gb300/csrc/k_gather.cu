@@ -35,50 +35,71 @@ __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float
     const bool inside = ix < P.nx && iy < P.ny;
     const float bx0 = (float)(blockIdx.x * 32), bx1 = (float)min((int)blockIdx.x * 32 + 31, P.nx - 1);
     const float by0 = (float)(blockIdx.y * 8), by1 = (float)min((int)blockIdx.y * 8 + 7, P.ny - 1);
-    float acc = 0.f;
-    for (int bl = 0; bl < nb; ++bl) {
-        const int b = b0 + bl;
+    __shared__ int s_list[kMaxCpPerChunk];
+    __shared__ int s_wcnt[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // 1) one thread per control point of the chunk tests whether its footprint
+    //    (union of output boxes; fu, fw are affine in (ix, iy)) meets this CTA
+    bool hit = false;
+    if ((int)threadIdx.x < nb) {
+        const int b = b0 + threadIdx.x;
         const CpTab &ct = P.cptab[b];
-        if (iz < ct.vj0 || iz >= ct.vj1) continue;
-        const CpGeo g = P.cpgeo[b];
-        // footprint test of the CTA: fu, fw are affine in (ix, iy)
-        const float u00 = fmaf(g.au, bx0, fmaf(g.bu, by0, g.cu0));
-        const float u10 = fmaf(g.au, bx1, fmaf(g.bu, by0, g.cu0));
-        const float u01 = fmaf(g.au, bx0, fmaf(g.bu, by1, g.cu0));
-        const float u11 = fmaf(g.au, bx1, fmaf(g.bu, by1, g.cu0));
-        const float umin = fminf(fminf(u00, u10), fminf(u01, u11));
-        const float umax = fmaxf(fmaxf(u00, u10), fmaxf(u01, u11));
-        if (umax < (float)ct.ui0 - 1.f || umin > (float)ct.ui1) continue;
-        const float w00 = fmaf(g.aw, bx0, fmaf(g.bw, by0, g.cw0));
-        const float w10 = fmaf(g.aw, bx1, fmaf(g.bw, by0, g.cw0));
-        const float w01 = fmaf(g.aw, bx0, fmaf(g.bw, by1, g.cw0));
-        const float w11 = fmaf(g.aw, bx1, fmaf(g.bw, by1, g.cw0));
-        const float wmin = fminf(fminf(w00, w10), fminf(w01, w11));
-        const float wmax = fmaxf(fmaxf(w00, w10), fmaxf(w01, w11));
-        if (wmax < (float)ct.k0 - 1.f || wmin > (float)ct.k1) continue;
-        if (!inside) continue;
-        float fu, fw;
-        voxel_to_beam(g, ix, iy, fu, fw);
-        const float bu = floorf(fu), bw = floorf(fw);
-        const int i0 = (int)bu, k0 = (int)bw;
-        const float tu = fu - bu, tw = fw - bw;
-        const float *base = P.region + (long long)bl * P.cap_o;
-        float val = 0.f;
-#pragma unroll
-        for (int dk = 0; dk < 2; ++dk) {
-            const int k = k0 + dk;
-            if (k < 0 || k >= L.nw) continue;
-            const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
-            const int4 ob = __ldg(reinterpret_cast<const int4 *>(&sp->oi0));
-            if (iz < ob.z || iz >= ob.w) continue;
-            const long long off = __ldg(&sp->off_o);
-            const float v0 = region_value(base, ob, off, i0, iz);
-            const float v1 = region_value(base, ob, off, i0 + 1, iz);
-            val += (dk ? tw : 1.f - tw) * ((1.f - tu) * v0 + tu * v1);
+        if (iz >= ct.vj0 && iz < ct.vj1) {
+            const CpGeo g = P.cpgeo[b];
+            const float u00 = fmaf(g.au, bx0, fmaf(g.bu, by0, g.cu0));
+            const float u10 = fmaf(g.au, bx1, fmaf(g.bu, by0, g.cu0));
+            const float u01 = fmaf(g.au, bx0, fmaf(g.bu, by1, g.cu0));
+            const float u11 = fmaf(g.au, bx1, fmaf(g.bu, by1, g.cu0));
+            const float w00 = fmaf(g.aw, bx0, fmaf(g.bw, by0, g.cw0));
+            const float w10 = fmaf(g.aw, bx1, fmaf(g.bw, by0, g.cw0));
+            const float w01 = fmaf(g.aw, bx0, fmaf(g.bw, by1, g.cw0));
+            const float w11 = fmaf(g.aw, bx1, fmaf(g.bw, by1, g.cw0));
+            const float umin = fminf(fminf(u00, u10), fminf(u01, u11));
+            const float umax = fmaxf(fmaxf(u00, u10), fmaxf(u01, u11));
+            const float wmin = fminf(fminf(w00, w10), fminf(w01, w11));
+            const float wmax = fmaxf(fmaxf(w00, w10), fmaxf(w01, w11));
+            hit = !(umax < (float)ct.ui0 - 1.f || umin > (float)ct.ui1 ||
+                    wmax < (float)ct.k0 - 1.f || wmin > (float)ct.k1);
         }
-        acc = fmaf(ct.cal_mu, val, acc);
     }
+    // 2) ordered compaction (keeps the CP order of the sum fixed)
+    const unsigned m = __ballot_sync(0xffffffffu, hit);
+    if (lane == 0) s_wcnt[wid] = __popc(m);
+    __syncthreads();
+    int off = 0, total = 0;
+    for (int w = 0; w < 8; ++w) {
+        off += (w < wid) ? s_wcnt[w] : 0;
+        total += s_wcnt[w];
+    }
+    if (hit) s_list[off + __popc(m & ((1u << lane) - 1u))] = threadIdx.x;
+    __syncthreads();
+    // 3) every voxel samples the listed control points in order
+    float acc = 0.f;
     if (inside) {
+        for (int n = 0; n < total; ++n) {
+            const int bl = s_list[n], b = b0 + bl;
+            const CpGeo &g = P.cpgeo[b];
+            float fu, fw;
+            voxel_to_beam(g, ix, iy, fu, fw);
+            const float bu = floorf(fu), bw = floorf(fw);
+            const int i0 = (int)bu, k0 = (int)bw;
+            const float tu = fu - bu, tw = fw - bw;
+            const float *base = P.region + (long long)bl * P.cap_o;
+            float val = 0.f;
+#pragma unroll
+            for (int dk = 0; dk < 2; ++dk) {
+                const int k = k0 + dk;
+                if (k < 0 || k >= L.nw) continue;
+                const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
+                const int4 ob = __ldg(reinterpret_cast<const int4 *>(&sp->oi0));
+                if (iz < ob.z || iz >= ob.w || i0 + 1 < ob.x || i0 >= ob.y) continue;
+                const long long o = __ldg(&sp->off_o);
+                const float v0 = region_value(base, ob, o, i0, iz);
+                const float v1 = region_value(base, ob, o, i0 + 1, iz);
+                val += (dk ? tw : 1.f - tw) * ((1.f - tu) * v0 + tu * v1);
+            }
+            acc = fmaf(P.cptab[b].cal_mu, val, acc);
+        }
         const long long idx = ((long long)iz * P.ny + iy) * P.nx + ix;
         dose[idx] = first ? acc : dose[idx] + acc;
     }
@@ -89,6 +110,20 @@ cudaError_t launch_gather(const PlanDev &P, int b0, int nb, float *dose, bool fi
     dim3 grid((P.nx + 31) / 32, (P.ny + 7) / 8, P.nz);
     k_gather<<<grid, 256, 0, s>>>(P, b0, nb, dose, first ? 1 : 0);
     return cudaGetLastError();
+}
+
+// Interval of d = ix - fx with |a d + b dy| < 1, intersected into [lo, hi]
+// (widened by a small margin; the exact weights decide membership).
+__device__ __forceinline__ void clip_band(float a, float bdy, float &lo, float &hi)
+{
+    if (fabsf(a) < 1e-3f) {
+        if (fabsf(bdy) >= 1.f + 1e-3f) hi = lo - 1.f;   // empty
+        return;
+    }
+    const float inv = 1.f / a;
+    const float e0 = (-1.f - bdy) * inv, e1 = (1.f - bdy) * inv;
+    lo = fmaxf(lo, fminf(e0, e1) - 1e-3f);
+    hi = fminf(hi, fmaxf(e0, e1) + 1e-3f);
 }
 
 __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
@@ -108,11 +143,17 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
         // voxel-index position of lattice point (i, k): rotation transpose
         const float fx = fmaf(di, g.au, fmaf(dk, g.aw, g.px0));
         const float fy = fmaf(di, g.bu, fmaf(dk, g.bw, g.py0));
-        const int x0 = max((int)ceilf(fx - 1.45f), 0), x1 = min((int)floorf(fx + 1.45f), P.nx - 1);
         const int y0 = max((int)ceilf(fy - 1.45f), 0), y1 = min((int)floorf(fy + 1.45f), P.ny - 1);
         const float *gp = gd + (long long)j * P.ny * P.nx;
         float s = 0.f;
         for (int iy = y0; iy <= y1; ++iy) {
+            // voxels of this row whose beam coordinates are within one lattice
+            // step of (i, k) in both u and w
+            const float dy = (float)iy - fy;
+            float lo = -1.45f, hi = 1.45f;
+            clip_band(g.au, g.bu * dy, lo, hi);
+            clip_band(g.aw, g.bw * dy, lo, hi);
+            const int x0 = max((int)ceilf(fx + lo), 0), x1 = min((int)floorf(fx + hi), P.nx - 1);
             for (int ix = x0; ix <= x1; ++ix) {
                 float fu, fw;
                 voxel_to_beam(g, ix, iy, fu, fw);
