@@ -55,6 +55,14 @@ def _args():
     return ap.parse_args()
 
 
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -260,12 +268,23 @@ def _gpu(args):
     arcs_per_step = w.plan.n_cp / CP_PER_ARC
     value = arcs_per_step * args.steps * world / (ms_max / 1e3)
 
-    # roofline of the dominant kernel: the direct FP32 convolution (forward and adjoint)
-    conv_ms = prof["conv_forward"]["total_ms"] + prof["conv_adjoint"]["total_ms"]
-    conv_launches = prof["conv_forward"]["launches"] + prof["conv_adjoint"]["launches"]
+    # roofline of the dominant kernel: the per-slice convolution (forward and
+    # adjoint), on the tensor cores where its tiles fit, else FP32 SIMT
+    conv_keys = ("conv_forward", "conv_adjoint", "conv_forward_tc", "conv_adjoint_tc")
+    conv_ms = sum(prof[k]["total_ms"] for k in conv_keys if k in prof)
+    conv_launches = sum(prof[k]["launches"] for k in conv_keys if k in prof)
+    tc_ms = sum(prof[k]["total_ms"] for k in ("conv_forward_tc", "conv_adjoint_tc") if k in prof)
     flops_total = 2.0 * work["conv_flops"] * args.steps          # two convolution passes per step
     achieved = flops_total / (conv_ms / 1e3) / 1e12
-    peak = SMS * FP32_LANES * 2 * 2070.0e6 / 1e12
+    peaks = _measured_peaks()
+    if tc_ms > 0.5 * conv_ms:
+        bound, peak = "tensor", peaks.get("bf16_tflops", 1900.0)
+        peak_src = ("measured bf16 dense burst (MEASURED_PEAKS.json)" if "bf16_tflops" in peaks
+                    else "fallback 1.9 PFLOP/s bf16")
+    else:
+        bound, peak = "alu", SMS * FP32_LANES * 2 * 2070.0e6 / 1e12
+        peak_src = "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
+    mma_flops = work.get("mma_flops", 0.0) * args.steps          # tensor FLOPs issued in the timed steps
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps}
                for k, v in prof.items() if not k.startswith("_") and v["launches"]}
 
@@ -321,12 +340,14 @@ def _gpu(args):
                           "step": "forward + adjoint of all control points",
                           "l2": "flushed between steps (256 MB write)",
                           "parallelism": "replicas" if world > 1 else "single"},
-               "roofline": {"bound": "alu", "kernel": "conv_forward+conv_adjoint",
+               "roofline": {"bound": bound, "kernel": "convolution (forward + adjoint)",
                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak, "traffic": None,
-                            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                            "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                            "flops": "algorithmic: 2 (2R+1)^2 per fluence-support point per pass",
                             "flops_per_launch": flops_total / max(conv_launches, 1),
-                            "ms_per_launch": conv_ms / max(conv_launches, 1)},
+                            "ms_per_launch": conv_ms / max(conv_launches, 1),
+                            "fp32_alu_frac": achieved / (SMS * FP32_LANES * 2 * 2070.0e6 / 1e12),
+                            "tensor_issued_tflops": (mma_flops / (tc_ms / 1e3) / 1e12) if tc_ms else None},
                "kernels": kernels, "work": work, "gpu_launches": launches,
                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)

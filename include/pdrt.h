@@ -71,6 +71,8 @@ typedef enum {
 #define PDRT_FLAG_NAN_INPUT 1u     /* a leaf, jaw or MU value was NaN/inf */
 #define PDRT_FLAG_CAPACITY 2u      /* internal: a slice's work exceeded the plan's scratch
                                       bound and was dropped (dose incomplete) */
+#define PDRT_FLAG_TIMEOUT 4u       /* a bounded wait on the tensor cores expired; the
+                                      kernel stopped early (result incomplete) */
 
 /*
  * Beam model (machine) constants, Sec. 2.2 and Sec. 2.4.
@@ -120,6 +122,7 @@ typedef struct {
     int32_t n_cp;
     int32_t chunk_cp;            /* control points processed per pass */
     size_t scratch_bytes;        /* device scratch owned by the plan */
+    int32_t tensor_cores;        /* 1: convolution tiles that fit run on the tensor cores */
 } pdrt_plan_info;
 
 /* Work counters of the last forward/backward call (for roofline accounting). */
@@ -129,10 +132,12 @@ typedef struct {
     int64_t region_points;       /* beam-frame points where dose is produced */
     int64_t taps;                /* (2R+1)^2 */
     double conv_flops;           /* 2 * taps * support_points: one convolution pass */
+    double mma_flops;            /* tensor-core FLOPs issued by one forward + one adjoint
+                                    convolution pass (BF16 three-term split, padded tiles) */
 } pdrt_work;
 
 /* Per-kernel device time accumulated while profiling is enabled. */
-#define PDRT_NUM_KERNELS 8
+#define PDRT_NUM_KERNELS 10
 typedef struct {
     const char *name[PDRT_NUM_KERNELS];
     int64_t launches[PDRT_NUM_KERNELS];
@@ -202,6 +207,14 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
                                const float *jaws_dev, const float *mu_dev,
                                const float *dose_grad_dev, float *dleaves_dev, float *djaws_dev,
                                float *dmu_dev, pdrt_stream_t stream);
+
+/*
+ * Route the per-slice convolution (Sec. 2.2.6) to the tensor cores (enable = 1,
+ * the default when the kernel radius allows it: BF16 three-term split, FP32
+ * accumulation) or to the FP32 SIMT kernel only (enable = 0).  Host only.
+ * Errors: EINVAL if enable = 1 and the radius is too large for the tensor tiles.
+ */
+pdrt_status pdrt_plan_set_tensor_cores(pdrt_plan_t p, int32_t enable);
 
 /* Lattice and scratch sizes of a plan (host only, no device work). */
 pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out);

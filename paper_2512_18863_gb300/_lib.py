@@ -17,9 +17,10 @@ MAX_PAIRS = 160
 MAX_RADIUS_PX = 44
 MAX_DEPTH_TABLE = 4096
 MAX_HU_POINTS = 32
-NUM_KERNELS = 8
+NUM_KERNELS = 10
 FLAG_NAN_INPUT = 1
 FLAG_CAPACITY = 2
+FLAG_TIMEOUT = 4
 
 STATUS = {0: "PDRT_OK", 1: "PDRT_EINVAL", 2: "PDRT_ESHAPE", 3: "PDRT_ECUDA", 4: "PDRT_ENOMEM",
           5: "PDRT_EDEVICE"}
@@ -45,12 +46,14 @@ class pdrt_machine(C.Structure):
 class pdrt_plan_info(C.Structure):
     _fields_ = [("nu", C.c_int32), ("nv", C.c_int32), ("nw", C.c_int32),
                 ("cu", C.c_double), ("cv", C.c_double), ("cw", C.c_double),
-                ("n_cp", C.c_int32), ("chunk_cp", C.c_int32), ("scratch_bytes", C.c_size_t)]
+                ("n_cp", C.c_int32), ("chunk_cp", C.c_int32), ("scratch_bytes", C.c_size_t),
+                ("tensor_cores", C.c_int32)]
 
 
 class pdrt_work(C.Structure):
     _fields_ = [("active_slices", C.c_int64), ("support_points", C.c_int64),
-                ("region_points", C.c_int64), ("taps", C.c_int64), ("conv_flops", C.c_double)]
+                ("region_points", C.c_int64), ("taps", C.c_int64), ("conv_flops", C.c_double),
+                ("mma_flops", C.c_double)]
 
 
 class pdrt_profile(C.Structure):
@@ -70,6 +73,7 @@ _SIG = {
     "pdrt_dose_forward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "pdrt_dose_backward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "pdrt_plan_get_info": (C.c_int, [_VP, C.POINTER(pdrt_plan_info)]),
+    "pdrt_plan_set_tensor_cores": (C.c_int, [_VP, C.c_int32]),
     "pdrt_plan_status": (C.c_int, [_VP, _VP, C.POINTER(C.c_uint32)]),
     "pdrt_plan_work": (C.c_int, [_VP, _VP, C.POINTER(pdrt_work)]),
     "pdrt_profile_enable": (C.c_int, [_VP, C.c_int32]),
@@ -160,6 +164,10 @@ def pdrt_dose_backward(grid, plan, leaves_ptr, jaws_ptr, mu_ptr, dose_grad_ptr, 
     _check(load().pdrt_dose_backward(_VP(grid), _VP(plan), _VP(leaves_ptr), _VP(jaws_ptr),
                                      _VP(mu_ptr), _VP(dose_grad_ptr), _VP(dleaves_ptr),
                                      _VP(djaws_ptr), _VP(dmu_ptr), _VP(stream)))
+
+
+def pdrt_plan_set_tensor_cores(plan, enable):
+    _check(load().pdrt_plan_set_tensor_cores(_VP(plan), 1 if enable else 0))
 
 
 def pdrt_plan_get_info(plan) -> dict:

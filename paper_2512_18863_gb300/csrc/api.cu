@@ -65,6 +65,7 @@ struct pdrt_plan_s {
     int n_cp;
     int chunk;
     int conv_blocks_fwd, conv_blocks_adj;
+    int tc_blocks;            // persistent grid of k_conv_tc (0: path unavailable)
     PlanDev dev;
     size_t scratch_bytes;
     std::vector<void *> allocs;
@@ -78,7 +79,8 @@ struct pdrt_plan_s {
 
 static const char *kKernelNames[PDRT_NUM_KERNELS] = {
     "hu_to_red", "project_raster", "wepl_tables", "conv_forward",
-    "gather_accumulate", "gather_transpose", "conv_adjoint", "mag_transpose_param_grad"};
+    "gather_accumulate", "gather_transpose", "conv_adjoint", "mag_transpose_param_grad",
+    "conv_forward_tc", "conv_adjoint_tc"};
 
 namespace {
 
@@ -343,6 +345,12 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
         G.sx_w = (float)sn;
         G.sy_w = (float)cs;
         G.px0 = (float)px0; G.py0 = (float)py0; G.pz0 = (float)pz0;
+        // a coefficient near 0 leaves dx unbounded by that band (+-3 exceeds the
+        // +-1.45 candidate window); the exact weights still decide membership
+        G.iu = fabs(au) > 1e-3 ? (float)(1.0 / fabs(au)) : 3.f;
+        G.ru = fabs(au) > 1e-3 ? (float)(bu / au) : 0.f;
+        G.iw = fabs(aw) > 1e-3 ? (float)(1.0 / fabs(aw)) : 3.f;
+        G.rw = fabs(aw) > 1e-3 ? (float)(bw / aw) : 0.f;
         double fu[4], fw[4];
         const int cxs[4] = {0, g->nx - 1, g->nx - 1, 0}, cys[4] = {0, 0, g->ny - 1, g->ny - 1};
         for (int c = 0; c < 4; ++c) {
@@ -409,7 +417,7 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     PLAN_TRY(dalloc(p, &P.region, (size_t)chunk * cap_o), "cudaMalloc(beam-frame region)");
     PLAN_TRY(dalloc(p, &P.adjbuf, (size_t)chunk * cap_a), "cudaMalloc(adjoint region)");
     PLAN_TRY(dalloc(p, &P.flags, 1), "cudaMalloc(flags)");
-    PLAN_TRY(dalloc(p, &P.counters, 2 * ((n_cp + chunk - 1) / chunk) + 2), "cudaMalloc(counters)");
+    PLAN_TRY(dalloc(p, &P.counters, 4 * ((n_cp + chunk - 1) / chunk) + 2), "cudaMalloc(counters)");
     P.leaf_bounds = lb;
     P.depth_dose = dd;
     P.cpgeo = dgeo;
@@ -435,6 +443,17 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     PLAN_TRY(conv_prepare(M, &bf, &ba), "convolution kernel set-up");
     p->conv_blocks_fwd = std::max(1, bf) * g->sm_count;
     p->conv_blocks_adj = std::max(1, ba) * g->sm_count;
+    // tensor-core convolution when its tiles fit in shared memory
+    p->tc_blocks = 0;
+    P.tc_enabled = 0;
+    if (conv_tc_smem_bytes(M.R) <= 220 * 1024) {
+        int bt = 0;
+        PLAN_TRY(conv_tc_prepare(M.R, &bt), "tensor-core convolution set-up");
+        if (bt > 0) {
+            p->tc_blocks = bt * g->sm_count;
+            P.tc_enabled = 1;
+        }
+    }
 #undef PLAN_TRY
     *out = p;
     return PDRT_OK;
@@ -465,9 +484,16 @@ pdrt_status pdrt_dose_forward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_
            "project_raster launch");
     CU_TRY(timed(p, K_TABLES, s, [&] { return launch_tables(P, s); }), "wepl_tables launch");
     const int n_chunks = (p->n_cp + p->chunk - 1) / p->chunk;
-    CU_TRY(cudaMemsetAsync(P.counters, 0, sizeof(unsigned) * n_chunks, s), "clear counters");
+    CU_TRY(cudaMemsetAsync(P.counters, 0, sizeof(unsigned) * 4 * n_chunks, s), "clear counters");
     for (int c = 0; c < n_chunks; ++c) {
         const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
+        if (P.tc_enabled)
+            CU_TRY(timed(p, K_CONV_TC_FWD, s,
+                         [&] {
+                             return launch_conv_tc(P, b0, nb, false, P.counters + 2 * n_chunks + c,
+                                                   p->tc_blocks, s);
+                         }),
+                   "conv_forward_tc launch");
         CU_TRY(timed(p, K_CONV_FWD, s,
                      [&] { return launch_conv(P, b0, nb, false, P.counters + c, p->conv_blocks_fwd, s); }),
                "conv_forward launch");
@@ -494,11 +520,18 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
     CU_TRY(timed(p, K_TABLES, s, [&] { return launch_tables(P, s); }), "wepl_tables launch");
     const int n_chunks = (p->n_cp + p->chunk - 1) / p->chunk;
     unsigned int *ctr = P.counters + n_chunks;
-    CU_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned) * n_chunks, s), "clear counters");
+    CU_TRY(cudaMemsetAsync(P.counters, 0, sizeof(unsigned) * 4 * n_chunks, s), "clear counters");
     for (int c = 0; c < n_chunks; ++c) {
         const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
         CU_TRY(timed(p, K_GATHER_T, s, [&] { return launch_gather_T(P, b0, nb, dose_grad_dev, s); }),
                "gather_transpose launch");
+        if (P.tc_enabled)
+            CU_TRY(timed(p, K_CONV_TC_ADJ, s,
+                         [&] {
+                             return launch_conv_tc(P, b0, nb, true, P.counters + 3 * n_chunks + c,
+                                                   p->tc_blocks, s);
+                         }),
+                   "conv_adjoint_tc launch");
         CU_TRY(timed(p, K_CONV_ADJ, s,
                      [&] { return launch_conv(P, b0, nb, true, ctr + c, p->conv_blocks_adj, s); }),
                "conv_adjoint launch");
@@ -514,6 +547,16 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
     return PDRT_OK;
 }
 
+pdrt_status pdrt_plan_set_tensor_cores(pdrt_plan_t p, int32_t enable)
+{
+    g_last_error.clear();
+    if (!p) return fail(PDRT_EINVAL, "NULL plan");
+    if (enable && p->tc_blocks <= 0)
+        return fail(PDRT_EINVAL, "the tensor-core convolution does not fit this kernel radius");
+    p->dev.tc_enabled = enable ? 1 : 0;
+    return PDRT_OK;
+}
+
 pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out)
 {
     g_last_error.clear();
@@ -524,6 +567,7 @@ pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out)
     out->n_cp = p->n_cp;
     out->chunk_cp = p->chunk;
     out->scratch_bytes = p->scratch_bytes;
+    out->tensor_cores = p->dev.tc_enabled;
     return PDRT_OK;
 }
 
@@ -557,6 +601,31 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
     const long long n = 2LL * p->dev.mach.R + 1;
     out->taps = n * n;
     out->conv_flops = 2.0 * (double)out->taps * (double)out->support_points;
+    out->mma_flops = 0.0;
+    if (p->dev.tc_enabled) {
+        // replay the tensor-core tile sizes (same rules as tc_boxes / tc_takes_slice)
+        const Lattice &L = p->dev.lat;
+        const int R = p->dev.mach.R;
+        std::vector<SliceTab> sl((size_t)p->n_cp * L.nw);
+        CU_TRY(cudaMemcpy(sl.data(), p->dev.slices, sizeof(SliceTab) * sl.size(), cudaMemcpyDeviceToHost),
+               "read slice tables");
+        for (const SliceTab &st : sl) {
+            for (int adj = 0; adj < 2; ++adj) {
+                const int ii0 = adj ? st.oi0 : st.pi0, ii1 = adj ? st.oi1 : st.pi1;
+                const int ij0 = adj ? st.oj0 : st.pj0, ij1 = adj ? st.oj1 : st.pj1;
+                const int oi0 = adj ? st.ai0 : st.oi0, oi1 = adj ? st.ai1 : st.oi1;
+                const int oj0 = adj ? st.aj0 : st.oj0, oj1 = adj ? st.aj1 : st.oj1;
+                (void)ii0; (void)ii1;
+                if (oi1 <= oi0 || oj1 <= oj0) continue;
+                const int nt = (oj1 - oj0 + 15) & ~15;
+                const int s0 = std::max(ij0, oj0 - R), s1 = std::min(ij1, oj0 + nt + R);
+                const int kt = ((s1 > s0 ? s1 - s0 : 0) + 15) & ~15;
+                if (nt < 16 || nt > kTcMaxN || kt < 16 || kt > kTcMaxK) continue;
+                const int mtiles = (oi1 - oi0 + 127) / 128;
+                out->mma_flops += (double)mtiles * (2 * R + 1) * (kt / 16) * 3 * 2.0 * 128 * nt * 16;
+            }
+        }
+    }
     return PDRT_OK;
 }
 

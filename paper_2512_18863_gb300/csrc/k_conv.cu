@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv(PlanDev P, int b0, int nb
         if (item >= n_items) break;
         const int bl = item / L.nw, k = item - bl * L.nw, b = b0 + bl;
         const SliceTab st = P.slices[(long long)b * L.nw + k];
+        if (tc_takes_slice(st, ADJ, R, P.tc_enabled)) continue;   // done on the tensor cores
         int in_i0, in_i1, in_j0, in_j1, out_i0, out_i1, out_j0, out_j1;
         float *dst;
         if (ADJ) {

@@ -1,0 +1,391 @@
+// Per-slice lateral convolution (Sec. 2.2.6) on the 5th-generation tensor
+// cores (tcgen05.mma, BF16 operands, FP32 accumulation in tensor memory).
+//
+// For one beam slice, out(i, j) = scale * sum_p sum_s in(i - p, s) K(|p|, j - s)
+// (forward: in = magnified fluence, out = D'; adjoint: in = gathered gradient,
+// out = h'; K is symmetric, so both are this sum).  Per kernel row p it is a
+// GEMM  D[m][n] += A_p[m][k] B_p[n][k]  with m = output row (M = 128 per
+// tile), n = output column (N <= 96), k = input column (K <= 96):
+//   * A_p[m][k] = in(i0 + m - p, s_k).  The input tile is stored K-major in
+//     8 x 16-byte core matrices with its rows 16 bytes apart, so the shift by
+//     p is just a descriptor start address (R - p rows further).
+//   * B_p[n][k] = K(|p|, j0 + n - s_k) is Toeplitz in (n, k).  With the K
+//     order reversed (s_k = s_end - 1 - k, applied to both operands, which
+//     leaves the sum unchanged) it becomes Hankel, h[n + k]; its core matrix
+//     (g, c) then depends only on g + c, so one 128-byte core matrix per
+//     diagonal is stored and the descriptor uses LBO = SBO = 128 bytes.
+// FP32 accuracy: each operand is split x = hi + lo into two BF16 values and
+// three products (hi.hi + hi.lo + lo.hi) are accumulated (relative error per
+// product <~ 3 * 2^-16).
+//
+// One CTA (8 warps) per slice, persistent over a work counter.  Thread 0
+// issues the MMAs; completion is signalled through an mbarrier
+// (tcgen05.commit); all waits are bounded and raise PDRT_FLAG_TIMEOUT.
+// Slices whose boxes exceed the tile limits are left to the FP32 SIMT kernel
+// (k_conv), which skips the slices this kernel takes (tc_takes_slice).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "pdrt_impl.cuh"
+
+namespace pdrt {
+
+namespace {
+
+constexpr int kTcM = 128;
+constexpr int kTcThreads = 256;      // 8 warps: two per tensor-memory lane quarter
+constexpr uint32_t kTmemCols = 128;   // >= kTcMaxN, power of two
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// tcgen05 shared-memory matrix descriptor, no swizzle, K-major core matrices
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version
+    return d;
+}
+
+// instruction descriptor: kind::f16, D = F32, A = B = BF16, both K-major
+__device__ __forceinline__ uint32_t instr_desc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(void *mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_try(void *mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+}  // namespace
+
+__host__ __device__ inline int tc_rows(int R) { return ((kTcM + 2 * R + 7) / 8) * 8; }
+
+int conv_tc_smem_bytes(int R)
+{
+    const int rows = tc_rows(R);
+    const int nd = kTcMaxN / 8 + kTcMaxK / 8 - 1;
+    const int a = 2 * rows * kTcMaxK * 2;           // hi + lo, bf16
+    const int bsz = (R + 1) * 2 * nd * 128;         // hi + lo Hankel core matrices per |p|
+    const int krow = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
+    return 128 + krow + a + bsz;
+}
+
+template <bool ADJ>
+__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, int nb,
+                                                    unsigned int *__restrict__ counter)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Lattice &L = P.lat;
+    const int R = P.mach.R;
+    const int rows = tc_rows(R);
+    const int nd_max = kTcMaxN / 8 + kTcMaxK / 8 - 1;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 8);
+    int *s_item = reinterpret_cast<int *>(smem + 16);
+    float *krow = reinterpret_cast<float *>(smem + 128);
+    const int krow_bytes = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
+    unsigned char *abase = smem + 128 + krow_bytes;             // [2][kt/8][rows][16 B]
+    unsigned char *bbase = abase + 2 * rows * kTcMaxK * 2;      // [R+1][2][nd][128 B]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_items = nb * L.nw;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(s_tmem)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *s_tmem;
+    uint32_t phase = 0;
+    bool timed_out = false;
+
+    while (!timed_out) {
+        if (tid == 0) *s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();
+        if (item >= n_items) break;
+        const int bl = item / L.nw, k = item - bl * L.nw, b = b0 + bl;
+        const SliceTab st = P.slices[(long long)b * L.nw + k];
+        if (!tc_takes_slice(st, ADJ, R, 1)) continue;
+        const TcBoxes bx = tc_boxes(st, ADJ, R);
+        const int kt = bx.kt, nt = bx.nt, nd = nt / 8 + kt / 8 - 1;
+        const int s_end = bx.s0 + kt;
+        const int out_w = bx.out_i1 - bx.out_i0;
+        float *dst = ADJ ? P.adjbuf + (long long)bl * P.cap_a + st.off_a
+                         : P.region + (long long)bl * P.cap_o + st.off_o;
+        const float scale = st.tdd * st.c2;
+
+        // kernel rows K(|p|, q), q in [-R, R]
+        for (int idx = tid; idx < (R + 1) * (2 * R + 1); idx += blockDim.x) {
+            const int p = idx / (2 * R + 1), q = idx - p * (2 * R + 1) - R;
+            const float pu = p * L.du, qv = q * L.dv;
+            const float r = sqrtf(pu * pu + qv * qv);
+            krow[idx] = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
+                        st.wn[2] * expf(-st.a[2] * r);
+        }
+        __syncthreads();
+        // Hankel core matrices: for |p| and diagonal d, element (r, t) = K(|p|, 8d + r + t + c0),
+        // c0 = j0 - s_end + 1 (zero outside |q| <= R)
+        const int c0 = bx.out_j0 - s_end + 1;
+        for (int idx = tid; idx < (R + 1) * nd * 8; idx += blockDim.x) {
+            const int p = idx / (nd * 8), rem = idx - p * nd * 8, d = rem >> 3, r = rem & 7;
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int t = 0; t < 8; t += 2) {
+                __nv_bfloat16 h0, l0, h1, l1;
+                const int q0 = 8 * d + r + t + c0, q1 = q0 + 1;
+                const float v0 = (q0 >= -R && q0 <= R) ? krow[p * (2 * R + 1) + q0 + R] : 0.f;
+                const float v1 = (q1 >= -R && q1 <= R) ? krow[p * (2 * R + 1) + q1 + R] : 0.f;
+                split_bf16(v0, h0, l0);
+                split_bf16(v1, h1, l1);
+                hw[t >> 1] = pack2(h0, h1);
+                lw[t >> 1] = pack2(l0, l1);
+            }
+            unsigned char *bp = bbase + ((size_t)p * 2 * nd_max) * 128 + (size_t)d * 128 + r * 16;
+            *reinterpret_cast<uint4 *>(bp) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4 *>(bp + (size_t)nd_max * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+        const uint32_t idesc = instr_desc(kTcM, nt);
+        const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
+        const int fa0 = P.cptab[b].fa0, fa1 = P.cptab[b].fa1, fc0 = P.cptab[b].fc0, fc1 = P.cptab[b].fc1;
+        const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
+        const int h_w = st.oi1 - st.oi0;
+        const int lbo_a = rows * 16;
+
+        for (int i0 = bx.out_i0; i0 < bx.out_i1; i0 += kTcM) {
+            const int r0 = i0 - R;   // input row of tile row 0
+            __syncthreads();
+            // input tile: element (row, k) = in(r0 + row, s_end - 1 - k), hi/lo BF16,
+            // 8 consecutive k per thread item (one 16-byte core-matrix row)
+            for (int idx = tid; idx < rows * (kt / 8); idx += blockDim.x) {
+                const int kc = idx / rows, row = idx - kc * rows;
+                const int u = r0 + row;
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int t = 0; t < 8; t += 2) {
+                    float v[2];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int s = s_end - 1 - (8 * kc + t + e);
+                        float x = 0.f;
+                        if (u >= bx.in_i0 && u < bx.in_i1 && s >= bx.in_j0 && s < bx.in_j1) {
+                            if (ADJ) {
+                                x = hsrc[(long long)(s - st.oj0) * h_w + (u - st.oi0)];
+                            } else {
+                                const float fa = mag_coord(st.m, u, L.cu), fc = mag_coord(st.m, s, L.cv);
+                                const float ba = floorf(fa), bc = floorf(fc);
+                                const int a0 = (int)ba, cc0 = (int)bc;
+                                const float ta = fa - ba, tc = fc - bc;
+                                const int Fc = fc1 - fc0;
+#pragma unroll
+                                for (int da = 0; da < 2; ++da) {
+                                    const int a = a0 + da;
+                                    if (a < fa0 || a >= fa1) continue;
+                                    const float wa = da ? ta : 1.f - ta;
+#pragma unroll
+                                    for (int dc = 0; dc < 2; ++dc) {
+                                        const int c = cc0 + dc;
+                                        if (c < fc0 || c >= fc1) continue;
+                                        const float wc = dc ? tc : 1.f - tc;
+                                        x += wa * wc * __ldg(&fmap[(long long)(a - fa0) * Fc + (c - fc0)]);
+                                    }
+                                }
+                            }
+                        }
+                        v[e] = x;
+                    }
+                    __nv_bfloat16 h0, l0, h1, l1;
+                    split_bf16(v[0], h0, l0);
+                    split_bf16(v[1], h1, l1);
+                    hw[t >> 1] = pack2(h0, h1);
+                    lw[t >> 1] = pack2(l0, l1);
+                }
+                unsigned char *ap = abase + (size_t)kc * lbo_a + row * 16;
+                *reinterpret_cast<uint4 *>(ap) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(ap + (size_t)rows * kTcMaxK * 2) =
+                    make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
+            fence_proxy_async();   // generic-proxy smem writes -> tensor core reads
+            fence_before();
+            __syncthreads();
+            fence_after();
+            if (tid == 0) {
+                const uint32_t a_hi = smem_u32(abase), a_lo = a_hi + rows * kTcMaxK * 2;
+                const uint32_t b_all = smem_u32(bbase);
+                uint32_t acc = 0;
+                for (int p = -R; p <= R; ++p) {
+                    const int ap = p < 0 ? -p : p;
+                    const uint32_t b_hi = b_all + (uint32_t)(ap * 2 * nd_max) * 128u;
+                    const uint32_t b_lo = b_hi + (uint32_t)nd_max * 128u;
+                    const uint32_t row_off = (uint32_t)(R - p) * 16u;
+                    for (int ks = 0; ks < kt / 16; ++ks) {
+                        const uint32_t aoff = row_off + (uint32_t)(2 * ks) * lbo_a;
+                        const uint32_t boff = (uint32_t)(2 * ks) * 128u;
+                        const uint64_t dah = smem_desc(a_hi + aoff, lbo_a, 128);
+                        const uint64_t dal = smem_desc(a_lo + aoff, lbo_a, 128);
+                        const uint64_t dbh = smem_desc(b_hi + boff, 128, 128);
+                        const uint64_t dbl = smem_desc(b_lo + boff, 128, 128);
+                        mma_bf16(tmem, dah, dbh, idesc, acc);
+                        acc = 1;
+                        mma_bf16(tmem, dah, dbl, idesc, 1);
+                        mma_bf16(tmem, dal, dbh, idesc, 1);
+                    }
+                }
+                mma_commit(mbar);
+            }
+            // wait for the MMAs: thread 0 polls the mbarrier (bounded) and
+            // broadcasts the outcome so the CTA stays convergent
+            if (tid == 0) {
+                long long spins = 0;
+                int ok = 1;
+                while (!mbar_try(mbar, phase)) {
+                    if (++spins > (1LL << 28)) {
+                        ok = 0;
+                        break;
+                    }
+                }
+                *s_item = ok;
+            }
+            __syncthreads();
+            const int ok = *s_item;
+            __syncthreads();
+            phase ^= 1u;
+            fence_after();
+            if (!ok) {
+                timed_out = true;
+                if (tid == 0) {
+                    atomicOr(P.flags, (unsigned)PDRT_FLAG_TIMEOUT);
+                    // give the MMAs in flight a second bounded wait before the
+                    // tensor memory is released
+                    long long spins = 0;
+                    while (!mbar_try(mbar, phase ^ 1u) && ++spins < (1LL << 28)) {
+                    }
+                }
+                break;
+            }
+            // epilogue: warp w reads TMEM lanes [32 (w % 4), +32) = output rows;
+            // the two warps of a lane quarter take alternate 16-column blocks
+            const int quarter = warp & 3, half = warp >> 2;
+            const int i = i0 + 32 * quarter + lane;
+            const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+            for (int cb = 16 * half; cb < nt; cb += 32) {
+                float v[16];
+                tmem_ld16(trow + (uint32_t)cb, v);
+                if (i < bx.out_i1) {
+                    float *o = dst + (i - bx.out_i0);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int j = bx.out_j0 + cb + q;
+                        if (j < bx.out_j1) o[(long long)(j - bx.out_j0) * out_w] = v[q] * scale;
+                    }
+                }
+            }
+            fence_before();
+        }
+    }
+    __syncthreads();
+    fence_after();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
+                           int grid_blocks, cudaStream_t s)
+{
+    const int smem = conv_tc_smem_bytes(P.mach.R);
+    if (adjoint)
+        k_conv_tc<true><<<grid_blocks, kTcThreads, smem, s>>>(P, b0, nb, counter);
+    else
+        k_conv_tc<false><<<grid_blocks, kTcThreads, smem, s>>>(P, b0, nb, counter);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_tc_prepare(int R, int *blocks_per_sm)
+{
+    const int smem = conv_tc_smem_bytes(R);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int n0 = 0, n1 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_conv_tc<false>, kTcThreads, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_conv_tc<true>, kTcThreads, smem);
+    if (e != cudaSuccess) return e;
+    int n = n0 < n1 ? n0 : n1;
+    // every resident CTA holds kTmemCols of the SM's 512 tensor-memory columns
+    const int tmem_cap = 512 / (int)kTmemCols;
+    *blocks_per_sm = n < tmem_cap ? n : tmem_cap;
+    return cudaSuccess;
+}
+
+}  // namespace pdrt

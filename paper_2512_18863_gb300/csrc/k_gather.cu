@@ -112,20 +112,6 @@ cudaError_t launch_gather(const PlanDev &P, int b0, int nb, float *dose, bool fi
     return cudaGetLastError();
 }
 
-// Interval of d = ix - fx with |a d + b dy| < 1, intersected into [lo, hi]
-// (widened by a small margin; the exact weights decide membership).
-__device__ __forceinline__ void clip_band(float a, float bdy, float &lo, float &hi)
-{
-    if (fabsf(a) < 1e-3f) {
-        if (fabsf(bdy) >= 1.f + 1e-3f) hi = lo - 1.f;   // empty
-        return;
-    }
-    const float inv = 1.f / a;
-    const float e0 = (-1.f - bdy) * inv, e1 = (1.f - bdy) * inv;
-    lo = fmaxf(lo, fminf(e0, e1) - 1e-3f);
-    hi = fminf(hi, fmaxf(e0, e1) + 1e-3f);
-}
-
 __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
 {
     const Lattice &L = P.lat;
@@ -150,9 +136,8 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
             // voxels of this row whose beam coordinates are within one lattice
             // step of (i, k) in both u and w
             const float dy = (float)iy - fy;
-            float lo = -1.45f, hi = 1.45f;
-            clip_band(g.au, g.bu * dy, lo, hi);
-            clip_band(g.aw, g.bw * dy, lo, hi);
+            const float lo = fmaxf(-1.45f, fmaxf(fmaf(-g.ru, dy, -g.iu), fmaf(-g.rw, dy, -g.iw))) - 1e-3f;
+            const float hi = fminf(1.45f, fminf(fmaf(-g.ru, dy, g.iu), fmaf(-g.rw, dy, g.iw))) + 1e-3f;
             const int x0 = max((int)ceilf(fx + lo), 0), x1 = min((int)floorf(fx + hi), P.nx - 1);
             for (int ix = x0; ix <= x1; ++ix) {
                 float fu, fw;

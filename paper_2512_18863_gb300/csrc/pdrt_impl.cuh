@@ -25,10 +25,12 @@ constexpr int kConvThreads = 128;        // 4 warps: 32 output rows x (4 x 16) o
 constexpr int kConvTJ = 16;              // output columns per lane
 constexpr int kConvCols = 64;            // output columns per CTA
 constexpr int kConvRows = 32;            // output rows per CTA (one per lane)
+constexpr int kTcMaxN = 96;              // tensor-core path: max output columns per slice
+constexpr int kTcMaxK = 96;              // tensor-core path: max input columns per slice
 
 enum KernelId {
     K_HU = 0, K_RASTER = 1, K_TABLES = 2, K_CONV_FWD = 3, K_GATHER = 4,
-    K_GATHER_T = 5, K_CONV_ADJ = 6, K_MAG_T_GRAD = 7
+    K_GATHER_T = 5, K_CONV_ADJ = 6, K_MAG_T_GRAD = 7, K_CONV_TC_FWD = 8, K_CONV_TC_ADJ = 9
 };
 
 struct Lattice {
@@ -57,6 +59,9 @@ struct CpGeo {
     float aw, bw, cw0;    // fw = aw*ix + bw*iy + cw0   (beam lattice index along w)
     float sx_w, sy_w;     // beam direction e_w projected to voxel index units (x, y)
     float px0, py0, pz0;  // isocentre in voxel index units
+    // transpose-gather bands: |fu - i| < 1 and |fw - k| < 1 at row offset dy
+    // hold for dx = ix - fx in (-iu - ru dy, iu - ru dy) and (-iw - rw dy, iw - rw dy)
+    float iu, ru, iw, rw;
 };
 
 struct CpTab {
@@ -101,6 +106,7 @@ struct PlanDev {
     long long cap_o, cap_a;  // floats per CP slot
     unsigned int *flags;
     unsigned int *counters;  // work-queue counters (per chunk launch)
+    int tc_enabled;          // 1: slices that fit the tensor-core tiles go to k_conv_tc
 };
 
 // Same float expression in every kernel that samples or transposes the
@@ -127,6 +133,41 @@ __device__ __forceinline__ float overlap_f(float x, float lo, float hi, float d)
     return X > 0.f ? X / d : 0.f;
 }
 
+
+// Boxes of one slice for one convolution direction, and the column ranges the
+// tensor-core path uses (input columns [s0, s0 + kt), kt and nt multiples of 16).
+struct TcBoxes {
+    int in_i0, in_i1, in_j0, in_j1, out_i0, out_i1, out_j0, out_j1;
+    int s0, kt, nt;
+};
+
+__device__ __forceinline__ TcBoxes tc_boxes(const SliceTab &st, bool adj, int R)
+{
+    TcBoxes b;
+    if (adj) {
+        b.in_i0 = st.oi0; b.in_i1 = st.oi1; b.in_j0 = st.oj0; b.in_j1 = st.oj1;
+        b.out_i0 = st.ai0; b.out_i1 = st.ai1; b.out_j0 = st.aj0; b.out_j1 = st.aj1;
+    } else {
+        b.in_i0 = st.pi0; b.in_i1 = st.pi1; b.in_j0 = st.pj0; b.in_j1 = st.pj1;
+        b.out_i0 = st.oi0; b.out_i1 = st.oi1; b.out_j0 = st.oj0; b.out_j1 = st.oj1;
+    }
+    const int ow = b.out_j1 - b.out_j0;
+    b.nt = ((ow > 0 ? ow : 0) + 15) & ~15;
+    b.s0 = max(b.in_j0, b.out_j0 - R);
+    const int s1 = min(b.in_j1, b.out_j0 + b.nt + R);
+    b.kt = ((s1 > b.s0 ? s1 - b.s0 : 0) + 15) & ~15;
+    return b;
+}
+
+// Every slice is convolved by exactly one of k_conv_tc (true) and k_conv (false).
+__device__ __forceinline__ bool tc_takes_slice(const SliceTab &st, bool adj, int R, int tc_enabled)
+{
+    if (!tc_enabled) return false;
+    const TcBoxes b = tc_boxes(st, adj, R);
+    if (b.out_i1 <= b.out_i0 || b.out_j1 <= b.out_j0) return false;
+    return b.nt >= 16 && b.nt <= kTcMaxN && b.kt >= 16 && b.kt <= kTcMaxK;
+}
+
 // launchers (one per kernel); each returns cudaGetLastError() of its launch
 cudaError_t launch_hu_to_red(const float *hu, float *red, long long n, const float *pts, int npts,
                              cudaStream_t s);
@@ -145,6 +186,10 @@ cudaError_t launch_param_grad(const PlanDev &P, const float *leaves, const float
 int conv_smem_bytes(const MachineDev &m);
 int conv_nq4_for_radius(int R);
 cudaError_t conv_prepare(const MachineDev &m, int *fwd_blocks_per_sm, int *adj_blocks_per_sm);
+cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
+                           int grid_blocks, cudaStream_t s);
+cudaError_t conv_tc_prepare(int R, int *blocks_per_sm);
+int conv_tc_smem_bytes(int R);
 void internal_set_error(const char *msg);   // sets pdrt_last_error() for this thread
 void internal_count_launch();                // counts one launch in pdrt_launch_count()
 

@@ -32,7 +32,8 @@ class DoseEngine:
     machine: beam model (synth.Machine or any object with the same fields)
     """
 
-    def __init__(self, phantom, machine, gantry_deg, iso, scratch_budget_bytes=0, device=None):
+    def __init__(self, phantom, machine, gantry_deg, iso, scratch_budget_bytes=0, device=None,
+                 tensor_cores=None):
         if not torch.cuda.is_available():
             raise RuntimeError("DoseEngine needs a CUDA device (GB300, sm_103a); no CPU path exists")
         _lib.load()
@@ -54,6 +55,8 @@ class DoseEngine:
                                                list(np.asarray(iso, float)), self._machine,
                                                scratch_budget_bytes, _stream_ptr())
             torch.cuda.current_stream().synchronize()   # hu is read by the grid kernel
+        if tensor_cores is not None:
+            _lib.pdrt_plan_set_tensor_cores(self._plan, tensor_cores)
         self.info = _lib.pdrt_plan_get_info(self._plan)
 
     # -- raw entry points (tensors on self.device, float32, contiguous) -----
@@ -83,6 +86,11 @@ class DoseEngine:
         return DoseFn.apply(leaves, jaws, mu, self)
 
     # -- diagnostics -----------------------------------------------------------
+    def set_tensor_cores(self, enable: bool):
+        """Route the convolution to the tensor cores (True) or the FP32 SIMT kernel."""
+        _lib.pdrt_plan_set_tensor_cores(self._plan, enable)
+        self.info = _lib.pdrt_plan_get_info(self._plan)
+
     def status_flags(self):
         return _lib.pdrt_plan_status(self._plan, _stream_ptr())
 

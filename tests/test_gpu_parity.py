@@ -47,9 +47,10 @@ def _assert_grad(gpu, ref, name):
 # ---------------------------------------------------------------------------
 # forward
 # ---------------------------------------------------------------------------
-def test_water_static_10x10_matches_oracle_and_closed_form():
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_water_static_10x10_matches_oracle_and_closed_form(tensor_cores):
     w = S.water_static_64()
-    gpu = _gpu_dose(w)
+    gpu = _gpu_dose(w, tensor_cores=tensor_cores)
     ref = O.Model(w.phantom, w.machine, w.plan).dose()
     _assert_dose(gpu, ref)
     iy = np.arange(64)
@@ -59,17 +60,20 @@ def test_water_static_10x10_matches_oracle_and_closed_form():
     np.testing.assert_allclose(gpu[32, :, 32], closed, rtol=2e-5)
 
 
+@pytest.mark.parametrize("tensor_cores", [True, False])
 @pytest.mark.parametrize("n,spacing,n_cp,r_px,seed", [
     ((24, 40, 40), 3.0, 6, 4, 7),      # several CTA tiles per slice
     ((23, 37, 41), 3.0, 5, 3, 8),      # ragged, odd grid, nx != ny
     ((20, 33, 33), 4.0, 4, 10, 9),     # R = 10 px
     ((18, 30, 30), 4.0, 3, 21, 10),    # R = 21 px
-    ((16, 28, 28), 5.0, 2, 44, 11),    # maximum radius
+    ((16, 28, 28), 5.0, 2, 44, 11),    # maximum radius (FP32 SIMT only)
     ((40, 48, 48), 2.0, 3, 13, 12),    # 2 mm grid, R = 13
 ])
-def test_pelvis_forward_matches_oracle(n, spacing, n_cp, r_px, seed):
+def test_pelvis_forward_matches_oracle(n, spacing, n_cp, r_px, seed, tensor_cores):
+    if tensor_cores and r_px > 24:
+        pytest.skip("radius beyond the tensor-core tiles")
     w = S.small_pelvis(seed=seed, n=n, spacing=spacing, n_cp=n_cp, r_px=r_px)
-    gpu = _gpu_dose(w)
+    gpu = _gpu_dose(w, tensor_cores=tensor_cores)
     ref = O.Model(w.phantom, w.machine, w.plan).dose()
     assert ref.max() > 0
     _assert_dose(gpu, ref)
@@ -99,15 +103,16 @@ def test_chunking_does_not_change_the_dose():
 # ---------------------------------------------------------------------------
 # gradients
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("tensor_cores", [True, False])
 @pytest.mark.parametrize("ste", [1, 0])
-def test_gradients_match_oracle(ste):
+def test_gradients_match_oracle(ste, tensor_cores):
     w = S.small_pelvis(seed=21, n=(20, 36, 36), n_cp=5, r_px=6)
     w.machine.ste = ste
     w.plan.leaves[1, 30] = (2.1, 2.4)          # a pair under w_min: clamp active
     w.plan.mu[2] = 0.004                       # below eps_mu
     rng = np.random.default_rng(5)
     g = rng.standard_normal(w.phantom.shape)
-    eng = _engine(w)
+    eng = _engine(w, tensor_cores=tensor_cores)
     dl, dj, dm = (t.cpu().numpy().astype(np.float64)
                   for t in eng.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g))
     rl, rj, rm = O.Model(w.phantom, w.machine, w.plan).dose_grad(g)
@@ -167,6 +172,23 @@ def test_field_larger_than_lattice_and_single_cp():
     _assert_dose(gpu, ref)
 
 
+def test_tensor_and_simt_paths_match_oracle_on_arc_subset():
+    """128x128x96 @ 3 mm, R = 13: both convolution paths against the oracle,
+    and no device flag (timeout, capacity) raised."""
+    w = S.pelvis_arc_128()
+    sel = np.arange(3, 178, 12)
+    sub = S.Workload(w.name, w.phantom, w.machine,
+                     S.Plan(w.plan.gantry_deg[sel], w.plan.iso, w.plan.leaves[sel],
+                            w.plan.jaws[sel], w.plan.mu[sel]))
+    ref = O.Model(sub.phantom, sub.machine, sub.plan).dose()
+    for tc in (True, False):
+        eng = _engine(sub, tensor_cores=tc)
+        d = eng.forward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu).cpu().numpy()
+        assert eng.status_flags() == 0
+        eng.close()
+        _assert_dose(d.astype(np.float64), ref)
+
+
 def test_nan_input_is_flagged():
     w = S.small_pelvis(n=(16, 24, 24), n_cp=2, r_px=3)
     eng = _engine(w)
@@ -182,6 +204,7 @@ def test_nan_input_is_flagged():
 def test_forward_and_backward_are_deterministic():
     w = S.small_pelvis(n=(20, 32, 32), n_cp=4, r_px=5)
     eng = _engine(w)
+    assert eng.info["tensor_cores"] == 1
     a = eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).clone()
     b = eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).clone()
     assert torch.equal(a, b)
