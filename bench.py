@@ -47,9 +47,10 @@ def _args():
     ap.add_argument("--cpu-sample-cps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="pelvis256", choices=["pelvis256", "pelvis128"],
+    ap.add_argument("--workload", default="pelvis256", choices=["pelvis256", "pelvis128", "batch32"],
                     help="pelvis256: 256x256x160 @ 2 mm, 2 x 178 CPs (headline); "
-                         "pelvis128: 128x128x96 @ 3 mm, 178 CPs (smaller case for profiler captures)")
+                         "pelvis128: 128x128x96 @ 3 mm, 178 CPs (smaller case for profiler captures); "
+                         "batch32: 32 uneven plans in one CUDA-graph launch (its own JSON line)")
     ap.add_argument("--scratch-gb", type=float, default=0.0,
                     help="plan scratch budget in GB (0 = library default)")
     return ap.parse_args()
@@ -356,10 +357,75 @@ def _gpu(args):
         dist.destroy_process_group()
 
 
+def _gpu_batch(args):
+    """32 plans of uneven grids (96..256 voxels per axis, 2-3 mm) and arcs
+    (90-356 CPs): per-plan schedules from the autotuner, then forward +
+    adjoint of all plans per CUDA-graph launch."""
+    import torch
+
+    from paper_2512_18863_gb300 import synth
+    from paper_2512_18863_gb300.batch import DoseBatch
+    from paper_2512_18863_gb300.engine import DoseEngine
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    ws = synth.uneven_batch(32)
+    budget = int((args.scratch_gb or 1.5) * 1e9)
+    engines, grads = [], []
+    for w in ws:
+        e = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso, scratch_budget_bytes=budget)
+        masks = {k: torch.tensor(v, device=e.device) for k, v in w.phantom.masks.items()}
+        d = e.forward(w.plan.leaves, w.plan.jaws, w.plan.mu)
+        g = _objective_grad(d, masks, torch)
+        e.autotune(w.plan.leaves, w.plan.jaws, w.plan.mu, g)
+        engines.append(e)
+        grads.append(g)
+    batch = DoseBatch(engines, [w.plan.leaves for w in ws], [w.plan.jaws for w in ws],
+                      [w.plan.mu for w in ws], grads, n_branches=4)
+    for _ in range(args.warmup):
+        batch.launch()
+    torch.cuda.synchronize()
+    lat = []
+    clocks = _Clocks(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    total_ms = 0.0
+    for _ in range(args.steps):
+        e0.record()
+        batch.launch()
+        e1.record()
+        lat.append(batch.plan_times_ms())     # synchronises
+        total_ms += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    lat = np.concatenate(lat)
+    n_cp = sum(w.plan.n_cp for w in ws)
+    if rank == 0:
+        out = {"metric": "batched dose evals/sec fwd+adjoint (32 uneven plans, one CUDA-graph launch)",
+               "value": len(ws) * args.steps * world / (total_ms / 1e3), "unit": "plan evals/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic (seeded pelvis phantoms, uneven grids and arcs)",
+               "config": {"workload": "batch32_uneven", "plans": len(ws), "control_points": n_cp,
+                          "grids": [list(w.phantom.shape[::-1]) for w in ws],
+                          "schedules": [[e.info["tensor_cores"], e.info["chunk_cp"]] for e in engines]},
+               "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                              "max": float(lat.max())},
+               "arc_evals_per_s": n_cp / CP_PER_ARC * args.steps * world / (total_ms / 1e3),
+               "gpu_launches": batch.kernels * args.steps, "graph_launches": args.steps,
+               "clocks": clk}
+        print(json.dumps(out), flush=True)
+    batch.close()
+    for e in engines:
+        e.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         _reference(args)
+    elif args.workload == "batch32":
+        _gpu_batch(args)
     else:
         _gpu(args)
 

@@ -272,6 +272,58 @@ pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int32_t ny, in
                                 const float *leaves_dev, const float *jaws_dev,
                                 const float *mu_dev, float *dose_dev, pdrt_stream_t stream);
 
+/*
+ * Control points per pass (1 .. the count chosen at upload; the scratch was
+ * sized for that count).  Fewer points per pass keep each pass's beam-frame
+ * dose closer to L2; more points mean fewer launches.  Host only.
+ */
+pdrt_status pdrt_plan_set_chunk(pdrt_plan_t p, int32_t chunk_cp);
+
+/*
+ * Autotuner: times one forward (+ adjoint if dose_grad_dev != NULL) pass of
+ * the plan for every candidate schedule -- convolution on the tensor cores or
+ * on the FP32 SIMT kernel, and the control points per pass (the uploaded
+ * count, 1/2 and 1/4 of it) -- with CUDA events on `stream`, keeps the
+ * fastest on the plan and reports it.  Output buffers are overwritten.
+ * Synchronous.
+ */
+typedef struct {
+    int32_t tensor_cores;        /* chosen convolution path */
+    int32_t chunk_cp;            /* chosen control points per pass */
+    float best_ms;               /* time of the chosen schedule */
+    int32_t n_candidates;        /* schedules timed */
+} pdrt_tune_result;
+pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_dev,
+                               const float *jaws_dev, const float *mu_dev, float *dose_dev,
+                               const float *dose_grad_dev, float *dleaves_dev, float *djaws_dev,
+                               float *dmu_dev, pdrt_stream_t stream, pdrt_tune_result *out);
+
+/*
+ * Batched launch (Sec. 2.2: the beam sequence is organised for batched
+ * operation).  Records the forward dose -- and the adjoint for every i with
+ * dose_grad_dev[i] != NULL -- of n independent plans into ONE CUDA graph whose
+ * n_branches parallel branches run the plans concurrently; pdrt_batch_launch
+ * replays it with a single graph launch.  Every array argument has n entries
+ * (device pointers as in pdrt_dose_forward / pdrt_dose_backward); a plan may
+ * appear once per batch; the buffers must stay valid while the batch exists.
+ * The recording calls no cudaMalloc.  Errors: EINVAL (NULL, n < 1, repeated
+ * plan, mismatched grid), ECUDA.
+ */
+typedef struct pdrt_batch_s *pdrt_batch_t;
+pdrt_status pdrt_batch_create(pdrt_batch_t *out, int32_t n, const pdrt_grid_t *grids,
+                              const pdrt_plan_t *plans, const float *const *leaves_dev,
+                              const float *const *jaws_dev, const float *const *mu_dev,
+                              float *const *dose_dev, const float *const *dose_grad_dev,
+                              float *const *dleaves_dev, float *const *djaws_dev,
+                              float *const *dmu_dev, int32_t n_branches, pdrt_stream_t stream);
+pdrt_status pdrt_batch_launch(pdrt_batch_t b, pdrt_stream_t stream);
+/* Synchronises `stream`; ms_out[i] = completion time of plan i in the last
+ * launch, measured from the start of that launch (CUDA events in the graph). */
+pdrt_status pdrt_batch_plan_times(pdrt_batch_t b, pdrt_stream_t stream, float *ms_out);
+/* Number of kernel nodes in the batch's graph (kernels run per launch). */
+int64_t pdrt_batch_kernels(pdrt_batch_t b);
+void pdrt_batch_destroy(pdrt_batch_t b);
+
 /* Number of kernels this library has launched since it was loaded. */
 int64_t pdrt_launch_count(void);
 

@@ -35,7 +35,8 @@ class OrcPlan(C.Structure):
                 ("n_pairs", C.c_int), ("leaf_bounds", PD), ("tau", D),
                 ("wmin_leaf", D), ("wmin_jaw", D), ("f_leaf", D), ("f_jaw", D),
                 ("eps_mu", D), ("r_px", C.c_int), ("alpha", (D * 3) * 3), ("beta", (D * 3) * 3),
-                ("n_t", C.c_int), ("dz_t", D), ("t_table", PD), ("cal", D), ("ste", C.c_int)]
+                ("n_t", C.c_int), ("dz_t", D), ("t_table", PD), ("cal", D), ("ste", C.c_int),
+                ("pen_fwhm_u", D), ("pen_fwhm_v", D), ("oap", D * 3)]
 
 
 class OrcLattice(C.Structure):
@@ -122,6 +123,9 @@ class Model:
         pl.t_table = _p(self._tt)
         pl.cal = machine.cal
         pl.ste = int(machine.ste)
+        pl.pen_fwhm_u = float(getattr(machine, "pen_fwhm_u", 0.0))
+        pl.pen_fwhm_v = float(getattr(machine, "pen_fwhm_v", 0.0))
+        pl.oap[:] = [float(x) for x in getattr(machine, "off_axis", (1.0, 0.0, 0.0))]
         self.cplan = pl
         L = OrcLattice()
         lib().orc_lattice_of(C.byref(g), C.byref(pl), C.byref(L))
@@ -179,6 +183,16 @@ class Model:
         lib().orc_fluence(C.byref(self.cplan), C.byref(self.lat), _p(_f64(lv_proj)),
                           _p(_f64(jw_proj)), _p(F))
         return F
+
+    def fluence_correct(self, F):
+        out = _f64(F).copy()
+        lib().orc_fluence_correct(C.byref(self.cplan), C.byref(self.lat), _p(out))
+        return out
+
+    def fluence_correct_T(self, G):
+        out = _f64(G).copy()
+        lib().orc_fluence_correct_T(C.byref(self.cplan), C.byref(self.lat), _p(out))
+        return out
 
     def fluence_vjp(self, b, dF, leaves=None, jaws=None):
         leaves = _f64(self.plan.leaves if leaves is None else leaves)

@@ -71,6 +71,11 @@ typedef struct {
     const double *t_table;     /* depth-dose table T(m dz_t), m = 0..n_t-1 */
     double cal;                /* output calibration (Sec. 2.4) */
     int ste;
+    /* fluence corrections (Sec. 2.2.2): source penumbra as Gaussian blurs of
+     * the given FWHM along u (leaf travel) and v (across leaf pairs / Y jaws),
+     * 0 = off; off-axis profile OAP(r) = oap[0] + oap[1] r + oap[2] r^2 */
+    double pen_fwhm_u, pen_fwhm_v;
+    double oap[3];
 } orc_plan;
 
 typedef struct {
@@ -223,6 +228,80 @@ void orc_fluence(const orc_plan *p, const orc_lattice *L, const double *lv,
             F[(long)c * L->nu + a] = fx * fy * (p->tau + (1.0 - p->tau) * fl);
         }
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.2.2, physics corrections applied in sequence to the raw aperture  */
+/* fluence (readings): source penumbra = separable Gaussian blur, sigma =   */
+/* FWHM / (2 sqrt(2 ln 2)), taps |t| <= ceil(3 sigma / pitch) normalised to */
+/* unit sum, zero outside the lattice; then the off-axis profile            */
+/* OAP(r) = c0 + c1 r + c2 r^2 with r the distance from the central axis at  */
+/* the isocentre plane.  Both are linear in F; the blur matrix is symmetric. */
+/* ------------------------------------------------------------------------ */
+int orc_penumbra_radius(double fwhm, double pitch)
+{
+    if (!(fwhm > 0.0)) return 0;
+    double sigma = fwhm / (2.0 * sqrt(2.0 * log(2.0)));
+    return (int)ceil(3.0 * sigma / pitch);
+}
+
+static void gauss_taps(double fwhm, double pitch, int rb, double *g)
+{
+    double sigma = fwhm / (2.0 * sqrt(2.0 * log(2.0)));
+    double s = 0.0;
+    for (int t = -rb; t <= rb; ++t) {
+        g[t + rb] = exp(-(t * pitch) * (t * pitch) / (2.0 * sigma * sigma));
+        s += g[t + rb];
+    }
+    for (int t = 0; t <= 2 * rb; ++t) g[t] /= s;
+}
+
+/* In-place blur of F [nv][nu] along u (axis 0) or v (axis 1). */
+static void blur_axis(double *F, int nu, int nv, int axis, double fwhm, double pitch)
+{
+    int rb = orc_penumbra_radius(fwhm, pitch);
+    if (rb == 0) return;
+    double *g = (double *)malloc(sizeof(double) * (2 * rb + 1));
+    double *tmp = (double *)malloc(sizeof(double) * nu * nv);
+    gauss_taps(fwhm, pitch, rb, g);
+    for (int c = 0; c < nv; ++c)
+        for (int a = 0; a < nu; ++a) {
+            double s = 0.0;
+            for (int t = -rb; t <= rb; ++t) {
+                int aa = axis == 0 ? a - t : a, cc = axis == 0 ? c : c - t;
+                if (aa < 0 || aa >= nu || cc < 0 || cc >= nv) continue;
+                s += g[t + rb] * F[(long)cc * nu + aa];
+            }
+            tmp[(long)c * nu + a] = s;
+        }
+    memcpy(F, tmp, sizeof(double) * nu * nv);
+    free(g); free(tmp);
+}
+
+double orc_off_axis(const orc_plan *p, double u, double v)
+{
+    double r = sqrt(u * u + v * v);
+    return p->oap[0] + p->oap[1] * r + p->oap[2] * r * r;
+}
+
+/* Penumbra then off-axis profile, in place on F [nv][nu]. */
+void orc_fluence_correct(const orc_plan *p, const orc_lattice *L, double *F)
+{
+    blur_axis(F, L->nu, L->nv, 0, p->pen_fwhm_u, L->du);
+    blur_axis(F, L->nu, L->nv, 1, p->pen_fwhm_v, L->dv);
+    for (int c = 0; c < L->nv; ++c)
+        for (int a = 0; a < L->nu; ++a)
+            F[(long)c * L->nu + a] *= orc_off_axis(p, (a - L->cu) * L->du, (c - L->cv) * L->dv);
+}
+
+/* Transpose of orc_fluence_correct (off-axis profile, then the blurs). */
+void orc_fluence_correct_T(const orc_plan *p, const orc_lattice *L, double *G)
+{
+    for (int c = 0; c < L->nv; ++c)
+        for (int a = 0; a < L->nu; ++a)
+            G[(long)c * L->nu + a] *= orc_off_axis(p, (a - L->cu) * L->du, (c - L->cv) * L->dv);
+    blur_axis(G, L->nu, L->nv, 1, p->pen_fwhm_v, L->dv);
+    blur_axis(G, L->nu, L->nv, 0, p->pen_fwhm_u, L->du);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -625,6 +704,7 @@ int orc_dose(const orc_grid *g, const orc_plan *p, const double *leaves, const d
         double jw[4], muh;
         orc_project_cp(p, leaves + (long)b * 2 * p->n_pairs, jaws + 4L * b, mu[b], lv, jw, &muh);
         orc_fluence(p, &L, lv, jw, F);
+        orc_fluence_correct(p, &L, F);
         orc_wepl(g, p, &L, b, z);
         orc_magnify(p, &L, F, Phi);
         orc_conv(p, &L, z, Phi, Dp, brute);
@@ -652,6 +732,7 @@ int orc_beam_dose(const orc_grid *g, const orc_plan *p, int b, const double *lea
     double jw[4], muh;
     orc_project_cp(p, leaves_cp, jaws_cp, 1.0, lv, jw, &muh);
     orc_fluence(p, &L, lv, jw, F);
+    orc_fluence_correct(p, &L, F);
     orc_wepl(g, p, &L, b, z);
     orc_magnify(p, &L, F, Phi);
     orc_conv(p, &L, z, Phi, Dp, 0);
@@ -778,8 +859,10 @@ int orc_dose_grad(const orc_grid *g, const orc_plan *p, const double *leaves, co
         const double *jc = jaws + 4L * b;
         orc_project_cp(p, lc, jc, mu[b], lv, jw, &muh);
         orc_fluence(p, &L, lv, jw, F);
+        orc_fluence_correct(p, &L, F);
         orc_wepl(g, p, &L, b, z);
-        /* jaw box in lattice pixels */
+        /* jaw box in lattice pixels, widened by the penumbra blur radius (the
+         * corrected fluence and the raw fluence's sensitivities live there) */
         int a0 = L.nu, a1 = -1, c0 = L.nv, c1 = -1;
         for (int a = 0; a < L.nu; ++a)
             if (orc_overlap((a - L.cu) * L.du, jw[0], jw[1], L.du) > 0.0) {
@@ -791,6 +874,13 @@ int orc_dose_grad(const orc_grid *g, const orc_plan *p, const double *leaves, co
                 if (c < c0) c0 = c;
                 if (c > c1) c1 = c;
             }
+        if (a1 >= 0 && c1 >= 0) {
+            int ru = orc_penumbra_radius(p->pen_fwhm_u, L.du), rv = orc_penumbra_radius(p->pen_fwhm_v, L.dv);
+            a0 = a0 - ru < 0 ? 0 : a0 - ru;
+            a1 = a1 + ru >= L.nu ? L.nu - 1 : a1 + ru;
+            c0 = c0 - rv < 0 ? 0 : c0 - rv;
+            c1 = c1 + rv >= L.nv ? L.nv - 1 : c1 + rv;
+        }
         double dmuh = 0.0;
         if (a1 >= 0 && c1 >= 0) {
             memset(h, 0, sizeof(double) * nvol);
@@ -814,7 +904,7 @@ int orc_dose_grad(const orc_grid *g, const orc_plan *p, const double *leaves, co
             orc_conv_T(p, &L, z, h, mask, hp);
             memset(gF, 0, sizeof(double) * nF);
             orc_magnify_T(p, &L, hp, mask, gF);
-            /* restrict to the box and scale */
+            /* restrict to the box, MU gradient on the corrected fluence */
             for (int c = 0; c < L.nv; ++c)
                 for (int a = 0; a < L.nu; ++a) {
                     long t = (long)c * L.nu + a;
@@ -825,6 +915,8 @@ int orc_dose_grad(const orc_grid *g, const orc_plan *p, const double *leaves, co
                     dmuh += p->cal * gF[t] * F[t];
                     gF[t] *= p->cal * muh;
                 }
+            /* back through the corrections to the raw aperture fluence */
+            orc_fluence_correct_T(p, &L, gF);
             orc_fluence_vjp(p, &L, lc, jc, gF, dleaves + (long)b * 2 * np, djaws + 4L * b);
         }
         dmu[b] = (p->ste || mu[b] >= p->eps_mu) ? dmuh : 0.0;

@@ -177,6 +177,35 @@ class TorchDose:
         fl = omega.T @ fu
         return fy[:, None] * fx[None, :] * (m.tau + (1 - m.tau) * fl)
 
+    def _blur_matrix(self, n, pitch, fwhm):
+        """Banded Gaussian blur matrix (zero padding), taps to ceil(3 sigma)."""
+        if not fwhm > 0:
+            return None
+        sigma = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+        rb = int(math.ceil(3.0 * sigma / pitch))
+        t = np.arange(-rb, rb + 1)
+        g = np.exp(-(t * pitch) ** 2 / (2 * sigma ** 2))
+        g /= g.sum()
+        B = np.zeros((n, n))
+        for d, gv in zip(t, g):
+            B += gv * np.eye(n, k=-d)
+        return torch.from_numpy(B)
+
+    def correct(self, F):
+        """Penumbra blurs along u then v, then the off-axis profile (Sec. 2.2.2)."""
+        L, m = self.L, self.m
+        Bu = self._blur_matrix(L["nu"], L["du"], getattr(m, "pen_fwhm_u", 0.0))
+        Bv = self._blur_matrix(L["nv"], L["dv"], getattr(m, "pen_fwhm_v", 0.0))
+        if Bu is not None:
+            F = F @ Bu.T
+        if Bv is not None:
+            F = Bv @ F
+        c = getattr(m, "off_axis", (1.0, 0.0, 0.0))
+        u = (np.arange(L["nu"]) - L["cu"]) * L["du"]
+        v = (np.arange(L["nv"]) - L["cv"]) * L["dv"]
+        r = np.sqrt(u[None, :] ** 2 + v[:, None] ** 2)
+        return F * torch.from_numpy(c[0] + c[1] * r + c[2] * r * r)
+
     def project(self, leaves_b, jaws_b, mu_b):
         m = self.m
         la, lb_ = _project(leaves_b[:, 0], leaves_b[:, 1], m.wmin_leaf, m.f_leaf, m.ste)
@@ -200,6 +229,6 @@ class TorchDose:
         out = None
         for b in range(len(self.gantry)):
             lv, jw, muh = self.project(leaves[b], jaws[b], mu[b])
-            d = self.m.cal * muh * self.beam(b, self.fluence(lv, jw))
+            d = self.m.cal * muh * self.beam(b, self.correct(self.fluence(lv, jw)))
             out = d if out is None else out + d
         return out

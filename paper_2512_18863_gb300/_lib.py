@@ -56,6 +56,11 @@ class pdrt_work(C.Structure):
                 ("mma_flops", C.c_double)]
 
 
+class pdrt_tune_result(C.Structure):
+    _fields_ = [("tensor_cores", C.c_int32), ("chunk_cp", C.c_int32), ("best_ms", C.c_float),
+                ("n_candidates", C.c_int32)]
+
+
 class pdrt_profile(C.Structure):
     _fields_ = [("name", C.c_char_p * NUM_KERNELS), ("launches", C.c_int64 * NUM_KERNELS),
                 ("total_ms", C.c_double * NUM_KERNELS), ("overflow", C.c_int32)]
@@ -81,6 +86,17 @@ _SIG = {
     "pdrt_cp_dose_static": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.c_double, C.POINTER(pdrt_machine), _VP, _VP, _VP, _VP, _VP]),
+    "pdrt_plan_set_chunk": (C.c_int, [_VP, C.c_int32]),
+    "pdrt_plan_autotune": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                     C.POINTER(pdrt_tune_result)]),
+    "pdrt_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP), C.POINTER(_VP),
+                                    C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP),
+                                    C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP),
+                                    C.c_int32, _VP]),
+    "pdrt_batch_launch": (C.c_int, [_VP, _VP]),
+    "pdrt_batch_plan_times": (C.c_int, [_VP, _VP, C.POINTER(C.c_float)]),
+    "pdrt_batch_kernels": (C.c_int64, [_VP]),
+    "pdrt_batch_destroy": (None, [_VP]),
     "pdrt_launch_count": (C.c_int64, []),
     "pdrt_last_error": (C.c_char_p, []),
 }
@@ -212,6 +228,55 @@ def pdrt_cp_dose_static(red_dev_ptr, nx, ny, nz, sx, sy, sz, origin_mm, iso_mm, 
                                       float(sy), float(sz), _dptr(origin_mm), _dptr(iso_mm),
                                       float(gantry_deg), C.byref(machine), _VP(leaves_ptr),
                                       _VP(jaws_ptr), _VP(mu_ptr), _VP(dose_ptr), _VP(stream)))
+
+
+def pdrt_plan_set_chunk(plan, chunk_cp):
+    _check(load().pdrt_plan_set_chunk(_VP(plan), int(chunk_cp)))
+
+
+def pdrt_plan_autotune(grid, plan, leaves_ptr, jaws_ptr, mu_ptr, dose_ptr, dose_grad_ptr,
+                       dleaves_ptr, djaws_ptr, dmu_ptr, stream) -> dict:
+    r = pdrt_tune_result()
+    _check(load().pdrt_plan_autotune(_VP(grid), _VP(plan), _VP(leaves_ptr), _VP(jaws_ptr),
+                                     _VP(mu_ptr), _VP(dose_ptr), _VP(dose_grad_ptr),
+                                     _VP(dleaves_ptr), _VP(djaws_ptr), _VP(dmu_ptr), _VP(stream),
+                                     C.byref(r)))
+    return {k: getattr(r, k) for k, _ in pdrt_tune_result._fields_}
+
+
+def _ptr_array(values):
+    return (_VP * len(values))(*[_VP(x) for x in values])
+
+
+def pdrt_batch_create(grids, plans, leaves, jaws, mu, dose, dose_grad, dleaves, djaws, dmu,
+                      n_branches, stream):
+    """All list arguments: one device pointer (int) per plan (None: no adjoint)."""
+    out = _VP()
+    n = len(plans)
+    arr = lambda xs: None if xs is None else _ptr_array([0 if x is None else x for x in xs])
+    _check(load().pdrt_batch_create(C.byref(out), n, _ptr_array(grids), _ptr_array(plans),
+                                    arr(leaves), arr(jaws), arr(mu), arr(dose), arr(dose_grad),
+                                    arr(dleaves), arr(djaws), arr(dmu), int(n_branches),
+                                    _VP(stream)))
+    return out.value
+
+
+def pdrt_batch_launch(batch, stream):
+    _check(load().pdrt_batch_launch(_VP(batch), _VP(stream)))
+
+
+def pdrt_batch_plan_times(batch, n, stream):
+    ms = (C.c_float * n)()
+    _check(load().pdrt_batch_plan_times(_VP(batch), _VP(stream), ms))
+    return list(ms)
+
+
+def pdrt_batch_kernels(batch) -> int:
+    return int(load().pdrt_batch_kernels(_VP(batch)))
+
+
+def pdrt_batch_destroy(batch):
+    load().pdrt_batch_destroy(_VP(batch))
 
 
 def machine_struct(machine) -> pdrt_machine:

@@ -64,6 +64,7 @@ struct pdrt_plan_s {
     pdrt_grid_t grid;
     int n_cp;
     int chunk;
+    int chunk_max;            // control points per pass the scratch was sized for
     int conv_blocks_fwd, conv_blocks_adj;
     int tc_blocks;            // persistent grid of k_conv_tc (0: path unavailable)
     PlanDev dev;
@@ -392,6 +393,7 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     long long chunk = budget > fixed ? (long long)((budget - fixed) / per_cp) : 1;
     chunk = std::max(1LL, std::min<long long>(chunk, std::min(n_cp, kMaxCpPerChunk)));
     p->chunk = (int)chunk;
+    p->chunk_max = (int)chunk;
 
     cudaError_t e = cudaSuccess;
     float *lb = nullptr, *dd = nullptr;
@@ -417,7 +419,7 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     PLAN_TRY(dalloc(p, &P.region, (size_t)chunk * cap_o), "cudaMalloc(beam-frame region)");
     PLAN_TRY(dalloc(p, &P.adjbuf, (size_t)chunk * cap_a), "cudaMalloc(adjoint region)");
     PLAN_TRY(dalloc(p, &P.flags, 1), "cudaMalloc(flags)");
-    PLAN_TRY(dalloc(p, &P.counters, 4 * ((n_cp + chunk - 1) / chunk) + 2), "cudaMalloc(counters)");
+    PLAN_TRY(dalloc(p, &P.counters, 4 * (size_t)n_cp + 2), "cudaMalloc(counters)");
     P.leaf_bounds = lb;
     P.depth_dose = dd;
     P.cpgeo = dgeo;
@@ -446,7 +448,7 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     // tensor-core convolution when its tiles fit in shared memory
     p->tc_blocks = 0;
     P.tc_enabled = 0;
-    if (conv_tc_smem_bytes(M.R) <= 220 * 1024) {
+    if (conv_tc_smem_bytes(M.R, true) <= 220 * 1024 && conv_tc_smem_bytes(M.R, false) <= 220 * 1024) {
         int bt = 0;
         PLAN_TRY(conv_tc_prepare(M.R, &bt), "tensor-core convolution set-up");
         if (bt > 0) {
@@ -620,7 +622,8 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
                 const int nt = (oj1 - oj0 + 15) & ~15;
                 const int s0 = std::max(ij0, oj0 - R), s1 = std::min(ij1, oj0 + nt + R);
                 const int kt = ((s1 > s0 ? s1 - s0 : 0) + 15) & ~15;
-                if (nt < 16 || nt > kTcMaxN || kt < 16 || kt > kTcMaxK) continue;
+                const int maxn = adj ? kTcAdjMaxN : kTcFwdMaxN, maxk = adj ? kTcAdjMaxK : kTcFwdMaxK;
+                if (nt < 16 || nt > maxn || kt < 16 || kt > maxk) continue;
                 const int mtiles = (oi1 - oi0 + 127) / 128;
                 out->mma_flops += (double)mtiles * (2 * R + 1) * (kt / 16) * 3 * 2.0 * 128 * nt * 16;
             }
@@ -662,5 +665,238 @@ pdrt_status pdrt_profile_read(pdrt_plan_t p, pdrt_stream_t stream, pdrt_profile 
     out->overflow = p->overflow ? 1 : 0;
     return PDRT_OK;
 }
+
+
+pdrt_status pdrt_plan_set_chunk(pdrt_plan_t p, int32_t chunk_cp)
+{
+    g_last_error.clear();
+    if (!p) return fail(PDRT_EINVAL, "NULL plan");
+    if (chunk_cp < 1 || chunk_cp > p->chunk_max)
+        return fail(PDRT_EINVAL, "chunk must be in 1..%d (the scratch bound)", p->chunk_max);
+    p->chunk = chunk_cp;
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_dev,
+                               const float *jaws_dev, const float *mu_dev, float *dose_dev,
+                               const float *dose_grad_dev, float *dleaves_dev, float *djaws_dev,
+                               float *dmu_dev, pdrt_stream_t stream, pdrt_tune_result *out)
+{
+    pdrt_status st = check_call(g, p);
+    if (st != PDRT_OK) return st;
+    if (!out || !dose_dev) return fail(PDRT_EINVAL, "NULL argument");
+    if (dose_grad_dev && (!dleaves_dev || !djaws_dev || !dmu_dev))
+        return fail(PDRT_EINVAL, "adjoint outputs are NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool prof = p->profiling;
+    p->profiling = false;
+    std::vector<std::pair<int, int>> cand;
+    for (int tc = (p->tc_blocks > 0 ? 1 : 0); tc >= 0; --tc)
+        for (int c : {p->chunk_max, (p->chunk_max + 1) / 2, (p->chunk_max + 3) / 4})
+            if (c >= 1 && (cand.empty() || cand.back() != std::make_pair(tc, c)))
+                cand.push_back({tc, c});
+    cudaEvent_t e0, e1;
+    CU_TRY(cudaEventCreate(&e0), "cudaEventCreate");
+    CU_TRY(cudaEventCreate(&e1), "cudaEventCreate");
+    float best = 1e30f;
+    std::pair<int, int> pick = cand.front();
+    pdrt_status rst = PDRT_OK;
+    for (const auto &c : cand) {
+        p->dev.tc_enabled = c.first;
+        p->chunk = c.second;
+        auto pass = [&]() -> pdrt_status {
+            pdrt_status r = pdrt_dose_forward(g, p, leaves_dev, jaws_dev, mu_dev, dose_dev, stream);
+            if (r == PDRT_OK && dose_grad_dev)
+                r = pdrt_dose_backward(g, p, leaves_dev, jaws_dev, mu_dev, dose_grad_dev, dleaves_dev,
+                                       djaws_dev, dmu_dev, stream);
+            return r;
+        };
+        if ((rst = pass()) != PDRT_OK) break;   // warm-up
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 2 && rst == PDRT_OK; ++r) rst = pass();
+        cudaEventRecord(e1, s);
+        if (rst != PDRT_OK) break;
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rst = cuda_fail(e, "autotune timing");
+            break;
+        }
+        if (ms * 0.5f < best) {
+            best = ms * 0.5f;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->dev.tc_enabled = pick.first;
+    p->chunk = pick.second;
+    p->profiling = prof;
+    if (rst != PDRT_OK) return rst;
+    out->tensor_cores = pick.first;
+    out->chunk_cp = pick.second;
+    out->best_ms = best;
+    out->n_candidates = (int32_t)cand.size();
+    return PDRT_OK;
+}
+
+}  // extern "C"
+
+struct pdrt_batch_s {
+    int n = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaStream_t> branches;
+    std::vector<cudaEvent_t> events;   // [0] = fork, [1 .. nbr] = branch joins (graph edges only)
+    std::vector<cudaEvent_t> marks;    // [0] = start, [1 .. n] = plan done (event-record nodes)
+    long long kernels = 0;
+};
+
+static void batch_free(pdrt_batch_t b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->marks) cudaEventDestroy(e);
+    for (cudaStream_t s : b->branches) cudaStreamDestroy(s);
+    delete b;
+}
+
+extern "C" {
+
+pdrt_status pdrt_batch_create(pdrt_batch_t *out, int32_t n, const pdrt_grid_t *grids,
+                              const pdrt_plan_t *plans, const float *const *leaves_dev,
+                              const float *const *jaws_dev, const float *const *mu_dev,
+                              float *const *dose_dev, const float *const *dose_grad_dev,
+                              float *const *dleaves_dev, float *const *djaws_dev,
+                              float *const *dmu_dev, int32_t n_branches, pdrt_stream_t stream)
+{
+    g_last_error.clear();
+    if (!out || !grids || !plans || !leaves_dev || !jaws_dev || !mu_dev || !dose_dev)
+        return fail(PDRT_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n < 1) return fail(PDRT_EINVAL, "empty batch");
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i] || !grids[i] || plans[i]->grid != grids[i])
+            return fail(PDRT_EINVAL, "plan %d missing or uploaded for another grid", i);
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return fail(PDRT_EINVAL, "plan %d appears twice", i);
+        if (dose_grad_dev && dose_grad_dev[i] &&
+            (!dleaves_dev || !djaws_dev || !dmu_dev || !dleaves_dev[i] || !djaws_dev[i] || !dmu_dev[i]))
+            return fail(PDRT_EINVAL, "adjoint outputs of plan %d are NULL", i);
+    }
+    const int nbr = std::max(1, std::min<int>(n_branches, n));
+    pdrt_batch_t b = new pdrt_batch_s();
+    b->n = n;
+    (void)stream;   // recording uses an internal origin stream (the caller's may be the legacy one)
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->branches.push_back(s);
+    for (int k = 0; k < nbr && e == cudaSuccess; ++k) {
+        cudaStream_t bs;
+        e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) b->branches.push_back(bs);
+    }
+    for (int k = 0; k < 1 + nbr && e == cudaSuccess; ++k) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->events.push_back(ev);
+    }
+    for (int k = 0; k < 1 + n && e == cudaSuccess; ++k) {
+        cudaEvent_t ev;
+        e = cudaEventCreate(&ev);
+        if (e == cudaSuccess) b->marks.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        batch_free(b);
+        return cuda_fail(e, "batch streams/events");
+    }
+    // balance branches by a work estimate (control points x grid voxels)
+    std::vector<int> order(n), owner(n);
+    std::vector<double> load(nbr, 0.0);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    auto cost = [&](int i) {
+        return (double)plans[i]->n_cp * grids[i]->nx * grids[i]->ny * grids[i]->nz;
+    };
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    for (int i : order) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        owner[i] = k;
+        load[k] += cost(i);
+    }
+    std::vector<bool> prof(n);
+    for (int i = 0; i < n; ++i) {
+        prof[i] = plans[i]->profiling;
+        plans[i]->profiling = false;
+    }
+    pdrt_status rst = PDRT_OK;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        // timing marks become event-record nodes; the fork/join events only add edges
+        cudaEventRecordWithFlags(b->marks[0], s, cudaEventRecordExternal);
+        cudaEventRecord(b->events[0], s);
+        for (int k = 0; k < nbr; ++k) cudaStreamWaitEvent(b->branches[1 + k], b->events[0], 0);
+        for (int i = 0; i < n && rst == PDRT_OK; ++i) {
+            pdrt_stream_t bs = (pdrt_stream_t)b->branches[1 + owner[i]];
+            rst = pdrt_dose_forward(grids[i], plans[i], leaves_dev[i], jaws_dev[i], mu_dev[i], dose_dev[i], bs);
+            if (rst == PDRT_OK && dose_grad_dev && dose_grad_dev[i])
+                rst = pdrt_dose_backward(grids[i], plans[i], leaves_dev[i], jaws_dev[i], mu_dev[i],
+                                         dose_grad_dev[i], dleaves_dev[i], djaws_dev[i], dmu_dev[i], bs);
+            cudaEventRecordWithFlags(b->marks[1 + i], b->branches[1 + owner[i]], cudaEventRecordExternal);
+        }
+        for (int k = 0; k < nbr; ++k) {
+            cudaEventRecord(b->events[1 + k], b->branches[1 + k]);
+            cudaStreamWaitEvent(s, b->events[1 + k], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(s, &b->graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    for (int i = 0; i < n; ++i) plans[i]->profiling = prof[i];
+    if (rst == PDRT_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (rst == PDRT_OK && e == cudaSuccess) {
+        size_t nn = 0;
+        e = cudaGraphGetNodes(b->graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess && nn) e = cudaGraphGetNodes(b->graph, nodes.data(), &nn);
+        for (size_t q = 0; q < nn && e == cudaSuccess; ++q) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                ++b->kernels;
+        }
+    }
+    if (rst != PDRT_OK || e != cudaSuccess) {
+        std::string msg = g_last_error;
+        batch_free(b);
+        if (rst != PDRT_OK) return fail(rst, "batch recording failed: %s", msg.c_str());
+        return cuda_fail(e, "batch graph capture");
+    }
+    *out = b;
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_batch_launch(pdrt_batch_t b, pdrt_stream_t stream)
+{
+    g_last_error.clear();
+    if (!b || !b->exec) return fail(PDRT_EINVAL, "NULL batch");
+    CU_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "cudaGraphLaunch");
+    g_launches.fetch_add(b->kernels);
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_batch_plan_times(pdrt_batch_t b, pdrt_stream_t stream, float *ms_out)
+{
+    g_last_error.clear();
+    if (!b || !ms_out) return fail(PDRT_EINVAL, "NULL argument");
+    CU_TRY(cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
+    for (int i = 0; i < b->n; ++i)
+        CU_TRY(cudaEventElapsedTime(&ms_out[i], b->marks[0], b->marks[1 + i]), "cudaEventElapsedTime");
+    return PDRT_OK;
+}
+
+int64_t pdrt_batch_kernels(pdrt_batch_t b) { return b ? b->kernels : 0; }
+
+void pdrt_batch_destroy(pdrt_batch_t b) { batch_free(b); }
 
 }  // extern "C"

@@ -280,7 +280,7 @@ template <int NQ4, bool ADJ>
 static cudaError_t prepare_one(int smem, int *blocks_per_sm)
 {
     auto kern = k_conv<NQ4, ADJ, ADJ ? kAdjRowsPerWarp : kFwdRowsPerWarp>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_full_smem(kern);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, kConvThreads, smem);
 }

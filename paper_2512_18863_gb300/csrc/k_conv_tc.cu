@@ -5,7 +5,7 @@
 // (forward: in = magnified fluence, out = D'; adjoint: in = gathered gradient,
 // out = h'; K is symmetric, so both are this sum).  Per kernel row p it is a
 // GEMM  D[m][n] += A_p[m][k] B_p[n][k]  with m = output row (M = 128 per
-// tile), n = output column (N <= 96), k = input column (K <= 96):
+// tile), n = output column, k = input column (N, K <= 96):
 //   * A_p[m][k] = in(i0 + m - p, s_k).  The input tile is stored K-major in
 //     8 x 16-byte core matrices with its rows 16 bytes apart, so the shift by
 //     p is just a descriptor start address (R - p rows further).
@@ -20,7 +20,10 @@
 //
 // One CTA (8 warps) per slice, persistent over a work counter.  Thread 0
 // issues the MMAs; completion is signalled through an mbarrier
-// (tcgen05.commit); all waits are bounded and raise PDRT_FLAG_TIMEOUT.
+// (tcgen05.commit); all waits are bounded and raise PDRT_FLAG_TIMEOUT.  The
+// kernel-row operands are built in phases of kTcPhase rows into a double
+// buffer, each phase while the previous phase's MMAs run; with the per
+// direction tile limits two CTAs fit on an SM.
 // Slices whose boxes exceed the tile limits are left to the FP32 SIMT kernel
 // (k_conv), which skips the slices this kernel takes (tc_takes_slice).
 #include <cuda_bf16.h>
@@ -34,7 +37,7 @@ namespace {
 
 constexpr int kTcM = 128;
 constexpr int kTcThreads = 256;      // 8 warps: two per tensor-memory lane quarter
-constexpr uint32_t kTmemCols = 128;   // >= kTcMaxN, power of two
+constexpr uint32_t kTmemCols = 128;   // >= the largest tile width N, power of two
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -120,32 +123,46 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
 
 __host__ __device__ inline int tc_rows(int R) { return ((kTcM + 2 * R + 7) / 8) * 8; }
 
-int conv_tc_smem_bytes(int R)
+template <bool ADJ>
+struct TcLimits {
+    static constexpr int MAXN = ADJ ? kTcAdjMaxN : kTcFwdMaxN;
+    static constexpr int MAXK = ADJ ? kTcAdjMaxK : kTcFwdMaxK;
+    static constexpr int ND = MAXN / 8 + MAXK / 8 - 1;   // Hankel diagonals per kernel row
+};
+
+// shared memory: [0,128) barrier / tmem address / broadcast; kernel rows;
+// input tile hi+lo [2][K/8][rows][16 B]; kernel-row operands, two buffers of
+// kTcPhase rows x hi+lo x ND core matrices
+int conv_tc_smem_bytes(int R, bool adjoint)
 {
     const int rows = tc_rows(R);
-    const int nd = kTcMaxN / 8 + kTcMaxK / 8 - 1;
-    const int a = 2 * rows * kTcMaxK * 2;           // hi + lo, bf16
-    const int bsz = (R + 1) * 2 * nd * 128;         // hi + lo Hankel core matrices per |p|
+    const int maxk = adjoint ? kTcAdjMaxK : kTcFwdMaxK;
+    const int nd = adjoint ? TcLimits<true>::ND : TcLimits<false>::ND;
     const int krow = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
+    const int a = 2 * rows * maxk * 2;
+    const int bsz = 2 * kTcPhase * 2 * nd * 128;
     return 128 + krow + a + bsz;
 }
 
 template <bool ADJ>
 __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, int nb,
-                                                    unsigned int *__restrict__ counter)
+                                                           unsigned int *__restrict__ counter)
 {
+    using Lim = TcLimits<ADJ>;
     extern __shared__ __align__(128) unsigned char smem[];
     const Lattice &L = P.lat;
     const int R = P.mach.R;
     const int rows = tc_rows(R);
-    const int nd_max = kTcMaxN / 8 + kTcMaxK / 8 - 1;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 8);
     int *s_item = reinterpret_cast<int *>(smem + 16);
     float *krow = reinterpret_cast<float *>(smem + 128);
     const int krow_bytes = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
-    unsigned char *abase = smem + 128 + krow_bytes;             // [2][kt/8][rows][16 B]
-    unsigned char *bbase = abase + 2 * rows * kTcMaxK * 2;      // [R+1][2][nd][128 B]
+    unsigned char *abase = smem + 128 + krow_bytes;
+    const int a_copy = rows * Lim::MAXK * 2;                    // bytes of one (hi or lo) tile
+    unsigned char *bbase = abase + 2 * a_copy;
+    const int b_row = 2 * Lim::ND * 128;                        // hi + lo of one kernel row
+    const int b_buf = kTcPhase * b_row;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = nb * L.nw;
 
@@ -192,27 +209,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
                         st.wn[2] * expf(-st.a[2] * r);
         }
         __syncthreads();
-        // Hankel core matrices: for |p| and diagonal d, element (r, t) = K(|p|, 8d + r + t + c0),
-        // c0 = j0 - s_end + 1 (zero outside |q| <= R)
+        // Hankel core matrices of kernel rows |p| in [p0, p1) into buffer `buf`:
+        // element (r, t) of diagonal d = K(|p|, 8d + r + t + c0), c0 = j0 - s_end + 1
         const int c0 = bx.out_j0 - s_end + 1;
-        for (int idx = tid; idx < (R + 1) * nd * 8; idx += blockDim.x) {
-            const int p = idx / (nd * 8), rem = idx - p * nd * 8, d = rem >> 3, r = rem & 7;
-            uint32_t hw[4], lw[4];
+        auto build_b = [&](int p0, int p1, int buf) {
+            const int n = (p1 - p0) * nd * 8;
+            for (int idx = tid; idx < n; idx += blockDim.x) {
+                const int pl = idx / (nd * 8), rem = idx - pl * nd * 8, d = rem >> 3, r = rem & 7;
+                const int p = p0 + pl;
+                uint32_t hw[4], lw[4];
 #pragma unroll
-            for (int t = 0; t < 8; t += 2) {
-                __nv_bfloat16 h0, l0, h1, l1;
-                const int q0 = 8 * d + r + t + c0, q1 = q0 + 1;
-                const float v0 = (q0 >= -R && q0 <= R) ? krow[p * (2 * R + 1) + q0 + R] : 0.f;
-                const float v1 = (q1 >= -R && q1 <= R) ? krow[p * (2 * R + 1) + q1 + R] : 0.f;
-                split_bf16(v0, h0, l0);
-                split_bf16(v1, h1, l1);
-                hw[t >> 1] = pack2(h0, h1);
-                lw[t >> 1] = pack2(l0, l1);
+                for (int t = 0; t < 8; t += 2) {
+                    __nv_bfloat16 h0, l0, h1, l1;
+                    const int q0 = 8 * d + r + t + c0, q1 = q0 + 1;
+                    const float v0 = (q0 >= -R && q0 <= R) ? krow[p * (2 * R + 1) + q0 + R] : 0.f;
+                    const float v1 = (q1 >= -R && q1 <= R) ? krow[p * (2 * R + 1) + q1 + R] : 0.f;
+                    split_bf16(v0, h0, l0);
+                    split_bf16(v1, h1, l1);
+                    hw[t >> 1] = pack2(h0, h1);
+                    lw[t >> 1] = pack2(l0, l1);
+                }
+                unsigned char *bp = bbase + (size_t)buf * b_buf + (size_t)pl * b_row + (size_t)d * 128 + r * 16;
+                *reinterpret_cast<uint4 *>(bp) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4 *>(bp + (size_t)Lim::ND * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
-            unsigned char *bp = bbase + ((size_t)p * 2 * nd_max) * 128 + (size_t)d * 128 + r * 16;
-            *reinterpret_cast<uint4 *>(bp) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4 *>(bp + (size_t)nd_max * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-        }
+        };
+        const int n_ph = (R + kTcPhase) / kTcPhase;   // phases over |p| = 0..R
         const uint32_t idesc = instr_desc(kTcM, nt);
         const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
         const int fa0 = P.cptab[b].fa0, fa1 = P.cptab[b].fa1, fc0 = P.cptab[b].fc0, fc1 = P.cptab[b].fc1;
@@ -220,7 +242,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
         const int h_w = st.oi1 - st.oi0;
         const int lbo_a = rows * 16;
 
-        for (int i0 = bx.out_i0; i0 < bx.out_i1; i0 += kTcM) {
+        for (int i0 = bx.out_i0; i0 < bx.out_i1 && !timed_out; i0 += kTcM) {
             const int r0 = i0 - R;   // input row of tile row 0
             __syncthreads();
             // input tile: element (row, k) = in(r0 + row, s_end - 1 - k), hi/lo BF16,
@@ -270,67 +292,80 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
                 }
                 unsigned char *ap = abase + (size_t)kc * lbo_a + row * 16;
                 *reinterpret_cast<uint4 *>(ap) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4 *>(ap + (size_t)rows * kTcMaxK * 2) =
-                    make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                *reinterpret_cast<uint4 *>(ap + a_copy) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
+            build_b(0, min(kTcPhase, R + 1), 0);
             fence_proxy_async();   // generic-proxy smem writes -> tensor core reads
             fence_before();
             __syncthreads();
             fence_after();
-            if (tid == 0) {
-                const uint32_t a_hi = smem_u32(abase), a_lo = a_hi + rows * kTcMaxK * 2;
-                const uint32_t b_all = smem_u32(bbase);
-                uint32_t acc = 0;
-                for (int p = -R; p <= R; ++p) {
-                    const int ap = p < 0 ? -p : p;
-                    const uint32_t b_hi = b_all + (uint32_t)(ap * 2 * nd_max) * 128u;
-                    const uint32_t b_lo = b_hi + (uint32_t)nd_max * 128u;
-                    const uint32_t row_off = (uint32_t)(R - p) * 16u;
-                    for (int ks = 0; ks < kt / 16; ++ks) {
-                        const uint32_t aoff = row_off + (uint32_t)(2 * ks) * lbo_a;
-                        const uint32_t boff = (uint32_t)(2 * ks) * 128u;
-                        const uint64_t dah = smem_desc(a_hi + aoff, lbo_a, 128);
-                        const uint64_t dal = smem_desc(a_lo + aoff, lbo_a, 128);
-                        const uint64_t dbh = smem_desc(b_hi + boff, 128, 128);
-                        const uint64_t dbl = smem_desc(b_lo + boff, 128, 128);
-                        mma_bf16(tmem, dah, dbh, idesc, acc);
-                        acc = 1;
-                        mma_bf16(tmem, dah, dbl, idesc, 1);
-                        mma_bf16(tmem, dal, dbh, idesc, 1);
-                    }
-                }
-                mma_commit(mbar);
-            }
-            // wait for the MMAs: thread 0 polls the mbarrier (bounded) and
-            // broadcasts the outcome so the CTA stays convergent
-            if (tid == 0) {
-                long long spins = 0;
-                int ok = 1;
-                while (!mbar_try(mbar, phase)) {
-                    if (++spins > (1LL << 28)) {
-                        ok = 0;
-                        break;
-                    }
-                }
-                *s_item = ok;
-            }
-            __syncthreads();
-            const int ok = *s_item;
-            __syncthreads();
-            phase ^= 1u;
-            fence_after();
-            if (!ok) {
-                timed_out = true;
+            uint32_t acc = 0;
+            for (int ph = 0; ph < n_ph; ++ph) {
+                const int p0 = ph * kTcPhase, p1 = min(p0 + kTcPhase, R + 1);
                 if (tid == 0) {
-                    atomicOr(P.flags, (unsigned)PDRT_FLAG_TIMEOUT);
-                    // give the MMAs in flight a second bounded wait before the
-                    // tensor memory is released
-                    long long spins = 0;
-                    while (!mbar_try(mbar, phase ^ 1u) && ++spins < (1LL << 28)) {
+                    const uint32_t a_hi = smem_u32(abase), a_lo = a_hi + (uint32_t)a_copy;
+                    const uint32_t b_buf0 = smem_u32(bbase) + (uint32_t)((ph & 1) * b_buf);
+                    for (int ap = p0; ap < p1; ++ap) {
+                        const uint32_t b_hi = b_buf0 + (uint32_t)((ap - p0) * b_row);
+                        const uint32_t b_lo = b_hi + (uint32_t)Lim::ND * 128u;
+                        for (int sg = (ap == 0 ? 1 : -1); sg <= 1; sg += 2) {
+                            const int p = sg * ap;
+                            const uint32_t row_off = (uint32_t)(R - p) * 16u;
+                            for (int ks = 0; ks < kt / 16; ++ks) {
+                                const uint32_t aoff = row_off + (uint32_t)(2 * ks) * lbo_a;
+                                const uint32_t boff = (uint32_t)(2 * ks) * 128u;
+                                const uint64_t dah = smem_desc(a_hi + aoff, lbo_a, 128);
+                                const uint64_t dal = smem_desc(a_lo + aoff, lbo_a, 128);
+                                const uint64_t dbh = smem_desc(b_hi + boff, 128, 128);
+                                const uint64_t dbl = smem_desc(b_lo + boff, 128, 128);
+                                mma_bf16(tmem, dah, dbh, idesc, acc);
+                                acc = 1;
+                                mma_bf16(tmem, dah, dbl, idesc, 1);
+                                mma_bf16(tmem, dal, dbh, idesc, 1);
+                            }
+                        }
                     }
+                    mma_commit(mbar);
                 }
-                break;
+                // operands of the next phase go to the other buffer while these MMAs run
+                // (that buffer's previous readers finished before this phase was issued)
+                if (ph + 1 < n_ph) {
+                    build_b(p1, min(p1 + kTcPhase, R + 1), (ph + 1) & 1);
+                    fence_proxy_async();
+                }
+                // wait for this phase's MMAs: thread 0 polls the mbarrier (bounded)
+                // and broadcasts the outcome so the CTA stays convergent
+                if (tid == 0) {
+                    long long spins = 0;
+                    int ok = 1;
+                    while (!mbar_try(mbar, phase)) {
+                        if (++spins > (1LL << 28)) {
+                            ok = 0;
+                            break;
+                        }
+                    }
+                    *s_item = ok;
+                }
+                fence_before();
+                __syncthreads();
+                const int ok = *s_item;
+                __syncthreads();
+                fence_after();
+                phase ^= 1u;
+                if (!ok) {
+                    timed_out = true;
+                    if (tid == 0) {
+                        atomicOr(P.flags, (unsigned)PDRT_FLAG_TIMEOUT);
+                        // a second bounded wait for the MMAs in flight before the
+                        // tensor memory is released
+                        long long spins = 0;
+                        while (!mbar_try(mbar, phase ^ 1u) && ++spins < (1LL << 28)) {
+                        }
+                    }
+                    break;
+                }
             }
+            if (timed_out) break;
             // epilogue: warp w reads TMEM lanes [32 (w % 4), +32) = output rows;
             // the two warps of a lane quarter take alternate 16-column blocks
             const int quarter = warp & 3, half = warp >> 2;
@@ -361,7 +396,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
 cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
                            int grid_blocks, cudaStream_t s)
 {
-    const int smem = conv_tc_smem_bytes(P.mach.R);
+    const int smem = conv_tc_smem_bytes(P.mach.R, adjoint);
     if (adjoint)
         k_conv_tc<true><<<grid_blocks, kTcThreads, smem, s>>>(P, b0, nb, counter);
     else
@@ -371,15 +406,15 @@ cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsig
 
 cudaError_t conv_tc_prepare(int R, int *blocks_per_sm)
 {
-    const int smem = conv_tc_smem_bytes(R);
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int s0 = conv_tc_smem_bytes(R, false), s1 = conv_tc_smem_bytes(R, true);
+    cudaError_t e = allow_full_smem(k_conv_tc<false>);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_conv_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = allow_full_smem(k_conv_tc<true>);
     if (e != cudaSuccess) return e;
     int n0 = 0, n1 = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_conv_tc<false>, kTcThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_conv_tc<false>, kTcThreads, s0);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_conv_tc<true>, kTcThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_conv_tc<true>, kTcThreads, s1);
     if (e != cudaSuccess) return e;
     int n = n0 < n1 ? n0 : n1;
     // every resident CTA holds kTmemCols of the SM's 512 tensor-memory columns

@@ -9,8 +9,9 @@
 //   z plane) skips a control point when its footprint misses the CTA.
 // k_gather_T: pull form of the transpose: every beam-frame point (i, j, k) of
 //   the output box gathers the dose gradient of the (at most 3 x 3) voxels of
-//   plane j whose bilinear stencil contains it, with the weights recomputed by
-//   the same float expressions as k_gather (voxel_to_beam), so it is the exact
+//   plane j whose bilinear stencil contains it; the voxel's beam coordinates
+//   come from the same float expression as in k_gather (voxel_to_beam) and
+//   the weight 1 - |f - n| equals the forward's 1 - t or t, so this is the
 //   transpose of the forward up to summation order.  No atomics.
 #include <math.h>
 
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
         // voxel-index position of lattice point (i, k): rotation transpose
         const float fx = fmaf(di, g.au, fmaf(dk, g.aw, g.px0));
         const float fy = fmaf(di, g.bu, fmaf(dk, g.bw, g.py0));
-        const int y0 = max((int)ceilf(fy - 1.45f), 0), y1 = min((int)floorf(fy + 1.45f), P.ny - 1);
+        const int y0 = max(__float2int_ru(fy - 1.45f), 0), y1 = min(__float2int_rd(fy + 1.45f), P.ny - 1);
         const float *gp = gd + (long long)j * P.ny * P.nx;
         float s = 0.f;
         for (int iy = y0; iy <= y1; ++iy) {
@@ -138,15 +139,14 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
             const float dy = (float)iy - fy;
             const float lo = fmaxf(-1.45f, fmaxf(fmaf(-g.ru, dy, -g.iu), fmaf(-g.rw, dy, -g.iw))) - 1e-3f;
             const float hi = fminf(1.45f, fminf(fmaf(-g.ru, dy, g.iu), fmaf(-g.rw, dy, g.iw))) + 1e-3f;
-            const int x0 = max((int)ceilf(fx + lo), 0), x1 = min((int)floorf(fx + hi), P.nx - 1);
+            const int x0 = max(__float2int_ru(fx + lo), 0), x1 = min(__float2int_rd(fx + hi), P.nx - 1);
             for (int ix = x0; ix <= x1; ++ix) {
                 float fu, fw;
                 voxel_to_beam(g, ix, iy, fu, fw);
-                const float bu = floorf(fu), bw = floorf(fw);
-                const int i0 = (int)bu, k0 = (int)bw;
-                const float tu = fu - bu, tw = fw - bw;
-                const float wu = (i == i0) ? 1.f - tu : ((i == i0 + 1) ? tu : 0.f);
-                const float ww = (k == k0) ? 1.f - tw : ((k == k0 + 1) ? tw : 0.f);
+                // bilinear weight of lattice point (i, k) in this voxel's stencil:
+                // 1 - |f - n| inside one lattice step (the forward's 1 - t and t)
+                const float wu = fmaxf(0.f, 1.f - fabsf(fu - (float)i));
+                const float ww = fmaxf(0.f, 1.f - fabsf(fw - (float)k));
                 const float wgt = ww * wu;
                 if (wgt != 0.f) s = fmaf(wgt, __ldg(&gp[(long long)iy * P.nx + ix]), s);
             }

@@ -25,8 +25,11 @@ constexpr int kConvThreads = 128;        // 4 warps: 32 output rows x (4 x 16) o
 constexpr int kConvTJ = 16;              // output columns per lane
 constexpr int kConvCols = 64;            // output columns per CTA
 constexpr int kConvRows = 32;            // output rows per CTA (one per lane)
-constexpr int kTcMaxN = 96;              // tensor-core path: max output columns per slice
-constexpr int kTcMaxK = 96;              // tensor-core path: max input columns per slice
+// tensor-core path tile limits (output columns N, input columns K) per direction:
+// the forward has wide outputs and narrow inputs, the adjoint the reverse
+constexpr int kTcFwdMaxN = 96, kTcFwdMaxK = 64;
+constexpr int kTcAdjMaxN = 64, kTcAdjMaxK = 96;
+constexpr int kTcPhase = 4;              // kernel rows |p| per double-buffered operand phase
 
 enum KernelId {
     K_HU = 0, K_RASTER = 1, K_TABLES = 2, K_CONV_FWD = 3, K_GATHER = 4,
@@ -165,7 +168,8 @@ __device__ __forceinline__ bool tc_takes_slice(const SliceTab &st, bool adj, int
     if (!tc_enabled) return false;
     const TcBoxes b = tc_boxes(st, adj, R);
     if (b.out_i1 <= b.out_i0 || b.out_j1 <= b.out_j0) return false;
-    return b.nt >= 16 && b.nt <= kTcMaxN && b.kt >= 16 && b.kt <= kTcMaxK;
+    const int maxn = adj ? kTcAdjMaxN : kTcFwdMaxN, maxk = adj ? kTcAdjMaxK : kTcFwdMaxK;
+    return b.nt >= 16 && b.nt <= maxn && b.kt >= 16 && b.kt <= maxk;
 }
 
 // launchers (one per kernel); each returns cudaGetLastError() of its launch
@@ -189,7 +193,29 @@ cudaError_t conv_prepare(const MachineDev &m, int *fwd_blocks_per_sm, int *adj_b
 cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
                            int grid_blocks, cudaStream_t s);
 cudaError_t conv_tc_prepare(int R, int *blocks_per_sm);
-int conv_tc_smem_bytes(int R);
+
+// Raises a kernel's dynamic shared-memory limit to everything the device
+// offers one block and asks for the largest shared-memory carve-out. The
+// limit is a property of the kernel, not of a launch: plans of different
+// kernel radii share one instantiation, so it is never lowered to one plan's
+// need (a smaller later plan would invalidate a larger earlier one).
+template <typename Kern>
+inline cudaError_t allow_full_smem(Kern kern)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+int conv_tc_smem_bytes(int R, bool adjoint);
 void internal_set_error(const char *msg);   // sets pdrt_last_error() for this thread
 void internal_count_launch();                // counts one launch in pdrt_launch_count()
 

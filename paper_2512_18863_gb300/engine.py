@@ -91,6 +91,29 @@ class DoseEngine:
         _lib.pdrt_plan_set_tensor_cores(self._plan, enable)
         self.info = _lib.pdrt_plan_get_info(self._plan)
 
+    def set_chunk(self, chunk_cp: int):
+        """Control points per pass (1 .. the count the scratch was sized for)."""
+        _lib.pdrt_plan_set_chunk(self._plan, chunk_cp)
+        self.info = _lib.pdrt_plan_get_info(self._plan)
+
+    def autotune(self, leaves, jaws, mu, dose_grad=None):
+        """Time the candidate schedules (tensor cores or SIMT, control points
+        per pass) on these inputs and keep the fastest on the plan."""
+        leaves, jaws, mu = self._params(leaves, jaws, mu)
+        out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        gptr = dl = dj = dm = None
+        if dose_grad is not None:
+            g = _f32(dose_grad, self.device)
+            dl, dj, dm = torch.empty_like(leaves), torch.empty_like(jaws), torch.empty_like(mu)
+            gptr = g.data_ptr()
+        r = _lib.pdrt_plan_autotune(self._grid, self._plan, leaves.data_ptr(), jaws.data_ptr(),
+                                    mu.data_ptr(), out.data_ptr(), gptr,
+                                    None if dl is None else dl.data_ptr(),
+                                    None if dj is None else dj.data_ptr(),
+                                    None if dm is None else dm.data_ptr(), _stream_ptr())
+        self.info = _lib.pdrt_plan_get_info(self._plan)
+        return r
+
     def status_flags(self):
         return _lib.pdrt_plan_status(self._plan, _stream_ptr())
 

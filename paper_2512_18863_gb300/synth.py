@@ -49,6 +49,12 @@ class Machine:
     eps_mu: float = 0.01
     cal: float = 1.0
     ste: int = 1
+    # fluence corrections of Sec. 2.2.2 beyond transmission: source penumbra
+    # FWHM along leaf travel (u) and across leaf pairs / Y jaws (v), mm (0 =
+    # off), and the off-axis profile coefficients c0 + c1 r + c2 r^2
+    pen_fwhm_u: float = 0.0
+    pen_fwhm_v: float = 0.0
+    off_axis: tuple = (1.0, 0.0, 0.0)
 
     @property
     def n_pairs(self) -> int:
@@ -125,6 +131,16 @@ def machine_model(seed: int, r_px: int, n_t: int = 501, dz_t: float = 1.0,
     return Machine(r_px=int(r_px), alpha=alpha, beta=beta, t_table=t, dz_t=dz_t)
 
 
+def with_corrections(m: Machine, seed: int, pen=(4.0, 6.0)) -> Machine:
+    """Seeded source-penumbra widths (FWHM, mm) and a mildly horned off-axis
+    profile (a few per cent over 100 mm), as commissioned beam models have."""
+    rng = np.random.default_rng(seed)
+    m.pen_fwhm_u = float(pen[0] * rng.uniform(0.8, 1.2))
+    m.pen_fwhm_v = float(pen[1] * rng.uniform(0.8, 1.2))
+    m.off_axis = (1.0, float(rng.uniform(1e-4, 3e-4)), float(rng.uniform(-2e-6, 2e-6)))
+    return m
+
+
 def water_phantom(n=(64, 64, 64), spacing=(2.5, 2.5, 2.5), hu=0.0) -> Phantom:
     """Uniform phantom; voxel index n//2 sits at 0 mm on every axis."""
     nz, ny, nx = n
@@ -135,9 +151,9 @@ def water_phantom(n=(64, 64, 64), spacing=(2.5, 2.5, 2.5), hu=0.0) -> Phantom:
 
 def _coords(ph: Phantom):
     nz, ny, nx = ph.hu.shape
-    x = ph.origin[0] + ph.spacing[0] * np.arange(nx)
-    y = ph.origin[1] + ph.spacing[1] * np.arange(ny)
-    z = ph.origin[2] + ph.spacing[2] * np.arange(nz)
+    x = (ph.origin[0] + ph.spacing[0] * np.arange(nx)).astype(np.float32)
+    y = (ph.origin[1] + ph.spacing[1] * np.arange(ny)).astype(np.float32)
+    z = (ph.origin[2] + ph.spacing[2] * np.arange(nz)).astype(np.float32)
     return np.meshgrid(z, y, x, indexing="ij")
 
 
@@ -291,3 +307,25 @@ def small_pelvis(seed=7, n=(24, 40, 40), spacing=3.0, n_cp=6, r_px=4, ptv_radii=
     ph = pelvis_phantom(n, (spacing,) * 3, seed=seed, ptv_radii=ptv_radii)
     pl = arc_plan(m, arc_angles(n_cp) + 7.5, seed=seed, ptv_radii=ptv_radii)
     return Workload(f"pelvis{n[2]}x{n[1]}x{n[0]}_{n_cp}cp_R{r_px}px", ph, m, pl)
+
+
+def uneven_batch(n_plans=32, seed=1003, r_cm=4.0):
+    """Plans of uneven size for the batched launch: grid axes uniform in
+    [96, 256] voxels (z capped at 160), 2-3 mm voxels, arcs of 90-356 control
+    points (two arcs above 178), kernel radius r_cm."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(n_plans):
+        nx, ny = (int(v) for v in rng.integers(96, 257, 2))
+        nz = int(rng.integers(96, 161))
+        sp = float(rng.choice([2.0, 2.5, 3.0]))
+        n_cp = int(rng.integers(90, 357))
+        m = machine_model(seed + 10 * q, r_px=int(round(r_cm * 10.0 / sp)))
+        ph = pelvis_phantom((nz, ny, nx), (sp, sp, sp), seed=seed + q)
+        if n_cp > 178:
+            ang = np.concatenate([arc_angles(n_cp // 2), arc_angles(n_cp - n_cp // 2, reverse=True)])
+        else:
+            ang = arc_angles(n_cp)
+        pl = arc_plan(m, ang, seed=seed + q)
+        out.append(Workload(f"plan{q}_{nx}x{ny}x{nz}_{sp:g}mm_{n_cp}cp", ph, m, pl))
+    return out

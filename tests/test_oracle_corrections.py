@@ -1,0 +1,110 @@
+"""Pins of the fluence corrections of Sec. 2.2.2 beyond transmission (source
+penumbra and off-axis profile) in the oracle, and of their adjoint."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from oracle import torch_ref
+from paper_2512_18863_gb300 import synth as S
+
+
+def _model(pen_u=4.0, pen_v=6.0, oap=(1.0, 0.0, 0.0), n=(41, 9, 41), ste=1):
+    nz, ny, nx = n
+    ph = S.Phantom(hu=np.zeros(n, np.float32), spacing=(2.0, 2.0, 2.5),
+                   origin=(-(nx // 2) * 2.0, -(ny // 2) * 2.0, -(nz // 2) * 2.5))
+    m = S.machine_model(61, r_px=3)
+    m.pen_fwhm_u, m.pen_fwhm_v, m.off_axis, m.ste = pen_u, pen_v, oap, ste
+    return O.Model(ph, m, S.static_field(m)), m
+
+
+def test_penumbra_of_a_single_pixel_is_the_normalised_gaussian():
+    """A one-pixel fluence blurred along u then v is the outer product of two
+    discrete Gaussians exp(-(t pitch)^2 / (2 sigma^2)), sigma = FWHM / 2.3548,
+    each of unit sum (the blur keeps the total fluence)."""
+    mod, m = _model(pen_u=5.0, pen_v=7.5)
+    L = mod.lattice
+    F = np.zeros((L["nv"], L["nu"]))
+    a0, c0 = int(L["cu"]), int(round(L["cv"]))
+    F[c0, a0] = 1.0
+    G = mod.fluence_correct(F)
+    assert G.sum() == pytest.approx(1.0, rel=1e-13)
+    su, sv = 5.0 / (2 * math.sqrt(2 * math.log(2))), 7.5 / (2 * math.sqrt(2 * math.log(2)))
+    for t in range(-4, 5):
+        assert G[c0, a0 + t] / G[c0, a0] == pytest.approx(math.exp(-(t * 2.0) ** 2 / (2 * su * su)), rel=1e-12)
+        assert G[c0 + t, a0] / G[c0, a0] == pytest.approx(math.exp(-(t * 2.5) ** 2 / (2 * sv * sv)), rel=1e-12)
+    assert G[c0 + 2, a0 + 3] == pytest.approx(G[c0 + 2, a0] * G[c0, a0 + 3] / G[c0, a0], rel=1e-12)
+    ru = math.ceil(3 * su / 2.0)
+    assert G[c0, a0 + ru] > 0 and G[c0, a0 + ru + 1] == 0.0
+
+
+def test_off_axis_profile_multiplies_by_c0_c1r_c2r2():
+    oap = (0.98, 2.5e-4, -1.5e-6)
+    mod, _ = _model(pen_u=0.0, pen_v=0.0, oap=oap)
+    L = mod.lattice
+    F = np.ones((L["nv"], L["nu"]))
+    G = mod.fluence_correct(F)
+    u = (np.arange(L["nu"]) - L["cu"]) * L["du"]
+    v = (np.arange(L["nv"]) - L["cv"]) * L["dv"]
+    r = np.sqrt(u[None, :] ** 2 + v[:, None] ** 2)
+    np.testing.assert_allclose(G, oap[0] + oap[1] * r + oap[2] * r * r, rtol=1e-14)
+
+
+def test_corrections_dot_product():
+    mod, _ = _model(oap=(1.0, 2e-4, 1e-6))
+    L = mod.lattice
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((L["nv"], L["nu"]))
+    y = rng.standard_normal((L["nv"], L["nu"]))
+    a, b = np.vdot(mod.fluence_correct(x), y), np.vdot(x, mod.fluence_correct_T(y))
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def _corrected_case(ste):
+    w = S.small_pelvis(seed=63, n=(12, 20, 20), spacing=4.0, n_cp=3, r_px=3,
+                       ptv_radii=(14.0, 12.0, 14.0))
+    S.with_corrections(w.machine, 5)
+    w.machine.ste = ste
+    return w
+
+
+@pytest.mark.parametrize("ste", [1, 0])
+def test_gradient_with_corrections_vs_central_fd(ste):
+    from tests.test_oracle_adjoint import _pick_params
+    w = _corrected_case(ste)
+    mod = O.Model(w.phantom, w.machine, w.plan)
+    rng = np.random.default_rng(17)
+    g = rng.standard_normal(w.phantom.shape)
+    dl, dj, dm = mod.dose_grad(g)
+    grads = {"leaves": dl, "jaws": dj, "mu": dm}
+    scale = {k: np.abs(v).max() for k, v in grads.items()}
+    base = {"leaves": w.plan.leaves.copy(), "jaws": w.plan.jaws.copy(), "mu": w.plan.mu.copy()}
+    picks = _pick_params(w, mod, rng, 30)
+    assert len(picks) >= 15
+    for name, ix in picks:
+        vals = []
+        for sgn in (+1, -1):
+            p = {k: v.copy() for k, v in base.items()}
+            p[name][ix] += sgn * 0.01
+            vals.append(np.vdot(g, mod.dose(p["leaves"], p["jaws"], p["mu"])))
+        fd = (vals[0] - vals[1]) / 0.02
+        assert abs(fd - grads[name][ix]) <= 1e-6 * scale[name] + 1e-9 * abs(grads[name][ix])
+
+
+def test_torch_restatement_with_corrections():
+    w = _corrected_case(1)
+    mod = O.Model(w.phantom, w.machine, w.plan)
+    D = mod.dose()
+    tm = torch_ref.TorchDose(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso)
+    leaves = torch.tensor(w.plan.leaves, dtype=torch.float64, requires_grad=True)
+    jaws = torch.tensor(w.plan.jaws, dtype=torch.float64, requires_grad=True)
+    mu = torch.tensor(w.plan.mu, dtype=torch.float64, requires_grad=True)
+    Dt = tm.dose(leaves, jaws, mu)
+    np.testing.assert_allclose(Dt.detach().numpy(), D, rtol=0, atol=1e-12 * D.max())
+    g = np.random.default_rng(19).standard_normal(w.phantom.shape)
+    (Dt * torch.from_numpy(g)).sum().backward()
+    dl, dj, dm = mod.dose_grad(g)
+    for a, b in ((leaves.grad.numpy(), dl), (jaws.grad.numpy(), dj), (mu.grad.numpy(), dm)):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
