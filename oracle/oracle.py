@@ -36,7 +36,8 @@ class OrcPlan(C.Structure):
                 ("wmin_leaf", D), ("wmin_jaw", D), ("f_leaf", D), ("f_jaw", D),
                 ("eps_mu", D), ("r_px", C.c_int), ("alpha", (D * 3) * 3), ("beta", (D * 3) * 3),
                 ("n_t", C.c_int), ("dz_t", D), ("t_table", PD), ("cal", D), ("ste", C.c_int),
-                ("pen_fwhm_u", D), ("pen_fwhm_v", D), ("oap", D * 3)]
+                ("pen_fwhm_u", D), ("pen_fwhm_v", D), ("oap", D * 3),
+                ("coll_deg", D)]
 
 
 class OrcLattice(C.Structure):
@@ -126,6 +127,7 @@ class Model:
         pl.pen_fwhm_u = float(getattr(machine, "pen_fwhm_u", 0.0))
         pl.pen_fwhm_v = float(getattr(machine, "pen_fwhm_v", 0.0))
         pl.oap[:] = [float(x) for x in getattr(machine, "off_axis", (1.0, 0.0, 0.0))]
+        pl.coll_deg = float(getattr(machine, "collimator_deg", 0.0))
         self.cplan = pl
         L = OrcLattice()
         lib().orc_lattice_of(C.byref(g), C.byref(pl), C.byref(L))
@@ -192,6 +194,17 @@ class Model:
     def fluence_correct_T(self, G):
         out = _f64(G).copy()
         lib().orc_fluence_correct_T(C.byref(self.cplan), C.byref(self.lat), _p(out))
+        return out
+
+    def rotate(self, F):
+        """Collimator rotation of a lattice map [nv][nu] (bilinear)."""
+        out = np.zeros((self.lat.nv, self.lat.nu))
+        lib().orc_rotate(C.byref(self.cplan), C.byref(self.lat), _p(_f64(F)), _p(out))
+        return out
+
+    def rotate_T(self, G):
+        out = np.zeros((self.lat.nv, self.lat.nu))
+        lib().orc_rotate_T(C.byref(self.cplan), C.byref(self.lat), _p(_f64(G)), _p(out))
         return out
 
     def fluence_vjp(self, b, dF, leaves=None, jaws=None):

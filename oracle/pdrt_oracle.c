@@ -76,6 +76,10 @@ typedef struct {
      * 0 = off; off-axis profile OAP(r) = oap[0] + oap[1] r + oap[2] r^2 */
     double pen_fwhm_u, pen_fwhm_v;
     double oap[3];
+    /* collimator angle (Sec. 2.2.2, last paragraph): the corrected map is
+     * turned by coll_deg in the (u, v) plane about the central axis before the
+     * projection; 0 = off */
+    double coll_deg;
 } orc_plan;
 
 typedef struct {
@@ -284,7 +288,48 @@ double orc_off_axis(const orc_plan *p, double u, double v)
     return p->oap[0] + p->oap[1] * r + p->oap[2] * r * r;
 }
 
-/* Penumbra then off-axis profile, in place on F [nv][nu]. */
+/* Source position, in fractional lattice indices, that the collimator
+ * rotation brings to lattice pixel (a, c).  A feature of the unrotated map at
+ * s = (u, v) appears at R(theta) s, so pixel x reads the map at R(-theta) x:
+ *   u' = cos(theta) u + sin(theta) v,   v' = -sin(theta) u + cos(theta) v. */
+void orc_rotation_source(const orc_plan *p, const orc_lattice *L, int a, int c, double *fa,
+                         double *fc)
+{
+    double th = p->coll_deg * ORC_PI / 180.0;
+    double u = (a - L->cu) * L->du, v = (c - L->cv) * L->dv;
+    double us = cos(th) * u + sin(th) * v, vs = -sin(th) * u + cos(th) * v;
+    *fa = L->cu + us / L->du;
+    *fc = L->cv + vs / L->dv;
+}
+
+static double bilinear2(const double *F, int nu, int nv, double fa, double fc);
+static void bilinear2_T(double *F, int nu, int nv, double fa, double fc, double val);
+
+/* out [nv][nu] = F turned by the collimator angle (bilinear, zero outside
+ * the lattice). */
+void orc_rotate(const orc_plan *p, const orc_lattice *L, const double *F, double *out)
+{
+    for (int c = 0; c < L->nv; ++c)
+        for (int a = 0; a < L->nu; ++a) {
+            double fa, fc;
+            orc_rotation_source(p, L, a, c, &fa, &fc);
+            out[(long)c * L->nu + a] = bilinear2(F, L->nu, L->nv, fa, fc);
+        }
+}
+
+/* out = rotate^T G (out is overwritten). */
+void orc_rotate_T(const orc_plan *p, const orc_lattice *L, const double *G, double *out)
+{
+    memset(out, 0, sizeof(double) * L->nu * L->nv);
+    for (int c = 0; c < L->nv; ++c)
+        for (int a = 0; a < L->nu; ++a) {
+            double fa, fc;
+            orc_rotation_source(p, L, a, c, &fa, &fc);
+            bilinear2_T(out, L->nu, L->nv, fa, fc, G[(long)c * L->nu + a]);
+        }
+}
+
+/* Penumbra, off-axis profile, then collimator rotation, in place on F [nv][nu]. */
 void orc_fluence_correct(const orc_plan *p, const orc_lattice *L, double *F)
 {
     blur_axis(F, L->nu, L->nv, 0, p->pen_fwhm_u, L->du);
@@ -292,11 +337,23 @@ void orc_fluence_correct(const orc_plan *p, const orc_lattice *L, double *F)
     for (int c = 0; c < L->nv; ++c)
         for (int a = 0; a < L->nu; ++a)
             F[(long)c * L->nu + a] *= orc_off_axis(p, (a - L->cu) * L->du, (c - L->cv) * L->dv);
+    if (p->coll_deg != 0.0) {
+        double *t = (double *)malloc(sizeof(double) * L->nu * L->nv);
+        orc_rotate(p, L, F, t);
+        memcpy(F, t, sizeof(double) * L->nu * L->nv);
+        free(t);
+    }
 }
 
-/* Transpose of orc_fluence_correct (off-axis profile, then the blurs). */
+/* Transpose of orc_fluence_correct (rotation, off-axis profile, then the blurs). */
 void orc_fluence_correct_T(const orc_plan *p, const orc_lattice *L, double *G)
 {
+    if (p->coll_deg != 0.0) {
+        double *t = (double *)malloc(sizeof(double) * L->nu * L->nv);
+        orc_rotate_T(p, L, G, t);
+        memcpy(G, t, sizeof(double) * L->nu * L->nv);
+        free(t);
+    }
     for (int c = 0; c < L->nv; ++c)
         for (int a = 0; a < L->nu; ++a)
             G[(long)c * L->nu + a] *= orc_off_axis(p, (a - L->cu) * L->du, (c - L->cv) * L->dv);
@@ -353,6 +410,42 @@ static void trilinear_T(double *V, int n0, int n1, int n2, double f0, double f1,
                 double w0 = d0 ? t0 : 1.0 - t0;
                 V[((long)i2 * n1 + i1) * n0 + i0] += w2 * w1 * w0 * val;
             }
+        }
+    }
+}
+
+/* Bilinear sample of F [nv][nu] at fractional indices (fa, fc), zero outside. */
+static double bilinear2(const double *F, int nu, int nv, double fa, double fc)
+{
+    double fl0 = floor(fa), fl1 = floor(fc);
+    int a0 = (int)fl0, c0 = (int)fl1;
+    double ta = fa - fl0, tc = fc - fl1;
+    double s = 0.0;
+    for (int dc = 0; dc < 2; ++dc) {
+        int c = c0 + dc;
+        if (c < 0 || c >= nv) continue;
+        for (int da = 0; da < 2; ++da) {
+            int a = a0 + da;
+            if (a < 0 || a >= nu) continue;
+            s += (dc ? tc : 1.0 - tc) * (da ? ta : 1.0 - ta) * F[(long)c * nu + a];
+        }
+    }
+    return s;
+}
+
+/* Adjoint of bilinear2(): F[...] += val * weight */
+static void bilinear2_T(double *F, int nu, int nv, double fa, double fc, double val)
+{
+    double fl0 = floor(fa), fl1 = floor(fc);
+    int a0 = (int)fl0, c0 = (int)fl1;
+    double ta = fa - fl0, tc = fc - fl1;
+    for (int dc = 0; dc < 2; ++dc) {
+        int c = c0 + dc;
+        if (c < 0 || c >= nv) continue;
+        for (int da = 0; da < 2; ++da) {
+            int a = a0 + da;
+            if (a < 0 || a >= nu) continue;
+            F[(long)c * nu + a] += (dc ? tc : 1.0 - tc) * (da ? ta : 1.0 - ta) * val;
         }
     }
 }
@@ -874,7 +967,10 @@ int orc_dose_grad(const orc_grid *g, const orc_plan *p, const double *leaves, co
                 if (c < c0) c0 = c;
                 if (c > c1) c1 = c;
             }
-        if (a1 >= 0 && c1 >= 0) {
+        if (a1 >= 0 && c1 >= 0 && p->coll_deg != 0.0) {
+            /* a turned map can reach any pixel: take the whole lattice */
+            a0 = 0; a1 = L.nu - 1; c0 = 0; c1 = L.nv - 1;
+        } else if (a1 >= 0 && c1 >= 0) {
             int ru = orc_penumbra_radius(p->pen_fwhm_u, L.du), rv = orc_penumbra_radius(p->pen_fwhm_v, L.dv);
             a0 = a0 - ru < 0 ? 0 : a0 - ru;
             a1 = a1 + ru >= L.nu ? L.nu - 1 : a1 + ru;

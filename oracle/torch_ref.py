@@ -192,7 +192,8 @@ class TorchDose:
         return torch.from_numpy(B)
 
     def correct(self, F):
-        """Penumbra blurs along u then v, then the off-axis profile (Sec. 2.2.2)."""
+        """Penumbra blurs along u then v, the off-axis profile, then the
+        collimator rotation (Sec. 2.2.2)."""
         L, m = self.L, self.m
         Bu = self._blur_matrix(L["nu"], L["du"], getattr(m, "pen_fwhm_u", 0.0))
         Bv = self._blur_matrix(L["nv"], L["dv"], getattr(m, "pen_fwhm_v", 0.0))
@@ -204,7 +205,33 @@ class TorchDose:
         u = (np.arange(L["nu"]) - L["cu"]) * L["du"]
         v = (np.arange(L["nv"]) - L["cv"]) * L["dv"]
         r = np.sqrt(u[None, :] ** 2 + v[:, None] ** 2)
-        return F * torch.from_numpy(c[0] + c[1] * r + c[2] * r * r)
+        F = F * torch.from_numpy(c[0] + c[1] * r + c[2] * r * r)
+        th = math.radians(getattr(m, "collimator_deg", 0.0))
+        if th != 0.0:
+            F = self._rotation(th, u, v) @ F.reshape(-1, 1)
+            F = F.reshape(L["nv"], L["nu"])
+        return F
+
+    def _rotation(self, th, u, v):
+        """Sparse bilinear resampling matrix of the collimator rotation: the
+        map at pixel x is read at R(-th) x (zero outside the lattice)."""
+        L = self.L
+        nu, nv = L["nu"], L["nv"]
+        U, V = np.meshgrid(u, v)                          # (nv, nu)
+        fa = L["cu"] + (math.cos(th) * U + math.sin(th) * V) / L["du"]
+        fc = L["cv"] + (-math.sin(th) * U + math.cos(th) * V) / L["dv"]
+        a0, c0 = np.floor(fa), np.floor(fc)
+        ta, tc = fa - a0, fc - c0
+        rows, cols, vals = [], [], []
+        dst = np.arange(nu * nv).reshape(nv, nu)
+        for dc, wc in ((0, 1 - tc), (1, tc)):
+            for da, wa in ((0, 1 - ta), (1, ta)):
+                aa, cc = a0.astype(int) + da, c0.astype(int) + dc
+                ok = (aa >= 0) & (aa < nu) & (cc >= 0) & (cc < nv)
+                rows.append(dst[ok]); cols.append((cc * nu + aa)[ok]); vals.append((wa * wc)[ok])
+        idx = torch.from_numpy(np.stack([np.concatenate(rows), np.concatenate(cols)]))
+        return torch.sparse_coo_tensor(idx, torch.from_numpy(np.concatenate(vals)), (nu * nv, nu * nv),
+                                       check_invariants=True)
 
     def project(self, leaves_b, jaws_b, mu_b):
         m = self.m

@@ -55,6 +55,7 @@ class Machine:
     pen_fwhm_u: float = 0.0
     pen_fwhm_v: float = 0.0
     off_axis: tuple = (1.0, 0.0, 0.0)
+    collimator_deg: float = 0.0   # collimator angle of every control point
 
     @property
     def n_pairs(self) -> int:
@@ -131,13 +132,15 @@ def machine_model(seed: int, r_px: int, n_t: int = 501, dz_t: float = 1.0,
     return Machine(r_px=int(r_px), alpha=alpha, beta=beta, t_table=t, dz_t=dz_t)
 
 
-def with_corrections(m: Machine, seed: int, pen=(4.0, 6.0)) -> Machine:
+def with_corrections(m: Machine, seed: int, pen=(4.0, 6.0), collimator_deg: float = 0.0) -> Machine:
     """Seeded source-penumbra widths (FWHM, mm) and a mildly horned off-axis
-    profile (a few per cent over 100 mm), as commissioned beam models have."""
+    profile (a few per cent over 100 mm), as commissioned beam models have,
+    and the given collimator angle."""
     rng = np.random.default_rng(seed)
     m.pen_fwhm_u = float(pen[0] * rng.uniform(0.8, 1.2))
     m.pen_fwhm_v = float(pen[1] * rng.uniform(0.8, 1.2))
     m.off_axis = (1.0, float(rng.uniform(1e-4, 3e-4)), float(rng.uniform(-2e-6, 2e-6)))
+    m.collimator_deg = float(collimator_deg)
     return m
 
 

@@ -1,5 +1,6 @@
 """Pins of the fluence corrections of Sec. 2.2.2 beyond transmission (source
-penumbra and off-axis profile) in the oracle, and of their adjoint."""
+penumbra, off-axis profile, collimator rotation) in the oracle, and of their
+adjoint."""
 import math
 
 import numpy as np
@@ -11,12 +12,13 @@ from oracle import torch_ref
 from paper_2512_18863_gb300 import synth as S
 
 
-def _model(pen_u=4.0, pen_v=6.0, oap=(1.0, 0.0, 0.0), n=(41, 9, 41), ste=1):
+def _model(pen_u=4.0, pen_v=6.0, oap=(1.0, 0.0, 0.0), n=(41, 9, 41), ste=1, coll=0.0, sz=2.5):
     nz, ny, nx = n
-    ph = S.Phantom(hu=np.zeros(n, np.float32), spacing=(2.0, 2.0, 2.5),
-                   origin=(-(nx // 2) * 2.0, -(ny // 2) * 2.0, -(nz // 2) * 2.5))
+    ph = S.Phantom(hu=np.zeros(n, np.float32), spacing=(2.0, 2.0, sz),
+                   origin=(-(nx // 2) * 2.0, -(ny // 2) * 2.0, -(nz // 2) * sz))
     m = S.machine_model(61, r_px=3)
     m.pen_fwhm_u, m.pen_fwhm_v, m.off_axis, m.ste = pen_u, pen_v, oap, ste
+    m.collimator_deg = coll
     return O.Model(ph, m, S.static_field(m)), m
 
 
@@ -62,18 +64,77 @@ def test_corrections_dot_product():
     assert abs(a - b) <= 1e-12 * abs(a)
 
 
-def _corrected_case(ste):
+def test_collimator_rotation_zero_is_identity():
+    mod, _ = _model(pen_u=0.0, pen_v=0.0, coll=0.0, sz=2.0)
+    F = np.random.default_rng(5).random((mod.lattice["nv"], mod.lattice["nu"]))
+    np.testing.assert_array_equal(mod.rotate(F), F)
+
+
+@pytest.mark.parametrize("coll", [90.0, 180.0, -90.0])
+def test_collimator_quarter_turns_permute_pixels(coll):
+    """With square pixels and the isocentre on a pixel centre, quarter turns
+    move pixels onto pixels: a feature at (u, v) lands at R(coll) (u, v); for
+    +90 deg an opening on the +u side appears on the +v side."""
+    mod, _ = _model(pen_u=0.0, pen_v=0.0, coll=coll, sz=2.0)
+    L = mod.lattice
+    assert L["du"] == L["dv"] and float(L["cu"]).is_integer() and float(L["cv"]).is_integer()
+    nu, nv, cu, cv = L["nu"], L["nv"], int(L["cu"]), int(L["cv"])
+    F = np.zeros((nv, nu))
+    rng = np.random.default_rng(7)
+    F[cv - 6:cv + 7, cu - 6:cu + 7] = rng.random((13, 13))   # asymmetric, well inside
+    G = mod.rotate(F)
+    q = int(round(coll / 90.0)) % 4
+    for c in range(cv - 8, cv + 9):
+        for a in range(cu - 8, cu + 9):
+            du_, dv_ = a - cu, c - cv
+            # source pixel R(-coll) (du_, dv_)
+            src = {0: (du_, dv_), 1: (dv_, -du_), 2: (-du_, -dv_), 3: (-dv_, du_)}[q]
+            assert G[c, a] == pytest.approx(F[cv + src[1], cu + src[0]], abs=1e-12)
+    if q == 1:
+        P = np.zeros((nv, nu)); P[cv, cu + 5] = 1.0
+        assert mod.rotate(P)[cv + 5, cu] == pytest.approx(1.0, abs=1e-12)
+
+
+def test_collimator_rotation_of_a_radial_map_within_interpolation_bound():
+    """A map that depends on r only is unchanged by a turn up to the bilinear
+    interpolation error, |err| <= (h^2 / 8) (|f_aa| + |f_cc|) with h = 1 pixel."""
+    mod, _ = _model(pen_u=0.0, pen_v=0.0, coll=37.0, sz=2.0)
+    L = mod.lattice
+    a = np.arange(L["nu"]) - L["cu"]
+    c = np.arange(L["nv"]) - L["cv"]
+    s = 6.0   # pixels
+    F = np.exp(-(a[None, :] ** 2 + c[:, None] ** 2) / (2 * s * s))
+    G = mod.rotate(F)
+    bound = 2.0 / 8.0 / (s * s)          # |f''| <= 1/s^2 per axis for a unit Gaussian
+    inner = (np.abs(a[None, :]) < L["cu"] - 3) & (np.abs(c[:, None]) < L["cv"] - 3)
+    assert np.abs(G - F)[inner].max() <= bound
+    assert np.abs(G - F)[inner].max() > 0.0
+
+
+def test_collimator_rotation_dot_product():
+    mod, _ = _model(coll=23.0)
+    L = mod.lattice
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((L["nv"], L["nu"]))
+    y = rng.standard_normal((L["nv"], L["nu"]))
+    a, b = np.vdot(mod.rotate(x), y), np.vdot(x, mod.rotate_T(y))
+    assert abs(a - b) <= 1e-12 * abs(a)
+    a, b = np.vdot(mod.fluence_correct(x), y), np.vdot(x, mod.fluence_correct_T(y))
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def _corrected_case(ste, coll=0.0):
     w = S.small_pelvis(seed=63, n=(12, 20, 20), spacing=4.0, n_cp=3, r_px=3,
                        ptv_radii=(14.0, 12.0, 14.0))
-    S.with_corrections(w.machine, 5)
+    S.with_corrections(w.machine, 5, collimator_deg=coll)
     w.machine.ste = ste
     return w
 
 
-@pytest.mark.parametrize("ste", [1, 0])
-def test_gradient_with_corrections_vs_central_fd(ste):
+@pytest.mark.parametrize("ste,coll", [(1, 0.0), (0, 0.0), (1, 17.0)])
+def test_gradient_with_corrections_vs_central_fd(ste, coll):
     from tests.test_oracle_adjoint import _pick_params
-    w = _corrected_case(ste)
+    w = _corrected_case(ste, coll)
     mod = O.Model(w.phantom, w.machine, w.plan)
     rng = np.random.default_rng(17)
     g = rng.standard_normal(w.phantom.shape)
@@ -93,8 +154,9 @@ def test_gradient_with_corrections_vs_central_fd(ste):
         assert abs(fd - grads[name][ix]) <= 1e-6 * scale[name] + 1e-9 * abs(grads[name][ix])
 
 
-def test_torch_restatement_with_corrections():
-    w = _corrected_case(1)
+@pytest.mark.parametrize("coll", [0.0, 17.0])
+def test_torch_restatement_with_corrections(coll):
+    w = _corrected_case(1, coll)
     mod = O.Model(w.phantom, w.machine, w.plan)
     D = mod.dose()
     tm = torch_ref.TorchDose(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso)
