@@ -51,6 +51,7 @@ extern "C" {
 
 #define PDRT_MAX_PAIRS 160        /* leaf pairs per bank */
 #define PDRT_MAX_RADIUS_PX 44     /* kernel half-window, pixels */
+#define PDRT_MAX_PEN_RADIUS_PX 16 /* source-penumbra blur half-window ceil(3 sigma / pitch) */
 #define PDRT_MAX_DEPTH_TABLE 4096 /* depth-dose table entries */
 #define PDRT_MAX_HU_POINTS 32     /* HU -> density calibration points */
 
@@ -96,6 +97,18 @@ typedef enum {
  *   ste             1: the projection of Sec. 2.2.1 is the identity in the
  *                   backward pass (straight-through estimator); 0: exact
  *                   Jacobian (zero gradient through active clamps).
+ *   pen_fwhm_u_mm, pen_fwhm_v_mm  source penumbra (Sec. 2.2.2): the aperture
+ *                   fluence is blurred along e_u, then along e_v, by a discrete
+ *                   Gaussian exp(-(t pitch)^2 / (2 sigma^2)), sigma = FWHM /
+ *                   (2 sqrt(2 ln 2)), |t| <= ceil(3 sigma / pitch), normalised
+ *                   to unit sum, zero outside the lattice. 0 = no blur.
+ *   off_axis[3]     off-axis profile (Sec. 2.2.2): the blurred map is
+ *                   multiplied by c0 + c1 r + c2 r^2, r = distance (mm) of the
+ *                   pixel centre from the central axis. (1, 0, 0) = off.
+ *   collimator_deg  collimator angle of every control point (Sec. 2.2.2, last
+ *                   paragraph): the corrected map is turned by this angle in the
+ *                   (e_u, e_v) plane; pixel x reads it bilinearly at R(-angle) x,
+ *                   zero outside the lattice. 0 = off.
  */
 typedef struct {
     double sid_mm;
@@ -113,6 +126,9 @@ typedef struct {
     double depth_dose[PDRT_MAX_DEPTH_TABLE];
     double cal;
     int32_t ste;
+    double pen_fwhm_u_mm, pen_fwhm_v_mm;
+    double off_axis[3];
+    double collimator_deg;
 } pdrt_machine;
 
 /* Beam-frame lattice and scratch layout of a plan (host-side query). */

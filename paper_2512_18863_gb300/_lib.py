@@ -40,7 +40,9 @@ class pdrt_machine(C.Structure):
                 ("kernel_radius_px", C.c_int32), ("kernel_alpha", (C.c_double * 3) * 3),
                 ("kernel_beta", (C.c_double * 3) * 3), ("n_depth", C.c_int32),
                 ("depth_step_mm", C.c_double), ("depth_dose", C.c_double * MAX_DEPTH_TABLE),
-                ("cal", C.c_double), ("ste", C.c_int32)]
+                ("cal", C.c_double), ("ste", C.c_int32),
+                ("pen_fwhm_u_mm", C.c_double), ("pen_fwhm_v_mm", C.c_double),
+                ("off_axis", C.c_double * 3), ("collimator_deg", C.c_double)]
 
 
 class pdrt_plan_info(C.Structure):
@@ -309,4 +311,8 @@ def machine_struct(machine) -> pdrt_machine:
         m.depth_dose[i] = float(x)
     m.cal = float(machine.cal)
     m.ste = int(machine.ste)
+    m.pen_fwhm_u_mm = float(getattr(machine, "pen_fwhm_u", 0.0))
+    m.pen_fwhm_v_mm = float(getattr(machine, "pen_fwhm_v", 0.0))
+    m.off_axis[:] = [float(x) for x in getattr(machine, "off_axis", (1.0, 0.0, 0.0))]
+    m.collimator_deg = float(getattr(machine, "collimator_deg", 0.0))
     return m

@@ -164,6 +164,41 @@ void needed_range(const double fu[4], const double fw[4], int k, int nu, int &lo
 void pdrt::internal_set_error(const char *msg) { g_last_error = msg ? msg : ""; }
 void pdrt::internal_count_launch() { g_launches.fetch_add(1); }
 
+// Penumbra taps, off-axis profile and collimator rotation of a machine
+// (Sec. 2.2.2) in device form; returns an error text or NULL.  The Gaussian
+// taps are evaluated and normalised in double precision on the host.
+const char *pdrt::machine_corrections(const pdrt_machine *m, double du, double dv, MachineDev &M)
+{
+    const double fw[2] = {m->pen_fwhm_u_mm, m->pen_fwhm_v_mm}, pitch[2] = {du, dv};
+    int rb[2] = {0, 0};
+    for (int ax = 0; ax < 2; ++ax) {
+        float *taps = ax ? M.gv : M.gu;
+        for (int t = 0; t < 2 * PDRT_MAX_PEN_RADIUS_PX + 1; ++t) taps[t] = 0.f;
+        if (!(fw[ax] > 0)) continue;
+        const double sigma = fw[ax] / (2.0 * sqrt(2.0 * log(2.0)));
+        const double r = ceil(3.0 * sigma / pitch[ax]);
+        if (r > PDRT_MAX_PEN_RADIUS_PX) return "penumbra blur wider than PDRT_MAX_PEN_RADIUS_PX pixels";
+        rb[ax] = (int)r;
+        double w[2 * PDRT_MAX_PEN_RADIUS_PX + 1], sum = 0.0;
+        for (int t = -rb[ax]; t <= rb[ax]; ++t) {
+            const double x = t * pitch[ax];
+            w[t + rb[ax]] = exp(-x * x / (2.0 * sigma * sigma));
+            sum += w[t + rb[ax]];
+        }
+        for (int t = 0; t <= 2 * rb[ax]; ++t) taps[t] = (float)(w[t] / sum);
+    }
+    M.rbu = rb[0];
+    M.rbv = rb[1];
+    for (int q = 0; q < 3; ++q) M.oap[q] = (float)m->off_axis[q];
+    const bool oap_on = !(m->off_axis[0] == 1.0 && m->off_axis[1] == 0.0 && m->off_axis[2] == 0.0);
+    M.rot = m->collimator_deg != 0.0 ? 1 : 0;
+    const double th = m->collimator_deg * M_PI / 180.0;
+    M.rot_c = (float)cos(th);
+    M.rot_s = (float)sin(th);
+    M.corr = (M.rbu > 0 || M.rbv > 0 || oap_on || M.rot) ? 1 : 0;
+    return nullptr;
+}
+
 extern "C" {
 
 const char *pdrt_last_error(void) { return g_last_error.c_str(); }
@@ -278,6 +313,12 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
                 return fail(PDRT_EINVAL, "kernel polynomial coefficients must be finite");
     for (int i = 0; i < m->n_depth; ++i)
         if (!is_fin(m->depth_dose[i])) return fail(PDRT_EINVAL, "depth-dose entry %d not finite", i);
+    if (!(m->pen_fwhm_u_mm >= 0) || !(m->pen_fwhm_v_mm >= 0) || !is_fin(m->pen_fwhm_u_mm) ||
+        !is_fin(m->pen_fwhm_v_mm))
+        return fail(PDRT_EINVAL, "penumbra FWHM must be non-negative and finite");
+    for (int q = 0; q < 3; ++q)
+        if (!is_fin(m->off_axis[q])) return fail(PDRT_EINVAL, "off-axis coefficients must be finite");
+    if (!is_fin(m->collimator_deg)) return fail(PDRT_EINVAL, "collimator angle must be finite");
     int dev = 0;
     CU_TRY(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev != g->device) return fail(PDRT_EINVAL, "current device differs from the grid's device");
@@ -326,6 +367,10 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     M.depth_step = (float)m->depth_step_mm;
     M.cal = (float)m->cal;
     M.ste = m->ste ? 1 : 0;
+    {
+        const char *why = machine_corrections(m, g->sx, g->sz, M);
+        if (why) return fail(PDRT_EINVAL, "%s", why);
+    }
 
     // ---- per-CP geometry and needed slice ranges
     std::vector<CpGeo> geo(n_cp);
@@ -386,7 +431,7 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     P.cap_o = cap_o;
     P.cap_a = cap_a;
 
-    const size_t fixed = sizeof(float) * 2 * (size_t)n_cp * L.nu * L.nv +
+    const size_t fixed = sizeof(float) * (M.corr ? 3 : 2) * (size_t)n_cp * L.nu * L.nv +
                          sizeof(SliceTab) * (size_t)n_cp * L.nw;
     const size_t budget = scratch_budget_bytes ? scratch_budget_bytes : ((size_t)8 << 30);
     const size_t per_cp = sizeof(float) * (size_t)(cap_o + cap_a);
@@ -416,6 +461,7 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     PLAN_TRY(dalloc(p, &P.slices, (size_t)n_cp * L.nw), "cudaMalloc(slice table)");
     PLAN_TRY(dalloc(p, &P.fbuf, (size_t)n_cp * L.nu * L.nv), "cudaMalloc(fluence)");
     PLAN_TRY(dalloc(p, &P.gfbuf, (size_t)n_cp * L.nu * L.nv), "cudaMalloc(fluence adjoint)");
+    if (M.corr) PLAN_TRY(dalloc(p, &P.tbuf, (size_t)n_cp * L.nu * L.nv), "cudaMalloc(raw fluence)");
     PLAN_TRY(dalloc(p, &P.region, (size_t)chunk * cap_o), "cudaMalloc(beam-frame region)");
     PLAN_TRY(dalloc(p, &P.adjbuf, (size_t)chunk * cap_a), "cudaMalloc(adjoint region)");
     PLAN_TRY(dalloc(p, &P.flags, 1), "cudaMalloc(flags)");

@@ -165,6 +165,78 @@ __device__ void block_sum(float (&v)[N], float *s_red)
     __syncthreads();
 }
 
+// Adjoint of the fluence corrections (collimator rotation, off-axis profile,
+// then the penumbra blurs; transposes in reverse order) for control point b:
+// reads the fluence adjoint in gfbuf over the final box, leaves the raw-map
+// adjoint in fbuf over the raw box (the corrected map there is no longer
+// needed).  The rotation transpose is a pull: every pixel of the blurred box
+// sums the final pixels whose bilinear source stencil contains it, with the
+// forward's own weights (rotation_source).  One block per control point.
+__device__ void uncorrect_adjoint(const PlanDev &P, int b, const CpTab &ct)
+{
+    const MachineDev &M = P.mach;
+    const Lattice &L = P.lat;
+    const long long slot = (long long)b * L.nu * L.nv;
+    const int Ca = ct.ca1 - ct.ca0, Cc = ct.cc1 - ct.cc0;
+    const int Fa = ct.fa1 - ct.fa0, Fc = ct.fc1 - ct.fc0;
+    float *gF = P.gfbuf + slot;
+    float *gb;   // OAP-weighted adjoint of the blurred map over the blurred box
+    __syncthreads();   // every thread is done reading gF for dMU
+    if (M.rot) {
+        gb = P.tbuf + slot;
+        // (a, c) - iso = Minv ((fa, fc) - iso), Minv = [[cos, -sin r], [sin / r, cos]], r = dv/du
+        const float r = L.dv / L.du;
+        const float ha = fabsf(M.rot_c) + fabsf(M.rot_s) * r + 0.01f;
+        const float hc = fabsf(M.rot_s) / r + fabsf(M.rot_c) + 0.01f;
+        for (int t = threadIdx.x; t < Ca * Cc; t += blockDim.x) {
+            const int ap = ct.ca0 + t / Cc, cp = ct.cc0 + t % Cc;
+            const float xa = (float)ap - L.cu, xc = (float)cp - L.cv;
+            const float a_s = L.cu + M.rot_c * xa - M.rot_s * r * xc;
+            const float c_s = L.cv + M.rot_s / r * xa + M.rot_c * xc;
+            const int alo = max((int)ceilf(a_s - ha), ct.fa0), ahi = min((int)floorf(a_s + ha), ct.fa1 - 1);
+            const int clo = max((int)ceilf(c_s - hc), ct.fc0), chi = min((int)floorf(c_s + hc), ct.fc1 - 1);
+            float s = 0.f;
+            for (int c = clo; c <= chi; ++c)
+                for (int a = alo; a <= ahi; ++a) {
+                    float fa, fc;
+                    rotation_source(M, L, a, c, fa, fc);
+                    const float ba = floorf(fa), bc = floorf(fc);
+                    const int ia = (int)ba, ic = (int)bc;
+                    const float wa = (ap == ia) ? 1.f - (fa - ba) : ((ap == ia + 1) ? fa - ba : 0.f);
+                    const float wc = (cp == ic) ? 1.f - (fc - bc) : ((cp == ic + 1) ? fc - bc : 0.f);
+                    if (wa != 0.f && wc != 0.f)
+                        s = fmaf(wa * wc, gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)], s);
+                }
+            gb[t] = s * off_axis_factor(M, L, ap, cp);
+        }
+    } else {
+        gb = gF;   // final box = blurred box
+        for (int t = threadIdx.x; t < Ca * Cc; t += blockDim.x)
+            gb[t] *= off_axis_factor(M, L, ct.ca0 + t / Cc, ct.cc0 + t % Cc);
+    }
+    __syncthreads();
+    // transposed blurs: raw(a, c) <- sum_s gv[s] sum_t gu[t] gb(a + t, c + s)
+    float *graw = P.fbuf + slot;
+    const int Ra = ct.ra1 - ct.ra0, Rc = ct.rc1 - ct.rc0;
+    for (int t = threadIdx.x; t < Ra * Rc; t += blockDim.x) {
+        const int a = ct.ra0 + t / Rc, c = ct.rc0 + t % Rc;
+        float s = 0.f;
+        for (int dv = -M.rbv; dv <= M.rbv; ++dv) {
+            const int cs = c + dv;
+            if (cs < ct.cc0 || cs >= ct.cc1) continue;
+            float q = 0.f;
+            for (int du = -M.rbu; du <= M.rbu; ++du) {
+                const int as = a + du;
+                if (as < ct.ca0 || as >= ct.ca1) continue;
+                q = fmaf(M.gu[du + M.rbu], gb[(long long)(as - ct.ca0) * Cc + (cs - ct.cc0)], q);
+            }
+            s = fmaf(M.gv[dv + M.rbv], q, s);
+        }
+        graw[t] = s;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) k_param_grad(PlanDev P, const float *__restrict__ leaves,
                                                     const float *__restrict__ jaws,
                                                     const float *__restrict__ mu,
@@ -193,18 +265,34 @@ __global__ void __launch_bounds__(256) k_param_grad(PlanDev P, const float *__re
     }
     __syncthreads();
     const CpTab ct = P.cptab[b];
-    const int Fa = ct.fa1 - ct.fa0, Fc = ct.fc1 - ct.fc0;
-    const float *gF = P.gfbuf + (long long)b * L.nu * L.nv;
-    const float *F = P.fbuf + (long long)b * L.nu * L.nv;
     const float dscale = ct.cal_mu;   // dL/dF = cal MU^ g_F
     const float hdv = 0.5f * L.dv;
-    // dMU^ and the four jaw edges: reduction over the support box
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    // g: adjoint of the raw aperture map over the box [ga0,ga1) x [gc0,gc1)
+    const float *g_raw;
+    int ga0, ga1, gc0, gc1;
+    if (M.corr) {
+        // dMU^ on the corrected map, then the adjoint back through the corrections
+        const int Fa = ct.fa1 - ct.fa0, Fc = ct.fc1 - ct.fc0;
+        const float *gF = P.gfbuf + (long long)b * L.nu * L.nv;
+        const float *F = P.fbuf + (long long)b * L.nu * L.nv;
+        for (int t = threadIdx.x; t < Fa * Fc; t += blockDim.x) acc[0] = fmaf(gF[t], F[t], acc[0]);
+        uncorrect_adjoint(P, b, ct);
+        g_raw = P.fbuf + (long long)b * L.nu * L.nv;
+        ga0 = ct.ra0; ga1 = ct.ra1; gc0 = ct.rc0; gc1 = ct.rc1;
+    } else {
+        g_raw = P.gfbuf + (long long)b * L.nu * L.nv;
+        ga0 = ct.fa0; ga1 = ct.fa1; gc0 = ct.fc0; gc1 = ct.fc1;
+    }
+    const int Fa = ga1 - ga0, Fc = gc1 - gc0;
+    const float *gF = g_raw;
+    const float *F = P.fbuf + (long long)b * L.nu * L.nv;
+    // dMU^ (no corrections) and the four jaw edges: reduction over the box
     if (Fa > 0 && Fc > 0) {
         for (int t = threadIdx.x; t < Fa * Fc; t += blockDim.x) {
-            const int a = ct.fa0 + t / Fc, c = ct.fc0 + t % Fc;
+            const int a = ga0 + t / Fc, c = gc0 + t % Fc;
             const float g = gF[t];
-            acc[0] = fmaf(g, F[t], acc[0]);
+            if (!M.corr) acc[0] = fmaf(g, F[t], acc[0]);
             const float u = ((float)a - L.cu) * L.du, v = ((float)c - L.cv) * L.dv;
             const float fx = overlap_f(u, s_j[0], s_j[1], L.du);
             const float fy = overlap_f(v, s_j[2], s_j[3], L.dv);
@@ -253,21 +341,21 @@ __global__ void __launch_bounds__(256) k_param_grad(PlanDev P, const float *__re
         if (Fa > 0 && Fc > 0) {
             const float lb0 = s_lb[i], lb1 = s_lb[i + 1];
             // rows c whose pixel [v - dv/2, v + dv/2] overlaps the strip
-            const int c_lo = max((int)floorf(L.cv + lb0 / L.dv - 0.5f), ct.fc0);
-            const int c_hi = min((int)ceilf(L.cv + lb1 / L.dv + 0.5f) + 1, ct.fc1);
+            const int c_lo = max((int)floorf(L.cv + lb0 / L.dv - 0.5f), gc0);
+            const int c_hi = min((int)ceilf(L.cv + lb1 / L.dv + 0.5f) + 1, gc1);
             for (int c = c_lo; c < c_hi; ++c) {
                 const float v = ((float)c - L.cv) * L.dv;
                 const float om = overlap_f(v, lb0, lb1, L.dv);
                 if (om <= 0.f) continue;
                 const float fy = overlap_f(v, s_j[2], s_j[3], L.dv);
                 if (fy <= 0.f) continue;
-                for (int a = ct.fa0; a < ct.fa1; ++a) {
+                for (int a = ga0; a < ga1; ++a) {
                     const float u = ((float)a - L.cu) * L.du;
                     const float dl = overlap_dlo(u, s_lo[i], s_hi[i], L.du);
                     const float dr = overlap_dhi(u, s_lo[i], s_hi[i], L.du);
                     if (dl == 0.f && dr == 0.f) continue;
                     const float fx = overlap_f(u, s_j[0], s_j[1], L.du);
-                    const float s = gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)] * dscale * fx * fy *
+                    const float s = gF[(long long)(a - ga0) * Fc + (c - gc0)] * dscale * fx * fy *
                                     (1.f - M.tau) * om;
                     gl = fmaf(s, dl, gl);
                     gr = fmaf(s, dr, gr);

@@ -92,6 +92,91 @@ __device__ __forceinline__ void support_range(float e0, float e1, float c, float
     if (hi <= lo) lo = hi = 0;
 }
 
+// Box of the pixels whose rotation source falls inside the bilinear reach of
+// the corrected box [ca0,ca1) x [cc0,cc1): sources with a in (ca0-1, ca1) and
+// c in (cc0-1, cc1).  The source rectangle's corners are turned forward by
+// R(angle); one extra pixel on each side absorbs rounding (the exact weights
+// of those pixels are 0).
+__device__ void rotated_box(const MachineDev &M, const Lattice &L, int ca0, int ca1, int cc0,
+                            int cc1, int &a0, int &a1, int &c0, int &c1)
+{
+    const float us[2] = {((float)(ca0 - 1) - L.cu) * L.du, ((float)ca1 - L.cu) * L.du};
+    const float vs[2] = {((float)(cc0 - 1) - L.cv) * L.dv, ((float)cc1 - L.cv) * L.dv};
+    float amin = 1e30f, amax = -1e30f, cmin = 1e30f, cmax = -1e30f;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            const float x = M.rot_c * us[i] - M.rot_s * vs[j];
+            const float y = M.rot_s * us[i] + M.rot_c * vs[j];
+            amin = fminf(amin, x); amax = fmaxf(amax, x);
+            cmin = fminf(cmin, y); cmax = fmaxf(cmax, y);
+        }
+    a0 = max((int)floorf(L.cu + amin / L.du) - 1, 0);
+    a1 = min((int)ceilf(L.cu + amax / L.du) + 2, L.nu);
+    c0 = max((int)floorf(L.cv + cmin / L.dv) - 1, 0);
+    c1 = min((int)ceilf(L.cv + cmax / L.dv) + 2, L.nv);
+    if (a1 <= a0 || c1 <= c0) a0 = a1 = c0 = c1 = 0;
+}
+
+// Fluence corrections of Sec. 2.2.2 after the raw aperture map of control
+// point b is in tbuf over the raw box:
+//   blurred(a, c) = OAP(a, c) sum_s gv[s] sum_t gu[t] raw(a - t, c - s)
+// over the blurred box (the raw map is zero outside its box, which lies in
+// the lattice, so this is the blur along u then v with zero padding), into
+// fbuf, or into gfbuf when the collimator rotation then resamples it into
+// fbuf over the final box.  One block per control point.
+__device__ void correct_fluence(const PlanDev &P, int b)
+{
+    const MachineDev &M = P.mach;
+    const Lattice &L = P.lat;
+    __syncthreads();
+    const CpTab ct = P.cptab[b];
+    const long long slot = (long long)b * L.nu * L.nv;
+    const float *raw = P.tbuf + slot;
+    const int Rc = ct.rc1 - ct.rc0;
+    const int Ca = ct.ca1 - ct.ca0, Cc = ct.cc1 - ct.cc0;
+    float *blur = (M.rot ? P.gfbuf : P.fbuf) + slot;
+    for (int t = threadIdx.x; t < Ca * Cc; t += blockDim.x) {
+        const int a = ct.ca0 + t / Cc, c = ct.cc0 + t % Cc;
+        float s = 0.f;
+        for (int dv = -M.rbv; dv <= M.rbv; ++dv) {
+            const int cs = c - dv;
+            if (cs < ct.rc0 || cs >= ct.rc1) continue;
+            float r = 0.f;
+            for (int du = -M.rbu; du <= M.rbu; ++du) {
+                const int as = a - du;
+                if (as < ct.ra0 || as >= ct.ra1) continue;
+                r = fmaf(M.gu[du + M.rbu], raw[(long long)(as - ct.ra0) * Rc + (cs - ct.rc0)], r);
+            }
+            s = fmaf(M.gv[dv + M.rbv], r, s);
+        }
+        blur[t] = s * off_axis_factor(M, L, a, c);
+    }
+    if (!M.rot) return;
+    __syncthreads();
+    float *F = P.fbuf + slot;
+    const int Fc = ct.fc1 - ct.fc0, Fa = ct.fa1 - ct.fa0;
+    for (int t = threadIdx.x; t < Fa * Fc; t += blockDim.x) {
+        const int a = ct.fa0 + t / Fc, c = ct.fc0 + t % Fc;
+        float fa, fc;
+        rotation_source(M, L, a, c, fa, fc);
+        const float ba = floorf(fa), bc = floorf(fc);
+        const int ia = (int)ba, ic = (int)bc;
+        const float ta = fa - ba, tc = fc - bc;
+        float v = 0.f;
+        for (int dc = 0; dc < 2; ++dc) {
+            const int cc = ic + dc;
+            if (cc < ct.cc0 || cc >= ct.cc1) continue;
+            const float wc = dc ? tc : 1.f - tc;
+            for (int da = 0; da < 2; ++da) {
+                const int aa = ia + da;
+                if (aa < ct.ca0 || aa >= ct.ca1) continue;
+                v = fmaf(wc * (da ? ta : 1.f - ta), blur[(long long)(aa - ct.ca0) * Cc + (cc - ct.cc0)], v);
+            }
+        }
+        F[t] = v;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_raster(PlanDev P, const float *__restrict__ leaves,
                                                 const float *__restrict__ jaws,
                                                 const float *__restrict__ mu)
@@ -131,13 +216,26 @@ __global__ void __launch_bounds__(256) k_raster(PlanDev P, const float *__restri
         CpTab &ct = P.cptab[b];
         ct.mu_hat = muh;
         ct.cal_mu = M.cal * muh;
-        ct.fa0 = a0; ct.fa1 = a1; ct.fc0 = c0; ct.fc1 = c1;
+        ct.ra0 = a0; ct.ra1 = a1; ct.rc0 = c0; ct.rc1 = c1;
+        int ca0 = a0, ca1 = a1, cc0 = c0, cc1 = c1;
+        if (M.corr && a1 > a0) {
+            ca0 = max(a0 - M.rbu, 0); ca1 = min(a1 + M.rbu, L.nu);
+            cc0 = max(c0 - M.rbv, 0); cc1 = min(c1 + M.rbv, L.nv);
+        }
+        ct.ca0 = ca0; ct.ca1 = ca1; ct.cc0 = cc0; ct.cc1 = cc1;
+        if (M.rot && ca1 > ca0) {
+            rotated_box(M, L, ca0, ca1, cc0, cc1, ct.fa0, ct.fa1, ct.fc0, ct.fc1);
+        } else {
+            ct.fa0 = ca0; ct.fa1 = ca1; ct.fc0 = cc0; ct.fc1 = cc1;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0 && s_bad) atomicOr(P.flags, (unsigned)PDRT_FLAG_NAN_INPUT);
     const int a0 = s_box[0], c0 = s_box[2];
     const int Fa = s_box[1] - a0, Fc = s_box[3] - c0;
-    float *F = P.fbuf + (long long)b * L.nu * L.nv;
+    // raw aperture map: straight into the fluence buffer, or into the scratch
+    // map that the corrections read
+    float *F = (M.corr ? P.tbuf : P.fbuf) + (long long)b * L.nu * L.nv;
     const float hdv = 0.5f * L.dv;
     for (int t = threadIdx.x; t < Fa * Fc; t += blockDim.x) {
         const int a = a0 + t / Fc, c = c0 + t % Fc;
@@ -162,6 +260,7 @@ __global__ void __launch_bounds__(256) k_raster(PlanDev P, const float *__restri
         }
         F[(long long)(a - a0) * Fc + (c - c0)] = val;
     }
+    if (M.corr) correct_fluence(P, b);
 }
 
 cudaError_t launch_raster(const PlanDev &P, const float *leaves, const float *jaws,

@@ -157,6 +157,7 @@ extern "C" pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int
     M.depth_step = (float)m->depth_step_mm;
     M.cal = (float)m->cal;
     M.ste = m->ste ? 1 : 0;
+    if (const char *why = machine_corrections(m, sx, sz, M)) return err(PDRT_EINVAL, why);
 
     // geometry of the control point and the needed slice ranges (host, double)
     const double px0 = (iso_mm[0] - origin_mm[0]) / sx, py0 = (iso_mm[1] - origin_mm[1]) / sy;
@@ -198,6 +199,9 @@ extern "C" pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int
     const size_t o_slices = take(sizeof(SliceTab) * L.nw);
     const size_t o_f = take(sizeof(float) * (size_t)L.nu * L.nv);
     const size_t o_region = take(sizeof(float) * (size_t)cap_o);
+    // corrections: raw map and blurred map scratch
+    const size_t o_t = M.corr ? take(sizeof(float) * (size_t)L.nu * L.nv) : 0;
+    const size_t o_g = M.corr ? take(sizeof(float) * (size_t)L.nu * L.nv) : 0;
     if (off > (size_t)PDRT_STATIC_SCRATCH_BYTES) {
         char msg[256];
         snprintf(msg, sizeof(msg),
@@ -253,6 +257,10 @@ extern "C" pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int
     P.cptab = reinterpret_cast<CpTab *>(base + o_cptab);
     P.slices = reinterpret_cast<SliceTab *>(base + o_slices);
     P.fbuf = reinterpret_cast<float *>(base + o_f);
+    if (M.corr) {
+        P.tbuf = reinterpret_cast<float *>(base + o_t);
+        P.gfbuf = reinterpret_cast<float *>(base + o_g);
+    }
     P.region = reinterpret_cast<float *>(base + o_region);
     P.cap_o = cap_o;
     P.cap_a = 1LL << 62;   // forward only: the adjoint buffer is never touched

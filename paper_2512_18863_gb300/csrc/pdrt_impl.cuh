@@ -7,6 +7,8 @@
 //   slices [n_cp][nw]        per-call slice table (depth, kernel, boxes, offsets)
 //   fbuf   [n_cp][nu*nv]     fluence maps over their support boxes, [a][c] (c fastest)
 //   gfbuf  [n_cp][nu*nv]     adjoint of the fluence maps, same layout
+//   tbuf   [n_cp][nu*nv]     raw aperture map / its adjoint when the fluence
+//                            corrections are on (each map over its own box)
 //   region [chunk][cap_o]    beam-frame dose D' (forward) or gathered gradient h
 //                            (adjoint) of one chunk of CPs; each slice's box is
 //                            stored [j][i] (i fastest) at slices[].off_o
@@ -55,6 +57,14 @@ struct MachineDev {
     float depth_step;
     float cal;
     int ste;
+    // fluence corrections (Sec. 2.2.2); corr = 0 skips all of them
+    int corr;
+    int rbu, rbv;                                  // penumbra half-windows (0 = no blur)
+    float gu[2 * PDRT_MAX_PEN_RADIUS_PX + 1];      // normalised Gaussian taps, index t + rb
+    float gv[2 * PDRT_MAX_PEN_RADIUS_PX + 1];
+    float oap[3];                                  // off-axis profile c0 + c1 r + c2 r^2
+    int rot;                                       // collimator rotation on
+    float rot_c, rot_s;                            // cos, sin of the collimator angle
 };
 
 struct CpGeo {
@@ -71,6 +81,8 @@ struct CpTab {
     float mu_hat;         // projected MU
     float cal_mu;         // cal * mu_hat
     int fa0, fa1, fc0, fc1;  // fluence support box [fa0,fa1) x [fc0,fc1) (pixels)
+    int ra0, ra1, rc0, rc1;  // raw aperture box (jaw support) before the corrections
+    int ca0, ca1, cc0, cc1;  // blurred box (raw box + penumbra half-windows)
     int ui0, ui1, vj0, vj1;  // union over slices of the output boxes (gather culling)
     int k0, k1;           // slices with work [k0,k1)
     long long tot_o, tot_a;  // floats used in the region / adjoint buffers
@@ -105,6 +117,7 @@ struct PlanDev {
     CpTab *cptab;
     SliceTab *slices;
     float *fbuf, *gfbuf;
+    float *tbuf;             // [n_cp][nu*nv] raw-map scratch of the corrections (NULL if off)
     float *region, *adjbuf;
     long long cap_o, cap_a;  // floats per CP slot
     unsigned int *flags;
@@ -125,6 +138,25 @@ __device__ __forceinline__ void voxel_to_beam(const CpGeo &g, int ix, int iy, fl
 {
     fu = fmaf(g.au, (float)ix, fmaf(g.bu, (float)iy, g.cu0));
     fw = fmaf(g.aw, (float)ix, fmaf(g.bw, (float)iy, g.cw0));
+}
+
+// Off-axis profile factor of lattice pixel (a, c) (Sec. 2.2.2).
+__device__ __forceinline__ float off_axis_factor(const MachineDev &M, const Lattice &L, int a, int c)
+{
+    const float u = ((float)a - L.cu) * L.du, v = ((float)c - L.cv) * L.dv;
+    const float r = sqrtf(u * u + v * v);
+    return fmaf(fmaf(M.oap[2], r, M.oap[1]), r, M.oap[0]);
+}
+
+// Fractional lattice indices that the collimator rotation brings to pixel
+// (a, c): pixel x reads the corrected map at R(-angle) x.  One expression for
+// the forward resampling and its transpose.
+__device__ __forceinline__ void rotation_source(const MachineDev &M, const Lattice &L, int a, int c,
+                                                float &fa, float &fc)
+{
+    const float u = ((float)a - L.cu) * L.du, v = ((float)c - L.cv) * L.dv;
+    fa = L.cu + fmaf(M.rot_c, u, M.rot_s * v) / L.du;
+    fc = L.cv + fmaf(-M.rot_s, u, M.rot_c * v) / L.dv;
 }
 
 __device__ __forceinline__ float overlap_f(float x, float lo, float hi, float d)
@@ -193,6 +225,9 @@ cudaError_t conv_prepare(const MachineDev &m, int *fwd_blocks_per_sm, int *adj_b
 cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
                            int grid_blocks, cudaStream_t s);
 cudaError_t conv_tc_prepare(int R, int *blocks_per_sm);
+// Device form of a machine's fluence corrections (taps, profile, rotation);
+// returns an error text or NULL.  Pitches du, dv in mm.
+const char *machine_corrections(const pdrt_machine *m, double du, double dv, MachineDev &M);
 
 // Raises a kernel's dynamic shared-memory limit to everything the device
 // offers one block and asks for the largest shared-memory carve-out. The

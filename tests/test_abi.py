@@ -64,3 +64,28 @@ def test_null_handles_rejected():
     assert lib.pdrt_plan_upload(C.byref(out), None, 1, None, None, C.byref(m), 0, None) == 1
     info = _lib.pdrt_plan_info()
     assert lib.pdrt_plan_get_info(None, C.byref(info)) == 1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """ctypes mirrors of the header's structs have the C compiler's sizes and
+    field offsets (a host C program built from include/pdrt.h prints them)."""
+    import subprocess
+    structs = {"pdrt_machine": _lib.pdrt_machine, "pdrt_plan_info": _lib.pdrt_plan_info,
+               "pdrt_work": _lib.pdrt_work, "pdrt_tune_result": _lib.pdrt_tune_result}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pdrt.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
