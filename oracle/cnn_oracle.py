@@ -141,3 +141,40 @@ def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     mh = m / (1.0 - beta1 ** t)
     vh = v / (1.0 - beta2 ** t)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def bev_project(bits, spacing, origin, iso, sid, gantry_deg, side, pitch, reach, step):
+    """Beam's-eye-view projection of a uint8 bit-mask volume bits [nz][ny][nx]
+    (the network input): for each gantry angle g and BEV pixel (py, px), the
+    ray from the source S = iso - sid e_w through iso + u e_u + v e_v, with
+    e_w = (sin g, cos g, 0), e_u = (cos g, -sin g, 0), e_v = (0, 0, 1),
+    u = (px - (side-1)/2) pitch, v = (py - (side-1)/2) pitch, is sampled at
+    depths w = -reach, -reach + step, ... (n = floor(2 reach / step) + 1
+    samples) beyond the isocentre plane, i.e. at S + (sid + w) / sid
+    (iso + u e_u + v e_v - S); channel s is 1 where a sample's nearest voxel
+    has bit s.  Returns float64 [n_cp][side][side][3]."""
+    nz, ny, nx = bits.shape
+    out = np.zeros((len(gantry_deg), side, side, 3))
+    half = 0.5 * (side - 1)
+    pu = (np.arange(side) - half) * pitch
+    U, V = np.meshgrid(pu, pu)                      # [py][px]
+    n_steps = int(2.0 * reach / step) + 1
+    for b, g in enumerate(np.deg2rad(np.asarray(gantry_deg, dtype=np.float64))):
+        ew = np.array([np.sin(g), np.cos(g), 0.0])
+        eu = np.array([np.cos(g), -np.sin(g), 0.0])
+        ev = np.array([0.0, 0.0, 1.0])
+        S = np.asarray(iso, dtype=np.float64) - sid * ew
+        P = np.asarray(iso, dtype=np.float64)[None, None, :] + U[..., None] * eu + V[..., None] * ev
+        acc = np.zeros((side, side), dtype=np.uint8)
+        for q in range(n_steps):
+            w = -reach + q * step
+            X = S + (sid + w) / sid * (P - S)
+            idx = [np.rint((X[..., d] - origin[d]) / spacing[d]).astype(np.int64) for d in range(3)]
+            ok = ((idx[0] >= 0) & (idx[0] < nx) & (idx[1] >= 0) & (idx[1] < ny)
+                  & (idx[2] >= 0) & (idx[2] < nz))
+            vals = np.zeros((side, side), dtype=np.uint8)
+            vals[ok] = bits[idx[2][ok], idx[1][ok], idx[0][ok]]
+            acc |= vals
+        for s in range(3):
+            out[b, :, :, s] = (acc >> s) & 1
+    return out

@@ -101,6 +101,21 @@ _SIG = {
     "pdrt_batch_destroy": (None, [_VP]),
     "pdrt_launch_count": (C.c_int64, []),
     "pdrt_last_error": (C.c_char_p, []),
+    # warm-start network (pdrt_cnn.h)
+    "pdrt_cnn_param_count": (C.c_int64, []),
+    "pdrt_cnn_create": (C.c_int, [C.POINTER(_VP), C.c_int32, _VP]),
+    "pdrt_cnn_destroy": (None, [_VP]),
+    "pdrt_cnn_set_params": (C.c_int, [_VP, _VP, _VP]),
+    "pdrt_cnn_get_params": (C.c_int, [_VP, _VP, _VP]),
+    "pdrt_cnn_forward": (C.c_int, [_VP, _VP, C.c_int32, _VP, _VP]),
+    "pdrt_cnn_backward": (C.c_int, [_VP, C.c_int32, _VP, _VP, _VP]),
+    "pdrt_cnn_train_step": (C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_float, _VP, _VP]),
+    "pdrt_cnn_read_activation": (C.c_int, [_VP, C.c_int32, C.c_int32, _VP, _VP]),
+    "pdrt_cnn_status": (C.c_int, [_VP, _VP, C.POINTER(C.c_uint32)]),
+    "pdrt_bev_project": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                   C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.c_double, C.c_int32, C.POINTER(C.c_double), C.c_int32,
+                                   C.c_double, C.c_double, C.c_double, _VP, _VP]),
 }
 
 _lock = threading.Lock()
@@ -316,3 +331,68 @@ def machine_struct(machine) -> pdrt_machine:
     m.off_axis[:] = [float(x) for x in getattr(machine, "off_axis", (1.0, 0.0, 0.0))]
     m.collimator_deg = float(getattr(machine, "collimator_deg", 0.0))
     return m
+
+
+# ---------------------------------------------------------------------------
+# warm-start network (pdrt_cnn.h): argument marshalling only
+# ---------------------------------------------------------------------------
+CNN_SIDE = 64
+CNN_IN_CH = 3
+CNN_OUT = 121
+
+
+def pdrt_cnn_param_count() -> int:
+    return int(load().pdrt_cnn_param_count())
+
+
+def pdrt_cnn_create(batch_max, stream):
+    out = _VP()
+    _check(load().pdrt_cnn_create(C.byref(out), int(batch_max), _VP(stream)))
+    return out.value
+
+
+def pdrt_cnn_destroy(net):
+    if net:
+        load().pdrt_cnn_destroy(_VP(net))
+
+
+def pdrt_cnn_set_params(net, params_dev, stream):
+    _check(load().pdrt_cnn_set_params(_VP(net), _VP(params_dev), _VP(stream)))
+
+
+def pdrt_cnn_get_params(net, params_dev, stream):
+    _check(load().pdrt_cnn_get_params(_VP(net), _VP(params_dev), _VP(stream)))
+
+
+def pdrt_cnn_forward(net, x_dev, n, y_dev, stream):
+    _check(load().pdrt_cnn_forward(_VP(net), _VP(x_dev), int(n), _VP(y_dev), _VP(stream)))
+
+
+def pdrt_cnn_backward(net, n, dy_dev, grads_dev, stream):
+    _check(load().pdrt_cnn_backward(_VP(net), int(n), _VP(dy_dev), _VP(grads_dev), _VP(stream)))
+
+
+def pdrt_cnn_train_step(net, x_dev, target_dev, n, lr, loss_dev, stream):
+    _check(load().pdrt_cnn_train_step(_VP(net), _VP(x_dev), _VP(target_dev), int(n), float(lr),
+                                      _VP(loss_dev), _VP(stream)))
+
+
+def pdrt_cnn_read_activation(net, layer, n, dst_dev, stream):
+    _check(load().pdrt_cnn_read_activation(_VP(net), int(layer), int(n), _VP(dst_dev), _VP(stream)))
+
+
+def pdrt_cnn_status(net, stream) -> int:
+    f = C.c_uint32(0)
+    _check(load().pdrt_cnn_status(_VP(net), _VP(stream), C.byref(f)))
+    return int(f.value)
+
+
+def pdrt_bev_project(masks_dev, nx, ny, nz, spacing, origin, iso, sid, gantry_deg, side, pitch,
+                     reach, step, out_dev, stream):
+    g = (C.c_double * len(gantry_deg))(*[float(x) for x in gantry_deg])
+    _check(load().pdrt_bev_project(_VP(masks_dev), int(nx), int(ny), int(nz), float(spacing[0]),
+                                   float(spacing[1]), float(spacing[2]),
+                                   (C.c_double * 3)(*[float(x) for x in origin]),
+                                   (C.c_double * 3)(*[float(x) for x in iso]), float(sid),
+                                   len(gantry_deg), g, int(side), float(pitch), float(reach),
+                                   float(step), _VP(out_dev), _VP(stream)))

@@ -34,7 +34,7 @@ def _cuda_lib_dir(nvcc: str) -> str:
 
 def _deps() -> list:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh"))
-                  + [os.path.join(INCLUDE, "pdrt.h")])
+                  + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
 def _stale(target: str, deps) -> bool:

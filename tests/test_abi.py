@@ -13,7 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    text = open(os.path.join(ROOT, "include", "pdrt.h")).read()
+    import glob
+    text = "".join(open(f).read() for f in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(pdrt_[a-z_]+)\s*\(", text)))
 
@@ -89,3 +90,20 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[name]) == C.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, f"{name}.{f}"
+
+
+def test_network_parameter_count_and_host_checks():
+    from oracle import cnn_oracle as N
+    from paper_2512_18863_gb300 import warmstart as W
+    p = N.init_params(0)
+    assert _lib.pdrt_cnn_param_count() == sum(v.size for v in p.values()) == 236601
+    assert [k for k, _ in W.param_layout()] == ["W1", "b1", "W2", "b2", "W3", "b3", "W4", "b4",
+                                                 "W5", "b5"]
+    for k, shp in W.param_layout():
+        assert p[k].shape == shp
+    with pytest.raises(_lib.PdrtError) as e:
+        _lib.pdrt_cnn_create(0, 0)
+    assert e.value.status == 1
+    with pytest.raises(_lib.PdrtError):
+        _lib.pdrt_bev_project(0, 4, 4, 4, (1.0, 1.0, 1.0), (0, 0, 0), (0, 0, 0), 1000.0, [0.0], 64,
+                              2.5, 50.0, 1.0, 0, 0)

@@ -108,3 +108,46 @@ def test_mse_and_adam_match_torch():
         opt.step()
         p, m, v = N.adam_step(p, g, m, v, t_, 1e-3)
     np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-12, atol=1e-15)
+
+
+def _ball_bits(center, r, n=(40, 40, 40), sp=(4.0, 4.0, 4.0), bit=0):
+    nz, ny, nx = n
+    origin = (-(nx - 1) / 2 * sp[0], -(ny - 1) / 2 * sp[1], -(nz - 1) / 2 * sp[2])
+    z, y, x = np.meshgrid(*[origin[d] + np.arange(n[2 - d]) * sp[d] for d in (2, 1, 0)], indexing="ij")
+    inside = (x - center[0]) ** 2 + (y - center[1]) ** 2 + (z - center[2]) ** 2 <= r * r
+    bits = np.zeros(n, np.uint8)
+    bits[inside] = 1 << bit
+    return bits, sp, origin
+
+
+def test_bev_projection_of_a_ball_at_the_isocentre_is_a_disc():
+    """A ball of radius r at the isocentre projects to a disc of radius
+    r / sqrt(1 - (r/sid)^2) at the isocentre plane, up to one voxel of
+    voxelisation, at every gantry angle."""
+    r, sid = 40.0, 1000.0
+    bits, sp, origin = _ball_bits((0.0, 0.0, 0.0), r)
+    out = N.bev_project(bits, sp, origin, (0.0, 0.0, 0.0), sid, [0.0, 37.0, 90.0], 64, 2.5, 100.0, 1.0)
+    pu = (np.arange(64) - 31.5) * 2.5
+    rr = np.hypot(*np.meshgrid(pu, pu))
+    R = r / np.sqrt(1 - (r / sid) ** 2)
+    for b in range(3):
+        m = out[b, :, :, 0]
+        assert np.all(m[rr < R - 4.0] == 1) and np.all(m[rr > R + 4.0] == 0)
+        assert np.all(out[b, :, :, 1:] == 0)
+
+
+def test_bev_projection_axes_and_gantry_rotation():
+    """e_u = (cos g, -sin g, 0), e_v = +z: a ball at +x lands at +u for gantry
+    0; a ball at -y lands at +u for gantry 90; a ball at +z lands at +v."""
+    pu = (np.arange(64) - 31.5) * 2.5
+    for center, g, axis in (((40.0, 0.0, 0.0), 0.0, "u"), ((0.0, -40.0, 0.0), 90.0, "u"),
+                            ((0.0, 0.0, 40.0), 0.0, "v")):
+        bits, sp, origin = _ball_bits(center, 15.0, bit=2)
+        m = N.bev_project(bits, sp, origin, (0.0, 0.0, 0.0), 1000.0, [g], 64, 2.5, 100.0, 1.0)[0, :, :, 2]
+        assert m.sum() > 20
+        py, px = np.nonzero(m)
+        cu, cv = pu[px].mean(), pu[py].mean()
+        if axis == "u":
+            assert 30.0 < cu < 50.0 and abs(cv) < 3.0
+        else:
+            assert 30.0 < cv < 50.0 and abs(cu) < 3.0
