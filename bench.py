@@ -47,6 +47,8 @@ def _args():
     ap.add_argument("--cpu-sample-cps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--warm-cases", type=int, default=6,
+                    help="held-out phantoms for the warm-versus-plain figure (0 = skip)")
     ap.add_argument("--workload", default="pelvis256", choices=["pelvis256", "pelvis128", "batch32"],
                     help="pelvis256: 256x256x160 @ 2 mm, 2 x 178 CPs (headline); "
                          "pelvis128: 128x128x96 @ 3 mm, 178 CPs (smaller case for profiler captures); "
@@ -208,6 +210,29 @@ def _reference(args):
         dist.destroy_process_group()
 
 
+def _warm_start(n_cases):
+    """Warm versus plain: dose evaluations the optimiser needs from the trained
+    network's proposal to reach the plain optimiser's best objective in 100
+    evaluations from an open-field start, on held-out phantoms."""
+    import os
+    from paper_2512_18863_gb300 import warmstart as W
+    path = W.default_weights_path()
+    if not os.path.exists(path):
+        return {"unavailable": "no trained weights at " + os.path.relpath(path)}
+    import numpy as np
+    d = np.load(path)
+    seeds = [int(x) for x in d["test_seeds"][:n_cases]]
+    net = W.load_net(path)
+    t0 = time.time()
+    rows = W.evaluate(net, seeds)
+    net.close()
+    out = W.summarise(rows)
+    out.update({"seconds": time.time() - t0, "held_out_seeds": seeds,
+                "trained_on_plans": int(len(d["train_seeds"])),
+                "network": "5-layer BF16 CNN (tcgen05, FP32 accumulate)"})
+    return out
+
+
 def _gpu(args):
     import torch
     import torch.distributed as dist
@@ -328,6 +353,19 @@ def _gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(w, args.cpu_sample_cps)
+    info = eng.info
+    # the literal "vs HBM roofline" figure: bytes the method must move per
+    # step (dose written, its gradient read, parameters and gradients) over
+    # the step time, against the measured copy bandwidth
+    alg_bytes = 4 * (2 * dose.numel() + 2 * (leaves.numel() + jaws.numel() + mu.numel()))
+    hbm_peak = _measured_peaks().get("hbm_gbs", 6800.0)
+    hbm = {"algorithmic_bytes_per_step": alg_bytes,
+           "achieved_gbs": alg_bytes / (ms_max / args.steps / 1e3) / 1e9, "peak_gbs": hbm_peak,
+           "frac": alg_bytes / (ms_max / args.steps / 1e3) / 1e9 / hbm_peak,
+           "note": "the step is bound by the convolution arithmetic, not by HBM"}
+    warm = None
+    if rank == 0 and world == 1 and args.warm_cases > 0:
+        warm = _warm_start(args.warm_cases)
 
     if rank == 0:
         nz, ny, nx = w.phantom.shape
@@ -350,6 +388,10 @@ def _gpu(args):
                             "fp32_alu_frac": achieved / (SMS * FP32_LANES * 2 * 2070.0e6 / 1e12),
                             "tensor_issued_tflops": (mma_flops / (tc_ms / 1e3) / 1e12) if tc_ms else None},
                "kernels": kernels, "work": work, "gpu_launches": launches,
+               "launch": {"tc_ctas_per_sm": info.get("tc_ctas_per_sm"),
+                          "simt_ctas_per_sm": info.get("simt_ctas_per_sm"),
+                          "chunk_cp": info.get("chunk_cp")},
+               "hbm_literal": hbm, "warm_start": warm,
                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     eng.close()

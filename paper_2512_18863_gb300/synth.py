@@ -332,3 +332,19 @@ def uneven_batch(n_plans=32, seed=1003, r_cm=4.0):
         pl = arc_plan(m, ang, seed=seed + q)
         out.append(Workload(f"plan{q}_{nx}x{ny}x{nz}_{sp:g}mm_{n_cp}cp", ph, m, pl))
     return out
+
+
+def warmstart_case(seed: int, n=(32, 56, 80), spacing=5.0, n_cp=36, machine_seed=1004,
+                   r_px=4) -> Workload:
+    """Phantoms of the learned warm start: seeded pelvis with a PTV ellipsoid of
+    radii uniform in [20, 40] mm per axis at an offset uniform in [-15, 15] mm
+    per axis, one machine (kernel radius 2 cm at 5 mm voxels) and an n_cp arc
+    whose jaws conform to the target."""
+    rng = np.random.default_rng(seed)
+    radii = tuple(float(r) for r in rng.uniform(20.0, 40.0, 3))
+    offset = tuple(float(o) for o in rng.uniform(-15.0, 15.0, 3))
+    m = machine_model(machine_seed, r_px=r_px)
+    ph = pelvis_phantom(n, (spacing,) * 3, seed=seed, ptv_radii=radii, ptv_offset=offset)
+    pl = arc_plan(m, arc_angles(n_cp), seed=seed, ptv_radii=radii, ptv_offset=offset)
+    nz, ny, nx = n
+    return Workload(f"warmstart{nx}x{ny}x{nz}_arc{n_cp}_seed{seed}", ph, m, pl)

@@ -206,3 +206,198 @@ def decode_plan(y, machine) -> tuple:
     lv = np.stack([lv.min(-1), lv.max(-1)], -1)
     mu = np.maximum(y[:, 120] * MU_SCALE, machine.eps_mu)
     return lv, mu
+
+
+# ---------------------------------------------------------------------------
+# plans from the engine's optimiser, training, evaluation
+# ---------------------------------------------------------------------------
+N_ITER = 100                 # the paper's iteration count for gradient optimisation
+OPT_LR, OPT_LR_MU = 0.5, 0.05
+
+
+@dataclass
+class Case:
+    work: object
+    engine: DoseEngine
+    masks: dict
+    presc: float
+    open_init: tuple
+
+
+def make_case(seed: int) -> Case:
+    """Phantom, engine and open-field start; the prescription is the mean PTV
+    dose of the open-field start (sets the dose scale of the objective)."""
+    w = S.warmstart_case(seed)
+    eng = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso)
+    masks = {k: w.phantom.masks[k] for k in STRUCTURES}
+    init = open_field_start(w.plan, w.machine)
+    D0 = eng.forward(*init)
+    presc = float(D0[torch.as_tensor(masks["ptv"], device=eng.device)].mean())
+    return Case(w, eng, masks, presc, init)
+
+
+def objective_of(case: Case, leaves, jaws, mu) -> float:
+    """The exact engine's objective value of a parameter set (one forward)."""
+    D = case.engine.forward(leaves, jaws, mu)
+    m = {k: torch.as_tensor(v, device=case.engine.device) for k, v in case.masks.items()}
+    return float(objective_quadratic(D, m, case.presc))
+
+
+def plain_optimise(case: Case, n_iter=N_ITER, target=None):
+    return optimise(case.engine, case.masks, case.presc, case.open_init, n_iter=n_iter, lr=OPT_LR,
+                    lr_mu=OPT_LR_MU, objective="quadratic", target=target)
+
+
+def generate(seeds, n_iter=N_ITER, log=None):
+    """Training pairs from the plain optimiser: inputs BF16 [N][64][64][3] and
+    targets FP32 [N][121] on the device, one row per control point."""
+    xs, ts = [], []
+    t0 = time.time()
+    for i, sd in enumerate(seeds):
+        c = make_case(int(sd))
+        res = plain_optimise(c, n_iter)
+        from .optimize import project_plan
+        lv, _, mu = project_plan(res.leaves, res.jaws, res.mu, c.work.machine)
+        xs.append(bev_inputs(c.work.phantom, c.work.plan.gantry_deg, c.work.plan.iso))
+        ts.append(torch.tensor(encode_plan(lv, mu), dtype=torch.float32, device=xs[-1].device))
+        c.engine.close()
+        if log and (i + 1) % 100 == 0:
+            log(f"generated {i + 1}/{len(seeds)} plans in {time.time() - t0:.1f} s")
+    return torch.cat(xs), torch.cat(ts)
+
+
+def train(net: WarmStartNet, X, T, epochs=30, batch=256, lr=1e-3, seed=0, log=None):
+    """Mini-batch Adam on the MSE (pdrt_cnn_train_step); lr decays by cosine."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    n = X.shape[0]
+    steps = epochs * max(1, n // batch)
+    loss = torch.zeros(1, device=X.device)
+    hist = []
+    k = 0
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g).to(X.device)
+        acc, cnt = 0.0, 0
+        for i in range(0, n - batch + 1, batch):
+            idx = perm[i:i + batch]
+            rate = 0.5 * lr * (1.0 + math.cos(math.pi * k / steps))
+            net.train_step(X[idx], T[idx], rate, loss)
+            k += 1
+            if i % (16 * batch) == 0:
+                acc += float(loss)
+                cnt += 1
+        hist.append(acc / max(cnt, 1))
+        if log:
+            log(f"epoch {ep + 1}/{epochs}: loss {hist[-1]:.5f}")
+    return hist
+
+
+def propose(net: WarmStartNet, case: Case):
+    """The network's (leaves, jaws, MU) for a case; jaws are the plan's."""
+    x = bev_inputs(case.work.phantom, case.work.plan.gantry_deg, case.work.plan.iso)
+    y = net.forward(x).cpu().numpy()
+    lv, mu = decode_plan(y, case.work.machine)
+    return lv, case.open_init[1].copy(), mu
+
+
+def evaluate(net: WarmStartNet, seeds, n_iter=N_ITER):
+    """Warm versus plain on held-out phantoms.  The plain optimiser runs
+    n_iter evaluations from the open-field start; its best objective J* is the
+    target.  The warm start costs one evaluation to judge the proposal
+    against the open-field start (the fallback when the proposal is worse),
+    then optimises until J <= J* (at most n_iter more evaluations)."""
+    rows = []
+    for sd in seeds:
+        c = make_case(int(sd))
+        plain = plain_optimise(c, n_iter)
+        j_star = min(plain.history)
+        plain_evals = int(np.argmin(plain.history)) + 1
+        prop = propose(net, c)
+        j_prop = objective_of(c, *prop)
+        j_open = plain.history[0]
+        start = prop if j_prop <= j_open else c.open_init
+        warm = optimise(c.engine, c.masks, c.presc, start, n_iter=n_iter, lr=OPT_LR, lr_mu=OPT_LR_MU,
+                        objective="quadratic", target=j_star)
+        reached = min(warm.history) <= j_star
+        D_p = c.engine.forward(plain.leaves, plain.jaws, plain.mu)
+        D_w = c.engine.forward(warm.leaves, warm.jaws, warm.mu)
+        rows.append({
+            "seed": int(sd), "j_open": j_open, "j_proposal": j_prop, "j_star": j_star,
+            "fallback": bool(j_prop > j_open), "plain_evals": plain_evals,
+            "warm_evals": 1 + warm.dose_evals, "reached": bool(reached),
+            "dose_diff_rel": float((D_w - D_p).abs().max() / D_p.max()),
+        })
+        c.engine.close()
+    return rows
+
+
+def summarise(rows) -> dict:
+    r = np.array([x["warm_evals"] / x["plain_evals"] for x in rows])
+    return {"cases": len(rows), "median_eval_ratio": float(np.median(r)),
+            "mean_eval_ratio": float(np.mean(r)),
+            "frac_at_most_half": float(np.mean(r <= 0.5)),
+            "reached": int(sum(x["reached"] for x in rows)),
+            "fallbacks": int(sum(x["fallback"] for x in rows)),
+            "median_plain_evals": float(np.median([x["plain_evals"] for x in rows])),
+            "median_warm_evals": float(np.median([x["warm_evals"] for x in rows])),
+            "median_proposal_over_open": float(np.median([x["j_proposal"] / x["j_open"] for x in rows])),
+            "median_dose_diff_rel": float(np.median([x["dose_diff_rel"] for x in rows]))}
+
+
+WEIGHTS_FILE = "warmstart_weights.npz"
+
+
+def default_weights_path() -> str:
+    import os
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", WEIGHTS_FILE)
+
+
+def load_net(path=None, batch_max=256) -> WarmStartNet:
+    d = np.load(path or default_weights_path())
+    return WarmStartNet(batch_max=batch_max, params=d["params"].astype(np.float64))
+
+
+def main(argv=None):
+    """Generate plans with the engine's optimiser, train the network on the
+    GPU, evaluate warm versus plain on held-out phantoms, save the weights."""
+    import argparse
+    import json
+    import os
+    ap = argparse.ArgumentParser(description=main.__doc__)
+    ap.add_argument("--train", type=int, default=2000)
+    ap.add_argument("--test", type=int, default=100)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--iters", type=int, default=N_ITER)
+    ap.add_argument("--out", default=os.path.dirname(default_weights_path()))
+    ap.add_argument("--seed", type=int, default=5000)
+    a = ap.parse_args(argv)
+    os.makedirs(a.out, exist_ok=True)
+    log = lambda s: print(s, flush=True)   # noqa: E731
+    t0 = time.time()
+    train_seeds = a.seed + np.arange(a.train)
+    test_seeds = a.seed + 100000 + np.arange(a.test)
+    X, T = generate(train_seeds, a.iters, log)
+    t_gen = time.time() - t0
+    net = WarmStartNet(batch_max=a.batch, seed=a.seed)
+    t1 = time.time()
+    hist = train(net, X, T, a.epochs, a.batch, a.lr, a.seed, log)
+    torch.cuda.synchronize()
+    t_train = time.time() - t1
+    if net.status() != 0:
+        raise RuntimeError("a tensor-core wait expired during training")
+    params = net.get_params()
+    np.savez(os.path.join(a.out, WEIGHTS_FILE), params=params.astype(np.float32),
+             loss=np.array(hist), train_seeds=train_seeds, test_seeds=test_seeds)
+    rows = evaluate(net, test_seeds, a.iters)
+    summ = summarise(rows)
+    summ.update({"train_plans": int(a.train), "samples": int(X.shape[0]), "epochs": a.epochs,
+                 "final_loss": hist[-1], "generate_s": t_gen, "train_s": t_train})
+    with open(os.path.join(a.out, "warmstart_eval.json"), "w") as f:
+        json.dump({"summary": summ, "cases": rows}, f, indent=1)
+    log(json.dumps(summ))
+    net.close()
+
+
+if __name__ == "__main__":
+    main()
