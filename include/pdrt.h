@@ -139,6 +139,8 @@ typedef struct {
     int32_t chunk_cp;            /* control points processed per pass */
     size_t scratch_bytes;        /* device scratch owned by the plan */
     int32_t tensor_cores;        /* 1: convolution tiles that fit run on the tensor cores */
+    int32_t tc_ctas_per_sm[2];   /* tensor-core convolution CTAs per SM (forward, adjoint) */
+    int32_t simt_ctas_per_sm[2]; /* resident FP32 convolution CTAs per SM (forward, adjoint) */
 } pdrt_plan_info;
 
 /* Work counters of the last forward/backward call (for roofline accounting). */

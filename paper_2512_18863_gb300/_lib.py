@@ -49,7 +49,8 @@ class pdrt_plan_info(C.Structure):
     _fields_ = [("nu", C.c_int32), ("nv", C.c_int32), ("nw", C.c_int32),
                 ("cu", C.c_double), ("cv", C.c_double), ("cw", C.c_double),
                 ("n_cp", C.c_int32), ("chunk_cp", C.c_int32), ("scratch_bytes", C.c_size_t),
-                ("tensor_cores", C.c_int32)]
+                ("tensor_cores", C.c_int32), ("tc_ctas_per_sm", C.c_int32 * 2),
+                ("simt_ctas_per_sm", C.c_int32 * 2)]
 
 
 class pdrt_work(C.Structure):
@@ -206,7 +207,10 @@ def pdrt_plan_set_tensor_cores(plan, enable):
 def pdrt_plan_get_info(plan) -> dict:
     info = pdrt_plan_info()
     _check(load().pdrt_plan_get_info(_VP(plan), C.byref(info)))
-    return {k: getattr(info, k) for k, _ in pdrt_plan_info._fields_}
+    out = {k: getattr(info, k) for k, _ in pdrt_plan_info._fields_}
+    out["simt_ctas_per_sm"] = list(out["simt_ctas_per_sm"])
+    out["tc_ctas_per_sm"] = list(out["tc_ctas_per_sm"])
+    return out
 
 
 def pdrt_plan_status(plan, stream) -> int:

@@ -66,7 +66,8 @@ struct pdrt_plan_s {
     int chunk;
     int chunk_max;            // control points per pass the scratch was sized for
     int conv_blocks_fwd, conv_blocks_adj;
-    int tc_blocks;            // persistent grid of k_conv_tc (0: path unavailable)
+    int tc_blocks;            // persistent grid of k_conv_tc<false> (0: path unavailable)
+    int tc_blocks_adj;        // persistent grid of k_conv_tc<true>
     PlanDev dev;
     size_t scratch_bytes;
     std::vector<void *> allocs;
@@ -437,6 +438,10 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     const size_t per_cp = sizeof(float) * (size_t)(cap_o + cap_a);
     long long chunk = budget > fixed ? (long long)((budget - fixed) / per_cp) : 1;
     chunk = std::max(1LL, std::min<long long>(chunk, std::min(n_cp, kMaxCpPerChunk)));
+    {   // equal passes: the same number of passes with the CPs spread evenly
+        const long long passes = (n_cp + chunk - 1) / chunk;
+        chunk = (n_cp + passes - 1) / passes;
+    }
     p->chunk = (int)chunk;
     p->chunk_max = (int)chunk;
 
@@ -493,12 +498,14 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     p->conv_blocks_adj = std::max(1, ba) * g->sm_count;
     // tensor-core convolution when its tiles fit in shared memory
     p->tc_blocks = 0;
+    p->tc_blocks_adj = 0;
     P.tc_enabled = 0;
     if (conv_tc_smem_bytes(M.R, true) <= 220 * 1024 && conv_tc_smem_bytes(M.R, false) <= 220 * 1024) {
-        int bt = 0;
-        PLAN_TRY(conv_tc_prepare(M.R, &bt), "tensor-core convolution set-up");
-        if (bt > 0) {
-            p->tc_blocks = bt * g->sm_count;
+        int bt_f = 0, bt_a = 0;
+        PLAN_TRY(conv_tc_prepare(M.R, &bt_f, &bt_a), "tensor-core convolution set-up");
+        if (bt_f > 0 && bt_a > 0) {
+            p->tc_blocks = bt_f * g->sm_count;
+            p->tc_blocks_adj = bt_a * g->sm_count;
             P.tc_enabled = 1;
         }
     }
@@ -577,7 +584,7 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
             CU_TRY(timed(p, K_CONV_TC_ADJ, s,
                          [&] {
                              return launch_conv_tc(P, b0, nb, true, P.counters + 3 * n_chunks + c,
-                                                   p->tc_blocks, s);
+                                                   p->tc_blocks_adj, s);
                          }),
                    "conv_adjoint_tc launch");
         CU_TRY(timed(p, K_CONV_ADJ, s,
@@ -616,6 +623,10 @@ pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out)
     out->chunk_cp = p->chunk;
     out->scratch_bytes = p->scratch_bytes;
     out->tensor_cores = p->dev.tc_enabled;
+    out->tc_ctas_per_sm[0] = p->grid->sm_count > 0 ? p->tc_blocks / p->grid->sm_count : 0;
+    out->tc_ctas_per_sm[1] = p->grid->sm_count > 0 ? p->tc_blocks_adj / p->grid->sm_count : 0;
+    out->simt_ctas_per_sm[0] = p->grid->sm_count > 0 ? p->conv_blocks_fwd / p->grid->sm_count : 0;
+    out->simt_ctas_per_sm[1] = p->grid->sm_count > 0 ? p->conv_blocks_adj / p->grid->sm_count : 0;
     return PDRT_OK;
 }
 

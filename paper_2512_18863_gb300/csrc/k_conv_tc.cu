@@ -74,9 +74,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
     const Lattice &L = P.lat;
     const int R = P.mach.R;
     const int rows = tc_rows(R);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 8);
-    int *s_item = reinterpret_cast<int *>(smem + 16);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);         // [2]: one per operand buffer
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 16);
+    int *s_item = reinterpret_cast<int *>(smem + 20);
     float *krow = reinterpret_cast<float *>(smem + 128);
     const int krow_bytes = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
     unsigned char *abase = smem + 128 + krow_bytes;
@@ -94,14 +94,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *s_tmem;
-    uint32_t phase = 0;
+    uint32_t parity[2] = {0u, 0u};
     bool timed_out = false;
 
     while (!timed_out) {
@@ -220,46 +221,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
             fence_before();
             __syncthreads();
             fence_after();
+            // Phase ph (kernel rows |p| in [ph*kTcPhase, ...)) reads operand buffer
+            // ph & 1 and commits to mbar[ph & 1].  Phase ph + 1 is built and issued
+            // while phase ph runs; its buffer is free once phase ph - 1 completed.
             uint32_t acc = 0;
-            for (int ph = 0; ph < n_ph; ++ph) {
+            auto issue = [&](int ph) {
                 const int p0 = ph * kTcPhase, p1 = min(p0 + kTcPhase, R + 1);
-                if (tid == 0) {
-                    const uint32_t a_hi = smem_u32(abase), a_lo = a_hi + (uint32_t)a_copy;
-                    const uint32_t b_buf0 = smem_u32(bbase) + (uint32_t)((ph & 1) * b_buf);
-                    for (int ap = p0; ap < p1; ++ap) {
-                        const uint32_t b_hi = b_buf0 + (uint32_t)((ap - p0) * b_row);
-                        const uint32_t b_lo = b_hi + (uint32_t)Lim::ND * 128u;
-                        for (int sg = (ap == 0 ? 1 : -1); sg <= 1; sg += 2) {
-                            const int p = sg * ap;
-                            const uint32_t row_off = (uint32_t)(R - p) * 16u;
-                            for (int ks = 0; ks < kt / 16; ++ks) {
-                                const uint32_t aoff = row_off + (uint32_t)(2 * ks) * lbo_a;
-                                const uint32_t boff = (uint32_t)(2 * ks) * 128u;
-                                const uint64_t dah = smem_desc(a_hi + aoff, lbo_a, 128);
-                                const uint64_t dal = smem_desc(a_lo + aoff, lbo_a, 128);
-                                const uint64_t dbh = smem_desc(b_hi + boff, 128, 128);
-                                const uint64_t dbl = smem_desc(b_lo + boff, 128, 128);
-                                mma_bf16(tmem, dah, dbh, idesc, acc);
-                                acc = 1;
-                                mma_bf16(tmem, dah, dbl, idesc, 1);
-                                mma_bf16(tmem, dal, dbh, idesc, 1);
-                            }
+                const uint32_t a_hi = smem_u32(abase), a_lo = a_hi + (uint32_t)a_copy;
+                const uint32_t b_buf0 = smem_u32(bbase) + (uint32_t)((ph & 1) * b_buf);
+                for (int ap = p0; ap < p1; ++ap) {
+                    const uint32_t b_hi = b_buf0 + (uint32_t)((ap - p0) * b_row);
+                    const uint32_t b_lo = b_hi + (uint32_t)Lim::ND * 128u;
+                    for (int sg = (ap == 0 ? 1 : -1); sg <= 1; sg += 2) {
+                        const int p = sg * ap;
+                        const uint32_t row_off = (uint32_t)(R - p) * 16u;
+                        for (int ks = 0; ks < kt / 16; ++ks) {
+                            const uint32_t aoff = row_off + (uint32_t)(2 * ks) * lbo_a;
+                            const uint32_t boff = (uint32_t)(2 * ks) * 128u;
+                            const uint64_t dah = smem_desc(a_hi + aoff, lbo_a, 128);
+                            const uint64_t dal = smem_desc(a_lo + aoff, lbo_a, 128);
+                            const uint64_t dbh = smem_desc(b_hi + boff, 128, 128);
+                            const uint64_t dbl = smem_desc(b_lo + boff, 128, 128);
+                            mma_bf16(tmem, dah, dbh, idesc, acc);
+                            acc = 1;
+                            mma_bf16(tmem, dah, dbl, idesc, 1);
+                            mma_bf16(tmem, dal, dbh, idesc, 1);
                         }
                     }
-                    mma_commit(mbar);
                 }
-                // operands of the next phase go to the other buffer while these MMAs run
-                // (that buffer's previous readers finished before this phase was issued)
-                if (ph + 1 < n_ph) {
-                    build_b(p1, min(p1 + kTcPhase, R + 1), (ph + 1) & 1);
-                    fence_proxy_async();
-                }
-                // wait for this phase's MMAs: thread 0 polls the mbarrier (bounded)
-                // and broadcasts the outcome so the CTA stays convergent
+                mma_commit(&mbar[ph & 1]);
+            };
+            // bounded wait of thread 0 on buffer s, outcome broadcast to the CTA
+            auto wait_buf = [&](int sb) -> bool {
                 if (tid == 0) {
                     long long spins = 0;
                     int ok = 1;
-                    while (!mbar_try(mbar, phase)) {
+                    while (!mbar_try(&mbar[sb], parity[sb])) {
                         if (++spins > (1LL << 28)) {
                             ok = 0;
                             break;
@@ -272,19 +269,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
                 const int ok = *s_item;
                 __syncthreads();
                 fence_after();
-                phase ^= 1u;
-                if (!ok) {
-                    timed_out = true;
-                    if (tid == 0) {
-                        atomicOr(P.flags, (unsigned)PDRT_FLAG_TIMEOUT);
-                        // a second bounded wait for the MMAs in flight before the
-                        // tensor memory is released
-                        long long spins = 0;
-                        while (!mbar_try(mbar, phase ^ 1u) && ++spins < (1LL << 28)) {
-                        }
-                    }
-                    break;
+                parity[sb] ^= 1u;
+                return ok != 0;
+            };
+            if (tid == 0) issue(0);
+            int waited = 0;   // phases [0, waited) are known complete
+            for (int ph = 0; ph + 1 < n_ph && !timed_out; ++ph) {
+                if (ph >= 1) {
+                    if (!wait_buf((ph - 1) & 1)) timed_out = true;
+                    waited = ph;
                 }
+                if (timed_out) break;
+                build_b((ph + 1) * kTcPhase, min((ph + 2) * kTcPhase, R + 1), (ph + 1) & 1);
+                fence_proxy_async();
+                fence_before();
+                __syncthreads();
+                fence_after();
+                if (tid == 0) issue(ph + 1);
+            }
+            for (int ph = waited; ph < n_ph && !timed_out; ++ph)
+                if (!wait_buf(ph & 1)) timed_out = true;
+            if (timed_out) {
+                if (tid == 0) {
+                    atomicOr(P.flags, (unsigned)PDRT_FLAG_TIMEOUT);
+                    // second bounded waits for MMAs still in flight before the
+                    // tensor memory is released
+                    long long spins = 0;
+                    while (!mbar_try(&mbar[0], parity[0]) && ++spins < (1LL << 28)) {
+                    }
+                    spins = 0;
+                    while (!mbar_try(&mbar[1], parity[1]) && ++spins < (1LL << 28)) {
+                    }
+                }
+                break;
             }
             if (timed_out) break;
             // epilogue: warp w reads TMEM lanes [32 (w % 4), +32) = output rows;
@@ -325,23 +342,40 @@ cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsig
     return cudaGetLastError();
 }
 
-cudaError_t conv_tc_prepare(int R, int *blocks_per_sm)
+// CTAs of one direction that fit on an SM: shared memory (with the per-block
+// reservation), registers and tensor-memory columns.  Computed from the
+// device limits; the persistent kernel is correct with any grid (CTAs only
+// pull work items and never wait for one another), so a grid larger than
+// what is resident only queues.
+template <bool ADJ>
+static cudaError_t tc_ctas_per_sm(int R, int *out)
 {
-    const int s0 = conv_tc_smem_bytes(R, false), s1 = conv_tc_smem_bytes(R, true);
-    cudaError_t e = allow_full_smem(k_conv_tc<false>);
+    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conv_tc<ADJ>);
     if (e != cudaSuccess) return e;
-    e = allow_full_smem(k_conv_tc<true>);
-    if (e != cudaSuccess) return e;
-    int n0 = 0, n1 = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n0, k_conv_tc<false>, kTcThreads, s0);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_conv_tc<true>, kTcThreads, s1);
-    if (e != cudaSuccess) return e;
-    int n = n0 < n1 ? n0 : n1;
-    // every resident CTA holds kTmemCols of the SM's 512 tensor-memory columns
-    const int tmem_cap = 512 / (int)kTmemCols;
-    *blocks_per_sm = n < tmem_cap ? n : tmem_cap;
+    const int per_cta = conv_tc_smem_bytes(R, ADJ) + (int)fa.sharedSizeBytes + resv;
+    const int by_smem = smem_sm / per_cta;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_sm / (regs_warp * (kTcThreads / 32));
+    const int by_tmem = 512 / (int)kTmemCols;   // each CTA holds kTmemCols of 512 columns
+    int n = by_smem < by_regs ? by_smem : by_regs;
+    n = n < by_tmem ? n : by_tmem;
+    *out = n;
     return cudaSuccess;
+}
+
+cudaError_t conv_tc_prepare(int R, int *fwd_blocks_per_sm, int *adj_blocks_per_sm)
+{
+    cudaError_t e = allow_full_smem(k_conv_tc<false>);
+    if (e == cudaSuccess) e = allow_full_smem(k_conv_tc<true>);
+    if (e == cudaSuccess) e = tc_ctas_per_sm<false>(R, fwd_blocks_per_sm);
+    if (e == cudaSuccess) e = tc_ctas_per_sm<true>(R, adj_blocks_per_sm);
+    return e;
 }
 
 }  // namespace pdrt

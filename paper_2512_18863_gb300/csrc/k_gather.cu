@@ -26,6 +26,32 @@ __device__ __forceinline__ float region_value(const float *__restrict__ base, co
     return __ldg(&base[off + (long long)(j - ob.z) * (ob.y - ob.x) + (i - ob.x)]);
 }
 
+// D'_b sampled bilinearly in (u, w) at plane iz (zero outside the slices'
+// output boxes and the lattice).  The voxel's beam coordinates (fu, fw) use
+// the same float expression as voxel_to_beam.
+__device__ __forceinline__ float sample_cp(const PlanDev &P, int bl, int b, float fu, float fw, int iz)
+{
+    const Lattice &L = P.lat;
+    const float bu = floorf(fu), bw = floorf(fw);
+    const int i0 = (int)bu, k0 = (int)bw;
+    const float tu = fu - bu, tw = fw - bw;
+    const float *base = P.region + (long long)bl * P.cap_o;
+    float val = 0.f;
+#pragma unroll
+    for (int dk = 0; dk < 2; ++dk) {
+        const int k = k0 + dk;
+        if (k < 0 || k >= L.nw) continue;
+        const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
+        const int4 ob = __ldg(reinterpret_cast<const int4 *>(&sp->oi0));
+        if (iz < ob.z || iz >= ob.w || i0 + 1 < ob.x || i0 >= ob.y) continue;
+        const long long o = __ldg(&sp->off_o);
+        const float v0 = region_value(base, ob, o, i0, iz);
+        const float v1 = region_value(base, ob, o, i0 + 1, iz);
+        val += (dk ? tw : 1.f - tw) * ((1.f - tu) * v0 + tu * v1);
+    }
+    return val;
+}
+
 __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float *__restrict__ dose,
                                                 int first)
 {
@@ -38,6 +64,9 @@ __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float
     const float by0 = (float)(blockIdx.y * 8), by1 = (float)min((int)blockIdx.y * 8 + 7, P.ny - 1);
     __shared__ int s_list[kMaxCpPerChunk];
     __shared__ int s_wcnt[8];
+    __shared__ float4 s_geo[kMaxCpPerChunk];    // au, bu, cu0, cal * MU
+    __shared__ float2 s_geo2[kMaxCpPerChunk];   // aw, bw
+    __shared__ float s_cw0[kMaxCpPerChunk];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     // 1) one thread per control point of the chunk tests whether its footprint
     //    (union of output boxes; fu, fw are affine in (ix, iy)) meets this CTA
@@ -74,32 +103,42 @@ __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float
     }
     if (hit) s_list[off + __popc(m & ((1u << lane) - 1u))] = threadIdx.x;
     __syncthreads();
-    // 3) every voxel samples the listed control points in order
+    // 3) per-CP constants of the listed control points into shared memory
+    for (int n = threadIdx.x; n < total; n += blockDim.x) {
+        const int b = b0 + s_list[n];
+        const CpGeo g = P.cpgeo[b];
+        s_geo[n] = make_float4(g.au, g.bu, g.cu0, P.cptab[b].cal_mu);
+        s_geo2[n] = make_float2(g.aw, g.bw);
+        s_cw0[n] = g.cw0;
+    }
+    __syncthreads();
+    // 4) every voxel samples the listed control points in order, two at a
+    //    time so that their slice-table and region loads overlap
     float acc = 0.f;
     if (inside) {
-        for (int n = 0; n < total; ++n) {
-            const int bl = s_list[n], b = b0 + bl;
-            const CpGeo &g = P.cpgeo[b];
-            float fu, fw;
-            voxel_to_beam(g, ix, iy, fu, fw);
-            const float bu = floorf(fu), bw = floorf(fw);
-            const int i0 = (int)bu, k0 = (int)bw;
-            const float tu = fu - bu, tw = fw - bw;
-            const float *base = P.region + (long long)bl * P.cap_o;
-            float val = 0.f;
+        const float fx = (float)ix, fy = (float)iy;
+        int n = 0;
+        for (; n + 1 < total; n += 2) {
+            float v[2];
 #pragma unroll
-            for (int dk = 0; dk < 2; ++dk) {
-                const int k = k0 + dk;
-                if (k < 0 || k >= L.nw) continue;
-                const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
-                const int4 ob = __ldg(reinterpret_cast<const int4 *>(&sp->oi0));
-                if (iz < ob.z || iz >= ob.w || i0 + 1 < ob.x || i0 >= ob.y) continue;
-                const long long o = __ldg(&sp->off_o);
-                const float v0 = region_value(base, ob, o, i0, iz);
-                const float v1 = region_value(base, ob, o, i0 + 1, iz);
-                val += (dk ? tw : 1.f - tw) * ((1.f - tu) * v0 + tu * v1);
+            for (int q = 0; q < 2; ++q) {
+                const int bl = s_list[n + q], b = b0 + bl;
+                const float4 gu = s_geo[n + q];
+                const float2 gw = s_geo2[n + q];
+                const float fu = fmaf(gu.x, fx, fmaf(gu.y, fy, gu.z));
+                const float fw = fmaf(gw.x, fx, fmaf(gw.y, fy, s_cw0[n + q]));
+                v[q] = sample_cp(P, bl, b, fu, fw, iz);
             }
-            acc = fmaf(P.cptab[b].cal_mu, val, acc);
+            acc = fmaf(s_geo[n].w, v[0], acc);
+            acc = fmaf(s_geo[n + 1].w, v[1], acc);
+        }
+        if (n < total) {
+            const int bl = s_list[n], b = b0 + bl;
+            const float4 gu = s_geo[n];
+            const float2 gw = s_geo2[n];
+            const float fu = fmaf(gu.x, fx, fmaf(gu.y, fy, gu.z));
+            const float fw = fmaf(gw.x, fx, fmaf(gw.y, fy, s_cw0[n]));
+            acc = fmaf(gu.w, sample_cp(P, bl, b, fu, fw, iz), acc);
         }
         const long long idx = ((long long)iz * P.ny + iy) * P.nx + ix;
         dose[idx] = first ? acc : dose[idx] + acc;
@@ -132,23 +171,36 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
         const float fy = fmaf(di, g.bu, fmaf(dk, g.bw, g.py0));
         const int y0 = max(__float2int_ru(fy - 1.45f), 0), y1 = min(__float2int_rd(fy + 1.45f), P.ny - 1);
         const float *gp = gd + (long long)j * P.ny * P.nx;
+        // at most 3 rows x 3 voxels: a fixed, fully unrolled window (rows from
+        // y0, voxels of each row from its band start x0) so the 9 loads are
+        // independent; candidates outside the band or the grid get weight 0
+        // and the non-zero terms keep their row-major order
         float s = 0.f;
-        for (int iy = y0; iy <= y1; ++iy) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int iy = y0 + r;
+            const bool row_ok = iy <= y1;
+            const int iyc = min(iy, P.ny - 1);
             // voxels of this row whose beam coordinates are within one lattice
             // step of (i, k) in both u and w
             const float dy = (float)iy - fy;
             const float lo = fmaxf(-1.45f, fmaxf(fmaf(-g.ru, dy, -g.iu), fmaf(-g.rw, dy, -g.iw))) - 1e-3f;
             const float hi = fminf(1.45f, fminf(fmaf(-g.ru, dy, g.iu), fmaf(-g.rw, dy, g.iw))) + 1e-3f;
             const int x0 = max(__float2int_ru(fx + lo), 0), x1 = min(__float2int_rd(fx + hi), P.nx - 1);
-            for (int ix = x0; ix <= x1; ++ix) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int ix = x0 + c;
+                const bool ok = row_ok && ix <= x1;
+                const int ixc = min(ix, P.nx - 1);
+                const float v = __ldg(&gp[(long long)iyc * P.nx + ixc]);
                 float fu, fw;
                 voxel_to_beam(g, ix, iy, fu, fw);
                 // bilinear weight of lattice point (i, k) in this voxel's stencil:
                 // 1 - |f - n| inside one lattice step (the forward's 1 - t and t)
                 const float wu = fmaxf(0.f, 1.f - fabsf(fu - (float)i));
                 const float ww = fmaxf(0.f, 1.f - fabsf(fw - (float)k));
-                const float wgt = ww * wu;
-                if (wgt != 0.f) s = fmaf(wgt, __ldg(&gp[(long long)iy * P.nx + ix]), s);
+                const float wgt = ok ? ww * wu : 0.f;
+                if (wgt != 0.f) s = fmaf(wgt, v, s);
             }
         }
         out[t] = s;

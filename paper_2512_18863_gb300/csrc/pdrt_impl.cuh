@@ -224,7 +224,7 @@ int conv_nq4_for_radius(int R);
 cudaError_t conv_prepare(const MachineDev &m, int *fwd_blocks_per_sm, int *adj_blocks_per_sm);
 cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
                            int grid_blocks, cudaStream_t s);
-cudaError_t conv_tc_prepare(int R, int *blocks_per_sm);
+cudaError_t conv_tc_prepare(int R, int *fwd_blocks_per_sm, int *adj_blocks_per_sm);
 // Device form of a machine's fluence corrections (taps, profile, rotation);
 // returns an error text or NULL.  Pitches du, dv in mm.
 const char *machine_corrections(const pdrt_machine *m, double du, double dv, MachineDev &M);

@@ -299,20 +299,73 @@ def propose(net: WarmStartNet, case: Case):
     return lv, case.open_init[1].copy(), mu
 
 
+def best_mu_scale(case: Case, D: torch.Tensor, lo=0.25, hi=4.0):
+    """(alpha, J(alpha D)): the global MU factor that minimises the objective
+    of a dose D.  The dose is linear in the MU (Eq. D_total), so alpha D is
+    the dose of the plan with every MU scaled by alpha and no further dose
+    evaluation is needed; J is convex in alpha (a sum of squares of affine and
+    rectified affine functions): a grid then golden-section search."""
+    dev = D.device
+    sel = {k: D[torch.as_tensor(v, device=dev)] for k, v in case.masks.items()}
+
+    def J(a):
+        return float(objective_quadratic_sel(sel, a, case.presc))
+
+    grid = np.geomspace(lo, hi, 61)
+    vals = [J(a) for a in grid]
+    k = int(np.argmin(vals))
+    a0, a1 = grid[max(k - 1, 0)], grid[min(k + 1, len(grid) - 1)]
+    g = (math.sqrt(5.0) - 1.0) / 2.0
+    x1, x2 = a1 - g * (a1 - a0), a0 + g * (a1 - a0)
+    f1, f2 = J(x1), J(x2)
+    for _ in range(40):
+        if f1 <= f2:
+            a1, x2, f2 = x2, x1, f1
+            x1 = a1 - g * (a1 - a0)
+            f1 = J(x1)
+        else:
+            a0, x1, f1 = x1, x2, f2
+            x2 = a0 + g * (a1 - a0)
+            f2 = J(x2)
+    a = 0.5 * (a0 + a1)
+    return a, J(a)
+
+
+def objective_quadratic_sel(sel: dict, alpha: float, presc: float, weights=None, oar_fraction=0.5):
+    """objective_quadratic of the dose alpha D, given the voxels of D inside
+    each structure (sel[name] = D[mask])."""
+    weights = weights or {"ptv": 100.0, "bladder": 1.0, "rectum": 10.0}
+    L = weights["ptv"] * ((alpha * sel["ptv"] - presc) ** 2).mean()
+    for name, lam in weights.items():
+        if name == "ptv" or name not in sel or lam == 0.0 or sel[name].numel() == 0:
+            continue
+        ex = torch.clamp(alpha * sel[name] - oar_fraction * presc, min=0.0)
+        L = L + lam * (ex ** 2).mean()
+    return L
+
+
+def judge(case: Case, prop):
+    """The exact engine's judgement of a proposal (one dose evaluation): the
+    proposal with its MU rescaled by best_mu_scale, and its objective."""
+    D = case.engine.forward(*prop)
+    alpha, j = best_mu_scale(case, D)
+    return (prop[0], prop[1], prop[2] * alpha), j, alpha
+
+
 def evaluate(net: WarmStartNet, seeds, n_iter=N_ITER):
     """Warm versus plain on held-out phantoms.  The plain optimiser runs
     n_iter evaluations from the open-field start; its best objective J* is the
     target.  The warm start costs one evaluation to judge the proposal
-    against the open-field start (the fallback when the proposal is worse),
-    then optimises until J <= J* (at most n_iter more evaluations)."""
+    (judge: objective with the best global MU scale) against the open-field
+    start (the fallback when the proposal is worse), then optimises until
+    J <= J* (at most n_iter more evaluations)."""
     rows = []
     for sd in seeds:
         c = make_case(int(sd))
         plain = plain_optimise(c, n_iter)
         j_star = min(plain.history)
         plain_evals = int(np.argmin(plain.history)) + 1
-        prop = propose(net, c)
-        j_prop = objective_of(c, *prop)
+        prop, j_prop, alpha = judge(c, propose(net, c))
         j_open = plain.history[0]
         start = prop if j_prop <= j_open else c.open_init
         warm = optimise(c.engine, c.masks, c.presc, start, n_iter=n_iter, lr=OPT_LR, lr_mu=OPT_LR_MU,
@@ -322,6 +375,7 @@ def evaluate(net: WarmStartNet, seeds, n_iter=N_ITER):
         D_w = c.engine.forward(warm.leaves, warm.jaws, warm.mu)
         rows.append({
             "seed": int(sd), "j_open": j_open, "j_proposal": j_prop, "j_star": j_star,
+            "mu_scale": float(alpha),
             "fallback": bool(j_prop > j_open), "plain_evals": plain_evals,
             "warm_evals": 1 + warm.dose_evals, "reached": bool(reached),
             "dose_diff_rel": float((D_w - D_p).abs().max() / D_p.max()),
@@ -371,9 +425,21 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=N_ITER)
     ap.add_argument("--out", default=os.path.dirname(default_weights_path()))
     ap.add_argument("--seed", type=int, default=5000)
+    ap.add_argument("--eval-only", default=None,
+                    help="evaluate the weights in this .npz on its held-out seeds (no training)")
     a = ap.parse_args(argv)
     os.makedirs(a.out, exist_ok=True)
     log = lambda s: print(s, flush=True)   # noqa: E731
+    if a.eval_only:
+        d = np.load(a.eval_only)
+        net = load_net(a.eval_only)
+        rows = evaluate(net, d["test_seeds"][:a.test], a.iters)
+        summ = summarise(rows)
+        with open(os.path.join(a.out, "warmstart_eval.json"), "w") as f:
+            json.dump({"summary": summ, "cases": rows}, f, indent=1)
+        log(json.dumps(summ))
+        net.close()
+        return
     t0 = time.time()
     train_seeds = a.seed + np.arange(a.train)
     test_seeds = a.seed + 100000 + np.arange(a.test)

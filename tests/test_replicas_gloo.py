@@ -1,0 +1,37 @@
+"""The N > 1 replica path of bench.py on CPU: two gloo ranks with different
+timed-region lengths agree on the slowest one and on the whole-job value."""
+import os
+import sys
+
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _rank(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port),
+                       "RANK": str(rank), "WORLD_SIZE": str(world)})
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = 100.0 + 50.0 * rank
+    t = bench.replica_time(ms, world, torch.device("cpu"))
+    out[rank] = (t, bench.whole_job_value(2.0, 5, world, t))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_replicas_take_the_slowest_time():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
+    assert out[0][0] == out[1][0] == 150.0
+    assert out[0][1] == out[1][1] == pytest.approx(2.0 * 5 * 2 / 0.150)

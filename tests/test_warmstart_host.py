@@ -50,3 +50,29 @@ def test_committed_weights_are_finite_and_complete():
     assert np.all(np.isfinite(d["params"]))
     assert len(d["train_seeds"]) >= 1000 and len(d["test_seeds"]) >= 50
     assert d["loss"][-1] < d["loss"][0]
+
+
+def test_best_mu_scale_finds_the_closed_form_optimum():
+    """With no organ above its threshold the objective is 100 mean((a D - p)^2),
+    minimised at a = p mean(D) / mean(D^2); with an overdosed organ the optimum
+    moves down and the search still finds the minimum of a fine grid."""
+    import torch
+    from types import SimpleNamespace
+    rng = np.random.default_rng(4)
+    n = (6, 7, 8)
+    ptv = rng.random(n) < 0.3
+    blad = (~ptv) & (rng.random(n) < 0.3)
+    D = torch.tensor(rng.uniform(0.5, 1.5, n))
+    case = SimpleNamespace(masks={"ptv": ptv, "bladder": blad, "rectum": np.zeros(n, bool)}, presc=2.0)
+    Dn = D.clone()
+    Dn[torch.as_tensor(blad)] = 0.0                   # organ dose zero: PTV term only
+    a, j = W.best_mu_scale(case, Dn)
+    d = Dn[torch.as_tensor(ptv)].numpy()
+    a_ref = 2.0 * d.mean() / (d * d).mean()
+    assert a == pytest.approx(a_ref, rel=1e-6)
+    a2, j2 = W.best_mu_scale(case, D)                 # bladder pushes the scale down
+    grid = np.linspace(0.25, 4.0, 20001)
+    sel = {k: D[torch.as_tensor(v)] for k, v in case.masks.items()}
+    vals = [float(W.objective_quadratic_sel(sel, g, 2.0)) for g in grid]
+    assert j2 <= min(vals) + 1e-9
+    assert a2 < a_ref
