@@ -418,6 +418,8 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
         cap_a = std::max(cap_a, sa);
     }
 
+    if (cap_o >= (1LL << 31) || L.nv > 32767)
+        return fail(PDRT_EINVAL, "grid too large for one control point's beam-frame region");
     pdrt_plan_t p = new pdrt_plan_s();
     p->grid = g;
     p->n_cp = n_cp;
@@ -464,6 +466,7 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     PLAN_TRY(dalloc(p, &dukr, (size_t)n_cp * L.nw), "cudaMalloc(slice ranges)");
     PLAN_TRY(dalloc(p, &P.cptab, n_cp), "cudaMalloc(cp table)");
     PLAN_TRY(dalloc(p, &P.slices, (size_t)n_cp * L.nw), "cudaMalloc(slice table)");
+    PLAN_TRY(dalloc(p, &P.gbox, (size_t)n_cp * L.nw), "cudaMalloc(gather boxes)");
     PLAN_TRY(dalloc(p, &P.fbuf, (size_t)n_cp * L.nu * L.nv), "cudaMalloc(fluence)");
     PLAN_TRY(dalloc(p, &P.gfbuf, (size_t)n_cp * L.nu * L.nv), "cudaMalloc(fluence adjoint)");
     if (M.corr) PLAN_TRY(dalloc(p, &P.tbuf, (size_t)n_cp * L.nu * L.nv), "cudaMalloc(raw fluence)");

@@ -21,7 +21,7 @@
 // One CTA (8 warps) per slice, persistent over a work counter.  Thread 0
 // issues the MMAs; completion is signalled through an mbarrier
 // (tcgen05.commit); all waits are bounded and raise PDRT_FLAG_TIMEOUT.  The
-// kernel-row operands are built in phases of kTcPhase rows into a double
+// kernel-row operands are built in phases of PHASE rows into a double
 // buffer, each phase while the previous phase's MMAs run; with the per
 // direction tile limits two CTAs fit on an SM.
 // Slices whose boxes exceed the tile limits are left to the FP32 SIMT kernel
@@ -49,11 +49,12 @@ struct TcLimits {
     static constexpr int MAXN = ADJ ? kTcAdjMaxN : kTcFwdMaxN;
     static constexpr int MAXK = ADJ ? kTcAdjMaxK : kTcFwdMaxK;
     static constexpr int ND = MAXN / 8 + MAXK / 8 - 1;   // Hankel diagonals per kernel row
+    static constexpr int PHASE = ADJ ? kTcPhaseAdj : kTcPhaseFwd;   // kernel rows per operand phase
 };
 
 // shared memory: [0,128) barrier / tmem address / broadcast; kernel rows;
 // input tile hi+lo [2][K/8][rows][16 B]; kernel-row operands, two buffers of
-// kTcPhase rows x hi+lo x ND core matrices
+// PHASE rows x hi+lo x ND core matrices
 int conv_tc_smem_bytes(int R, bool adjoint)
 {
     const int rows = tc_rows(R);
@@ -61,7 +62,7 @@ int conv_tc_smem_bytes(int R, bool adjoint)
     const int nd = adjoint ? TcLimits<true>::ND : TcLimits<false>::ND;
     const int krow = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
     const int a = 2 * rows * maxk * 2;
-    const int bsz = 2 * kTcPhase * 2 * nd * 128;
+    const int bsz = 2 * (adjoint ? kTcPhaseAdj : kTcPhaseFwd) * 2 * nd * 128;
     return 128 + krow + a + bsz;
 }
 
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
     const int a_copy = rows * Lim::MAXK * 2;                    // bytes of one (hi or lo) tile
     unsigned char *bbase = abase + 2 * a_copy;
     const int b_row = 2 * Lim::ND * 128;                        // hi + lo of one kernel row
-    const int b_buf = kTcPhase * b_row;
+    const int b_buf = Lim::PHASE * b_row;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = nb * L.nw;
 
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
                 *reinterpret_cast<uint4 *>(bp + (size_t)Lim::ND * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
         };
-        const int n_ph = (R + kTcPhase) / kTcPhase;   // phases over |p| = 0..R
+        const int n_ph = (R + Lim::PHASE) / Lim::PHASE;   // phases over |p| = 0..R
         const uint32_t idesc = instr_desc(kTcM, nt);
         const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
         const int fa0 = P.cptab[b].fa0, fa1 = P.cptab[b].fa1, fc0 = P.cptab[b].fc0, fc1 = P.cptab[b].fc1;
@@ -216,36 +217,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
                 *reinterpret_cast<uint4 *>(ap) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                 *reinterpret_cast<uint4 *>(ap + a_copy) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
-            build_b(0, min(kTcPhase, R + 1), 0);
+            build_b(0, min(Lim::PHASE, R + 1), 0);
             fence_proxy_async();   // generic-proxy smem writes -> tensor core reads
             fence_before();
             __syncthreads();
             fence_after();
-            // Phase ph (kernel rows |p| in [ph*kTcPhase, ...)) reads operand buffer
+            // Phase ph (kernel rows |p| in [ph*PHASE, ...)) reads operand buffer
             // ph & 1 and commits to mbar[ph & 1].  Phase ph + 1 is built and issued
             // while phase ph runs; its buffer is free once phase ph - 1 completed.
             uint32_t acc = 0;
+            // Descriptors are built once per tile; every operand offset is a
+            // multiple of 16 bytes and smem addresses stay below 256 KB, so the
+            // descriptor of base + off is the base descriptor + (off >> 4) in
+            // its 14-bit start-address field (no carry out of the field).
+            const uint32_t a_hi0 = smem_u32(abase);
+            const uint64_t da_hi0 = smem_desc(a_hi0, lbo_a, 128);
+            const uint64_t da_lo0 = smem_desc(a_hi0 + (uint32_t)a_copy, lbo_a, 128);
+            const uint64_t db0 = smem_desc(smem_u32(bbase), 128, 128);
+            const uint64_t a_ks = (uint64_t)((2u * (uint32_t)lbo_a) >> 4);   // per K step
+            const uint64_t b_ks = (uint64_t)((2u * 128u) >> 4);
+            const uint64_t b_lo_off = (uint64_t)(((uint32_t)Lim::ND * 128u) >> 4);
+            const int n_ks = kt / 16;
             auto issue = [&](int ph) {
-                const int p0 = ph * kTcPhase, p1 = min(p0 + kTcPhase, R + 1);
-                const uint32_t a_hi = smem_u32(abase), a_lo = a_hi + (uint32_t)a_copy;
-                const uint32_t b_buf0 = smem_u32(bbase) + (uint32_t)((ph & 1) * b_buf);
+                const int p0 = ph * Lim::PHASE, p1 = min(p0 + Lim::PHASE, R + 1);
+                const uint64_t db_buf = db0 + (uint64_t)(((uint32_t)((ph & 1) * b_buf)) >> 4);
                 for (int ap = p0; ap < p1; ++ap) {
-                    const uint32_t b_hi = b_buf0 + (uint32_t)((ap - p0) * b_row);
-                    const uint32_t b_lo = b_hi + (uint32_t)Lim::ND * 128u;
+                    const uint64_t dbh_row = db_buf + (uint64_t)(((uint32_t)((ap - p0) * b_row)) >> 4);
+                    const uint64_t dbl_row = dbh_row + b_lo_off;
                     for (int sg = (ap == 0 ? 1 : -1); sg <= 1; sg += 2) {
-                        const int p = sg * ap;
-                        const uint32_t row_off = (uint32_t)(R - p) * 16u;
-                        for (int ks = 0; ks < kt / 16; ++ks) {
-                            const uint32_t aoff = row_off + (uint32_t)(2 * ks) * lbo_a;
-                            const uint32_t boff = (uint32_t)(2 * ks) * 128u;
-                            const uint64_t dah = smem_desc(a_hi + aoff, lbo_a, 128);
-                            const uint64_t dal = smem_desc(a_lo + aoff, lbo_a, 128);
-                            const uint64_t dbh = smem_desc(b_hi + boff, 128, 128);
-                            const uint64_t dbl = smem_desc(b_lo + boff, 128, 128);
+                        const uint64_t row = (uint64_t)(R - sg * ap);      // (row_off >> 4): rows 16 B apart
+                        uint64_t dah = da_hi0 + row, dal = da_lo0 + row;
+                        uint64_t dbh = dbh_row, dbl = dbl_row;
+                        for (int ks = 0; ks < n_ks; ++ks) {
                             mma_bf16(tmem, dah, dbh, idesc, acc);
                             acc = 1;
                             mma_bf16(tmem, dah, dbl, idesc, 1);
                             mma_bf16(tmem, dal, dbh, idesc, 1);
+                            dah += a_ks;
+                            dal += a_ks;
+                            dbh += b_ks;
+                            dbl += b_ks;
                         }
                     }
                 }
@@ -280,7 +291,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
                     waited = ph;
                 }
                 if (timed_out) break;
-                build_b((ph + 1) * kTcPhase, min((ph + 2) * kTcPhase, R + 1), (ph + 1) & 1);
+                build_b((ph + 1) * Lim::PHASE, min((ph + 2) * Lim::PHASE, R + 1), (ph + 1) & 1);
                 fence_proxy_async();
                 fence_before();
                 __syncthreads();

@@ -19,13 +19,6 @@
 
 namespace pdrt {
 
-__device__ __forceinline__ float region_value(const float *__restrict__ base, const int4 ob,
-                                              long long off, int i, int j)
-{
-    if (i < ob.x || i >= ob.y || j < ob.z || j >= ob.w) return 0.f;
-    return __ldg(&base[off + (long long)(j - ob.z) * (ob.y - ob.x) + (i - ob.x)]);
-}
-
 // D'_b sampled bilinearly in (u, w) at plane iz (zero outside the slices'
 // output boxes and the lattice).  The voxel's beam coordinates (fu, fw) use
 // the same float expression as voxel_to_beam.
@@ -41,12 +34,13 @@ __device__ __forceinline__ float sample_cp(const PlanDev &P, int bl, int b, floa
     for (int dk = 0; dk < 2; ++dk) {
         const int k = k0 + dk;
         if (k < 0 || k >= L.nw) continue;
-        const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
-        const int4 ob = __ldg(reinterpret_cast<const int4 *>(&sp->oi0));
-        if (iz < ob.z || iz >= ob.w || i0 + 1 < ob.x || i0 >= ob.y) continue;
-        const long long o = __ldg(&sp->off_o);
-        const float v0 = region_value(base, ob, o, i0, iz);
-        const float v1 = region_value(base, ob, o, i0 + 1, iz);
+        // one 16-byte record: region offset, u start, u width, v range
+        const int4 gb = __ldg(&P.gbox[(long long)b * L.nw + k]);
+        const int ox = gb.y, ow = gb.z, oj0 = gb.w & 0xFFFF, oj1 = gb.w >> 16;
+        if (iz < oj0 || iz >= oj1 || i0 + 1 < ox || i0 >= ox + ow) continue;
+        const float *row = base + gb.x + (long long)(iz - oj0) * ow;
+        const float v0 = (i0 >= ox) ? __ldg(&row[i0 - ox]) : 0.f;
+        const float v1 = (i0 + 1 < ox + ow) ? __ldg(&row[i0 + 1 - ox]) : 0.f;
         val += (dk ? tw : 1.f - tw) * ((1.f - tu) * v0 + tu * v1);
     }
     return val;

@@ -471,6 +471,9 @@ __global__ void __launch_bounds__(kTabThreads) k_tables(PlanDev P)
                 atomicOr(P.flags, (unsigned)PDRT_FLAG_CAPACITY);
             }
             P.slices[(long long)b * L.nw + k] = st;
+            // offsets fit 31 bits (cap_o is checked at upload); v bounds 16 bits
+            P.gbox[(long long)b * L.nw + k] =
+                make_int4((int)st.off_o, st.oi0, st.oi1 - st.oi0, st.oj0 | (st.oj1 << 16));
         }
         carry += tot;
         carry_o += to;

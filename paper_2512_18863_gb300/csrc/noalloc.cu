@@ -197,6 +197,7 @@ extern "C" pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int
     const size_t o_dd = take(sizeof(float) * m->n_depth);
     const size_t o_ukr = take(sizeof(int2) * L.nw);
     const size_t o_slices = take(sizeof(SliceTab) * L.nw);
+    const size_t o_gbox = take(sizeof(int4) * L.nw);
     const size_t o_f = take(sizeof(float) * (size_t)L.nu * L.nv);
     const size_t o_region = take(sizeof(float) * (size_t)cap_o);
     // corrections: raw map and blurred map scratch
@@ -256,6 +257,7 @@ extern "C" pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int
     P.ukr = reinterpret_cast<const int2 *>(base + o_ukr);
     P.cptab = reinterpret_cast<CpTab *>(base + o_cptab);
     P.slices = reinterpret_cast<SliceTab *>(base + o_slices);
+    P.gbox = reinterpret_cast<int4 *>(base + o_gbox);
     P.fbuf = reinterpret_cast<float *>(base + o_f);
     if (M.corr) {
         P.tbuf = reinterpret_cast<float *>(base + o_t);

@@ -5,6 +5,8 @@
 //   ukr    [n_cp][nw]        static needed u-range of every beam slice (int2)
 //   cptab  [n_cp]            per-call CP state (projected MU, fluence support box, ...)
 //   slices [n_cp][nw]        per-call slice table (depth, kernel, boxes, offsets)
+//   gbox   [n_cp][nw]        the gather's copy of each slice's output box and
+//                            region offset, one 16-byte record
 //   fbuf   [n_cp][nu*nv]     fluence maps over their support boxes, [a][c] (c fastest)
 //   gfbuf  [n_cp][nu*nv]     adjoint of the fluence maps, same layout
 //   tbuf   [n_cp][nu*nv]     raw aperture map / its adjoint when the fluence
@@ -31,7 +33,10 @@ constexpr int kConvRows = 32;            // output rows per CTA (one per lane)
 // the forward has wide outputs and narrow inputs, the adjoint the reverse
 constexpr int kTcFwdMaxN = 96, kTcFwdMaxK = 64;
 constexpr int kTcAdjMaxN = 64, kTcAdjMaxK = 96;
-constexpr int kTcPhase = 4;              // kernel rows |p| per double-buffered operand phase
+// kernel rows |p| per double-buffered operand phase: the forward's smaller
+// phase buffers let three CTAs share an SM, the adjoint's larger input tile
+// allows two
+constexpr int kTcPhaseFwd = 2, kTcPhaseAdj = 4;
 
 enum KernelId {
     K_HU = 0, K_RASTER = 1, K_TABLES = 2, K_CONV_FWD = 3, K_GATHER = 4,
@@ -116,6 +121,7 @@ struct PlanDev {
     const int2 *ukr;
     CpTab *cptab;
     SliceTab *slices;
+    int4 *gbox;              // [n_cp][nw] per slice: {off_o, oi0, oi1 - oi0, oj0 | oj1 << 16} for the gather
     float *fbuf, *gfbuf;
     float *tbuf;             // [n_cp][nu*nv] raw-map scratch of the corrections (NULL if off)
     float *region, *adjbuf;
