@@ -392,12 +392,6 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
         G.sx_w = (float)sn;
         G.sy_w = (float)cs;
         G.px0 = (float)px0; G.py0 = (float)py0; G.pz0 = (float)pz0;
-        // a coefficient near 0 leaves dx unbounded by that band (+-3 exceeds the
-        // +-1.45 candidate window); the exact weights still decide membership
-        G.iu = fabs(au) > 1e-3 ? (float)(1.0 / fabs(au)) : 3.f;
-        G.ru = fabs(au) > 1e-3 ? (float)(bu / au) : 0.f;
-        G.iw = fabs(aw) > 1e-3 ? (float)(1.0 / fabs(aw)) : 3.f;
-        G.rw = fabs(aw) > 1e-3 ? (float)(bw / aw) : 0.f;
         double fu[4], fw[4];
         const int cxs[4] = {0, g->nx - 1, g->nx - 1, 0}, cys[4] = {0, 0, g->ny - 1, g->ny - 1};
         for (int c = 0; c < 4; ++c) {

@@ -8,8 +8,8 @@
 //   No atomics; the CP order of the sum is fixed.  A CTA (32 x 8 voxels of one
 //   z plane) skips a control point when its footprint misses the CTA.
 // k_gather_T: pull form of the transpose: every beam-frame point (i, j, k) of
-//   the output box gathers the dose gradient of the (at most 3 x 3) voxels of
-//   plane j whose bilinear stencil contains it; the voxel's beam coordinates
+//   the output box gathers the dose gradient of the voxels of plane j whose
+//   bilinear stencil contains it (all inside a 3 x 3 window); the voxel's beam coordinates
 //   come from the same float expression as in k_gather (voxel_to_beam) and
 //   the weight 1 - |f - n| equals the forward's 1 - t or t, so this is the
 //   transpose of the forward up to summation order.  No atomics.
@@ -157,47 +157,45 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
     const CpGeo g = P.cpgeo[b];
     float *out = P.region + (long long)bl * P.cap_o + sp->off_o;
     const float dk = (float)k - L.cw;
-    for (int t = threadIdx.x; t < ow * oh; t += blockDim.x) {
-        const int i = ob.x + t % ow, j = ob.z + t / ow;
-        const float di = (float)i - L.cu;
-        // voxel-index position of lattice point (i, k): rotation transpose
-        const float fx = fmaf(di, g.au, fmaf(dk, g.aw, g.px0));
-        const float fy = fmaf(di, g.bu, fmaf(dk, g.bw, g.py0));
-        const int y0 = max(__float2int_ru(fy - 1.45f), 0), y1 = min(__float2int_rd(fy + 1.45f), P.ny - 1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // warps take output rows j, lanes consecutive i (no index division)
+    for (int jj = warp; jj < oh; jj += 8) {
+        const int j = ob.z + jj;
         const float *gp = gd + (long long)j * P.ny * P.nx;
-        // at most 3 rows x 3 voxels: a fixed, fully unrolled window (rows from
-        // y0, voxels of each row from its band start x0) so the 9 loads are
-        // independent; candidates outside the band or the grid get weight 0
-        // and the non-zero terms keep their row-major order
-        float s = 0.f;
+        for (int ii = lane; ii < ow; ii += 32) {
+            const int i = ob.x + ii;
+            const float di = (float)i - L.cu;
+            // voxel-index position of lattice point (i, k): rotation transpose
+            const float fx = fmaf(di, g.au, fmaf(dk, g.aw, g.px0));
+            const float fy = fmaf(di, g.bu, fmaf(dk, g.bw, g.py0));
+            // a voxel whose bilinear stencil holds (i, k) has |fu - i| < 1 and
+            // |fw - k| < 1, so its centre is within sqrt(2) of (fx, fy) on
+            // each axis: inside the 3 x 3 window around the rounded position.
+            // The weights are the forward's (voxel_to_beam, 1 - |f - n|); the
+            // non-zero terms are summed in row-major order.
+            const int cx = __float2int_rn(fx), cy = __float2int_rn(fy);
+            float s = 0.f;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const int iy = y0 + r;
-            const bool row_ok = iy <= y1;
-            const int iyc = min(iy, P.ny - 1);
-            // voxels of this row whose beam coordinates are within one lattice
-            // step of (i, k) in both u and w
-            const float dy = (float)iy - fy;
-            const float lo = fmaxf(-1.45f, fmaxf(fmaf(-g.ru, dy, -g.iu), fmaf(-g.rw, dy, -g.iw))) - 1e-3f;
-            const float hi = fminf(1.45f, fminf(fmaf(-g.ru, dy, g.iu), fmaf(-g.rw, dy, g.iw))) + 1e-3f;
-            const int x0 = max(__float2int_ru(fx + lo), 0), x1 = min(__float2int_rd(fx + hi), P.nx - 1);
+            for (int r = -1; r <= 1; ++r) {
+                const int iy = cy + r;
+                const bool row_ok = iy >= 0 && iy < P.ny;
+                const int iyc = min(max(iy, 0), P.ny - 1);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int ix = x0 + c;
-                const bool ok = row_ok && ix <= x1;
-                const int ixc = min(ix, P.nx - 1);
-                const float v = __ldg(&gp[(long long)iyc * P.nx + ixc]);
-                float fu, fw;
-                voxel_to_beam(g, ix, iy, fu, fw);
-                // bilinear weight of lattice point (i, k) in this voxel's stencil:
-                // 1 - |f - n| inside one lattice step (the forward's 1 - t and t)
-                const float wu = fmaxf(0.f, 1.f - fabsf(fu - (float)i));
-                const float ww = fmaxf(0.f, 1.f - fabsf(fw - (float)k));
-                const float wgt = ok ? ww * wu : 0.f;
-                if (wgt != 0.f) s = fmaf(wgt, v, s);
+                for (int c = -1; c <= 1; ++c) {
+                    const int ix = cx + c;
+                    const bool ok = row_ok && ix >= 0 && ix < P.nx;
+                    const int ixc = min(max(ix, 0), P.nx - 1);
+                    const float v = __ldg(&gp[(long long)iyc * P.nx + ixc]);
+                    float fu, fw;
+                    voxel_to_beam(g, ix, iy, fu, fw);
+                    const float wu = fmaxf(0.f, 1.f - fabsf(fu - (float)i));
+                    const float ww = fmaxf(0.f, 1.f - fabsf(fw - (float)k));
+                    const float wgt = ok ? ww * wu : 0.f;
+                    if (wgt != 0.f) s = fmaf(wgt, v, s);
+                }
             }
+            out[(long long)jj * ow + ii] = s;
         }
-        out[t] = s;
     }
 }
 

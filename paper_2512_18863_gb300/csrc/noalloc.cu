@@ -168,10 +168,6 @@ extern "C" pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int
     G.cw0 = (float)(H - sn * px0 - cs * py0);
     G.sx_w = (float)sn; G.sy_w = (float)cs;
     G.px0 = (float)px0; G.py0 = (float)py0; G.pz0 = (float)cv;
-    G.iu = fabs(cs) > 1e-3 ? (float)(1.0 / fabs(cs)) : 3.f;
-    G.ru = fabs(cs) > 1e-3 ? (float)(-sn / cs) : 0.f;
-    G.iw = fabs(sn) > 1e-3 ? (float)(1.0 / fabs(sn)) : 3.f;
-    G.rw = fabs(sn) > 1e-3 ? (float)(cs / sn) : 0.f;
     double fu[4], fw[4];
     const int cxs[4] = {0, nx - 1, nx - 1, 0}, cys[4] = {0, 0, ny - 1, ny - 1};
     for (int c = 0; c < 4; ++c) {

@@ -77,9 +77,6 @@ struct CpGeo {
     float aw, bw, cw0;    // fw = aw*ix + bw*iy + cw0   (beam lattice index along w)
     float sx_w, sy_w;     // beam direction e_w projected to voxel index units (x, y)
     float px0, py0, pz0;  // isocentre in voxel index units
-    // transpose-gather bands: |fu - i| < 1 and |fw - k| < 1 at row offset dy
-    // hold for dx = ix - fx in (-iu - ru dy, iu - ru dy) and (-iw - rw dy, iw - rw dy)
-    float iu, ru, iw, rw;
 };
 
 struct CpTab {
