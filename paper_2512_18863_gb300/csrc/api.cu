@@ -659,7 +659,8 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
     out->conv_flops = 2.0 * (double)out->taps * (double)out->support_points;
     out->mma_flops = 0.0;
     if (p->dev.tc_enabled) {
-        // replay the tensor-core tile sizes (same rules as tc_boxes / tc_takes_slice)
+        // replay the tensor-core tiling of k_conv_tc (row tiles, column tiles,
+        // input chunks)
         const Lattice &L = p->dev.lat;
         const int R = p->dev.mach.R;
         std::vector<SliceTab> sl((size_t)p->n_cp * L.nw);
@@ -671,15 +672,24 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
                 const int ij0 = adj ? st.oj0 : st.pj0, ij1 = adj ? st.oj1 : st.pj1;
                 const int oi0 = adj ? st.ai0 : st.oi0, oi1 = adj ? st.ai1 : st.oi1;
                 const int oj0 = adj ? st.aj0 : st.oj0, oj1 = adj ? st.aj1 : st.oj1;
-                (void)ii0; (void)ii1;
                 if (oi1 <= oi0 || oj1 <= oj0) continue;
-                const int nt = (oj1 - oj0 + 15) & ~15;
-                const int s0 = std::max(ij0, oj0 - R), s1 = std::min(ij1, oj0 + nt + R);
-                const int kt = ((s1 > s0 ? s1 - s0 : 0) + 15) & ~15;
+                if (ii1 <= ii0 || ij1 <= ij0) continue;
                 const int maxn = adj ? kTcAdjMaxN : kTcFwdMaxN, maxk = adj ? kTcAdjMaxK : kTcFwdMaxK;
-                if (nt < 16 || nt > maxn || kt < 16 || kt > maxk) continue;
                 const int mtiles = (oi1 - oi0 + 127) / 128;
-                out->mma_flops += (double)mtiles * (2 * R + 1) * (kt / 16) * 3 * 2.0 * 128 * nt * 16;
+                const int ow = oj1 - oj0, n_ct = (ow + maxn - 1) / maxn;
+                const int w_ct = (((ow + n_ct - 1) / n_ct) + 15) & ~15;
+                for (int ct = 0; ct < n_ct; ++ct) {
+                    const int j0 = oj0 + ct * w_ct, j1 = std::min(oj1, j0 + w_ct);
+                    const int nt = ((j1 - j0) + 15) & ~15;
+                    const int sa = std::max(ij0, j0 - R), sb = std::min(ij1, j0 + nt + R);
+                    const int n_kc = sb > sa ? (sb - sa + maxk - 1) / maxk : 0;
+                    const int w_kc = n_kc ? (((sb - sa + n_kc - 1) / n_kc) + 15) & ~15 : 16;
+                    for (int kc = 0; kc < n_kc; ++kc) {
+                        const int ka = sa + kc * w_kc, kb = std::min(sb, ka + w_kc);
+                        const int kt = ((kb - ka) + 15) & ~15;
+                        out->mma_flops += (double)mtiles * (2 * R + 1) * (kt / 16) * 3 * 2.0 * 128 * nt * 16;
+                    }
+                }
             }
         }
     }

@@ -24,8 +24,11 @@
 // kernel-row operands are built in phases of PHASE rows into a double
 // buffer, each phase while the previous phase's MMAs run; with the per
 // direction tile limits two CTAs fit on an SM.
-// Slices whose boxes exceed the tile limits are left to the FP32 SIMT kernel
-// (k_conv), which skips the slices this kernel takes (tc_takes_slice).
+// Boxes wider than one tile are split into output-column tiles of at most
+// MAXN columns and, per column tile, chunks of at most MAXK of the input
+// columns within R of it; the chunks accumulate in tensor memory.  With
+// tensor cores on this kernel takes every slice; the FP32 SIMT kernel
+// (k_conv) skips the slices taken here (tc_takes_slice).
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -66,8 +69,11 @@ int conv_tc_smem_bytes(int R, bool adjoint)
     return 128 + krow + a + bsz;
 }
 
+// forward: at most 80 registers per thread, so three CTAs of 256 threads fit
+// the register file (its shared memory allows three per SM); the adjoint's
+// shared memory allows two
 template <bool ADJ>
-__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, int nb,
+__global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, int b0, int nb,
                                                            unsigned int *__restrict__ counter)
 {
     using Lim = TcLimits<ADJ>;
@@ -116,8 +122,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
         const SliceTab st = P.slices[(long long)b * L.nw + k];
         if (!tc_takes_slice(st, ADJ, R, 1)) continue;
         const TcBoxes bx = tc_boxes(st, ADJ, R);
-        const int kt = bx.kt, nt = bx.nt, nd = nt / 8 + kt / 8 - 1;
-        const int s_end = bx.s0 + kt;
         const int out_w = bx.out_i1 - bx.out_i0;
         float *dst = ADJ ? P.adjbuf + (long long)bl * P.cap_a + st.off_a
                          : P.region + (long long)bl * P.cap_o + st.off_o;
@@ -132,10 +136,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
                         st.wn[2] * expf(-st.a[2] * r);
         }
         __syncthreads();
+        // Tiling of the slice: output-column tiles of at most MAXN columns
+        // (balanced widths), and per column tile chunks of at most MAXK of the
+        // input columns within R of it; the chunks accumulate in tensor memory.
+        int nt = 16, kt = 16, nd = 1, s_end = 0, c0 = 0;
         // Hankel core matrices of kernel rows |p| in [p0, p1) into buffer `buf`:
         // element (r, t) of diagonal d = K(|p|, 8d + r + t + c0), c0 = j0 - s_end + 1
-        const int c0 = bx.out_j0 - s_end + 1;
-        auto build_b = [&](int p0, int p1, int buf) {
+        auto build_b = [&](int p0, int p1, int buf, const int nd, const int c0) {
             const int n = (p1 - p0) * nd * 8;
             for (int idx = tid; idx < n; idx += blockDim.x) {
                 const int pl = idx / (nd * 8), rem = idx - pl * nd * 8, d = rem >> 3, r = rem & 7;
@@ -158,181 +165,211 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(PlanDev P, int b0, in
             }
         };
         const int n_ph = (R + Lim::PHASE) / Lim::PHASE;   // phases over |p| = 0..R
-        const uint32_t idesc = instr_desc(kTcM, nt);
         const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
         const int fa0 = P.cptab[b].fa0, fa1 = P.cptab[b].fa1, fc0 = P.cptab[b].fc0, fc1 = P.cptab[b].fc1;
         const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
         const int h_w = st.oi1 - st.oi0;
         const int lbo_a = rows * 16;
+        // Descriptors are built once; every operand offset is a multiple of 16
+        // bytes and smem addresses stay below 256 KB, so the descriptor of
+        // base + off is the base descriptor + (off >> 4) in its 14-bit
+        // start-address field (no carry out of the field).
+        const uint32_t a_hi0 = smem_u32(abase);
+        const uint64_t da_hi0 = smem_desc(a_hi0, lbo_a, 128);
+        const uint64_t da_lo0 = smem_desc(a_hi0 + (uint32_t)a_copy, lbo_a, 128);
+        const uint64_t db0 = smem_desc(smem_u32(bbase), 128, 128);
+        const uint64_t a_ks = (uint64_t)((2u * (uint32_t)lbo_a) >> 4);   // per K step
+        const uint64_t b_ks = (uint64_t)((2u * 128u) >> 4);
+        const uint64_t b_lo_off = (uint64_t)(((uint32_t)Lim::ND * 128u) >> 4);
+        uint32_t acc = 0;
+        // Phase ph (kernel rows |p| in [ph*PHASE, ...)) reads operand buffer
+        // ph & 1 and commits to mbar[ph & 1].
+        auto issue = [&](int ph, const int n_ks, const uint32_t idesc) {
+            const int p0 = ph * Lim::PHASE, p1 = min(p0 + Lim::PHASE, R + 1);
+            const uint64_t db_buf = db0 + (uint64_t)(((uint32_t)((ph & 1) * b_buf)) >> 4);
+            for (int ap = p0; ap < p1; ++ap) {
+                const uint64_t dbh_row = db_buf + (uint64_t)(((uint32_t)((ap - p0) * b_row)) >> 4);
+                const uint64_t dbl_row = dbh_row + b_lo_off;
+                for (int sg = (ap == 0 ? 1 : -1); sg <= 1; sg += 2) {
+                    const uint64_t row = (uint64_t)(R - sg * ap);      // (row_off >> 4): rows 16 B apart
+                    uint64_t dah = da_hi0 + row, dal = da_lo0 + row;
+                    uint64_t dbh = dbh_row, dbl = dbl_row;
+                    for (int ks = 0; ks < n_ks; ++ks) {
+                        mma_bf16(tmem, dah, dbh, idesc, acc);
+                        acc = 1;
+                        mma_bf16(tmem, dah, dbl, idesc, 1);
+                        mma_bf16(tmem, dal, dbh, idesc, 1);
+                        dah += a_ks;
+                        dal += a_ks;
+                        dbh += b_ks;
+                        dbl += b_ks;
+                    }
+                }
+            }
+            mma_commit(&mbar[ph & 1]);
+        };
+        // bounded wait of thread 0 on buffer sb, outcome broadcast to the CTA
+        auto wait_buf = [&](int sb) -> bool {
+            if (tid == 0) {
+                long long spins = 0;
+                int ok = 1;
+                while (!mbar_try(&mbar[sb], parity[sb])) {
+                    if (++spins > (1LL << 28)) {
+                        ok = 0;
+                        break;
+                    }
+                }
+                *s_item = ok;
+            }
+            fence_before();
+            __syncthreads();
+            const int ok = *s_item;
+            __syncthreads();
+            fence_after();
+            parity[sb] ^= 1u;
+            return ok != 0;
+        };
+        const int ow = bx.out_j1 - bx.out_j0;
+        const int n_ct = (ow + Lim::MAXN - 1) / Lim::MAXN;
+        const int w_ct = (((ow + n_ct - 1) / n_ct) + 15) & ~15;   // <= MAXN (a multiple of 16)
 
         for (int i0 = bx.out_i0; i0 < bx.out_i1 && !timed_out; i0 += kTcM) {
             const int r0 = i0 - R;   // input row of tile row 0
-            __syncthreads();
-            // input tile: element (row, k) = in(r0 + row, s_end - 1 - k), hi/lo BF16,
-            // 8 consecutive k per thread item (one 16-byte core-matrix row)
-            for (int idx = tid; idx < rows * (kt / 8); idx += blockDim.x) {
-                const int kc = idx / rows, row = idx - kc * rows;
-                const int u = r0 + row;
-                uint32_t hw[4], lw[4];
+            for (int ct = 0; ct < n_ct && !timed_out; ++ct) {
+                const int j0 = bx.out_j0 + ct * w_ct, j1 = min(bx.out_j1, j0 + w_ct);
+                nt = ((j1 - j0) + 15) & ~15;
+                const uint32_t idesc = instr_desc(kTcM, nt);
+                const int sa = max(bx.in_j0, j0 - R), sb = min(bx.in_j1, j0 + nt + R);
+                const int n_kc = sb > sa ? (sb - sa + Lim::MAXK - 1) / Lim::MAXK : 0;
+                const int w_kc = n_kc ? (((sb - sa + n_kc - 1) / n_kc) + 15) & ~15 : 16;
+                acc = 0;
+                for (int kc_i = 0; kc_i < n_kc && !timed_out; ++kc_i) {
+                    // input columns [ka, kb) of this chunk; K position k holds
+                    // column s_end - 1 - k (reversed order, Hankel kernel operand)
+                    const int ka = sa + kc_i * w_kc, kb = min(sb, ka + w_kc);
+                    kt = ((kb - ka) + 15) & ~15;
+                    s_end = ka + kt;
+                    c0 = j0 - s_end + 1;
+                    nd = nt / 8 + kt / 8 - 1;
+                    // the previous chunk's MMAs have completed (waited); before the
+                    // first chunk the previous epilogue's barrier already holds
+                    if (kc_i > 0) __syncthreads();
+                    // input tile: element (row, k) = in(r0 + row, s_end - 1 - k), hi/lo BF16,
+                    // 8 consecutive k per thread item (one 16-byte core-matrix row)
+                    for (int idx = tid; idx < rows * (kt / 8); idx += blockDim.x) {
+                        const int kcol = idx / rows, row = idx - kcol * rows;
+                        const int u = r0 + row;
+                        uint32_t hw[4], lw[4];
 #pragma unroll
-                for (int t = 0; t < 8; t += 2) {
-                    float v[2];
+                        for (int t = 0; t < 8; t += 2) {
+                            float v[2];
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int s = s_end - 1 - (8 * kc + t + e);
-                        float x = 0.f;
-                        if (u >= bx.in_i0 && u < bx.in_i1 && s >= bx.in_j0 && s < bx.in_j1) {
-                            if (ADJ) {
-                                x = hsrc[(long long)(s - st.oj0) * h_w + (u - st.oi0)];
-                            } else {
-                                const float fa = mag_coord(st.m, u, L.cu), fc = mag_coord(st.m, s, L.cv);
-                                const float ba = floorf(fa), bc = floorf(fc);
-                                const int a0 = (int)ba, cc0 = (int)bc;
-                                const float ta = fa - ba, tc = fc - bc;
-                                const int Fc = fc1 - fc0;
+                            for (int e = 0; e < 2; ++e) {
+                                const int s = s_end - 1 - (8 * kcol + t + e);
+                                float x = 0.f;
+                                if (u >= bx.in_i0 && u < bx.in_i1 && s >= ka && s < kb) {
+                                    if (ADJ) {
+                                        x = hsrc[(long long)(s - st.oj0) * h_w + (u - st.oi0)];
+                                    } else {
+                                        const float fa = mag_coord(st.m, u, L.cu), fc = mag_coord(st.m, s, L.cv);
+                                        const float ba = floorf(fa), bc = floorf(fc);
+                                        const int a0 = (int)ba, cc0 = (int)bc;
+                                        const float ta = fa - ba, tc = fc - bc;
+                                        const int Fc = fc1 - fc0;
 #pragma unroll
-                                for (int da = 0; da < 2; ++da) {
-                                    const int a = a0 + da;
-                                    if (a < fa0 || a >= fa1) continue;
-                                    const float wa = da ? ta : 1.f - ta;
+                                        for (int da = 0; da < 2; ++da) {
+                                            const int a = a0 + da;
+                                            if (a < fa0 || a >= fa1) continue;
+                                            const float wa = da ? ta : 1.f - ta;
 #pragma unroll
-                                    for (int dc = 0; dc < 2; ++dc) {
-                                        const int c = cc0 + dc;
-                                        if (c < fc0 || c >= fc1) continue;
-                                        const float wc = dc ? tc : 1.f - tc;
-                                        x += wa * wc * __ldg(&fmap[(long long)(a - fa0) * Fc + (c - fc0)]);
+                                            for (int dc = 0; dc < 2; ++dc) {
+                                                const int c = cc0 + dc;
+                                                if (c < fc0 || c >= fc1) continue;
+                                                const float wc = dc ? tc : 1.f - tc;
+                                                x += wa * wc * __ldg(&fmap[(long long)(a - fa0) * Fc + (c - fc0)]);
+                                            }
+                                        }
                                     }
                                 }
+                                v[e] = x;
                             }
+                            __nv_bfloat16 h0, l0, h1, l1;
+                            split_bf16(v[0], h0, l0);
+                            split_bf16(v[1], h1, l1);
+                            hw[t >> 1] = pack2(h0, h1);
+                            lw[t >> 1] = pack2(l0, l1);
                         }
-                        v[e] = x;
+                        unsigned char *ap = abase + (size_t)kcol * lbo_a + row * 16;
+                        *reinterpret_cast<uint4 *>(ap) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4 *>(ap + a_copy) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
-                    __nv_bfloat16 h0, l0, h1, l1;
-                    split_bf16(v[0], h0, l0);
-                    split_bf16(v[1], h1, l1);
-                    hw[t >> 1] = pack2(h0, h1);
-                    lw[t >> 1] = pack2(l0, l1);
+                    const int n_ks = kt / 16;
+                    build_b(0, min(Lim::PHASE, R + 1), 0, nd, c0);
+                    fence_proxy_async();   // generic-proxy smem writes -> tensor core reads
+                    fence_before();
+                    __syncthreads();
+                    fence_after();
+                    // phase ph + 1 is built and issued while phase ph runs; its
+                    // buffer is free once phase ph - 1 completed
+                    if (tid == 0) issue(0, n_ks, idesc);
+                    int waited = 0;   // phases [0, waited) are known complete
+                    for (int ph = 0; ph + 1 < n_ph && !timed_out; ++ph) {
+                        if (ph >= 1) {
+                            if (!wait_buf((ph - 1) & 1)) timed_out = true;
+                            waited = ph;
+                        }
+                        if (timed_out) break;
+                        build_b((ph + 1) * Lim::PHASE, min((ph + 2) * Lim::PHASE, R + 1), (ph + 1) & 1, nd, c0);
+                        fence_proxy_async();
+                        fence_before();
+                        __syncthreads();
+                        fence_after();
+                        if (tid == 0) issue(ph + 1, n_ks, idesc);
+                    }
+                    for (int ph = waited; ph < n_ph && !timed_out; ++ph)
+                        if (!wait_buf(ph & 1)) timed_out = true;
                 }
-                unsigned char *ap = abase + (size_t)kc * lbo_a + row * 16;
-                *reinterpret_cast<uint4 *>(ap) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4 *>(ap + a_copy) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-            }
-            build_b(0, min(Lim::PHASE, R + 1), 0);
-            fence_proxy_async();   // generic-proxy smem writes -> tensor core reads
-            fence_before();
-            __syncthreads();
-            fence_after();
-            // Phase ph (kernel rows |p| in [ph*PHASE, ...)) reads operand buffer
-            // ph & 1 and commits to mbar[ph & 1].  Phase ph + 1 is built and issued
-            // while phase ph runs; its buffer is free once phase ph - 1 completed.
-            uint32_t acc = 0;
-            // Descriptors are built once per tile; every operand offset is a
-            // multiple of 16 bytes and smem addresses stay below 256 KB, so the
-            // descriptor of base + off is the base descriptor + (off >> 4) in
-            // its 14-bit start-address field (no carry out of the field).
-            const uint32_t a_hi0 = smem_u32(abase);
-            const uint64_t da_hi0 = smem_desc(a_hi0, lbo_a, 128);
-            const uint64_t da_lo0 = smem_desc(a_hi0 + (uint32_t)a_copy, lbo_a, 128);
-            const uint64_t db0 = smem_desc(smem_u32(bbase), 128, 128);
-            const uint64_t a_ks = (uint64_t)((2u * (uint32_t)lbo_a) >> 4);   // per K step
-            const uint64_t b_ks = (uint64_t)((2u * 128u) >> 4);
-            const uint64_t b_lo_off = (uint64_t)(((uint32_t)Lim::ND * 128u) >> 4);
-            const int n_ks = kt / 16;
-            auto issue = [&](int ph) {
-                const int p0 = ph * Lim::PHASE, p1 = min(p0 + Lim::PHASE, R + 1);
-                const uint64_t db_buf = db0 + (uint64_t)(((uint32_t)((ph & 1) * b_buf)) >> 4);
-                for (int ap = p0; ap < p1; ++ap) {
-                    const uint64_t dbh_row = db_buf + (uint64_t)(((uint32_t)((ap - p0) * b_row)) >> 4);
-                    const uint64_t dbl_row = dbh_row + b_lo_off;
-                    for (int sg = (ap == 0 ? 1 : -1); sg <= 1; sg += 2) {
-                        const uint64_t row = (uint64_t)(R - sg * ap);      // (row_off >> 4): rows 16 B apart
-                        uint64_t dah = da_hi0 + row, dal = da_lo0 + row;
-                        uint64_t dbh = dbh_row, dbl = dbl_row;
-                        for (int ks = 0; ks < n_ks; ++ks) {
-                            mma_bf16(tmem, dah, dbh, idesc, acc);
-                            acc = 1;
-                            mma_bf16(tmem, dah, dbl, idesc, 1);
-                            mma_bf16(tmem, dal, dbh, idesc, 1);
-                            dah += a_ks;
-                            dal += a_ks;
-                            dbh += b_ks;
-                            dbl += b_ks;
+                if (timed_out) {
+                    if (tid == 0) {
+                        atomicOr(P.flags, (unsigned)PDRT_FLAG_TIMEOUT);
+                        // second bounded waits for MMAs still in flight before the
+                        // tensor memory is released
+                        long long spins = 0;
+                        while (!mbar_try(&mbar[0], parity[0]) && ++spins < (1LL << 28)) {
+                        }
+                        spins = 0;
+                        while (!mbar_try(&mbar[1], parity[1]) && ++spins < (1LL << 28)) {
                         }
                     }
+                    break;
                 }
-                mma_commit(&mbar[ph & 1]);
-            };
-            // bounded wait of thread 0 on buffer s, outcome broadcast to the CTA
-            auto wait_buf = [&](int sb) -> bool {
-                if (tid == 0) {
-                    long long spins = 0;
-                    int ok = 1;
-                    while (!mbar_try(&mbar[sb], parity[sb])) {
-                        if (++spins > (1LL << 28)) {
-                            ok = 0;
-                            break;
-                        }
-                    }
-                    *s_item = ok;
-                }
-                fence_before();
-                __syncthreads();
-                const int ok = *s_item;
-                __syncthreads();
-                fence_after();
-                parity[sb] ^= 1u;
-                return ok != 0;
-            };
-            if (tid == 0) issue(0);
-            int waited = 0;   // phases [0, waited) are known complete
-            for (int ph = 0; ph + 1 < n_ph && !timed_out; ++ph) {
-                if (ph >= 1) {
-                    if (!wait_buf((ph - 1) & 1)) timed_out = true;
-                    waited = ph;
-                }
-                if (timed_out) break;
-                build_b((ph + 1) * Lim::PHASE, min((ph + 2) * Lim::PHASE, R + 1), (ph + 1) & 1);
-                fence_proxy_async();
-                fence_before();
-                __syncthreads();
-                fence_after();
-                if (tid == 0) issue(ph + 1);
-            }
-            for (int ph = waited; ph < n_ph && !timed_out; ++ph)
-                if (!wait_buf(ph & 1)) timed_out = true;
-            if (timed_out) {
-                if (tid == 0) {
-                    atomicOr(P.flags, (unsigned)PDRT_FLAG_TIMEOUT);
-                    // second bounded waits for MMAs still in flight before the
-                    // tensor memory is released
-                    long long spins = 0;
-                    while (!mbar_try(&mbar[0], parity[0]) && ++spins < (1LL << 28)) {
-                    }
-                    spins = 0;
-                    while (!mbar_try(&mbar[1], parity[1]) && ++spins < (1LL << 28)) {
-                    }
-                }
-                break;
-            }
-            if (timed_out) break;
-            // epilogue: warp w reads TMEM lanes [32 (w % 4), +32) = output rows;
-            // the two warps of a lane quarter take alternate 16-column blocks
-            const int quarter = warp & 3, half = warp >> 2;
-            const int i = i0 + 32 * quarter + lane;
-            const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
-            for (int cb = 16 * half; cb < nt; cb += 32) {
-                float v[16];
-                tmem_ld16(trow + (uint32_t)cb, v);
-                if (i < bx.out_i1) {
-                    float *o = dst + (i - bx.out_i0);
+                // epilogue: warp w reads TMEM lanes [32 (w % 4), +32) = output rows;
+                // the two warps of a lane quarter take alternate 16-column blocks;
+                // the tile writes its own columns [j0, j1)
+                const int quarter = warp & 3, half = warp >> 2;
+                const int i = i0 + 32 * quarter + lane;
+                const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+                for (int cb = 16 * half; cb < nt; cb += 32) {
+                    float v[16];
+                    if (n_kc > 0) {
+                        tmem_ld16(trow + (uint32_t)cb, v);
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        const int j = bx.out_j0 + cb + q;
-                        if (j < bx.out_j1) o[(long long)(j - bx.out_j0) * out_w] = v[q] * scale;
+                        for (int q = 0; q < 16; ++q) v[q] = 0.f;
+                    }
+                    if (i < bx.out_i1) {
+                        float *o = dst + (i - bx.out_i0);
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int j = j0 + cb + q;
+                            if (j < j1) o[(long long)(j - bx.out_j0) * out_w] = v[q] * scale;
+                        }
                     }
                 }
+                fence_before();
+                __syncthreads();   // TMEM reads done before the next tile's MMAs
+                fence_after();
             }
-            fence_before();
         }
     }
     __syncthreads();

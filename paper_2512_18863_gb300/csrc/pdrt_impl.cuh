@@ -29,9 +29,10 @@ constexpr int kConvThreads = 128;        // 4 warps: 32 output rows x (4 x 16) o
 constexpr int kConvTJ = 16;              // output columns per lane
 constexpr int kConvCols = 64;            // output columns per CTA
 constexpr int kConvRows = 32;            // output rows per CTA (one per lane)
-// tensor-core path tile limits (output columns N, input columns K) per direction:
-// the forward has wide outputs and narrow inputs, the adjoint the reverse
-constexpr int kTcFwdMaxN = 96, kTcFwdMaxK = 64;
+// tensor-core tile limits (output columns N, input columns K per chunk) per
+// direction: the forward has wide outputs and narrow inputs, the adjoint the
+// reverse; wider boxes are split into column tiles and input chunks
+constexpr int kTcFwdMaxN = 128, kTcFwdMaxK = 64;
 constexpr int kTcAdjMaxN = 64, kTcAdjMaxK = 96;
 // kernel rows |p| per double-buffered operand phase: the forward's smaller
 // phase buffers let three CTAs share an SM, the adjoint's larger input tile
@@ -176,11 +177,11 @@ __device__ __forceinline__ float overlap_f(float x, float lo, float hi, float d)
 // tensor-core path uses (input columns [s0, s0 + kt), kt and nt multiples of 16).
 struct TcBoxes {
     int in_i0, in_i1, in_j0, in_j1, out_i0, out_i1, out_j0, out_j1;
-    int s0, kt, nt;
 };
 
 __device__ __forceinline__ TcBoxes tc_boxes(const SliceTab &st, bool adj, int R)
 {
+    (void)R;
     TcBoxes b;
     if (adj) {
         b.in_i0 = st.oi0; b.in_i1 = st.oi1; b.in_j0 = st.oj0; b.in_j1 = st.oj1;
@@ -189,22 +190,17 @@ __device__ __forceinline__ TcBoxes tc_boxes(const SliceTab &st, bool adj, int R)
         b.in_i0 = st.pi0; b.in_i1 = st.pi1; b.in_j0 = st.pj0; b.in_j1 = st.pj1;
         b.out_i0 = st.oi0; b.out_i1 = st.oi1; b.out_j0 = st.oj0; b.out_j1 = st.oj1;
     }
-    const int ow = b.out_j1 - b.out_j0;
-    b.nt = ((ow > 0 ? ow : 0) + 15) & ~15;
-    b.s0 = max(b.in_j0, b.out_j0 - R);
-    const int s1 = min(b.in_j1, b.out_j0 + b.nt + R);
-    b.kt = ((s1 > b.s0 ? s1 - b.s0 : 0) + 15) & ~15;
     return b;
 }
 
-// Every slice is convolved by exactly one of k_conv_tc (true) and k_conv (false).
+// Every slice is convolved by exactly one of k_conv_tc (true) and k_conv
+// (false): the tensor-core kernel tiles any box (column tiles and input
+// chunks), so with tensor cores on it takes every slice with work.
 __device__ __forceinline__ bool tc_takes_slice(const SliceTab &st, bool adj, int R, int tc_enabled)
 {
     if (!tc_enabled) return false;
     const TcBoxes b = tc_boxes(st, adj, R);
-    if (b.out_i1 <= b.out_i0 || b.out_j1 <= b.out_j0) return false;
-    const int maxn = adj ? kTcAdjMaxN : kTcFwdMaxN, maxk = adj ? kTcAdjMaxK : kTcFwdMaxK;
-    return b.nt >= 16 && b.nt <= maxn && b.kt >= 16 && b.kt <= maxk;
+    return b.out_i1 > b.out_i0 && b.out_j1 > b.out_j0 && b.in_i1 > b.in_i0 && b.in_j1 > b.in_j0;
 }
 
 // launchers (one per kernel); each returns cudaGetLastError() of its launch
