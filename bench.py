@@ -49,7 +49,7 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--warm-cases", type=int, default=6,
                     help="held-out phantoms for the warm-versus-plain figure (0 = skip)")
-    ap.add_argument("--workload", default="pelvis256", choices=["pelvis256", "pelvis128", "batch32"],
+    ap.add_argument("--workload", default="pelvis256", choices=["pelvis256", "pelvis128", "paper180", "batch32"],
                     help="pelvis256: 256x256x160 @ 2 mm, 2 x 178 CPs (headline); "
                          "pelvis128: 128x128x96 @ 3 mm, 178 CPs (smaller case for profiler captures); "
                          "batch32: 32 uneven plans in one CUDA-graph launch (its own JSON line)")
@@ -93,6 +93,8 @@ def _workload(r_cm, name="pelvis256"):
     from paper_2512_18863_gb300 import synth
     if name == "pelvis128":
         return synth.pelvis_arc_128(r_cm=r_cm)
+    if name == "paper180":
+        return synth.paper_table_arc()
     return synth.pelvis_two_arc_256(r_cm=r_cm)
 
 
@@ -383,7 +385,7 @@ def _gpu(args):
 
     if rank == 0:
         nz, ny, nx = w.phantom.shape
-        sp = float(w.phantom.spacing[0])
+        sp = [float(x) for x in w.phantom.spacing]
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -497,12 +497,14 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     p->tc_blocks = 0;
     p->tc_blocks_adj = 0;
     P.tc_enabled = 0;
-    if (conv_tc_smem_bytes(M.R, true) <= 220 * 1024 && conv_tc_smem_bytes(M.R, false) <= 220 * 1024) {
-        int bt_f = 0, bt_a = 0;
-        PLAN_TRY(conv_tc_prepare(M.R, &bt_f, &bt_a), "tensor-core convolution set-up");
+    {
+        int bt_f = 0, bt_a = 0, ph_f = 1, ph_a = 1;
+        PLAN_TRY(conv_tc_prepare(M.R, &bt_f, &bt_a, &ph_f, &ph_a), "tensor-core convolution set-up");
         if (bt_f > 0 && bt_a > 0) {
             p->tc_blocks = bt_f * g->sm_count;
             p->tc_blocks_adj = bt_a * g->sm_count;
+            P.tc_phase[0] = ph_f;
+            P.tc_phase[1] = ph_a;
             P.tc_enabled = 1;
         }
     }

@@ -21,7 +21,8 @@
 // One CTA (8 warps) per slice, persistent over a work counter.  Thread 0
 // issues the MMAs; completion is signalled through an mbarrier
 // (tcgen05.commit); all waits are bounded and raise PDRT_FLAG_TIMEOUT.  The
-// kernel-row operands are built in phases of PHASE rows into a double
+// kernel-row operands are built in phases of PHASE rows (chosen per plan:
+// the deepest phase that keeps the most CTAs per SM) into a double
 // buffer, each phase while the previous phase's MMAs run; with the per
 // direction tile limits two CTAs fit on an SM.
 // Boxes wider than one tile are split into output-column tiles of at most
@@ -52,20 +53,19 @@ struct TcLimits {
     static constexpr int MAXN = ADJ ? kTcAdjMaxN : kTcFwdMaxN;
     static constexpr int MAXK = ADJ ? kTcAdjMaxK : kTcFwdMaxK;
     static constexpr int ND = MAXN / 8 + MAXK / 8 - 1;   // Hankel diagonals per kernel row
-    static constexpr int PHASE = ADJ ? kTcPhaseAdj : kTcPhaseFwd;   // kernel rows per operand phase
 };
 
 // shared memory: [0,128) barrier / tmem address / broadcast; kernel rows;
 // input tile hi+lo [2][K/8][rows][16 B]; kernel-row operands, two buffers of
-// PHASE rows x hi+lo x ND core matrices
-int conv_tc_smem_bytes(int R, bool adjoint)
+// `phase` rows x hi+lo x ND core matrices
+int conv_tc_smem_bytes(int R, bool adjoint, int phase)
 {
     const int rows = tc_rows(R);
     const int maxk = adjoint ? kTcAdjMaxK : kTcFwdMaxK;
     const int nd = adjoint ? TcLimits<true>::ND : TcLimits<false>::ND;
     const int krow = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
     const int a = 2 * rows * maxk * 2;
-    const int bsz = 2 * (adjoint ? kTcPhaseAdj : kTcPhaseFwd) * 2 * nd * 128;
+    const int bsz = 2 * phase * 2 * nd * 128;
     return 128 + krow + a + bsz;
 }
 
@@ -90,7 +90,8 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
     const int a_copy = rows * Lim::MAXK * 2;                    // bytes of one (hi or lo) tile
     unsigned char *bbase = abase + 2 * a_copy;
     const int b_row = 2 * Lim::ND * 128;                        // hi + lo of one kernel row
-    const int b_buf = Lim::PHASE * b_row;
+    const int PHASE = ADJ ? P.tc_phase[1] : P.tc_phase[0];   // kernel rows per operand phase
+    const int b_buf = PHASE * b_row;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int n_items = nb * L.nw;
 
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                 *reinterpret_cast<uint4 *>(bp + (size_t)Lim::ND * 128) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
         };
-        const int n_ph = (R + Lim::PHASE) / Lim::PHASE;   // phases over |p| = 0..R
+        const int n_ph = (R + PHASE) / PHASE;   // phases over |p| = 0..R
         const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
         const int fa0 = P.cptab[b].fa0, fa1 = P.cptab[b].fa1, fc0 = P.cptab[b].fc0, fc1 = P.cptab[b].fc1;
         const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
         // Phase ph (kernel rows |p| in [ph*PHASE, ...)) reads operand buffer
         // ph & 1 and commits to mbar[ph & 1].
         auto issue = [&](int ph, const int n_ks, const uint32_t idesc) {
-            const int p0 = ph * Lim::PHASE, p1 = min(p0 + Lim::PHASE, R + 1);
+            const int p0 = ph * PHASE, p1 = min(p0 + PHASE, R + 1);
             const uint64_t db_buf = db0 + (uint64_t)(((uint32_t)((ph & 1) * b_buf)) >> 4);
             for (int ap = p0; ap < p1; ++ap) {
                 const uint64_t dbh_row = db_buf + (uint64_t)(((uint32_t)((ap - p0) * b_row)) >> 4);
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                         *reinterpret_cast<uint4 *>(ap + a_copy) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
                     const int n_ks = kt / 16;
-                    build_b(0, min(Lim::PHASE, R + 1), 0, nd, c0);
+                    build_b(0, min(PHASE, R + 1), 0, nd, c0);
                     fence_proxy_async();   // generic-proxy smem writes -> tensor core reads
                     fence_before();
                     __syncthreads();
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                             waited = ph;
                         }
                         if (timed_out) break;
-                        build_b((ph + 1) * Lim::PHASE, min((ph + 2) * Lim::PHASE, R + 1), (ph + 1) & 1, nd, c0);
+                        build_b((ph + 1) * PHASE, min((ph + 2) * PHASE, R + 1), (ph + 1) & 1, nd, c0);
                         fence_proxy_async();
                         fence_before();
                         __syncthreads();
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
 cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
                            int grid_blocks, cudaStream_t s)
 {
-    const int smem = conv_tc_smem_bytes(P.mach.R, adjoint);
+    const int smem = conv_tc_smem_bytes(P.mach.R, adjoint, P.tc_phase[adjoint ? 1 : 0]);
     if (adjoint)
         k_conv_tc<true><<<grid_blocks, kTcThreads, smem, s>>>(P, b0, nb, counter);
     else
@@ -396,7 +397,7 @@ cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsig
 // pull work items and never wait for one another), so a grid larger than
 // what is resident only queues.
 template <bool ADJ>
-static cudaError_t tc_ctas_per_sm(int R, int *out)
+static cudaError_t tc_ctas_per_sm(int R, int phase, int *out)
 {
     int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -406,7 +407,7 @@ static cudaError_t tc_ctas_per_sm(int R, int *out)
     cudaFuncAttributes fa;
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conv_tc<ADJ>);
     if (e != cudaSuccess) return e;
-    const int per_cta = conv_tc_smem_bytes(R, ADJ) + (int)fa.sharedSizeBytes + resv;
+    const int per_cta = conv_tc_smem_bytes(R, ADJ, phase) + (int)fa.sharedSizeBytes + resv;
     const int by_smem = smem_sm / per_cta;
     const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
     const int by_regs = regs_sm / (regs_warp * (kTcThreads / 32));
@@ -417,12 +418,33 @@ static cudaError_t tc_ctas_per_sm(int R, int *out)
     return cudaSuccess;
 }
 
-cudaError_t conv_tc_prepare(int R, int *fwd_blocks_per_sm, int *adj_blocks_per_sm)
+// Per direction: the phase depth (kernel rows per operand buffer, 4..1) that
+// gives the most CTAs per SM, the deepest one among equals (fewer barriers).
+template <bool ADJ>
+static cudaError_t pick_phase(int R, int *blocks, int *phase)
+{
+    *blocks = 0;
+    *phase = 1;
+    for (int ph = 4; ph >= 1; --ph) {
+        if (conv_tc_smem_bytes(R, ADJ, ph) > 220 * 1024) continue;
+        int n = 0;
+        cudaError_t e = tc_ctas_per_sm<ADJ>(R, ph, &n);
+        if (e != cudaSuccess) return e;
+        if (n > *blocks) {
+            *blocks = n;
+            *phase = ph;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t conv_tc_prepare(int R, int *fwd_blocks_per_sm, int *adj_blocks_per_sm, int *fwd_phase,
+                            int *adj_phase)
 {
     cudaError_t e = allow_full_smem(k_conv_tc<false>);
     if (e == cudaSuccess) e = allow_full_smem(k_conv_tc<true>);
-    if (e == cudaSuccess) e = tc_ctas_per_sm<false>(R, fwd_blocks_per_sm);
-    if (e == cudaSuccess) e = tc_ctas_per_sm<true>(R, adj_blocks_per_sm);
+    if (e == cudaSuccess) e = pick_phase<false>(R, fwd_blocks_per_sm, fwd_phase);
+    if (e == cudaSuccess) e = pick_phase<true>(R, adj_blocks_per_sm, adj_phase);
     return e;
 }
 

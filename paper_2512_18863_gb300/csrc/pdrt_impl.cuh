@@ -34,10 +34,6 @@ constexpr int kConvRows = 32;            // output rows per CTA (one per lane)
 // reverse; wider boxes are split into column tiles and input chunks
 constexpr int kTcFwdMaxN = 128, kTcFwdMaxK = 64;
 constexpr int kTcAdjMaxN = 64, kTcAdjMaxK = 96;
-// kernel rows |p| per double-buffered operand phase: the forward's smaller
-// phase buffers let three CTAs share an SM, the adjoint's larger input tile
-// allows two
-constexpr int kTcPhaseFwd = 2, kTcPhaseAdj = 4;
 
 enum KernelId {
     K_HU = 0, K_RASTER = 1, K_TABLES = 2, K_CONV_FWD = 3, K_GATHER = 4,
@@ -126,7 +122,8 @@ struct PlanDev {
     long long cap_o, cap_a;  // floats per CP slot
     unsigned int *flags;
     unsigned int *counters;  // work-queue counters (per chunk launch)
-    int tc_enabled;          // 1: slices that fit the tensor-core tiles go to k_conv_tc
+    int tc_enabled;          // 1: every slice with work goes to k_conv_tc
+    int tc_phase[2];         // kernel rows per operand phase of k_conv_tc (forward, adjoint)
 };
 
 // Same float expression in every kernel that samples or transposes the
@@ -223,7 +220,8 @@ int conv_nq4_for_radius(int R);
 cudaError_t conv_prepare(const MachineDev &m, int *fwd_blocks_per_sm, int *adj_blocks_per_sm);
 cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
                            int grid_blocks, cudaStream_t s);
-cudaError_t conv_tc_prepare(int R, int *fwd_blocks_per_sm, int *adj_blocks_per_sm);
+cudaError_t conv_tc_prepare(int R, int *fwd_blocks_per_sm, int *adj_blocks_per_sm, int *fwd_phase,
+                            int *adj_phase);
 // Device form of a machine's fluence corrections (taps, profile, rotation);
 // returns an error text or NULL.  Pitches du, dv in mm.
 const char *machine_corrections(const pdrt_machine *m, double du, double dv, MachineDev &M);
@@ -249,7 +247,7 @@ inline cudaError_t allow_full_smem(Kern kern)
                                  (int)cudaSharedmemCarveoutMaxShared);
     return e;
 }
-int conv_tc_smem_bytes(int R, bool adjoint);
+int conv_tc_smem_bytes(int R, bool adjoint, int phase);
 void internal_set_error(const char *msg);   // sets pdrt_last_error() for this thread
 void internal_count_launch();                // counts one launch in pdrt_launch_count()
 

@@ -304,6 +304,16 @@ def pelvis_two_arc_256(seed=1002, n_cp_arc=178, r_cm=4.0, shape=(160, 256, 256),
     return Workload(f"pelvis{nx}x{ny}x{nz}_2x{n_cp_arc}cp_R{r_cm:g}cm", ph, m, pl)
 
 
+def paper_table_arc(seed=1006) -> Workload:
+    """The shape of the paper's timing table (Sec. 3.4): a 180-CP arc on a
+    105 x 224 x 224 grid with a 55-pixel lateral kernel (R = 27 px); voxel
+    size 2.5 mm in-plane, 3 mm between slices (not stated there)."""
+    m = machine_model(seed, r_px=27)
+    ph = pelvis_phantom((105, 224, 224), (2.5, 2.5, 3.0), seed=seed)
+    pl = arc_plan(m, arc_angles(180), seed=seed)
+    return Workload("pelvis224x224x105_arc180_K55", ph, m, pl)
+
+
 def small_pelvis(seed=7, n=(24, 40, 40), spacing=3.0, n_cp=6, r_px=4, ptv_radii=(20.0, 15.0, 18.0)):
     """Reduced pelvis case for parity tests (several CTA tiles, ragged edges)."""
     m = machine_model(seed, r_px=r_px)

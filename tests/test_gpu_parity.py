@@ -254,3 +254,69 @@ def test_full_size_gradient_sampled_against_oracle(c3):
     _assert_grad(dj, rj, "jaws")
     _assert_grad(dm, rm, "mu")
     eng.close()
+
+
+def test_full_size_8cm_kernel_sampled_against_oracle():
+    """R = 40 px (8 cm at 2 mm): output and input boxes wider than one
+    tensor-core tile (column tiles and input-column chunks), full grid, one
+    control point: dose and gradients against the oracle."""
+    w = S.pelvis_two_arc_256(r_cm=8.0)
+    sub = _subplan(w, np.array([60]))
+    gpu = _gpu_dose(sub)
+    mod = O.Model(sub.phantom, sub.machine, sub.plan)
+    ref = mod.dose()
+    _assert_dose(gpu, ref)
+    g = np.random.default_rng(12).standard_normal(sub.phantom.shape).astype(np.float32)
+    eng = _engine(sub)
+    assert eng.info["tensor_cores"] == 1
+    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
+                  for t in eng.backward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu, g))
+    eng.close()
+    rl, rj, rm = mod.dose_grad(g.astype(np.float64))
+    _assert_grad(dl, rl, "leaves")
+    _assert_grad(dj, rj, "jaws")
+    _assert_grad(dm, rm, "mu")
+
+
+def test_full_size_gradient_vs_central_differences(c3):
+    """Two-arc plan at full size (356 CPs): the adjoint on 64 random
+    differentiable parameters (leaf edges, jaw edges, MUs away from kinks) of
+    8 random control points against central differences (0.01 mm / 0.01 MU)
+    of L = <g, D>.  D is a sum over control points (Eq. D_total), so the
+    difference of L is that of the perturbed control point's own dose: it is
+    taken on a one-CP plan (L summed in FP64), which keeps the FP32 rounding
+    of the 356-term dose sum out of the 0.01 mm difference."""
+    import torch
+    from tests.test_oracle_adjoint import _pick_params
+    rng = np.random.default_rng(21)
+    eng = _engine(c3)
+    g = rng.standard_normal(c3.phantom.shape).astype(np.float32)
+    grads = dict(zip(("leaves", "jaws", "mu"),
+                     (t.cpu().numpy().astype(np.float64)
+                      for t in eng.backward(c3.plan.leaves, c3.plan.jaws, c3.plan.mu, g))))
+    eng.close()
+    scale = {k: np.abs(v).max() for k, v in grads.items()}
+    cps = np.sort(rng.choice(c3.plan.n_cp, 8, replace=False))
+    sub8 = _subplan(c3, cps)
+    picks = _pick_params(sub8, O.Model(sub8.phantom, sub8.machine, sub8.plan), rng, 64)
+    assert len(picks) == 64
+    h = 0.01
+    for j, b in enumerate(cps):
+        one = _subplan(c3, np.array([b]))
+        e1 = _engine(one)
+        gt = torch.tensor(g, device=e1.device, dtype=torch.float64)
+        base = {"leaves": one.plan.leaves, "jaws": one.plan.jaws, "mu": one.plan.mu}
+        for name, ix in picks:
+            if ix[0] != j:
+                continue
+            ix1 = (0,) + tuple(ix[1:])
+            vals = []
+            for sgn in (+1, -1):
+                p = {k: v.copy() for k, v in base.items()}
+                p[name][ix1] += sgn * h
+                D = e1.forward(p["leaves"], p["jaws"], p["mu"])
+                vals.append(float((D.double() * gt).sum()))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            an = grads[name][(b,) + tuple(ix[1:])]
+            assert abs(fd - an) <= 1e-3 * scale[name], (name, b, ix, fd, an, scale[name])
+        e1.close()
