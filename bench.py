@@ -98,6 +98,17 @@ def _workload(r_cm, name="pelvis256"):
     return synth.pelvis_two_arc_256(r_cm=r_cm)
 
 
+def _config(w, world):
+    """The workload description both arms print (identical for the ratio)."""
+    nz, ny, nx = w.phantom.shape
+    return {"workload": w.name, "grid": [nx, ny, nz],
+            "spacing_mm": [float(x) for x in w.phantom.spacing],
+            "n_cp": int(w.plan.n_cp), "kernel_radius_px": int(w.machine.r_px),
+            "step": "forward + adjoint of all control points",
+            "l2": "flushed between steps (256 MB write)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def _subplan(w, sel):
     from paper_2512_18863_gb300 import synth
     return synth.Workload(w.name, w.phantom, w.machine,
@@ -210,13 +221,11 @@ def _reference(args):
             times.append(time.perf_counter() - t0)
     per_step = float(np.mean(times))
     value = (1.0 / CP_PER_ARC) / per_step
-    nz, ny, nx = w.phantom.shape
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded pelvis phantom and VMAT arcs)",
-           "config": {"workload": w.name, "grid": [nx, ny, nz], "spacing_mm": 2.0,
-                      "n_cp": int(w.plan.n_cp), "kernel_radius_px": int(w.machine.r_px)},
+           "config": _config(w, world),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                             "kind": "oracle",
                             "sample": "one control point per step (fwd+adjoint), full grid"},
@@ -384,18 +393,11 @@ def _gpu(args):
         warm = _warm_start(args.warm_cases)
 
     if rank == 0:
-        nz, ny, nx = w.phantom.shape
-        sp = [float(x) for x in w.phantom.spacing]
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded pelvis phantom and VMAT arcs)",
-               "config": {"workload": w.name, "grid": [nx, ny, nz], "spacing_mm": sp,
-                          "n_cp": int(w.plan.n_cp), "kernel_radius_px": int(w.machine.r_px),
-                          "step": "forward + adjoint of all control points",
-                          "scratch_gb": args.scratch_gb,
-                          "l2": "flushed between steps (256 MB write)",
-                          "parallelism": "replicas" if world > 1 else "single"},
+               "config": _config(w, world),
                "roofline": {"bound": bound, "kernel": "convolution (forward + adjoint)",
                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                             "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
@@ -405,7 +407,7 @@ def _gpu(args):
                             "fp32_alu_frac": achieved / (SMS * FP32_LANES * 2 * 2070.0e6 / 1e12),
                             "tensor_issued_tflops": (mma_flops / (tc_ms / 1e3) / 1e12) if tc_ms else None},
                "kernels": kernels, "work": work, "gpu_launches": launches,
-               "launch": {"tc_ctas_per_sm": info.get("tc_ctas_per_sm"),
+               "launch": {"scratch_gb": args.scratch_gb, "tc_ctas_per_sm": info.get("tc_ctas_per_sm"),
                           "simt_ctas_per_sm": info.get("simt_ctas_per_sm"),
                           "chunk_cp": info.get("chunk_cp")},
                "hbm_literal": hbm, "warm_start": warm,

@@ -548,9 +548,11 @@ pdrt_status pdrt_dose_forward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_
                                                    p->tc_blocks, s);
                          }),
                    "conv_forward_tc launch");
-        CU_TRY(timed(p, K_CONV_FWD, s,
-                     [&] { return launch_conv(P, b0, nb, false, P.counters + c, p->conv_blocks_fwd, s); }),
-               "conv_forward launch");
+        // with tensor cores on, k_conv_tc takes every slice (tc_takes_slice)
+        if (!P.tc_enabled)
+            CU_TRY(timed(p, K_CONV_FWD, s,
+                         [&] { return launch_conv(P, b0, nb, false, P.counters + c, p->conv_blocks_fwd, s); }),
+                   "conv_forward launch");
         CU_TRY(timed(p, K_GATHER, s, [&] { return launch_gather(P, b0, nb, dose_dev, c == 0, s); }),
                "gather launch");
     }
@@ -586,9 +588,10 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
                                                    p->tc_blocks_adj, s);
                          }),
                    "conv_adjoint_tc launch");
-        CU_TRY(timed(p, K_CONV_ADJ, s,
-                     [&] { return launch_conv(P, b0, nb, true, ctr + c, p->conv_blocks_adj, s); }),
-               "conv_adjoint launch");
+        if (!P.tc_enabled)
+            CU_TRY(timed(p, K_CONV_ADJ, s,
+                         [&] { return launch_conv(P, b0, nb, true, ctr + c, p->conv_blocks_adj, s); }),
+                   "conv_adjoint launch");
         CU_TRY(timed(p, K_MAG_T_GRAD, s, [&] { return launch_mag_T(P, b0, nb, s); }),
                "mag_transpose launch");
     }
