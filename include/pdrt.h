@@ -186,8 +186,9 @@ void pdrt_grid_destroy(pdrt_grid_t g);
  *   iso_mm           isocentre, patient frame (host, 3 values).
  *   m                beam model (host, copied).
  *   scratch_budget_bytes  upper bound on the device scratch the plan may own
- *                    (0 = library default); it sets how many control points
- *                    one pass processes.
+ *                    (0 = library default: a quarter of the free device
+ *                    memory, between 1 and 32 GiB); it sets how many control
+ *                    points one pass processes (passes are balanced).
  * The plan owns all device scratch the forward and backward passes need.
  * Errors: EINVAL (bad values; kernel radius above PDRT_MAX_RADIUS_PX;
  * SID not larger than the grid's reach from the isocentre), ENOMEM, ECUDA.

@@ -66,7 +66,7 @@ def test_water_static_10x10_matches_oracle_and_closed_form(tensor_cores):
     ((23, 37, 41), 3.0, 5, 3, 8),      # ragged, odd grid, nx != ny
     ((20, 33, 33), 4.0, 4, 10, 9),     # R = 10 px
     ((18, 30, 30), 4.0, 3, 21, 10),    # R = 21 px
-    ((16, 28, 28), 5.0, 2, 44, 11),    # maximum radius (tiles too wide: FP32 SIMT)
+    ((16, 28, 28), 5.0, 2, 44, 11),    # maximum radius: column tiles and input chunks
     ((40, 48, 48), 2.0, 3, 13, 12),    # 2 mm grid, R = 13
 ])
 def test_pelvis_forward_matches_oracle(n, spacing, n_cp, r_px, seed, tensor_cores):
