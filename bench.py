@@ -407,7 +407,8 @@ def _gpu(args):
                             "fp32_alu_frac": achieved / (SMS * FP32_LANES * 2 * 2070.0e6 / 1e12),
                             "tensor_issued_tflops": (mma_flops / (tc_ms / 1e3) / 1e12) if tc_ms else None},
                "kernels": kernels, "work": work, "gpu_launches": launches,
-               "launch": {"scratch_gb": args.scratch_gb, "tc_ctas_per_sm": info.get("tc_ctas_per_sm"),
+               "launch": {"scratch_gb": args.scratch_gb, "tc_phase": info.get("tc_phase"),
+                          "tc_ctas_per_sm": info.get("tc_ctas_per_sm"),
                           "simt_ctas_per_sm": info.get("simt_ctas_per_sm"),
                           "chunk_cp": info.get("chunk_cp")},
                "hbm_literal": hbm, "warm_start": warm,
@@ -469,7 +470,9 @@ def _gpu_batch(args):
                "data": "synthetic (seeded pelvis phantoms, uneven grids and arcs)",
                "config": {"workload": "batch32_uneven", "plans": len(ws), "control_points": n_cp,
                           "grids": [list(w.phantom.shape[::-1]) for w in ws],
-                          "schedules": [[e.info["tensor_cores"], e.info["chunk_cp"]] for e in engines]},
+                          "schedules": [{"tensor_cores": e.info["tensor_cores"], "chunk_cp": e.info["chunk_cp"],
+                                         "tc_phase": e.info["tc_phase"],
+                                         "tc_ctas_per_sm": e.info["tc_ctas_per_sm"]} for e in engines]},
                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                               "max": float(lat.max())},
                "arc_evals_per_s": n_cp / CP_PER_ARC * args.steps * world / (total_ms / 1e3),

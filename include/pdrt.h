@@ -141,6 +141,7 @@ typedef struct {
     int32_t tensor_cores;        /* 1: convolution tiles that fit run on the tensor cores */
     int32_t tc_ctas_per_sm[2];   /* tensor-core convolution CTAs per SM (forward, adjoint) */
     int32_t simt_ctas_per_sm[2]; /* resident FP32 convolution CTAs per SM (forward, adjoint) */
+    int32_t tc_phase[2];         /* tensor-core kernel rows per operand phase (forward, adjoint) */
 } pdrt_plan_info;
 
 /* Work counters of the last forward/backward call (for roofline accounting). */
@@ -299,11 +300,22 @@ pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int32_t ny, in
 pdrt_status pdrt_plan_set_chunk(pdrt_plan_t p, int32_t chunk_cp);
 
 /*
- * Autotuner: times one forward (+ adjoint if dose_grad_dev != NULL) pass of
- * the plan for every candidate schedule -- convolution on the tensor cores or
- * on the FP32 SIMT kernel, and the control points per pass (the uploaded
- * count, 1/2 and 1/4 of it) -- with CUDA events on `stream`, keeps the
- * fastest on the plan and reports it.  Output buffers are overwritten.
+ * Tensor-core tile shape: kernel rows per operand phase of the forward and
+ * adjoint convolution (1..4; sets the shared memory per CTA and so the CTAs
+ * per SM).  The upload picks, per direction, the deepest phase that keeps the
+ * most CTAs per SM.  Errors: EINVAL (tensor-core path unavailable, or a phase
+ * outside 1..4 or that does not fit).  Host only.
+ */
+pdrt_status pdrt_plan_set_tc_phase(pdrt_plan_t p, int32_t phase_forward, int32_t phase_adjoint);
+
+/*
+ * Autotuner: times forward (+ adjoint if dose_grad_dev != NULL) passes of the
+ * plan with CUDA events on `stream` and keeps the fastest schedule, searched
+ * one coordinate at a time from the upload's choice: the convolution path
+ * (tensor cores or FP32 SIMT), then the tensor-core tile shape of each
+ * direction (kernel rows per operand phase, 1..4, which sets the shared
+ * memory and so the CTAs per SM), then the control points per pass (the
+ * uploaded count, 1/2 and 1/4 of it).  Output buffers are overwritten.
  * Synchronous.
  */
 typedef struct {
@@ -311,6 +323,8 @@ typedef struct {
     int32_t chunk_cp;            /* chosen control points per pass */
     float best_ms;               /* time of the chosen schedule */
     int32_t n_candidates;        /* schedules timed */
+    int32_t phase[2];            /* tensor-core kernel rows per operand phase (forward, adjoint) */
+    int32_t tc_ctas_per_sm[2];   /* resulting tensor-core CTAs per SM (forward, adjoint) */
 } pdrt_tune_result;
 pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_dev,
                                const float *jaws_dev, const float *mu_dev, float *dose_dev,

@@ -50,7 +50,7 @@ class pdrt_plan_info(C.Structure):
                 ("cu", C.c_double), ("cv", C.c_double), ("cw", C.c_double),
                 ("n_cp", C.c_int32), ("chunk_cp", C.c_int32), ("scratch_bytes", C.c_size_t),
                 ("tensor_cores", C.c_int32), ("tc_ctas_per_sm", C.c_int32 * 2),
-                ("simt_ctas_per_sm", C.c_int32 * 2)]
+                ("simt_ctas_per_sm", C.c_int32 * 2), ("tc_phase", C.c_int32 * 2)]
 
 
 class pdrt_work(C.Structure):
@@ -61,7 +61,7 @@ class pdrt_work(C.Structure):
 
 class pdrt_tune_result(C.Structure):
     _fields_ = [("tensor_cores", C.c_int32), ("chunk_cp", C.c_int32), ("best_ms", C.c_float),
-                ("n_candidates", C.c_int32)]
+                ("n_candidates", C.c_int32), ("phase", C.c_int32 * 2), ("tc_ctas_per_sm", C.c_int32 * 2)]
 
 
 class pdrt_profile(C.Structure):
@@ -90,6 +90,7 @@ _SIG = {
                                       C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.c_double, C.POINTER(pdrt_machine), _VP, _VP, _VP, _VP, _VP]),
     "pdrt_plan_set_chunk": (C.c_int, [_VP, C.c_int32]),
+    "pdrt_plan_set_tc_phase": (C.c_int, [_VP, C.c_int32, C.c_int32]),
     "pdrt_plan_autotune": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                      C.POINTER(pdrt_tune_result)]),
     "pdrt_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP), C.POINTER(_VP),
@@ -210,6 +211,7 @@ def pdrt_plan_get_info(plan) -> dict:
     out = {k: getattr(info, k) for k, _ in pdrt_plan_info._fields_}
     out["simt_ctas_per_sm"] = list(out["simt_ctas_per_sm"])
     out["tc_ctas_per_sm"] = list(out["tc_ctas_per_sm"])
+    out["tc_phase"] = list(out["tc_phase"])
     return out
 
 
@@ -262,7 +264,10 @@ def pdrt_plan_autotune(grid, plan, leaves_ptr, jaws_ptr, mu_ptr, dose_ptr, dose_
                                      _VP(mu_ptr), _VP(dose_ptr), _VP(dose_grad_ptr),
                                      _VP(dleaves_ptr), _VP(djaws_ptr), _VP(dmu_ptr), _VP(stream),
                                      C.byref(r)))
-    return {k: getattr(r, k) for k, _ in pdrt_tune_result._fields_}
+    out = {k: getattr(r, k) for k, _ in pdrt_tune_result._fields_}
+    for k in ("phase", "tc_ctas_per_sm"):
+        out[k] = list(out[k])
+    return out
 
 
 def _ptr_array(values):
@@ -400,3 +405,7 @@ def pdrt_bev_project(masks_dev, nx, ny, nz, spacing, origin, iso, sid, gantry_de
                                    (C.c_double * 3)(*[float(x) for x in iso]), float(sid),
                                    len(gantry_deg), g, int(side), float(pitch), float(reach),
                                    float(step), _VP(out_dev), _VP(stream)))
+
+
+def pdrt_plan_set_tc_phase(plan, phase_forward, phase_adjoint):
+    _check(load().pdrt_plan_set_tc_phase(_VP(plan), int(phase_forward), int(phase_adjoint)))

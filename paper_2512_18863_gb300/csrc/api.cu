@@ -634,6 +634,8 @@ pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out)
     out->tc_ctas_per_sm[1] = p->grid->sm_count > 0 ? p->tc_blocks_adj / p->grid->sm_count : 0;
     out->simt_ctas_per_sm[0] = p->grid->sm_count > 0 ? p->conv_blocks_fwd / p->grid->sm_count : 0;
     out->simt_ctas_per_sm[1] = p->grid->sm_count > 0 ? p->conv_blocks_adj / p->grid->sm_count : 0;
+    out->tc_phase[0] = p->dev.tc_phase[0];
+    out->tc_phase[1] = p->dev.tc_phase[1];
     return PDRT_OK;
 }
 
@@ -751,6 +753,23 @@ pdrt_status pdrt_plan_set_chunk(pdrt_plan_t p, int32_t chunk_cp)
     return PDRT_OK;
 }
 
+pdrt_status pdrt_plan_set_tc_phase(pdrt_plan_t p, int32_t phase_forward, int32_t phase_adjoint)
+{
+    g_last_error.clear();
+    if (!p) return fail(PDRT_EINVAL, "NULL plan");
+    if (p->tc_blocks <= 0) return fail(PDRT_EINVAL, "tensor-core path unavailable for this plan");
+    int nf = 0, na = 0;
+    CU_TRY(conv_tc_ctas(p->dev.mach.R, false, phase_forward, &nf), "tensor-core occupancy");
+    CU_TRY(conv_tc_ctas(p->dev.mach.R, true, phase_adjoint, &na), "tensor-core occupancy");
+    if (phase_forward > 4 || phase_adjoint > 4 || nf < 1 || na < 1)
+        return fail(PDRT_EINVAL, "phase depths must be in 1..4 and fit in shared memory");
+    p->dev.tc_phase[0] = phase_forward;
+    p->dev.tc_phase[1] = phase_adjoint;
+    p->tc_blocks = nf * p->grid->sm_count;
+    p->tc_blocks_adj = na * p->grid->sm_count;
+    return PDRT_OK;
+}
+
 pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_dev,
                                const float *jaws_dev, const float *mu_dev, float *dose_dev,
                                const float *dose_grad_dev, float *dleaves_dev, float *djaws_dev,
@@ -764,54 +783,106 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
     cudaStream_t s = (cudaStream_t)stream;
     const bool prof = p->profiling;
     p->profiling = false;
-    std::vector<std::pair<int, int>> cand;
-    for (int tc = (p->tc_blocks > 0 ? 1 : 0); tc >= 0; --tc)
-        for (int c : {p->chunk_max, (p->chunk_max + 1) / 2, (p->chunk_max + 3) / 4})
-            if (c >= 1 && (cand.empty() || cand.back() != std::make_pair(tc, c)))
-                cand.push_back({tc, c});
+    const int sm = g->sm_count, R = p->dev.mach.R;
+    struct Sched {
+        int tc, chunk, ph_f, ph_a;
+    };
+    const bool tc_ok = p->tc_blocks > 0;
+    const Sched start = {p->dev.tc_enabled, p->chunk, p->dev.tc_phase[0], p->dev.tc_phase[1]};
+    int ctas_f = tc_ok ? p->tc_blocks / sm : 0, ctas_a = tc_ok ? p->tc_blocks_adj / sm : 0;
+    auto apply = [&](const Sched &c) -> pdrt_status {
+        p->dev.tc_enabled = c.tc;
+        p->chunk = c.chunk;
+        if (tc_ok) {
+            int nf = 0, na = 0;
+            CU_TRY(conv_tc_ctas(R, false, c.ph_f, &nf), "tensor-core occupancy");
+            CU_TRY(conv_tc_ctas(R, true, c.ph_a, &na), "tensor-core occupancy");
+            p->dev.tc_phase[0] = c.ph_f;
+            p->dev.tc_phase[1] = c.ph_a;
+            p->tc_blocks = nf * sm;
+            p->tc_blocks_adj = na * sm;
+            ctas_f = nf;
+            ctas_a = na;
+        }
+        return PDRT_OK;
+    };
     cudaEvent_t e0, e1;
     CU_TRY(cudaEventCreate(&e0), "cudaEventCreate");
     CU_TRY(cudaEventCreate(&e1), "cudaEventCreate");
-    float best = 1e30f;
-    std::pair<int, int> pick = cand.front();
-    pdrt_status rst = PDRT_OK;
-    for (const auto &c : cand) {
-        p->dev.tc_enabled = c.first;
-        p->chunk = c.second;
+    int n_timed = 0;
+    auto time_of = [&](const Sched &c, float *ms) -> pdrt_status {
+        pdrt_status r = apply(c);
+        if (r != PDRT_OK) return r;
         auto pass = [&]() -> pdrt_status {
-            pdrt_status r = pdrt_dose_forward(g, p, leaves_dev, jaws_dev, mu_dev, dose_dev, stream);
-            if (r == PDRT_OK && dose_grad_dev)
-                r = pdrt_dose_backward(g, p, leaves_dev, jaws_dev, mu_dev, dose_grad_dev, dleaves_dev,
+            pdrt_status q = pdrt_dose_forward(g, p, leaves_dev, jaws_dev, mu_dev, dose_dev, stream);
+            if (q == PDRT_OK && dose_grad_dev)
+                q = pdrt_dose_backward(g, p, leaves_dev, jaws_dev, mu_dev, dose_grad_dev, dleaves_dev,
                                        djaws_dev, dmu_dev, stream);
-            return r;
+            return q;
         };
-        if ((rst = pass()) != PDRT_OK) break;   // warm-up
+        if ((r = pass()) != PDRT_OK) return r;   // warm-up
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 2 && rst == PDRT_OK; ++r) rst = pass();
+        for (int k = 0; k < 2 && r == PDRT_OK; ++k) r = pass();
         cudaEventRecord(e1, s);
-        if (rst != PDRT_OK) break;
-        float ms = 0.f;
+        if (r != PDRT_OK) return r;
         cudaError_t e = cudaEventSynchronize(e1);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            rst = cuda_fail(e, "autotune timing");
-            break;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+        *ms *= 0.5f;
+        ++n_timed;
+        return PDRT_OK;
+    };
+    Sched best = start;
+    float best_ms = 1e30f;
+    pdrt_status rst = time_of(best, &best_ms);
+    auto consider = [&](const Sched &c) {
+        if (rst != PDRT_OK) return;
+        float ms = 0.f;
+        rst = time_of(c, &ms);
+        if (rst == PDRT_OK && ms < best_ms) {
+            best_ms = ms;
+            best = c;
         }
-        if (ms * 0.5f < best) {
-            best = ms * 0.5f;
-            pick = c;
-        }
+    };
+    // 1) convolution path
+    if (tc_ok) {
+        Sched c = best;
+        c.tc = best.tc ? 0 : 1;
+        consider(c);
+    }
+    // 2) tensor-core tile shape per direction (phase depths that fit)
+    if (tc_ok && best.tc) {
+        for (int dir = 0; dir < 2; ++dir)
+            for (int ph = 1; ph <= 4; ++ph) {
+                if (ph == (dir ? best.ph_a : best.ph_f)) continue;
+                int n = 0;
+                if (conv_tc_ctas(R, dir == 1, ph, &n) != cudaSuccess || n < 1) continue;
+                Sched c = best;
+                (dir ? c.ph_a : c.ph_f) = ph;
+                consider(c);
+            }
+    }
+    // 3) control points per pass
+    for (int ch : {p->chunk_max, (p->chunk_max + 1) / 2, (p->chunk_max + 3) / 4}) {
+        if (ch < 1 || ch == best.chunk) continue;
+        Sched c = best;
+        c.chunk = ch;
+        consider(c);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    p->dev.tc_enabled = pick.first;
-    p->chunk = pick.second;
+    pdrt_status ra = apply(rst == PDRT_OK ? best : start);
     p->profiling = prof;
     if (rst != PDRT_OK) return rst;
-    out->tensor_cores = pick.first;
-    out->chunk_cp = pick.second;
-    out->best_ms = best;
-    out->n_candidates = (int32_t)cand.size();
+    if (ra != PDRT_OK) return ra;
+    out->tensor_cores = best.tc;
+    out->chunk_cp = best.chunk;
+    out->best_ms = best_ms;
+    out->n_candidates = n_timed;
+    out->phase[0] = best.ph_f;
+    out->phase[1] = best.ph_a;
+    out->tc_ctas_per_sm[0] = ctas_f;
+    out->tc_ctas_per_sm[1] = ctas_a;
     return PDRT_OK;
 }
 

@@ -418,6 +418,13 @@ static cudaError_t tc_ctas_per_sm(int R, int phase, int *out)
     return cudaSuccess;
 }
 
+cudaError_t conv_tc_ctas(int R, bool adjoint, int phase, int *ctas)
+{
+    *ctas = 0;
+    if (phase < 1 || conv_tc_smem_bytes(R, adjoint, phase) > 220 * 1024) return cudaSuccess;
+    return adjoint ? tc_ctas_per_sm<true>(R, phase, ctas) : tc_ctas_per_sm<false>(R, phase, ctas);
+}
+
 // Per direction: the phase depth (kernel rows per operand buffer, 4..1) that
 // gives the most CTAs per SM, the deepest one among equals (fewer barriers).
 template <bool ADJ>

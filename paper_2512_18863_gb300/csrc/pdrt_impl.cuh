@@ -222,6 +222,8 @@ cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsig
                            int grid_blocks, cudaStream_t s);
 cudaError_t conv_tc_prepare(int R, int *fwd_blocks_per_sm, int *adj_blocks_per_sm, int *fwd_phase,
                             int *adj_phase);
+// CTAs per SM of k_conv_tc for a phase depth (0 if the phase does not fit).
+cudaError_t conv_tc_ctas(int R, bool adjoint, int phase, int *ctas);
 // Device form of a machine's fluence corrections (taps, profile, rotation);
 // returns an error text or NULL.  Pitches du, dv in mm.
 const char *machine_corrections(const pdrt_machine *m, double du, double dv, MachineDev &M);

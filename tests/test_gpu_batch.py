@@ -51,6 +51,28 @@ def test_autotune_keeps_results_and_picks_a_schedule():
     assert r["n_candidates"] >= 2 and r["best_ms"] > 0
     assert 1 <= r["chunk_cp"] <= w.plan.n_cp
     assert e.info["chunk_cp"] == r["chunk_cp"] and e.info["tensor_cores"] == r["tensor_cores"]
+    if r["tensor_cores"]:
+        # the chosen tile shape (phase depth) is live on the plan
+        assert all(1 <= ph <= 4 for ph in r["phase"])
+        assert e.info["tc_ctas_per_sm"] == r["tc_ctas_per_sm"] and min(r["tc_ctas_per_sm"]) >= 1
     d = e.forward(w.plan.leaves, w.plan.jaws, w.plan.mu)
     assert torch.allclose(d, ref, rtol=0, atol=1e-5 * float(ref.max()))
+    e.close()
+
+
+def test_every_tensor_core_tile_shape_gives_the_same_dose():
+    """Each phase depth the autotuner may pick (1..4 kernel rows per operand
+    buffer, per direction) computes the same dose and gradients."""
+    from paper_2512_18863_gb300 import _lib
+    w = _plans()[0]
+    e = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso)
+    g = np.random.default_rng(3).standard_normal(w.phantom.shape).astype(np.float32)
+    ref = e.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).clone()
+    rg = [t.clone() for t in e.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g)]
+    for ph in (1, 2, 3, 4):
+        _lib.pdrt_plan_set_tc_phase(e._plan, ph, ph)
+        d = e.forward(w.plan.leaves, w.plan.jaws, w.plan.mu)
+        assert torch.allclose(d, ref, rtol=0, atol=1e-5 * float(ref.max())), ph
+        for a, b in zip(e.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g), rg):
+            assert torch.allclose(a, b, rtol=0, atol=1e-4 * float(b.abs().max())), ph
     e.close()
