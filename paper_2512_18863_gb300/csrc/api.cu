@@ -584,6 +584,9 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
     CU_TRY(cudaMemsetAsync(P.counters, 0, sizeof(unsigned) * 4 * n_chunks, s), "clear counters");
     for (int c = 0; c < n_chunks; ++c) {
         const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
+        // the gathered gradient h is formed by its own kernel (fusing the
+        // gather into the tensor-core adjoint's operand build measured slower:
+        // its few warps do not hide the gather's load latency)
         CU_TRY(timed(p, K_GATHER_T, s, [&] { return launch_gather_T(P, b0, nb, dose_grad_dev, s); }),
                "gather_transpose launch");
         if (P.tc_enabled)
@@ -593,7 +596,7 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
                                                    p->tc_blocks_adj, s);
                          }),
                    "conv_adjoint_tc launch");
-        if (!P.tc_enabled)
+        else
             CU_TRY(timed(p, K_CONV_ADJ, s,
                          [&] { return launch_conv(P, b0, nb, true, ctr + c, p->conv_blocks_adj, s); }),
                    "conv_adjoint launch");

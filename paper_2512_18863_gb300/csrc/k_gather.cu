@@ -156,46 +156,12 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
     if (ow <= 0 || oh <= 0) return;
     const CpGeo g = P.cpgeo[b];
     float *out = P.region + (long long)bl * P.cap_o + sp->off_o;
-    const float dk = (float)k - L.cw;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // warps take output rows j, lanes consecutive i (no index division)
     for (int jj = warp; jj < oh; jj += 8) {
-        const int j = ob.z + jj;
-        const float *gp = gd + (long long)j * P.ny * P.nx;
-        for (int ii = lane; ii < ow; ii += 32) {
-            const int i = ob.x + ii;
-            const float di = (float)i - L.cu;
-            // voxel-index position of lattice point (i, k): rotation transpose
-            const float fx = fmaf(di, g.au, fmaf(dk, g.aw, g.px0));
-            const float fy = fmaf(di, g.bu, fmaf(dk, g.bw, g.py0));
-            // a voxel whose bilinear stencil holds (i, k) has |fu - i| < 1 and
-            // |fw - k| < 1, so its centre is within sqrt(2) of (fx, fy) on
-            // each axis: inside the 3 x 3 window around the rounded position.
-            // The weights are the forward's (voxel_to_beam, 1 - |f - n|); the
-            // non-zero terms are summed in row-major order.
-            const int cx = __float2int_rn(fx), cy = __float2int_rn(fy);
-            float s = 0.f;
-#pragma unroll
-            for (int r = -1; r <= 1; ++r) {
-                const int iy = cy + r;
-                const bool row_ok = iy >= 0 && iy < P.ny;
-                const int iyc = min(max(iy, 0), P.ny - 1);
-#pragma unroll
-                for (int c = -1; c <= 1; ++c) {
-                    const int ix = cx + c;
-                    const bool ok = row_ok && ix >= 0 && ix < P.nx;
-                    const int ixc = min(max(ix, 0), P.nx - 1);
-                    const float v = __ldg(&gp[(long long)iyc * P.nx + ixc]);
-                    float fu, fw;
-                    voxel_to_beam(g, ix, iy, fu, fw);
-                    const float wu = fmaxf(0.f, 1.f - fabsf(fu - (float)i));
-                    const float ww = fmaxf(0.f, 1.f - fabsf(fw - (float)k));
-                    const float wgt = ok ? ww * wu : 0.f;
-                    if (wgt != 0.f) s = fmaf(wgt, v, s);
-                }
-            }
-            out[(long long)jj * ow + ii] = s;
-        }
+        const float *gp = gd + (long long)(ob.z + jj) * P.ny * P.nx;
+        for (int ii = lane; ii < ow; ii += 32)
+            out[(long long)jj * ow + ii] = gather_t_point(g, L, P.nx, P.ny, gp, ob.x + ii, k);
     }
 }
 
