@@ -156,12 +156,19 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
     if (ow <= 0 || oh <= 0) return;
     const CpGeo g = P.cpgeo[b];
     float *out = P.region + (long long)bl * P.cap_o + sp->off_o;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // warps take output rows j, lanes consecutive i (no index division)
-    for (int jj = warp; jj < oh; jj += 8) {
+    // flat index t = jj * ow + ii over the box; (ii, jj) advanced by the
+    // block stride with a carry instead of a division per point
+    const int stride = blockDim.x, dq = stride / ow, dr = stride - dq * ow;
+    int jj = threadIdx.x / ow, ii = threadIdx.x - jj * ow;
+    for (int t = threadIdx.x; t < ow * oh; t += stride) {
         const float *gp = gd + (long long)(ob.z + jj) * P.ny * P.nx;
-        for (int ii = lane; ii < ow; ii += 32)
-            out[(long long)jj * ow + ii] = gather_t_point(g, L, P.nx, P.ny, gp, ob.x + ii, k);
+        out[t] = gather_t_point(g, L, P.nx, P.ny, gp, ob.x + ii, k);
+        ii += dr;
+        jj += dq;
+        if (ii >= ow) {
+            ii -= ow;
+            ++jj;
+        }
     }
 }
 
