@@ -237,6 +237,14 @@ def _reference(args):
         dist.destroy_process_group()
 
 
+# DRAM bytes (read + write) of the tensor-core convolution per fluence-support
+# point and pass, from a one-pass ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the 256x256x160 two-arc plan at R = 20 px: forward
+# 12.03 (output write), adjoint 18.35 (gathered-gradient read + output write).
+# Valid for that workload and this kernel version only.
+_TRAFFIC_B_PER_SUPPORT_POINT = {"workload": "pelvis256x256x160_2x178cp_R4cm", "fwd": 12.03, "adj": 18.35}
+
+
 def _warm_start(n_cases):
     """Warm versus plain: dose evaluations the optimiser needs from the trained
     network's proposal to reach the plain optimiser's best objective in 100
@@ -336,6 +344,10 @@ def _gpu(args):
         bound, peak = "alu", SMS * FP32_LANES * 2 * 2070.0e6 / 1e12
         peak_src = "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
     mma_flops = work.get("mma_flops", 0.0) * args.steps          # tensor FLOPs issued in the timed steps
+    traffic = None
+    if w.name == _TRAFFIC_B_PER_SUPPORT_POINT["workload"] and tc_ms > 0.5 * conv_ms:
+        per_point = _TRAFFIC_B_PER_SUPPORT_POINT["fwd"] + _TRAFFIC_B_PER_SUPPORT_POINT["adj"]
+        traffic = per_point * work["support_points"] * args.steps / max(conv_launches, 1)
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps}
                for k, v in prof.items() if not k.startswith("_") and v["launches"]}
 
@@ -400,7 +412,10 @@ def _gpu(args):
                "config": _config(w, world),
                "roofline": {"bound": bound, "kernel": "convolution (forward + adjoint)",
                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                            "frac": achieved / peak, "traffic": traffic,
+                            "traffic_source": ("ncu DRAM bytes per support point at this workload, "
+                                               "scaled to the launch" if traffic else None),
+                            "peak_source": peak_src,
                             "flops": "algorithmic: 2 (2R+1)^2 per fluence-support point per pass",
                             "flops_per_launch": flops_total / max(conv_launches, 1),
                             "ms_per_launch": conv_ms / max(conv_launches, 1),
