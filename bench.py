@@ -327,7 +327,7 @@ def _gpu(args):
     value = whole_job_value(arcs_per_step, args.steps, world, ms_max)
 
     # roofline of the dominant kernel: the per-slice convolution (forward and
-    # adjoint), on the tensor cores where its tiles fit, else FP32 SIMT
+    # adjoint), on the tensor cores, or FP32 SIMT when they are off
     conv_keys = ("conv_forward", "conv_adjoint", "conv_forward_tc", "conv_adjoint_tc")
     conv_ms = sum(prof[k]["total_ms"] for k in conv_keys if k in prof)
     conv_launches = sum(prof[k]["launches"] for k in conv_keys if k in prof)

@@ -138,7 +138,7 @@ typedef struct {
     int32_t n_cp;
     int32_t chunk_cp;            /* control points processed per pass */
     size_t scratch_bytes;        /* device scratch owned by the plan */
-    int32_t tensor_cores;        /* 1: convolution tiles that fit run on the tensor cores */
+    int32_t tensor_cores;        /* 1: the convolution runs on the tensor cores (every slice) */
     int32_t tc_ctas_per_sm[2];   /* tensor-core convolution CTAs per SM (forward, adjoint) */
     int32_t simt_ctas_per_sm[2]; /* resident FP32 convolution CTAs per SM (forward, adjoint) */
     int32_t tc_phase[2];         /* tensor-core kernel rows per operand phase (forward, adjoint) */
@@ -230,9 +230,10 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
 
 /*
  * Route the per-slice convolution (Sec. 2.2.6) to the tensor cores (enable = 1,
- * the default when the kernel radius allows it: BF16 three-term split, FP32
- * accumulation) or to the FP32 SIMT kernel only (enable = 0).  Host only.
- * Errors: EINVAL if enable = 1 and the radius is too large for the tensor tiles.
+ * the default: BF16 three-term split, FP32 accumulation, every slice tiled)
+ * or to the FP32 SIMT kernel (enable = 0).  Host only.
+ * Errors: EINVAL if enable = 1 and the tensor-core kernel does not fit in
+ * shared memory (it fits for every radius up to PDRT_MAX_RADIUS_PX).
  */
 pdrt_status pdrt_plan_set_tensor_cores(pdrt_plan_t p, int32_t enable);
 

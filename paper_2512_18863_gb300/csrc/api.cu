@@ -498,7 +498,7 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     PLAN_TRY(conv_prepare(M, &bf, &ba), "convolution kernel set-up");
     p->conv_blocks_fwd = std::max(1, bf) * g->sm_count;
     p->conv_blocks_adj = std::max(1, ba) * g->sm_count;
-    // tensor-core convolution when its tiles fit in shared memory
+    // tensor-core convolution: phase depth and CTAs per SM per direction
     p->tc_blocks = 0;
     p->tc_blocks_adj = 0;
     P.tc_enabled = 0;
