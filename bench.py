@@ -47,9 +47,11 @@ def _args():
     ap.add_argument("--cpu-sample-cps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--corrections", action="store_true",
+                    help="penumbra, off-axis profile and collimator rotation on (Sec. 2.2.2)")
     ap.add_argument("--warm-cases", type=int, default=6,
                     help="held-out phantoms for the warm-versus-plain figure (0 = skip)")
-    ap.add_argument("--workload", default="pelvis256", choices=["pelvis256", "pelvis128", "paper180", "batch32"],
+    ap.add_argument("--workload", default="pelvis256", choices=["pelvis256", "pelvis128", "paper180", "batch32", "optimise"],
                     help="pelvis256: 256x256x160 @ 2 mm, 2 x 178 CPs (headline); "
                          "pelvis128: 128x128x96 @ 3 mm, 178 CPs (smaller case for profiler captures); "
                          "batch32: 32 uneven plans in one CUDA-graph launch (its own JSON line)")
@@ -89,13 +91,19 @@ def _dist():
     return world, rank, local
 
 
-def _workload(r_cm, name="pelvis256"):
+def _workload(r_cm, name="pelvis256", corrections=False):
     from paper_2512_18863_gb300 import synth
     if name == "pelvis128":
-        return synth.pelvis_arc_128(r_cm=r_cm)
-    if name == "paper180":
-        return synth.paper_table_arc()
-    return synth.pelvis_two_arc_256(r_cm=r_cm)
+        w = synth.pelvis_arc_128(r_cm=r_cm)
+    elif name == "paper180":
+        w = synth.paper_table_arc()
+    else:
+        w = synth.pelvis_two_arc_256(r_cm=r_cm)
+    if corrections:
+        # source penumbra, off-axis profile and a 15 degree collimator angle
+        synth.with_corrections(w.machine, 1007, collimator_deg=15.0)
+        w = synth.Workload(w.name + "_corrected", w.phantom, w.machine, w.plan)
+    return w
 
 
 def _config(w, world):
@@ -206,7 +214,7 @@ def _reference(args):
             dist.destroy_process_group()
             return
     from oracle import oracle
-    w = _workload(args.r_cm, args.workload)
+    w = _workload(args.r_cm, args.workload, args.corrections)
     rng = np.random.default_rng(0)
     times = []
     for s in range(args.warmup + args.steps):
@@ -279,7 +287,7 @@ def _gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = _workload(args.r_cm, args.workload)
+    w = _workload(args.r_cm, args.workload, args.corrections)
     eng = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso,
                      scratch_budget_bytes=int(args.scratch_gb * 1e9))
     dev = eng.device
@@ -499,12 +507,48 @@ def _gpu_batch(args):
         e.close()
 
 
+def _gpu_optimise(args):
+    """Gradient plan optimisation (Adam, quadratic objective) of the two-arc
+    plan from an open-field start: seconds per 100 iterations (one forward +
+    adjoint, objective and Adam step each)."""
+    import torch
+
+    from paper_2512_18863_gb300 import optimize as opt
+    from paper_2512_18863_gb300.engine import DoseEngine
+
+    torch.cuda.set_device(0)
+    w = _workload(args.r_cm, "pelvis256")
+    eng = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso,
+                     scratch_budget_bytes=int(args.scratch_gb * 1e9))
+    masks = {k: w.phantom.masks[k] for k in ("ptv", "bladder", "rectum")}
+    init = opt.open_field_start(w.plan, w.machine)
+    D0 = eng.forward(*init)
+    presc = float(D0[torch.as_tensor(masks["ptv"], device=eng.device)].mean())
+    opt.optimise(eng, masks, presc, init, n_iter=args.warmup, objective="quadratic")
+    torch.cuda.synchronize()
+    n = max(args.steps, 1) * 10
+    t0 = time.perf_counter()
+    res = opt.optimise(eng, masks, presc, init, n_iter=n, objective="quadratic")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out = {"metric": "plan optimisation iterations/sec (fwd + adjoint + Adam, two-arc 256x256x160 plan)",
+           "value": n / dt, "unit": "iterations/s", "n_gpus": 1, "steps": n, "warmup": args.warmup,
+           "ms_per_step": dt / n * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded pelvis phantom and VMAT arcs)",
+           "config": _config(w, 1), "seconds_per_100_iterations": dt / n * 100,
+           "objective_first_last": [res.history[0], res.history[-1]]}
+    print(json.dumps(out), flush=True)
+    eng.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         _reference(args)
     elif args.workload == "batch32":
         _gpu_batch(args)
+    elif args.workload == "optimise":
+        _gpu_optimise(args)
     else:
         _gpu(args)
 
