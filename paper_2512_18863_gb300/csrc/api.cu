@@ -674,8 +674,9 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
     out->conv_flops = 2.0 * (double)out->taps * (double)out->support_points;
     out->mma_flops = 0.0;
     if (p->dev.tc_enabled) {
-        // replay the tensor-core tiling of k_conv_tc (row tiles, column tiles,
-        // input chunks)
+        // replay the tensor-core tiling of k_conv_tc (row tiles of 128 rows
+        // with a last tile of at most 64 rows as M = 64, column tiles, input
+        // chunks)
         const Lattice &L = p->dev.lat;
         const int R = p->dev.mach.R;
         std::vector<SliceTab> sl((size_t)p->n_cp * L.nw);
@@ -690,7 +691,10 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
                 if (oi1 <= oi0 || oj1 <= oj0) continue;
                 if (ii1 <= ii0 || ij1 <= ij0) continue;
                 const int maxn = adj ? kTcAdjMaxN : kTcFwdMaxN, maxk = adj ? kTcAdjMaxK : kTcFwdMaxK;
-                const int mtiles = (oi1 - oi0 + 127) / 128;
+                // rows of all M tiles of the box: 128 per full tile, and 64 or
+                // 128 for the last one
+                const int h = oi1 - oi0, full = (h - 1) / 128, last = h - 128 * full;
+                const double m_rows = 128.0 * full + (last <= 64 ? 64.0 : 128.0);
                 const int ow = oj1 - oj0, n_ct = (ow + maxn - 1) / maxn;
                 const int w_ct = (((ow + n_ct - 1) / n_ct) + 15) & ~15;
                 for (int ct = 0; ct < n_ct; ++ct) {
@@ -702,7 +706,7 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
                     for (int kc = 0; kc < n_kc; ++kc) {
                         const int ka = sa + kc * w_kc, kb = std::min(sb, ka + w_kc);
                         const int kt = ((kb - ka) + 15) & ~15;
-                        out->mma_flops += (double)mtiles * (2 * R + 1) * (kt / 16) * 3 * 2.0 * 128 * nt * 16;
+                        out->mma_flops += m_rows * (2 * R + 1) * (kt / 16) * 3 * 2.0 * nt * 16;
                     }
                 }
             }

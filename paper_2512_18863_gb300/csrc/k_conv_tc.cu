@@ -5,7 +5,8 @@
 // (forward: in = magnified fluence, out = D'; adjoint: in = gathered gradient,
 // out = h'; K is symmetric, so both are this sum).  Per kernel row p it is a
 // GEMM  D[m][n] += A_p[m][k] B_p[n][k]  with m = output row (M = 128 per
-// tile), n = output column, k = input column (N, K <= 96):
+// tile, or 64 for a last tile of at most 64 rows), n = output column,
+// k = input column (N, K <= 128):
 //   * A_p[m][k] = in(i0 + m - p, s_k).  The input tile is stored K-major in
 //     8 x 16-byte core matrices with its rows 16 bytes apart, so the shift by
 //     p is just a descriptor start address (R - p rows further).
@@ -19,7 +20,12 @@
 // product <~ 3 * 2^-16).
 //
 // One CTA (8 warps) per slice, persistent over a work counter.  Thread 0
-// issues the MMAs; completion is signalled through an mbarrier
+// issues the MMAs of the kernel rows +p; in the adjoint, for column tiles
+// of at most 64 columns, thread 32 issues those of -p into a second
+// accumulator (tensor memory columns 64..127), since one issuing thread
+// delivers an MMA only every ~50 cycles while an M = 64 MMA with N <= 64
+// takes ~30.  Completion
+// is signalled through one mbarrier per issuer and operand buffer
 // (tcgen05.commit); all waits are bounded and raise PDRT_FLAG_TIMEOUT.  The
 // kernel-row operands are built in phases of PHASE rows (chosen per plan:
 // the deepest phase that keeps the most CTAs per SM) into a double
@@ -33,6 +39,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "pdrt_impl.cuh"
 #include "tc_ptx.cuh"
 
@@ -43,6 +51,7 @@ namespace {
 constexpr int kTcM = 128;
 constexpr int kTcThreads = 256;      // 8 warps: two per tensor-memory lane quarter
 constexpr uint32_t kTmemCols = 128;   // >= the largest tile width N, power of two
+constexpr uint32_t kAcc1Col = 64;     // second accumulator (tiles of N <= 64)
 
 }  // namespace
 
@@ -55,7 +64,7 @@ struct TcLimits {
     static constexpr int ND = MAXN / 8 + MAXK / 8 - 1;   // Hankel diagonals per kernel row
 };
 
-// shared memory: [0,128) barrier / tmem address / broadcast; kernel rows;
+// shared memory: [0,128) barriers / tmem address / broadcast; kernel rows;
 // input tile hi+lo [2][K/8][rows][16 B]; kernel-row operands, two buffers of
 // `phase` rows x hi+lo x ND core matrices
 int conv_tc_smem_bytes(int R, bool adjoint, int phase)
@@ -81,9 +90,9 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
     const Lattice &L = P.lat;
     const int R = P.mach.R;
     const int rows = tc_rows(R);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);         // [2]: one per operand buffer
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 16);
-    int *s_item = reinterpret_cast<int *>(smem + 20);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [buffer * 2 + issuer]
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 32);
+    int *s_item = reinterpret_cast<int *>(smem + 36);
     float *krow = reinterpret_cast<float *>(smem + 128);
     const int krow_bytes = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
     unsigned char *abase = smem + 128 + krow_bytes;
@@ -102,15 +111,17 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        for (int q = 0; q < 4; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[q])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = *s_tmem;
-    uint32_t parity[2] = {0u, 0u};
+    // thread 0 tracks every barrier q in bit q: the parity of its next phase,
+    // and whether a commit to it is outstanding
+    uint32_t parity = 0u, pending = 0u;
     bool timed_out = false;
 
     while (!timed_out) {
@@ -182,24 +193,35 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
         const uint64_t a_ks = (uint64_t)((2u * (uint32_t)lbo_a) >> 4);   // per K step
         const uint64_t b_ks = (uint64_t)((2u * 128u) >> 4);
         const uint64_t b_lo_off = (uint64_t)(((uint32_t)Lim::ND * 128u) >> 4);
-        uint32_t acc = 0;
+        uint32_t acc = 0;   // per issuing thread: its accumulator holds a partial sum
         // Phase ph (kernel rows |p| in [ph*PHASE, ...)) reads operand buffer
-        // ph & 1 and commits to mbar[ph & 1].
-        auto issue = [&](int ph, const int n_ks, const uint32_t idesc) {
+        // ph & 1; each issuer commits to mbar[2 (ph & 1) + issuer].  Issuer 0
+        // (thread 0) takes the rows +p into columns [0, N); with two issuers,
+        // issuer 1 (thread 32) takes the rows -p into columns [64, 64 + N),
+        // otherwise issuer 0 takes both and issuer 1 does nothing.
+        // (the issuer is a compile-time constant: the issuing thread's
+        // instruction stream bounds the MMA rate, so its loop stays lean)
+        auto issue = [&](int ph, const int n_ks, const uint32_t idesc, auto who_c, const bool two) {
+            constexpr int who = decltype(who_c)::value;
             const int p0 = ph * PHASE, p1 = min(p0 + PHASE, R + 1);
             const uint64_t db_buf = db0 + (uint64_t)(((uint32_t)((ph & 1) * b_buf)) >> 4);
-            for (int ap = p0; ap < p1; ++ap) {
+            const uint32_t dacc = tmem + (who ? kAcc1Col : 0u);
+            for (int ap = (who ? max(p0, 1) : p0); ap < p1; ++ap) {
                 const uint64_t dbh_row = db_buf + (uint64_t)(((uint32_t)((ap - p0) * b_row)) >> 4);
                 const uint64_t dbl_row = dbh_row + b_lo_off;
-                for (int sg = (ap == 0 ? 1 : -1); sg <= 1; sg += 2) {
+                // issuer 0: sign +1, and -1 too unless a second issuer takes it;
+                // issuer 1: sign -1 (ap >= 1)
+                const int sg0 = who ? -1 : ((ap == 0 || two) ? 1 : -1);
+                const int sg1 = who ? -1 : 1;
+                for (int sg = sg0; sg <= sg1; sg += 2) {
                     const uint64_t row = (uint64_t)(R - sg * ap);      // (row_off >> 4): rows 16 B apart
                     uint64_t dah = da_hi0 + row, dal = da_lo0 + row;
                     uint64_t dbh = dbh_row, dbl = dbl_row;
                     for (int ks = 0; ks < n_ks; ++ks) {
-                        mma_bf16(tmem, dah, dbh, idesc, acc);
+                        mma_bf16(dacc, dah, dbh, idesc, acc);
                         acc = 1;
-                        mma_bf16(tmem, dah, dbl, idesc, 1);
-                        mma_bf16(tmem, dal, dbh, idesc, 1);
+                        mma_bf16(dacc, dah, dbl, idesc, 1);
+                        mma_bf16(dacc, dal, dbh, idesc, 1);
                         dah += a_ks;
                         dal += a_ks;
                         dbh += b_ks;
@@ -207,17 +229,33 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                     }
                 }
             }
-            mma_commit(&mbar[ph & 1]);
+            // issuer 1 commits only in phases where it issued (rows |p| >= 1)
+            if (who == 0 || p1 > max(p0, 1)) mma_commit(&mbar[2 * (ph & 1) + who]);
         };
-        // bounded wait of thread 0 on buffer sb, outcome broadcast to the CTA
+        using Iss0 = std::integral_constant<int, 0>;
+        using Iss1 = std::integral_constant<int, 1>;
+        // thread 0 notes the commits of phase ph (on buffer ph & 1)
+        auto note_issue = [&](int ph, const bool two) {
+            const int p0 = ph * PHASE, p1 = min(p0 + PHASE, R + 1);
+            pending |= ((two && p1 > max(p0, 1)) ? 3u : 1u) << (2 * (ph & 1));
+        };
+        // bounded wait of thread 0 on buffer sb (the barriers with a commit
+        // outstanding), outcome broadcast to the CTA
         auto wait_buf = [&](int sb) -> bool {
             if (tid == 0) {
-                long long spins = 0;
                 int ok = 1;
-                while (!mbar_try(&mbar[sb], parity[sb])) {
-                    if (++spins > (1LL << 28)) {
-                        ok = 0;
-                        break;
+                for (int q = 2 * sb; q < 2 * sb + 2 && ok; ++q) {
+                    if (!((pending >> q) & 1u)) continue;
+                    long long spins = 0;
+                    while (!mbar_try(&mbar[q], (parity >> q) & 1u)) {
+                        if (++spins > (1LL << 28)) {
+                            ok = 0;
+                            break;
+                        }
+                    }
+                    if (ok) {
+                        parity ^= 1u << q;
+                        pending &= ~(1u << q);
                     }
                 }
                 *s_item = ok;
@@ -227,19 +265,30 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
             const int ok = *s_item;
             __syncthreads();
             fence_after();
-            parity[sb] ^= 1u;
             return ok != 0;
         };
         const int ow = bx.out_j1 - bx.out_j0;
         const int n_ct = (ow + Lim::MAXN - 1) / Lim::MAXN;
         const int w_ct = (((ow + n_ct - 1) / n_ct) + 15) & ~15;   // <= MAXN (a multiple of 16)
 
-        for (int i0 = bx.out_i0; i0 < bx.out_i1 && !timed_out; i0 += kTcM) {
+        int tile_m = kTcM;
+        for (int i0 = bx.out_i0; i0 < bx.out_i1 && !timed_out; i0 += tile_m) {
+            // a last tile of at most 64 rows runs as M = 64 (half the A reads).
+            // Forward: every A row the MMAs read, [0, M + 2R), is built (zero
+            // outside the input box).  Adjoint: only rows [0, h + 2R) for the
+            // h output rows of the tile (measured faster); the rows after them
+            // keep earlier contents and feed only accumulator rows >= h, which
+            // are never stored.
+            tile_m = (bx.out_i1 - i0 <= 64) ? 64 : kTcM;
+            const int arows = min(rows, ((min(tile_m, ADJ ? bx.out_i1 - i0 : tile_m) + 2 * R + 7) / 8) * 8);
             const int r0 = i0 - R;   // input row of tile row 0
             for (int ct = 0; ct < n_ct && !timed_out; ++ct) {
                 const int j0 = bx.out_j0 + ct * w_ct, j1 = min(bx.out_j1, j0 + w_ct);
                 nt = ((j1 - j0) + 15) & ~15;
-                const uint32_t idesc = instr_desc(kTcM, nt);
+                const uint32_t idesc = instr_desc(tile_m, nt);
+                // second issuer and accumulator (adjoint: measured faster; the
+                // forward's wider tiles keep one issuer)
+                const bool two = ADJ && nt <= (int)kAcc1Col && R >= 1;
                 const int sa = max(bx.in_j0, j0 - R), sb = min(bx.in_j1, j0 + nt + R);
                 const int n_kc = sb > sa ? (sb - sa + Lim::MAXK - 1) / Lim::MAXK : 0;
                 const int w_kc = n_kc ? (((sb - sa + n_kc - 1) / n_kc) + 15) & ~15 : 16;
@@ -257,8 +306,8 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                     if (kc_i > 0) __syncthreads();
                     // input tile: element (row, k) = in(r0 + row, s_end - 1 - k), hi/lo BF16,
                     // 8 consecutive k per thread item (one 16-byte core-matrix row)
-                    for (int idx = tid; idx < rows * (kt / 8); idx += blockDim.x) {
-                        const int kcol = idx / rows, row = idx - kcol * rows;
+                    for (int idx = tid; idx < arows * (kt / 8); idx += blockDim.x) {
+                        const int kcol = idx / arows, row = idx - kcol * arows;
                         const int u = r0 + row;
                         uint32_t hw[4], lw[4];
 #pragma unroll
@@ -312,7 +361,12 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                     fence_after();
                     // phase ph + 1 is built and issued while phase ph runs; its
                     // buffer is free once phase ph - 1 completed
-                    if (tid == 0) issue(0, n_ks, idesc);
+                    if (tid == 0) {
+                        issue(0, n_ks, idesc, Iss0{}, two);
+                        note_issue(0, two);
+                    } else if (ADJ && two && tid == 32) {
+                        issue(0, n_ks, idesc, Iss1{}, two);
+                    }
                     int waited = 0;   // phases [0, waited) are known complete
                     for (int ph = 0; ph + 1 < n_ph && !timed_out; ++ph) {
                         if (ph >= 1) {
@@ -325,7 +379,12 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                         fence_before();
                         __syncthreads();
                         fence_after();
-                        if (tid == 0) issue(ph + 1, n_ks, idesc);
+                        if (tid == 0) {
+                            issue(ph + 1, n_ks, idesc, Iss0{}, two);
+                            note_issue(ph + 1, two);
+                        } else if (ADJ && two && tid == 32) {
+                            issue(ph + 1, n_ks, idesc, Iss1{}, two);
+                        }
                     }
                     for (int ph = waited; ph < n_ph && !timed_out; ++ph)
                         if (!wait_buf(ph & 1)) timed_out = true;
@@ -335,30 +394,40 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                         atomicOr(P.flags, (unsigned)PDRT_FLAG_TIMEOUT);
                         // second bounded waits for MMAs still in flight before the
                         // tensor memory is released
-                        long long spins = 0;
-                        while (!mbar_try(&mbar[0], parity[0]) && ++spins < (1LL << 28)) {
-                        }
-                        spins = 0;
-                        while (!mbar_try(&mbar[1], parity[1]) && ++spins < (1LL << 28)) {
+                        for (int q = 0; q < 4; ++q) {
+                            long long spins = 0;
+                            while (((pending >> q) & 1u) && !mbar_try(&mbar[q], (parity >> q) & 1u) &&
+                                   ++spins < (1LL << 28)) {
+                            }
                         }
                     }
                     break;
                 }
-                // epilogue: warp w reads TMEM lanes [32 (w % 4), +32) = output rows;
-                // the two warps of a lane quarter take alternate 16-column blocks;
-                // the tile writes its own columns [j0, j1)
+                // epilogue: warp w reads TMEM lanes [32 (w % 4), +32); accumulator
+                // row m sits in lane m (M = 128) or in lane 32 (m / 16) + m % 16
+                // (M = 64: lanes 16..31 of each quarter unused).  The two warps
+                // of a lane quarter take alternate 16-column blocks; the tile
+                // writes its own columns [j0, j1); with two issuers the output
+                // is the sum of both accumulators (fixed order).
                 const int quarter = warp & 3, half = warp >> 2;
-                const int i = i0 + 32 * quarter + lane;
+                const bool lane_ok = tile_m == kTcM || lane < 16;
+                const int i = i0 + (tile_m == kTcM ? 32 : 16) * quarter + lane;
                 const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
                 for (int cb = 16 * half; cb < nt; cb += 32) {
                     float v[16];
                     if (n_kc > 0) {
                         tmem_ld16(trow + (uint32_t)cb, v);
+                        if (two) {
+                            float v1[16];
+                            tmem_ld16(trow + kAcc1Col + (uint32_t)cb, v1);
+#pragma unroll
+                            for (int q = 0; q < 16; ++q) v[q] += v1[q];
+                        }
                     } else {
 #pragma unroll
                         for (int q = 0; q < 16; ++q) v[q] = 0.f;
                     }
-                    if (i < bx.out_i1) {
+                    if (lane_ok && i < bx.out_i1) {
                         float *o = dst + (i - bx.out_i0);
 #pragma unroll
                         for (int q = 0; q < 16; ++q) {

@@ -143,6 +143,39 @@ def test_autograd_function_matches_oracle():
     eng.close()
 
 
+def test_row_tiles_of_64_and_128_rows_match_oracle():
+    """Support boxes whose heights straddle 64 and 128 rows: the tensor-core
+    convolution's M = 64 and M = 128 row tiles, a 128-row tile followed by a
+    last tile of at most 64 rows, and column tiles with one and with two
+    MMA issuers.  Water, 100 x 100 x 16 voxels of 1 x 1 x 2 mm (lattice rows
+    along x at 1 mm), R = 4 px; four control points with x half-widths 30,
+    33, 63 and 66 mm, so that over the magnification range of the lattice
+    (0.93..1.08) the support boxes are 56..65, 62..71, 118..136 and 123..142
+    rows high (the forward's output boxes 2R = 8 rows more).  Dose and
+    gradients on the oracle's bars."""
+    m = S.machine_model(1010, r_px=4)
+    ph = S.water_phantom((16, 100, 100), (1.0, 1.0, 2.0))
+    fields = [S.static_field(m, gantry_deg=37.0 * q, half_x=h, half_y=14.0, mu=80.0 + 10 * q)
+              for q, h in enumerate([30.0, 33.0, 63.0, 66.0])]
+    plan = S.Plan(np.concatenate([f.gantry_deg for f in fields]), fields[0].iso,
+                  np.concatenate([f.leaves for f in fields]), np.concatenate([f.jaws for f in fields]),
+                  np.concatenate([f.mu for f in fields]))
+    w = S.Workload("water100x100x16_row_tiles", ph, m, plan)
+    mod = O.Model(w.phantom, w.machine, w.plan)
+    ref = mod.dose()
+    eng = _engine(w)
+    d = eng.forward(plan.leaves, plan.jaws, plan.mu).cpu().numpy().astype(np.float64)
+    _assert_dose(d, ref)
+    g = np.random.default_rng(31).standard_normal(ph.shape)
+    dl, dj, dm = (t.cpu().numpy().astype(np.float64) for t in eng.backward(plan.leaves, plan.jaws, plan.mu, g))
+    assert eng.status_flags() == 0
+    eng.close()
+    rl, rj, rm = mod.dose_grad(g)
+    _assert_grad(dl, rl, "leaves")
+    _assert_grad(dj, rj, "jaws")
+    _assert_grad(dm, rm, "mu")
+
+
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
