@@ -12,7 +12,11 @@
 //   bilinear stencil contains it (all inside a 3 x 3 window); the voxel's beam coordinates
 //   come from the same float expression as in k_gather (voxel_to_beam) and
 //   the weight 1 - |f - n| equals the forward's 1 - t or t, so this is the
-//   transpose of the forward up to summation order.  No atomics.
+//   transpose of the forward up to summation order.  No atomics.  The taps
+//   of a lattice column (i, k) do not depend on the plane j: one CTA per
+//   slice k builds them once per column into shared memory (gather_t_taps)
+//   and its threads then sweep the planes, each thread one column with its
+//   taps in registers (a few loads and FMAs per point).
 #include <math.h>
 
 #include "pdrt_impl.cuh"
@@ -49,7 +53,6 @@ __device__ __forceinline__ float sample_cp(const PlanDev &P, int bl, int b, floa
 __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float *__restrict__ dose,
                                                 int first)
 {
-    const Lattice &L = P.lat;
     const int ix = blockIdx.x * 32 + (threadIdx.x & 31);
     const int iy = blockIdx.y * 8 + (threadIdx.x >> 5);
     const int iz = blockIdx.z;
@@ -146,29 +149,55 @@ cudaError_t launch_gather(const PlanDev &P, int b0, int nb, float *dose, bool fi
     return cudaGetLastError();
 }
 
+namespace {
+constexpr int kGtCols = 128;   // lattice columns per pass of k_gather_T (<= its 256 threads)
+}
+
 __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
 {
     const Lattice &L = P.lat;
     const int k = blockIdx.x, bl = blockIdx.y, b = b0 + bl;
     const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
-    const int4 ob = *reinterpret_cast<const int4 *>(&sp->oi0);
+    const int4 ob = *reinterpret_cast<const int4 *>(&sp->oi0);   // oi0, oi1, oj0, oj1
     const int ow = ob.y - ob.x, oh = ob.w - ob.z;
     if (ow <= 0 || oh <= 0) return;
     const CpGeo g = P.cpgeo[b];
     float *out = P.region + (long long)bl * P.cap_o + sp->off_o;
-    // flat index t = jj * ow + ii over the box; (ii, jj) advanced by the
-    // block stride with a carry instead of a division per point
-    const int stride = blockDim.x, dq = stride / ow, dr = stride - dq * ow;
-    int jj = threadIdx.x / ow, ii = threadIdx.x - jj * ow;
-    for (int t = threadIdx.x; t < ow * oh; t += stride) {
-        const float *gp = gd + (long long)(ob.z + jj) * P.ny * P.nx;
-        out[t] = gather_t_point(g, L, P.nx, P.ny, gp, ob.x + ii, k);
-        ii += dr;
-        jj += dq;
-        if (ii >= ow) {
-            ii -= ow;
-            ++jj;
+    __shared__ float s_w[9 * kGtCols];   // tap q of column t at [q * kGtCols + t]
+    __shared__ int s_off[9 * kGtCols];
+    __shared__ int s_n[kGtCols];
+    // the box's columns in n_ch passes of w_ch <= kGtCols columns; a pass
+    // covers rows_pp planes at a time (thread: column tid % w_ch, plane
+    // tid / w_ch)
+    const int n_ch = (ow + kGtCols - 1) / kGtCols, w_ch = (ow + n_ch - 1) / n_ch;
+    const int rows_pp = (int)blockDim.x / w_ch;
+    const int t = (int)threadIdx.x % w_ch, r = (int)threadIdx.x / w_ch;
+    for (int c0 = 0; c0 < ow; c0 += w_ch) {
+        const int cw = min(w_ch, ow - c0);
+        if ((int)threadIdx.x < cw)
+            s_n[threadIdx.x] = gather_t_taps(g, L, P.nx, P.ny, ob.x + c0 + (int)threadIdx.x, k,
+                                             s_w + threadIdx.x, s_off + threadIdx.x, kGtCols);
+        __syncthreads();
+        if (t < cw && r < rows_pp) {
+            const int n = s_n[t];
+            float w[9];
+            int off[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                w[q] = (q < n) ? s_w[q * kGtCols + t] : 0.f;
+                off[q] = (q < n) ? s_off[q * kGtCols + t] : 0;
+            }
+            const long long plane = (long long)P.ny * P.nx;
+            for (int jj = r; jj < oh; jj += rows_pp) {
+                const float *gp = gd + (long long)(ob.z + jj) * plane;
+                float sum = 0.f;
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                    if (q < n) sum = fmaf(w[q], __ldg(&gp[off[q]]), sum);
+                out[(long long)jj * ow + c0 + t] = sum;
+            }
         }
+        __syncthreads();
     }
 }
 

@@ -141,41 +141,45 @@ __device__ __forceinline__ void voxel_to_beam(const CpGeo &g, int ix, int iy, fl
     fw = fmaf(g.aw, (float)ix, fmaf(g.bw, (float)iy, g.cw0));
 }
 
-// Pull-form transpose of the gather (k_gather) at beam-frame point (i, j, k)
-// of one control point: the dose gradient of the voxels of plane j (gp points
-// at that plane) whose bilinear stencil holds lattice point (i, k).  Such a
-// voxel's centre is within sqrt(2) voxels of the point's rotated position on
-// each axis, so the 3 x 3 window around the rounded position holds all of
-// them; the weights are the forward's (voxel_to_beam, 1 - |f - n|) and the
-// non-zero terms are summed in row-major order.
-__device__ __forceinline__ float gather_t_point(const CpGeo &g, const Lattice &L, int nx, int ny,
-                                                const float *__restrict__ gp, int i, int k)
+// Pull-form transpose of the gather (k_gather) at lattice column (i, k) of
+// one control point: the voxels (ix, iy) of a plane whose bilinear stencil
+// holds lattice point (i, k), with their weights.  Such a voxel's centre is
+// within sqrt(2) voxels of the point's rotated position on each axis, so the
+// 3 x 3 window around the rounded position holds all of them; the weights
+// are the forward's (voxel_to_beam, 1 - |f - n|).  The taps depend on (i, k)
+// only, not on the plane: they are written once (non-zero ones, row-major
+// order, weight w[q * stride] and in-plane offset off[q * stride] = iy * nx +
+// ix; the count is returned) and every plane j sums
+// w[0] g_j[off[0]] + w[stride] g_j[off[stride]] + ... in that order.
+__device__ __forceinline__ int gather_t_taps(const CpGeo &g, const Lattice &L, int nx, int ny, int i, int k,
+                                             float *w, int *off, int stride)
 {
     const float di = (float)i - L.cu, dk = (float)k - L.cw;
     const float fx = fmaf(di, g.au, fmaf(dk, g.aw, g.px0));
     const float fy = fmaf(di, g.bu, fmaf(dk, g.bw, g.py0));
     const int cx = __float2int_rn(fx), cy = __float2int_rn(fy);
-    float s = 0.f;
+    int n = 0;
 #pragma unroll
     for (int r = -1; r <= 1; ++r) {
         const int iy = cy + r;
         const bool row_ok = iy >= 0 && iy < ny;
-        const int iyc = min(max(iy, 0), ny - 1);
 #pragma unroll
         for (int c = -1; c <= 1; ++c) {
             const int ix = cx + c;
             const bool ok = row_ok && ix >= 0 && ix < nx;
-            const int ixc = min(max(ix, 0), nx - 1);
-            const float v = __ldg(&gp[(long long)iyc * nx + ixc]);
             float fu, fw;
             voxel_to_beam(g, ix, iy, fu, fw);
             const float wu = fmaxf(0.f, 1.f - fabsf(fu - (float)i));
             const float ww = fmaxf(0.f, 1.f - fabsf(fw - (float)k));
             const float wgt = ok ? ww * wu : 0.f;
-            if (wgt != 0.f) s = fmaf(wgt, v, s);
+            if (wgt != 0.f) {
+                w[n * stride] = wgt;
+                off[n * stride] = iy * nx + ix;
+                ++n;
+            }
         }
     }
-    return s;
+    return n;
 }
 
 // Off-axis profile factor of lattice pixel (a, c) (Sec. 2.2.2).
