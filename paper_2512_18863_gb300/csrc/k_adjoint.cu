@@ -19,18 +19,16 @@ namespace pdrt {
 constexpr int kMagStage = 1024;   // slices staged in shared memory per pass
 
 struct MagSlice {
-    float m;
+    float m, inv_m;   // magnification and 1 / m (staged once per slice)
     int ai0, ai1, aj0, aj1;
-    int pad;
     long long off_a;
 };
 
 // candidate lattice indices idx with |mag_coord(m, idx, c) - p| < 1, widened
-// by a small margin (the exact weights decide)
-__device__ __forceinline__ void mag_candidates(int p, float c, float m, int lo_box, int hi_box,
+// by a small margin (the exact weights decide); inv = 1 / m
+__device__ __forceinline__ void mag_candidates(int p, float c, float inv, int lo_box, int hi_box,
                                                int &lo, int &hi)
 {
-    const float inv = 1.f / m;
     lo = max((int)floorf(c + ((float)p - 1.f - c) * inv - 1e-3f) + 1, lo_box);
     hi = min((int)ceilf(c + ((float)p + 1.f - c) * inv + 1e-3f), hi_box);   // exclusive
 }
@@ -54,8 +52,8 @@ __global__ void __launch_bounds__(256) k_mag_T(PlanDev P, int b0)
             const SliceTab *sp = sl + kc + q;
             MagSlice e;
             e.m = sp->m;
+            e.inv_m = 1.f / e.m;
             e.ai0 = sp->ai0; e.ai1 = sp->ai1; e.aj0 = sp->aj0; e.aj1 = sp->aj1;
-            e.pad = 0;
             e.off_a = sp->off_a;
             s_sl[q] = e;
         }
@@ -67,8 +65,8 @@ __global__ void __launch_bounds__(256) k_mag_T(PlanDev P, int b0)
                 const MagSlice e = s_sl[q];
                 if (e.ai1 <= e.ai0 || e.aj1 <= e.aj0) continue;
                 int i_lo, i_hi, j_lo, j_hi;
-                mag_candidates(a, L.cu, e.m, e.ai0, e.ai1, i_lo, i_hi);
-                mag_candidates(c, L.cv, e.m, e.aj0, e.aj1, j_lo, j_hi);
+                mag_candidates(a, L.cu, e.inv_m, e.ai0, e.ai1, i_lo, i_hi);
+                mag_candidates(c, L.cv, e.inv_m, e.aj0, e.aj1, j_lo, j_hi);
                 if (i_hi <= i_lo || j_hi <= j_lo) continue;
                 const float *h = hb + e.off_a;
                 const int aw = e.ai1 - e.ai0;

@@ -1,7 +1,8 @@
 // Rotation back to the patient grid and MU-weighted accumulation
 // (Sec. 2.2.7, Eq. D_total), and its transpose.
 //
-// k_gather: one thread per voxel, looping over the control points of a chunk;
+// k_gather: one thread per voxel (a warp: 8 x 4 voxels), looping over the
+//   control points of a chunk;
 //   the voxel samples the beam-frame dose D'_b bilinearly in (u, w) (its v
 //   coordinate is an exact lattice plane, so trilinear reduces to bilinear),
 //   sums cal * MU_b * sample in a register and writes the voxel once per chunk.
@@ -53,8 +54,11 @@ __device__ __forceinline__ float sample_cp(const PlanDev &P, int bl, int b, floa
 __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float *__restrict__ dose,
                                                 int first)
 {
-    const int ix = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int iy = blockIdx.y * 8 + (threadIdx.x >> 5);
+    // warp w covers voxels 8 x 4 (x, y) of the CTA's 32 x 8: whatever the
+    // gantry angle, a warp's samples then fall in few beam slices and rows
+    const int wq = threadIdx.x >> 5, lq = threadIdx.x & 31;
+    const int ix = blockIdx.x * 32 + (wq & 3) * 8 + (lq & 7);
+    const int iy = blockIdx.y * 8 + (wq >> 2) * 4 + (lq >> 3);
     const int iz = blockIdx.z;
     const bool inside = ix < P.nx && iy < P.ny;
     const float bx0 = (float)(blockIdx.x * 32), bx1 = (float)min((int)blockIdx.x * 32 + 31, P.nx - 1);
