@@ -16,8 +16,9 @@
 //   transpose of the forward up to summation order.  No atomics.  The taps
 //   of a lattice column (i, k) do not depend on the plane j: one CTA per
 //   slice k builds them once per column into shared memory (gather_t_taps)
-//   and its threads then sweep the planes, each thread one column with its
-//   taps in registers (a few loads and FMAs per point).
+//   and its threads then sweep the planes, each thread one column (per
+//   point a few 8-byte tap reads from shared memory, loads and FMAs; taps in
+//   shared memory rather than registers keep six CTAs resident).
 #include <math.h>
 
 #include "pdrt_impl.cuh"
@@ -157,7 +158,7 @@ namespace {
 constexpr int kGtCols = 128;   // lattice columns per pass of k_gather_T (<= its 256 threads)
 }
 
-__global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
+__global__ void __launch_bounds__(256, 6) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
 {
     const Lattice &L = P.lat;
     const int k = blockIdx.x, bl = blockIdx.y, b = b0 + bl;
@@ -167,8 +168,7 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
     if (ow <= 0 || oh <= 0) return;
     const CpGeo g = P.cpgeo[b];
     float *out = P.region + (long long)bl * P.cap_o + sp->off_o;
-    __shared__ float s_w[9 * kGtCols];   // tap q of column t at [q * kGtCols + t]
-    __shared__ int s_off[9 * kGtCols];
+    __shared__ GtTap s_tap[9 * kGtCols];   // tap q of column t at [q * kGtCols + t]
     __shared__ int s_n[kGtCols];
     // the box's columns in n_ch passes of w_ch <= kGtCols columns; a pass
     // covers rows_pp planes at a time (thread: column tid % w_ch, plane
@@ -180,24 +180,18 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
         const int cw = min(w_ch, ow - c0);
         if ((int)threadIdx.x < cw)
             s_n[threadIdx.x] = gather_t_taps(g, L, P.nx, P.ny, ob.x + c0 + (int)threadIdx.x, k,
-                                             s_w + threadIdx.x, s_off + threadIdx.x, kGtCols);
+                                             s_tap + threadIdx.x, kGtCols);
         __syncthreads();
         if (t < cw && r < rows_pp) {
             const int n = s_n[t];
-            float w[9];
-            int off[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                w[q] = (q < n) ? s_w[q * kGtCols + t] : 0.f;
-                off[q] = (q < n) ? s_off[q * kGtCols + t] : 0;
-            }
             const long long plane = (long long)P.ny * P.nx;
             for (int jj = r; jj < oh; jj += rows_pp) {
                 const float *gp = gd + (long long)(ob.z + jj) * plane;
                 float sum = 0.f;
-#pragma unroll
-                for (int q = 0; q < 9; ++q)
-                    if (q < n) sum = fmaf(w[q], __ldg(&gp[off[q]]), sum);
+                for (int q = 0; q < n; ++q) {
+                    const GtTap tp = s_tap[q * kGtCols + t];
+                    sum = fmaf(tp.w, __ldg(&gp[tp.off]), sum);
+                }
                 out[(long long)jj * ow + c0 + t] = sum;
             }
         }

@@ -148,11 +148,16 @@ __device__ __forceinline__ void voxel_to_beam(const CpGeo &g, int ix, int iy, fl
 // 3 x 3 window around the rounded position holds all of them; the weights
 // are the forward's (voxel_to_beam, 1 - |f - n|).  The taps depend on (i, k)
 // only, not on the plane: they are written once (non-zero ones, row-major
-// order, weight w[q * stride] and in-plane offset off[q * stride] = iy * nx +
-// ix; the count is returned) and every plane j sums
-// w[0] g_j[off[0]] + w[stride] g_j[off[stride]] + ... in that order.
+// order, taps[q * stride] = {weight, in-plane offset iy * nx + ix}; the count
+// is returned) and every plane j sums w_0 g_j[off_0] + w_1 g_j[off_1] + ...
+// in that order.
+struct GtTap {
+    float w;
+    int off;
+};
+
 __device__ __forceinline__ int gather_t_taps(const CpGeo &g, const Lattice &L, int nx, int ny, int i, int k,
-                                             float *w, int *off, int stride)
+                                             GtTap *taps, int stride)
 {
     const float di = (float)i - L.cu, dk = (float)k - L.cw;
     const float fx = fmaf(di, g.au, fmaf(dk, g.aw, g.px0));
@@ -173,8 +178,7 @@ __device__ __forceinline__ int gather_t_taps(const CpGeo &g, const Lattice &L, i
             const float ww = fmaxf(0.f, 1.f - fabsf(fw - (float)k));
             const float wgt = ok ? ww * wu : 0.f;
             if (wgt != 0.f) {
-                w[n * stride] = wgt;
-                off[n * stride] = iy * nx + ix;
+                taps[n * stride] = GtTap{wgt, iy * nx + ix};
                 ++n;
             }
         }
