@@ -1,13 +1,15 @@
 // Rotation back to the patient grid and MU-weighted accumulation
 // (Sec. 2.2.7, Eq. D_total), and its transpose.
 //
-// k_gather: one thread per voxel (a warp: 8 x 4 voxels), looping over the
-//   control points of a chunk;
-//   the voxel samples the beam-frame dose D'_b bilinearly in (u, w) (its v
-//   coordinate is an exact lattice plane, so trilinear reduces to bilinear),
-//   sums cal * MU_b * sample in a register and writes the voxel once per chunk.
-//   No atomics; the CP order of the sum is fixed.  A CTA (32 x 8 voxels of one
-//   z plane) skips a control point when its footprint misses the CTA.
+// k_gather: one thread per voxel column (ix, iy) of two z planes (a warp:
+//   8 x 4 columns), looping over the control points of a chunk; the voxel
+//   samples the beam-frame dose D'_b bilinearly in (u, w) (its v coordinate
+//   is an exact lattice plane, so trilinear reduces to bilinear), sums
+//   cal * MU_b * sample in a register and writes the voxel once per chunk.
+//   (u, w), the slice records and the weights depend on (ix, iy) only, so
+//   they serve both planes.  No atomics; the CP order of each voxel's sum is
+//   fixed.  A CTA (32 x 8 columns of two planes) skips a control point when
+//   its footprint misses the CTA.
 // k_gather_T: pull form of the transpose: every beam-frame point (i, j, k) of
 //   the output box gathers the dose gradient of the voxels of plane j whose
 //   bilinear stencil contains it (all inside a 3 x 3 window); the voxel's beam coordinates
@@ -16,40 +18,52 @@
 //   transpose of the forward up to summation order.  No atomics.  The taps
 //   of a lattice column (i, k) do not depend on the plane j: one CTA per
 //   slice k builds them once per column into shared memory (gather_t_taps)
-//   and its threads then sweep the planes, each thread one column (per
-//   point a few 8-byte tap reads from shared memory, loads and FMAs; taps in
-//   shared memory rather than registers keep six CTAs resident).
+//   and its threads then sweep the planes, each thread one column and two
+//   planes at a time (per pair of points a few 8-byte tap reads from shared
+//   memory, loads and FMAs; taps in shared memory rather than registers keep
+//   six CTAs resident).
 #include <math.h>
 
 #include "pdrt_impl.cuh"
 
 namespace pdrt {
 
-// D'_b sampled bilinearly in (u, w) at plane iz (zero outside the slices'
-// output boxes and the lattice).  The voxel's beam coordinates (fu, fw) use
-// the same float expression as voxel_to_beam.
-__device__ __forceinline__ float sample_cp(const PlanDev &P, int bl, int b, float fu, float fw, int iz)
+// D'_b sampled bilinearly in (u, w) at planes iz (va) and iz + 1 (vb), zero
+// outside the slices' output boxes and the lattice; the coordinate and
+// slice-record work is shared by the two planes.  The voxel's beam
+// coordinates (fu, fw) use the same float expression as voxel_to_beam.
+__device__ __forceinline__ void sample_cp2(const PlanDev &P, int bl, int b, float fu, float fw, int iz,
+                                           float &va, float &vb)
 {
     const Lattice &L = P.lat;
     const float bu = floorf(fu), bw = floorf(fw);
     const int i0 = (int)bu, k0 = (int)bw;
     const float tu = fu - bu, tw = fw - bw;
     const float *base = P.region + (long long)bl * P.cap_o;
-    float val = 0.f;
+    va = 0.f;
+    vb = 0.f;
 #pragma unroll
     for (int dk = 0; dk < 2; ++dk) {
         const int k = k0 + dk;
         if (k < 0 || k >= L.nw) continue;
-        // one 16-byte record: region offset, u start, u width, v range
         const int4 gb = __ldg(&P.gbox[(long long)b * L.nw + k]);
         const int ox = gb.y, ow = gb.z, oj0 = gb.w & 0xFFFF, oj1 = gb.w >> 16;
-        if (iz < oj0 || iz >= oj1 || i0 + 1 < ox || i0 >= ox + ow) continue;
-        const float *row = base + gb.x + (long long)(iz - oj0) * ow;
-        const float v0 = (i0 >= ox) ? __ldg(&row[i0 - ox]) : 0.f;
-        const float v1 = (i0 + 1 < ox + ow) ? __ldg(&row[i0 + 1 - ox]) : 0.f;
-        val += (dk ? tw : 1.f - tw) * ((1.f - tu) * v0 + tu * v1);
+        if (iz + 1 < oj0 || iz >= oj1 || i0 + 1 < ox || i0 >= ox + ow) continue;
+        const bool lo_ok = i0 >= ox, hi_ok = i0 + 1 < ox + ow;
+        const float wk = dk ? tw : 1.f - tw;
+        if (iz >= oj0) {
+            const float *row = base + gb.x + (long long)(iz - oj0) * ow;
+            const float v0 = lo_ok ? __ldg(&row[i0 - ox]) : 0.f;
+            const float v1 = hi_ok ? __ldg(&row[i0 + 1 - ox]) : 0.f;
+            va += wk * ((1.f - tu) * v0 + tu * v1);
+        }
+        if (iz + 1 < oj1) {
+            const float *row = base + gb.x + (long long)(iz + 1 - oj0) * ow;
+            const float v0 = lo_ok ? __ldg(&row[i0 - ox]) : 0.f;
+            const float v1 = hi_ok ? __ldg(&row[i0 + 1 - ox]) : 0.f;
+            vb += wk * ((1.f - tu) * v0 + tu * v1);
+        }
     }
-    return val;
 }
 
 __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float *__restrict__ dose,
@@ -60,7 +74,8 @@ __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float
     const int wq = threadIdx.x >> 5, lq = threadIdx.x & 31;
     const int ix = blockIdx.x * 32 + (wq & 3) * 8 + (lq & 7);
     const int iy = blockIdx.y * 8 + (wq >> 2) * 4 + (lq >> 3);
-    const int iz = blockIdx.z;
+    const int iz = 2 * blockIdx.z;          // planes iz and iz + 1 (if inside)
+    const bool has1 = iz + 1 < P.nz;
     const bool inside = ix < P.nx && iy < P.ny;
     const float bx0 = (float)(blockIdx.x * 32), bx1 = (float)min((int)blockIdx.x * 32 + 31, P.nx - 1);
     const float by0 = (float)(blockIdx.y * 8), by1 = (float)min((int)blockIdx.y * 8 + 7, P.ny - 1);
@@ -76,7 +91,7 @@ __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float
     if ((int)threadIdx.x < nb) {
         const int b = b0 + threadIdx.x;
         const CpTab &ct = P.cptab[b];
-        if (iz >= ct.vj0 && iz < ct.vj1) {
+        if (iz + (has1 ? 1 : 0) >= ct.vj0 && iz < ct.vj1) {
             const CpGeo g = P.cpgeo[b];
             const float u00 = fmaf(g.au, bx0, fmaf(g.bu, by0, g.cu0));
             const float u10 = fmaf(g.au, bx1, fmaf(g.bu, by0, g.cu0));
@@ -114,14 +129,15 @@ __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float
         s_cw0[n] = g.cw0;
     }
     __syncthreads();
-    // 4) every voxel samples the listed control points in order, two at a
-    //    time so that their slice-table and region loads overlap
-    float acc = 0.f;
+    // 4) every voxel column samples the listed control points in order, two
+    //    at a time so that their slice-table and region loads overlap (a
+    //    control point listed for one plane only adds exact zeros to the other)
+    float acc0 = 0.f, acc1 = 0.f;
     if (inside) {
         const float fx = (float)ix, fy = (float)iy;
         int n = 0;
         for (; n + 1 < total; n += 2) {
-            float v[2];
+            float va[2], vb[2];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
                 const int bl = s_list[n + q], b = b0 + bl;
@@ -129,10 +145,12 @@ __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float
                 const float2 gw = s_geo2[n + q];
                 const float fu = fmaf(gu.x, fx, fmaf(gu.y, fy, gu.z));
                 const float fw = fmaf(gw.x, fx, fmaf(gw.y, fy, s_cw0[n + q]));
-                v[q] = sample_cp(P, bl, b, fu, fw, iz);
+                sample_cp2(P, bl, b, fu, fw, iz, va[q], vb[q]);
             }
-            acc = fmaf(s_geo[n].w, v[0], acc);
-            acc = fmaf(s_geo[n + 1].w, v[1], acc);
+            acc0 = fmaf(s_geo[n].w, va[0], acc0);
+            acc0 = fmaf(s_geo[n + 1].w, va[1], acc0);
+            acc1 = fmaf(s_geo[n].w, vb[0], acc1);
+            acc1 = fmaf(s_geo[n + 1].w, vb[1], acc1);
         }
         if (n < total) {
             const int bl = s_list[n], b = b0 + bl;
@@ -140,16 +158,21 @@ __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float
             const float2 gw = s_geo2[n];
             const float fu = fmaf(gu.x, fx, fmaf(gu.y, fy, gu.z));
             const float fw = fmaf(gw.x, fx, fmaf(gw.y, fy, s_cw0[n]));
-            acc = fmaf(gu.w, sample_cp(P, bl, b, fu, fw, iz), acc);
+            float va, vb;
+            sample_cp2(P, bl, b, fu, fw, iz, va, vb);
+            acc0 = fmaf(gu.w, va, acc0);
+            acc1 = fmaf(gu.w, vb, acc1);
         }
-        const long long idx = ((long long)iz * P.ny + iy) * P.nx + ix;
-        dose[idx] = first ? acc : dose[idx] + acc;
+        const long long plane = (long long)P.ny * P.nx;
+        const long long idx = (long long)iz * plane + (long long)iy * P.nx + ix;
+        dose[idx] = first ? acc0 : dose[idx] + acc0;
+        if (has1) dose[idx + plane] = first ? acc1 : dose[idx + plane] + acc1;
     }
 }
 
 cudaError_t launch_gather(const PlanDev &P, int b0, int nb, float *dose, bool first, cudaStream_t s)
 {
-    dim3 grid((P.nx + 31) / 32, (P.ny + 7) / 8, P.nz);
+    dim3 grid((P.nx + 31) / 32, (P.ny + 7) / 8, (P.nz + 1) / 2);
     k_gather<<<grid, 256, 0, s>>>(P, b0, nb, dose, first ? 1 : 0);
     return cudaGetLastError();
 }
@@ -185,14 +208,18 @@ __global__ void __launch_bounds__(256, 6) k_gather_T(PlanDev P, int b0, const fl
         if (t < cw && r < rows_pp) {
             const int n = s_n[t];
             const long long plane = (long long)P.ny * P.nx;
-            for (int jj = r; jj < oh; jj += rows_pp) {
+            // two planes per pass share each tap record
+            for (int jj = 2 * r; jj < oh; jj += 2 * rows_pp) {
                 const float *gp = gd + (long long)(ob.z + jj) * plane;
-                float sum = 0.f;
+                const bool two = jj + 1 < oh;
+                float sum0 = 0.f, sum1 = 0.f;
                 for (int q = 0; q < n; ++q) {
                     const GtTap tp = s_tap[q * kGtCols + t];
-                    sum = fmaf(tp.w, __ldg(&gp[tp.off]), sum);
+                    sum0 = fmaf(tp.w, __ldg(&gp[tp.off]), sum0);
+                    if (two) sum1 = fmaf(tp.w, __ldg(&gp[plane + tp.off]), sum1);
                 }
-                out[(long long)jj * ow + c0 + t] = sum;
+                out[(long long)jj * ow + c0 + t] = sum0;
+                if (two) out[(long long)(jj + 1) * ow + c0 + t] = sum1;
             }
         }
         __syncthreads();
