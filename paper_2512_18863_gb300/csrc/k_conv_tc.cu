@@ -309,22 +309,40 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                     for (int idx = tid; idx < arows * (kt / 8); idx += blockDim.x) {
                         const int kcol = idx / arows, row = idx - kcol * arows;
                         const int u = r0 + row;
+                        unsigned char *ap = abase + (size_t)kcol * lbo_a + row * 16;
+                        // the item's 8 input columns, s_end - 8 (kcol + 1) .. s_end - 1 - 8 kcol
+                        const int s_hi = s_end - 1 - 8 * kcol, s_lo = s_hi - 7;
+                        if (u < bx.in_i0 || u >= bx.in_i1 || s_hi < ka || s_lo >= kb) {
+                            // outside the input box: zeros
+                            *reinterpret_cast<uint4 *>(ap) = make_uint4(0u, 0u, 0u, 0u);
+                            *reinterpret_cast<uint4 *>(ap + a_copy) = make_uint4(0u, 0u, 0u, 0u);
+                            continue;
+                        }
+                        // forward: the row's magnified coordinate, once per item
+                        float ta = 0.f;
+                        int a0 = 0;
+                        if (!ADJ) {
+                            const float fa = mag_coord(st.m, u, L.cu);
+                            const float ba = floorf(fa);
+                            a0 = (int)ba;
+                            ta = fa - ba;
+                        }
                         uint32_t hw[4], lw[4];
 #pragma unroll
                         for (int t = 0; t < 8; t += 2) {
                             float v[2];
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
-                                const int s = s_end - 1 - (8 * kcol + t + e);
+                                const int s = s_hi - (t + e);
                                 float x = 0.f;
-                                if (u >= bx.in_i0 && u < bx.in_i1 && s >= ka && s < kb) {
+                                if (s >= ka && s < kb) {
                                     if (ADJ) {
                                         x = hsrc[(long long)(s - st.oj0) * h_w + (u - st.oi0)];
                                     } else {
-                                        const float fa = mag_coord(st.m, u, L.cu), fc = mag_coord(st.m, s, L.cv);
-                                        const float ba = floorf(fa), bc = floorf(fc);
-                                        const int a0 = (int)ba, cc0 = (int)bc;
-                                        const float ta = fa - ba, tc = fc - bc;
+                                        const float fc = mag_coord(st.m, s, L.cv);
+                                        const float bc = floorf(fc);
+                                        const int cc0 = (int)bc;
+                                        const float tc = fc - bc;
                                         const int Fc = fc1 - fc0;
 #pragma unroll
                                         for (int da = 0; da < 2; ++da) {
@@ -349,7 +367,6 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 2 : 3) k_conv_tc(PlanDev P, 
                             hw[t >> 1] = pack2(h0, h1);
                             lw[t >> 1] = pack2(l0, l1);
                         }
-                        unsigned char *ap = abase + (size_t)kcol * lbo_a + row * 16;
                         *reinterpret_cast<uint4 *>(ap) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                         *reinterpret_cast<uint4 *>(ap + a_copy) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
