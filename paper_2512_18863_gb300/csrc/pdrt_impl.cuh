@@ -33,7 +33,7 @@ constexpr int kConvRows = 32;            // output rows per CTA (one per lane)
 // direction: the forward has wide outputs and narrow inputs, the adjoint the
 // reverse; wider boxes are split into column tiles and input chunks
 constexpr int kTcFwdMaxN = 128, kTcFwdMaxK = 64;
-constexpr int kTcAdjMaxN = 64, kTcAdjMaxK = 96;
+constexpr int kTcAdjMaxN = 64, kTcAdjMaxK = 48;
 
 enum KernelId {
     K_HU = 0, K_RASTER = 1, K_TABLES = 2, K_CONV_FWD = 3, K_GATHER = 4,
