@@ -16,12 +16,25 @@
 
 namespace pdrt {
 
-constexpr int kMagStage = 1024;   // slices staged in shared memory per pass
+constexpr int kMtA = 16, kMtC = 16;   // pixel tile of a CTA (a, c)
+constexpr int kMtS = 32;               // slices per table batch
+constexpr int kMtTaps = 4;             // non-zero lattice taps per pixel and axis, at most
 
 struct MagSlice {
     float m, inv_m;   // magnification and 1 / m (staged once per slice)
     int ai0, ai1, aj0, aj1;
     long long off_a;
+};
+
+// One pixel's taps along one axis for one slice: lattice indices lo, lo + 1,
+// ... with weights w[] (zero where no tap).  A lattice point idx samples the
+// pixels floor(f) and floor(f) + 1 of f = mag_coord(m, idx, c); p gets a
+// non-zero weight only for f in (p - 1, p + 1), an open interval of length 2
+// holding at most ceil(2 / m) < 4 points (m > 1/2: the plan's source distance
+// exceeds the lattice reach), and those points are consecutive.
+struct MagTap {
+    int lo;
+    float w[kMtTaps];
 };
 
 // candidate lattice indices idx with |mag_coord(m, idx, c) - p| < 1, widened
@@ -33,6 +46,37 @@ __device__ __forceinline__ void mag_candidates(int p, float c, float inv, int lo
     hi = min((int)ceilf(c + ((float)p + 1.f - c) * inv + 1e-3f), hi_box);   // exclusive
 }
 
+// taps of pixel p over the lattice indices [lo_box, hi_box) of one slice
+__device__ __forceinline__ MagTap mag_taps(int p, float c, const MagSlice &e, int lo_box, int hi_box)
+{
+    MagTap t;
+    t.lo = 0;
+#pragma unroll
+    for (int q = 0; q < kMtTaps; ++q) t.w[q] = 0.f;
+    int lo, hi;
+    mag_candidates(p, c, e.inv_m, lo_box, hi_box, lo, hi);
+    int first = -1;
+    for (int idx = lo; idx < hi; ++idx) {
+        const float f = mag_coord(e.m, idx, c);
+        const float bf = floorf(f);
+        const int p0 = (int)bf;
+        const float tf = f - bf;
+        const float w = (p == p0) ? 1.f - tf : ((p == p0 + 1) ? tf : 0.f);
+        if (w == 0.f) continue;
+        if (first < 0) {
+            first = idx;
+            t.lo = idx;
+        }
+        if (idx - first < kMtTaps) t.w[idx - first] = w;
+    }
+    return t;
+}
+
+// Pull form: a CTA owns a 16 x 16 tile of fluence pixels of one control point
+// and sweeps the slices in batches; per batch it tabulates the taps of its 16
+// pixel rows and 16 pixel columns (they are separable), then each pixel sums
+//   sum_j wc(c, j) sum_i wa(a, i) h'(i, j)
+// slice by slice, j then i in increasing order (non-zero terms only).
 __global__ void __launch_bounds__(256) k_mag_T(PlanDev P, int b0)
 {
     const Lattice &L = P.lat;
@@ -40,71 +84,75 @@ __global__ void __launch_bounds__(256) k_mag_T(PlanDev P, int b0)
     const CpTab ct = P.cptab[b];
     const int Fa = ct.fa1 - ct.fa0, Fc = ct.fc1 - ct.fc0;
     if (Fa <= 0 || Fc <= 0) return;
-    __shared__ MagSlice s_sl[kMagStage];
+    __shared__ MagSlice s_sl[kMtS];
+    __shared__ MagTap s_ta[kMtS][kMtA];
+    __shared__ MagTap s_tc[kMtS][kMtC];
     float *gF = P.gfbuf + (long long)b * L.nu * L.nv;
     const float *hb = P.adjbuf + (long long)bl * P.cap_a;
     const SliceTab *sl = P.slices + (long long)b * L.nw;
-    const int n = Fa * Fc;
-    for (int kc = ct.k0; kc < ct.k1; kc += kMagStage) {
-        const int kn = min(kMagStage, ct.k1 - kc);
-        __syncthreads();
-        for (int q = threadIdx.x; q < kn; q += blockDim.x) {
-            const SliceTab *sp = sl + kc + q;
-            MagSlice e;
-            e.m = sp->m;
-            e.inv_m = 1.f / e.m;
-            e.ai0 = sp->ai0; e.ai1 = sp->ai1; e.aj0 = sp->aj0; e.aj1 = sp->aj1;
-            e.off_a = sp->off_a;
-            s_sl[q] = e;
-        }
-        __syncthreads();
-        for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n; t += gridDim.y * blockDim.x) {
-            const int a = ct.fa0 + t % Fa, c = ct.fc0 + t / Fa;   // consecutive threads: consecutive a
-            float s = 0.f;
-            for (int q = 0; q < kn; ++q) {
-                const MagSlice e = s_sl[q];
-                if (e.ai1 <= e.ai0 || e.aj1 <= e.aj0) continue;
-                int i_lo, i_hi, j_lo, j_hi;
-                mag_candidates(a, L.cu, e.inv_m, e.ai0, e.ai1, i_lo, i_hi);
-                mag_candidates(c, L.cv, e.inv_m, e.aj0, e.aj1, j_lo, j_hi);
-                if (i_hi <= i_lo || j_hi <= j_lo) continue;
-                const float *h = hb + e.off_a;
-                const int aw = e.ai1 - e.ai0;
-                for (int j = j_lo; j < j_hi; ++j) {
-                    const float fc = mag_coord(e.m, j, L.cv);
-                    const float bc = floorf(fc);
-                    const int c0 = (int)bc;
-                    const float tc = fc - bc;
-                    const float wc = (c == c0) ? 1.f - tc : ((c == c0 + 1) ? tc : 0.f);
-                    if (wc == 0.f) continue;
-                    float sr = 0.f;
-                    for (int i = i_lo; i < i_hi; ++i) {
-                        const float fa = mag_coord(e.m, i, L.cu);
-                        const float ba = floorf(fa);
-                        const int a0 = (int)ba;
-                        const float ta = fa - ba;
-                        const float wa = (a == a0) ? 1.f - ta : ((a == a0 + 1) ? ta : 0.f);
-                        if (wa != 0.f) sr = fmaf(wa, h[(long long)(j - e.aj0) * aw + (i - e.ai0)], sr);
-                    }
-                    s = fmaf(wc, sr, s);
+    const int nta = (Fa + kMtA - 1) / kMtA, ntc = (Fc + kMtC - 1) / kMtC;
+    const int la = (int)threadIdx.x % kMtA, lc = (int)threadIdx.x / kMtA;   // 16 x 16 threads
+    for (int tile = blockIdx.y; tile < nta * ntc; tile += gridDim.y) {
+        const int ta0 = (tile % nta) * kMtA, tc0 = (tile / nta) * kMtC;
+        const int a = ct.fa0 + ta0 + la, c = ct.fc0 + tc0 + lc;
+        const bool inside = ta0 + la < Fa && tc0 + lc < Fc;
+        float s = 0.f;
+        for (int kc = ct.k0; kc < ct.k1; kc += kMtS) {
+            const int kn = min(kMtS, ct.k1 - kc);
+            __syncthreads();   // the previous batch's tables are no longer read
+            for (int q = threadIdx.x; q < kn; q += blockDim.x) {
+                const SliceTab *sp = sl + kc + q;
+                MagSlice e;
+                e.m = sp->m;
+                e.inv_m = 1.f / e.m;
+                e.ai0 = sp->ai0; e.ai1 = sp->ai1; e.aj0 = sp->aj0; e.aj1 = sp->aj1;
+                e.off_a = sp->off_a;
+                s_sl[q] = e;
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < kn * (kMtA + kMtC); q += blockDim.x) {
+                const int ks = q / (kMtA + kMtC), r = q - ks * (kMtA + kMtC);
+                const MagSlice e = s_sl[ks];
+                const bool live = e.ai1 > e.ai0 && e.aj1 > e.aj0;
+                if (r < kMtA) {
+                    MagTap t = live ? mag_taps(ct.fa0 + ta0 + r, L.cu, e, e.ai0, e.ai1) : MagTap{0, {0.f, 0.f, 0.f, 0.f}};
+                    s_ta[ks][r] = t;
+                } else {
+                    MagTap t = live ? mag_taps(ct.fc0 + tc0 + r - kMtA, L.cv, e, e.aj0, e.aj1)
+                                    : MagTap{0, {0.f, 0.f, 0.f, 0.f}};
+                    s_tc[ks][r - kMtA] = t;
                 }
             }
-            float *dstp = &gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)];
-            *dstp = (kc == ct.k0) ? s : *dstp + s;
+            __syncthreads();
+            if (inside) {
+                for (int ks = 0; ks < kn; ++ks) {
+                    const MagTap tc = s_tc[ks][lc];
+                    const MagTap ta = s_ta[ks][la];
+                    const MagSlice &e = s_sl[ks];
+                    const float *h = hb + e.off_a;
+                    const int aw = e.ai1 - e.ai0;
+#pragma unroll
+                    for (int jt = 0; jt < kMtTaps; ++jt) {
+                        const float wc = tc.w[jt];
+                        if (wc == 0.f) continue;
+                        const float *hr = h + (long long)(tc.lo + jt - e.aj0) * aw + (ta.lo - e.ai0);
+                        float sr = 0.f;
+#pragma unroll
+                        for (int it = 0; it < kMtTaps; ++it)
+                            if (ta.w[it] != 0.f) sr = fmaf(ta.w[it], hr[it], sr);
+                        s = fmaf(wc, sr, s);
+                    }
+                }
+            }
         }
-    }
-    if (ct.k1 <= ct.k0) {
-        // no slice with work: the adjoint of the fluence map is zero
-        for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < n; t += gridDim.y * blockDim.x) {
-            const int a = ct.fa0 + t % Fa, c = ct.fc0 + t / Fa;
-            gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)] = 0.f;
-        }
+        // every pixel of the tile is written (zero when no slice has work)
+        if (inside) gF[(long long)(a - ct.fa0) * Fc + (c - ct.fc0)] = s;
     }
 }
 
 cudaError_t launch_mag_T(const PlanDev &P, int b0, int nb, cudaStream_t s)
 {
-    dim3 grid(nb, 16);
+    dim3 grid(nb, 24);   // pixel tiles of a control point, strided over blockIdx.y
     k_mag_T<<<grid, 256, 0, s>>>(P, b0);
     return cudaGetLastError();
 }
@@ -176,7 +224,7 @@ __device__ void uncorrect_adjoint(const PlanDev &P, int b, const CpTab &ct)
     const Lattice &L = P.lat;
     const long long slot = (long long)b * L.nu * L.nv;
     const int Ca = ct.ca1 - ct.ca0, Cc = ct.cc1 - ct.cc0;
-    const int Fa = ct.fa1 - ct.fa0, Fc = ct.fc1 - ct.fc0;
+    const int Fc = ct.fc1 - ct.fc0;
     float *gF = P.gfbuf + slot;
     float *gb;   // OAP-weighted adjoint of the blurred map over the blurred box
     __syncthreads();   // every thread is done reading gF for dMU
