@@ -248,9 +248,9 @@ def _reference(args):
 # DRAM bytes (read + write) of the tensor-core convolution per fluence-support
 # point and pass, from a one-pass ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the 256x256x160 two-arc plan at R = 20 px: forward
-# 12.03 (output write), adjoint 18.33 (gathered-gradient read + output write).
+# 12.03 (output write), adjoint 18.27 (gathered-gradient read + output write).
 # Valid for that workload and this kernel version only.
-_TRAFFIC_B_PER_SUPPORT_POINT = {"workload": "pelvis256x256x160_2x178cp_R4cm", "fwd": 12.03, "adj": 18.33}
+_TRAFFIC_B_PER_SUPPORT_POINT = {"workload": "pelvis256x256x160_2x178cp_R4cm", "fwd": 12.03, "adj": 18.27}
 
 
 def _warm_start(n_cases):
