@@ -143,13 +143,16 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
                          : P.region + (long long)bl * P.cap_o + st.off_o;
         const float scale = st.tdd * st.c2;
 
-        // kernel rows K(|p|, q), q in [-R, R]
-        for (int idx = tid; idx < (R + 1) * (2 * R + 1); idx += blockDim.x) {
-            const int p = idx / (2 * R + 1), q = idx - p * (2 * R + 1) - R;
+        // kernel rows K(|p|, q), q in [-R, R]; K(|p|, -q) = K(|p|, q) (the same
+        // float expression: r depends on q * q), so q >= 0 is computed and mirrored
+        for (int idx = tid; idx < (R + 1) * (R + 1); idx += blockDim.x) {
+            const int p = idx / (R + 1), q = idx - p * (R + 1);
             const float pu = p * L.du, qv = q * L.dv;
             const float r = sqrtf(pu * pu + qv * qv);
-            krow[idx] = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
-                        st.wn[2] * expf(-st.a[2] * r);
+            const float v = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
+                            st.wn[2] * expf(-st.a[2] * r);
+            krow[p * (2 * R + 1) + R + q] = v;
+            krow[p * (2 * R + 1) + R - q] = v;
         }
         __syncthreads();
         // Tiling of the slice: output-column tiles of at most MAXN columns
