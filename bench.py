@@ -51,10 +51,14 @@ def _args():
                     help="penumbra, off-axis profile and collimator rotation on (Sec. 2.2.2)")
     ap.add_argument("--warm-cases", type=int, default=6,
                     help="held-out phantoms for the warm-versus-plain figure (0 = skip)")
-    ap.add_argument("--workload", default="pelvis256", choices=["pelvis256", "pelvis128", "paper180", "batch32", "optimise"],
+    ap.add_argument("--workload", default="pelvis256",
+                    choices=["pelvis256", "pelvis128", "water64", "paper180", "batch32", "optimise"],
                     help="pelvis256: 256x256x160 @ 2 mm, 2 x 178 CPs (headline); "
                          "pelvis128: 128x128x96 @ 3 mm, 178 CPs (smaller case for profiler captures); "
+                         "water64: one static 10 x 10 cm field on 64^3 water at 2.5 mm (R = 2 cm); "
                          "batch32: 32 uneven plans in one CUDA-graph launch (its own JSON line)")
+    ap.add_argument("--step-stats", type=int, default=20,
+                    help="single steps timed after the run for median / p10 / p90 (0: skip)")
     ap.add_argument("--scratch-gb", type=float, default=24.0,
                     help="plan scratch budget in GB (0 = library default)")
     return ap.parse_args()
@@ -95,6 +99,8 @@ def _workload(r_cm, name="pelvis256", corrections=False):
     from paper_2512_18863_gb300 import synth
     if name == "pelvis128":
         w = synth.pelvis_arc_128(r_cm=r_cm)
+    elif name == "water64":
+        w = synth.water_static_64()
     elif name == "paper180":
         w = synth.paper_table_arc()
     else:
@@ -126,7 +132,10 @@ def _subplan(w, sel):
 
 def _objective_grad(D, masks, torch):
     """dL/dD of L = 100 mean_PTV (D - Dp)^2 + sum_s l_s mean_s max(D - d_s, 0)^2
-    (prescription Dp = 0.9 x median PTV dose; OAR thresholds 0.5 Dp)."""
+    (prescription Dp = 0.9 x median PTV dose; OAR thresholds 0.5 Dp).  A
+    phantom without structures (water) takes L = mean (D - 0.9 max D)^2."""
+    if "ptv" not in masks:
+        return (2.0 * (D - 0.9 * float(D.max())) / D.numel()).contiguous()
     ptv = masks["ptv"]
     dp = 0.9 * float(D[ptv].median())
     g = torch.zeros_like(D)
@@ -185,6 +194,44 @@ class _Clocks:
                 "reasons": sorted(reasons)}
 
 
+def _cpu_model():
+    """The host CPU's model name (lscpu), else the architecture."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def _step_stats(eng, leaves, jaws, mu, g, dose, flush, n):
+    """Device time of single steps (CUDA events around each, L2 flushed
+    before it): median, p10 and p90 of n forward-only and of n forward +
+    adjoint steps."""
+    import torch
+    out = {}
+    for name, adj in (("forward", False), ("forward_adjoint", True)):
+        ev = []
+        for _ in range(n):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            eng.forward(leaves, jaws, mu, out=dose)
+            if adj:
+                eng.backward(leaves, jaws, mu, g)
+            b.record()
+            ev.append((a, b))
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        p10, p50, p90 = (float(x) for x in np.percentile(ms, [10, 50, 90]))
+        out[name] = {"median_ms": p50, "p10_ms": p10, "p90_ms": p90, "n": int(n)}
+    return out
+
+
 def _cpu_baseline(w, n_cps):
     """FP64 oracle forward + adjoint on n_cps control points at full size."""
     from oracle import oracle
@@ -198,7 +245,7 @@ def _cpu_baseline(w, n_cps):
     mod.dose_grad(g)
     dt = time.perf_counter() - t0
     return {"value": (n_cps / CP_PER_ARC) / dt, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
+            "kind": "oracle", "cpu_model": _cpu_model(),
             "sample": f"{n_cps} of {w.plan.n_cp} control points (fwd+adjoint) on the full "
                       f"{'x'.join(str(s) for s in w.phantom.shape[::-1])} grid, FP64, OpenMP; "
                       f"{dt:.1f} s"}
@@ -235,7 +282,7 @@ def _reference(args):
            "data": "synthetic (seeded pelvis phantom and VMAT arcs)",
            "config": _config(w, world),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
-                            "kind": "oracle",
+                            "kind": "oracle", "cpu_model": _cpu_model(),
                             "sample": "one control point per step (fwd+adjoint), full grid"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -358,6 +405,9 @@ def _gpu(args):
         traffic = per_point * work["support_points"] * args.steps / max(conv_launches, 1)
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps}
                for k, v in prof.items() if not k.startswith("_") and v["launches"]}
+    # per-step distribution (after the timed region, outside it)
+    step_ms = (_step_stats(eng, leaves, jaws, mu, g, dose, flush, args.step_stats)
+               if args.step_stats > 0 else None)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -434,7 +484,7 @@ def _gpu(args):
                           "tc_ctas_per_sm": info.get("tc_ctas_per_sm"),
                           "simt_ctas_per_sm": info.get("simt_ctas_per_sm"),
                           "chunk_cp": info.get("chunk_cp")},
-               "hbm_literal": hbm, "warm_start": warm,
+               "hbm_literal": hbm, "warm_start": warm, "step_ms": step_ms,
                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
     eng.close()
