@@ -16,12 +16,11 @@
 //   come from the same float expression as in k_gather (voxel_to_beam) and
 //   the weight 1 - |f - n| equals the forward's 1 - t or t, so this is the
 //   transpose of the forward up to summation order.  No atomics.  The taps
-//   of a lattice column (i, k) do not depend on the plane j: one CTA per
-//   slice k builds them once per column into shared memory (gather_t_taps)
-//   and its threads then sweep the planes, each thread one column and two
-//   planes at a time (per pair of points a few 8-byte tap reads from shared
-//   memory, loads and FMAs; taps in shared memory rather than registers keep
-//   six CTAs resident).
+//   of a lattice column (i, k) do not depend on the plane j: a thread owns
+//   one column of one slice, builds its taps once and sweeps the planes two
+//   at a time.  A warp holds 8 columns x 4 adjacent slices, a small patch of
+//   the rotated lattice, so its loads touch few cache lines at any gantry
+//   angle (32 columns of one slice touched up to 32).
 #include <math.h>
 
 #include "pdrt_impl.cuh"
@@ -178,57 +177,73 @@ cudaError_t launch_gather(const PlanDev &P, int b0, int nb, float *dose, bool fi
 }
 
 namespace {
-constexpr int kGtCols = 128;   // lattice columns per pass of k_gather_T (<= its 256 threads)
+constexpr int kGtS = 4;              // beam slices per CTA of k_gather_T
+constexpr int kGtW = 8;              // lattice columns per warp (x kGtS slices = 32 lanes)
+constexpr int kGtCols = 8 * kGtW;    // lattice columns per pass of a CTA (8 warps)
 }
 
-__global__ void __launch_bounds__(256, 6) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
+// One CTA per control point and group of kGtS consecutive beam slices; lane
+// (c, s) of a warp owns lattice column i0 + c of slice k0 + s, so a warp's
+// 8 x 4 points form a small patch of the rotated lattice whose voxel taps
+// fall in few cache lines at any gantry angle.  Each thread builds its
+// column's taps once (they do not depend on the plane) and sweeps its
+// slice's planes two at a time.
+__global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
 {
     const Lattice &L = P.lat;
-    const int k = blockIdx.x, bl = blockIdx.y, b = b0 + bl;
-    const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
-    const int4 ob = *reinterpret_cast<const int4 *>(&sp->oi0);   // oi0, oi1, oj0, oj1
-    const int ow = ob.y - ob.x, oh = ob.w - ob.z;
-    if (ow <= 0 || oh <= 0) return;
+    const int kg = blockIdx.x * kGtS, bl = blockIdx.y, b = b0 + bl;
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int sl = lane / kGtW, cl = lane % kGtW;   // slice and column of this lane
+    const int k = kg + sl;
+    int4 ob = make_int4(0, 0, 0, 0);                // oi0, oi1, oj0, oj1
+    long long off_o = 0;
+    if (k < L.nw) {
+        const SliceTab *sp = &P.slices[(long long)b * L.nw + k];
+        ob = *reinterpret_cast<const int4 *>(&sp->oi0);
+        off_o = sp->off_o;
+    }
+    const bool live = ob.y > ob.x && ob.w > ob.z;
+    // the group's union of u ranges (every thread computes the same)
+    int ui0 = 1 << 30, ui1 = -(1 << 30);
+#pragma unroll
+    for (int q = 0; q < kGtS; ++q) {
+        const int kq = kg + q;
+        if (kq >= L.nw) break;
+        const int4 oq = *reinterpret_cast<const int4 *>(&P.slices[(long long)b * L.nw + kq].oi0);
+        if (oq.y > oq.x && oq.w > oq.z) {
+            ui0 = min(ui0, oq.x);
+            ui1 = max(ui1, oq.y);
+        }
+    }
+    if (ui1 <= ui0) return;   // no slice of the group has work (uniform)
     const CpGeo g = P.cpgeo[b];
-    float *out = P.region + (long long)bl * P.cap_o + sp->off_o;
-    __shared__ GtTap s_tap[9 * kGtCols];   // tap q of column t at [q * kGtCols + t]
-    __shared__ int s_n[kGtCols];
-    // the box's columns in n_ch passes of w_ch <= kGtCols columns; a pass
-    // covers rows_pp planes at a time (thread: column tid % w_ch, plane
-    // tid / w_ch)
-    const int n_ch = (ow + kGtCols - 1) / kGtCols, w_ch = (ow + n_ch - 1) / n_ch;
-    const int rows_pp = (int)blockDim.x / w_ch;
-    const int t = (int)threadIdx.x % w_ch, r = (int)threadIdx.x / w_ch;
-    for (int c0 = 0; c0 < ow; c0 += w_ch) {
-        const int cw = min(w_ch, ow - c0);
-        if ((int)threadIdx.x < cw)
-            s_n[threadIdx.x] = gather_t_taps(g, L, P.nx, P.ny, ob.x + c0 + (int)threadIdx.x, k,
-                                             s_tap + threadIdx.x, kGtCols);
-        __syncthreads();
-        if (t < cw && r < rows_pp) {
-            const int n = s_n[t];
-            const long long plane = (long long)P.ny * P.nx;
-            // two planes per pass share each tap record
-            for (int jj = 2 * r; jj < oh; jj += 2 * rows_pp) {
+    const int ow = ob.y - ob.x, oh = ob.w - ob.z;
+    float *out = P.region + (long long)bl * P.cap_o + off_o;
+    __shared__ GtTap s_tap[9 * 256];   // tap q of thread t at [q * 256 + t]
+    const long long plane = (long long)P.ny * P.nx;
+    for (int c0 = ui0; c0 < ui1; c0 += kGtCols) {
+        const int i = c0 + warp * kGtW + cl;
+        if (live && i >= ob.x && i < ob.y) {
+            const int n = gather_t_taps(g, L, P.nx, P.ny, i, k, s_tap + threadIdx.x, 256);
+            for (int jj = 0; jj < oh; jj += 2) {
                 const float *gp = gd + (long long)(ob.z + jj) * plane;
                 const bool two = jj + 1 < oh;
                 float sum0 = 0.f, sum1 = 0.f;
                 for (int q = 0; q < n; ++q) {
-                    const GtTap tp = s_tap[q * kGtCols + t];
+                    const GtTap tp = s_tap[q * 256 + threadIdx.x];
                     sum0 = fmaf(tp.w, __ldg(&gp[tp.off]), sum0);
                     if (two) sum1 = fmaf(tp.w, __ldg(&gp[plane + tp.off]), sum1);
                 }
-                out[(long long)jj * ow + c0 + t] = sum0;
-                if (two) out[(long long)(jj + 1) * ow + c0 + t] = sum1;
+                out[(long long)jj * ow + (i - ob.x)] = sum0;
+                if (two) out[(long long)(jj + 1) * ow + (i - ob.x)] = sum1;
             }
         }
-        __syncthreads();
     }
 }
 
 cudaError_t launch_gather_T(const PlanDev &P, int b0, int nb, const float *g, cudaStream_t s)
 {
-    dim3 grid(P.lat.nw, nb);
+    dim3 grid((P.lat.nw + kGtS - 1) / kGtS, nb);
     k_gather_T<<<grid, 256, 0, s>>>(P, b0, g);
     return cudaGetLastError();
 }
