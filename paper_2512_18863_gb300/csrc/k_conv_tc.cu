@@ -24,13 +24,14 @@
 // of at most 64 columns, thread 32 issues those of -p into a second
 // accumulator (tensor memory columns 64..127), since one issuing thread
 // delivers an MMA only every ~50 cycles while an M = 64 MMA with N <= 64
-// takes ~30.  Completion
-// is signalled through one mbarrier per issuer and operand buffer
-// (tcgen05.commit); all waits are bounded and raise PDRT_FLAG_TIMEOUT.  The
-// kernel-row operands are built in phases of PHASE rows (chosen per plan:
-// the deepest phase that keeps the most CTAs per SM) into a double
-// buffer, each phase while the previous phase's MMAs run; with the per
-// direction tile limits two CTAs fit on an SM.
+// takes ~30.  Completion is signalled through one mbarrier per issuer and
+// operand buffer (tcgen05.commit); all waits are bounded and raise
+// PDRT_FLAG_TIMEOUT.  The kernel-row operands are built in phases of PHASE
+// rows (chosen per plan: the deepest phase that keeps the most CTAs per SM)
+// into a double buffer, each phase while the previous phase's MMAs run; with
+// the per direction tile limits three forward or four adjoint CTAs fit on an
+// SM at R = 20 px, and several resident CTAs overlap one another's operand
+// builds with their MMAs.
 // Boxes wider than one tile are split into output-column tiles of at most
 // MAXN columns and, per column tile, chunks of at most MAXK of the input
 // columns within R of it; the chunks accumulate in tensor memory.  With
