@@ -13,9 +13,8 @@
  *   -> RadiologicalDepth (Sec. 2.2.4, WEPL integral)
  *   -> PencilBeamKernel (Sec. 2.2.5) -> BeamWiseConvolution (Sec. 2.2.6)
  *   -> BeamRotation + MU-weighted sum (Sec. 2.2.7, Eq. D_total).
- * The paper leaves the discretisation open; the readings used here are the
- * ones listed in DESIGN.md ("Readings of the paper") and are repeated at each
- * function below.  The adjoint functions are the exact transposes of the
+ * The paper leaves the discretisation open; the reading taken for each
+ * open point is stated at the function that implements it.  The adjoint functions are the exact transposes of the
  * linear stages plus the derivative of the overlap formula (Sec. 2.2.2 states
  * that it gives stable subgradients); the projection of Sec. 2.2.1 is passed
  * through as the identity when ste != 0 (straight-through estimator).

@@ -2,7 +2,7 @@
 
 The paper's Discussion ("Future directions") proposes a network that learns
 delivery parameters from target and organ-at-risk masks, with the dose
-engine as the judge.  Here a 5-layer BF16 CNN (include/pdrt_cnn.h) maps the
+engine as the arbiter.  Here a 5-layer BF16 CNN (include/pdrt_cnn.h) maps the
 beam's-eye-view projection of the PTV, bladder and rectum masks of each
 control point to its 60 leaf pairs and MU; it is trained on plans that the
 engine's own gradient optimiser (optimize.optimise) produced on seeded
@@ -344,8 +344,8 @@ def objective_quadratic_sel(sel: dict, alpha: float, presc: float, weights=None,
     return L
 
 
-def judge(case: Case, prop):
-    """The exact engine's judgement of a proposal (one dose evaluation): the
+def assess(case: Case, prop):
+    """The exact engine's assessment of a proposal (one dose evaluation): the
     proposal with its MU rescaled by best_mu_scale, and its objective."""
     D = case.engine.forward(*prop)
     alpha, j = best_mu_scale(case, D)
@@ -355,8 +355,8 @@ def judge(case: Case, prop):
 def evaluate(net: WarmStartNet, seeds, n_iter=N_ITER):
     """Warm versus plain on held-out phantoms.  The plain optimiser runs
     n_iter evaluations from the open-field start; its best objective J* is the
-    target.  The warm start costs one evaluation to judge the proposal
-    (judge: objective with the best global MU scale) against the open-field
+    target.  The warm start costs one evaluation to assess the proposal
+    (assess: objective with the best global MU scale) against the open-field
     start (the fallback when the proposal is worse), then optimises until
     J <= J* (at most n_iter more evaluations)."""
     rows = []
@@ -365,7 +365,7 @@ def evaluate(net: WarmStartNet, seeds, n_iter=N_ITER):
         plain = plain_optimise(c, n_iter)
         j_star = min(plain.history)
         plain_evals = int(np.argmin(plain.history)) + 1
-        prop, j_prop, alpha = judge(c, propose(net, c))
+        prop, j_prop, alpha = assess(c, propose(net, c))
         j_open = plain.history[0]
         start = prop if j_prop <= j_open else c.open_init
         warm = optimise(c.engine, c.masks, c.presc, start, n_iter=n_iter, lr=OPT_LR, lr_mu=OPT_LR_MU,

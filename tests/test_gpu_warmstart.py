@@ -1,5 +1,5 @@
 """Learned warm start: what the trained network gains over the plain
-optimiser, judged by the exact engine (dose evaluations to reach the plain
+optimiser, assessed by the exact engine (dose evaluations to reach the plain
 optimiser's best objective of 100 evaluations from an open-field start)."""
 import os
 
@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 def test_bad_proposal_falls_back_to_the_open_field_start():
     """A network with zero weights proposes closed leaves and minimum MU; the
-    engine judges it worse than the open field, the optimiser falls back and
+    engine rates it worse than the open field, the optimiser falls back and
     then needs exactly the plain optimiser's evaluations (plus the judging one)."""
     p = {k: np.zeros(shp) for k, shp in W.param_layout()}
     net = W.WarmStartNet(batch_max=64, params=p)
