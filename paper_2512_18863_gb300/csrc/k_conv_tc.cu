@@ -19,12 +19,13 @@
 // three products (hi.hi + hi.lo + lo.hi) are accumulated (relative error per
 // product <~ 3 * 2^-16).
 //
-// One CTA (8 warps) per slice, persistent over a work counter.  Thread 0
-// issues the MMAs of the kernel rows +p; in the adjoint, for column tiles
-// of at most 64 columns, thread 32 issues those of -p into a second
-// accumulator (tensor memory columns 64..127), since one issuing thread
-// delivers an MMA only every ~50 cycles while an M = 64 MMA with N <= 64
-// takes ~30.  Completion is signalled through one mbarrier per issuer and
+// One CTA (8 warps) per slice, persistent over a work counter.  Warp 0
+// issues the MMAs of the kernel rows +p (the whole warp runs the issuing
+// loop on warp-uniform descriptors, lane 0 executes the MMAs); in the
+// adjoint, for column tiles of at most 64 columns, warp 1 issues those of -p
+// into a second accumulator (tensor memory columns 64..127), since one
+// issuing thread delivers an MMA only every ~50 cycles while an M = 64 MMA
+// with N <= 64 takes ~30.  Completion is signalled through one mbarrier per issuer and
 // operand buffer (tcgen05.commit); all waits are bounded and raise
 // PDRT_FLAG_TIMEOUT.  The kernel-row operands are built in phases of PHASE
 // rows (chosen per plan: the deepest phase that keeps the most CTAs per SM)
@@ -123,7 +124,9 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
     fence_before();
     __syncthreads();
     fence_after();
-    const uint32_t tmem = *s_tmem;
+    // values the issuing loop depends on are made warp-uniform (lane 0's
+    // value) so that its descriptor arithmetic stays warp-uniform
+    const uint32_t tmem = __shfl_sync(0xffffffffu, *s_tmem, 0);
     // thread 0 tracks every barrier q in bit q: the parity of its next phase,
     // and whether a commit to it is outstanding
     uint32_t parity = 0u, pending = 0u;
@@ -204,9 +207,10 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
         uint32_t acc = 0;   // per issuing thread: its accumulator holds a partial sum
         // Phase ph (kernel rows |p| in [ph*PHASE, ...)) reads operand buffer
         // ph & 1; each issuer commits to mbar[2 (ph & 1) + issuer].  Issuer 0
-        // (thread 0) takes the rows +p into columns [0, N); with two issuers,
-        // issuer 1 (thread 32) takes the rows -p into columns [64, 64 + N),
-        // otherwise issuer 0 takes both and issuer 1 does nothing.
+        // (warp 0) takes the rows +p into columns [0, N); with two issuers,
+        // issuer 1 (warp 1) takes the rows -p into columns [64, 64 + N),
+        // otherwise issuer 0 takes both and issuer 1 does nothing.  Each
+        // issuer's lane 0 executes its MMAs and commits.
         // (the issuer is a compile-time constant: the issuing thread's
         // instruction stream bounds the MMA rate, so its loop stays lean)
         auto issue = [&](int ph, const int n_ks, const uint32_t idesc, auto who_c, const bool two) {
@@ -226,10 +230,10 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
                     uint64_t dah = da_hi0 + row, dal = da_lo0 + row;
                     uint64_t dbh = dbh_row, dbl = dbl_row;
                     for (int ks = 0; ks < n_ks; ++ks) {
-                        mma_bf16(dacc, dah, dbh, idesc, acc);
+                        mma_bf16_warp(dacc, dah, dbh, idesc, acc);
                         acc = 1;
-                        mma_bf16(dacc, dah, dbl, idesc, 1);
-                        mma_bf16(dacc, dal, dbh, idesc, 1);
+                        mma_bf16_warp(dacc, dah, dbl, idesc, 1);
+                        mma_bf16_warp(dacc, dal, dbh, idesc, 1);
                         dah += a_ks;
                         dal += a_ks;
                         dbh += b_ks;
@@ -238,11 +242,12 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
                 }
             }
             // issuer 1 commits only in phases where it issued (rows |p| >= 1)
-            if (who == 0 || p1 > max(p0, 1)) mma_commit(&mbar[2 * (ph & 1) + who]);
+            if (who == 0 || p1 > max(p0, 1)) mma_commit_warp(&mbar[2 * (ph & 1) + who]);
         };
         using Iss0 = std::integral_constant<int, 0>;
         using Iss1 = std::integral_constant<int, 1>;
-        // thread 0 notes the commits of phase ph (on buffer ph & 1)
+        // warp 0 notes the commits of phase ph (on buffer ph & 1); thread 0
+        // waits on them
         auto note_issue = [&](int ph, const bool two) {
             const int p0 = ph * PHASE, p1 = min(p0 + PHASE, R + 1);
             pending |= ((two && p1 > max(p0, 1)) ? 3u : 1u) << (2 * (ph & 1));
@@ -293,10 +298,10 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
             for (int ct = 0; ct < n_ct && !timed_out; ++ct) {
                 const int j0 = bx.out_j0 + ct * w_ct, j1 = min(bx.out_j1, j0 + w_ct);
                 nt = ((j1 - j0) + 15) & ~15;
-                const uint32_t idesc = instr_desc(tile_m, nt);
+                const uint32_t idesc = __shfl_sync(0xffffffffu, instr_desc(tile_m, nt), 0);
                 // second issuer and accumulator (adjoint: measured faster; the
                 // forward's wider tiles keep one issuer)
-                const bool two = ADJ && nt <= (int)kAcc1Col && R >= 1;
+                const bool two = __shfl_sync(0xffffffffu, (int)(ADJ && nt <= (int)kAcc1Col && R >= 1), 0) != 0;
                 const int sa = max(bx.in_j0, j0 - R), sb = min(bx.in_j1, j0 + nt + R);
                 const int n_kc = sb > sa ? (sb - sa + Lim::MAXK - 1) / Lim::MAXK : 0;
                 const int w_kc = n_kc ? (((sb - sa + n_kc - 1) / n_kc) + 15) & ~15 : 16;
@@ -378,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
                         *reinterpret_cast<uint4 *>(ap) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                         *reinterpret_cast<uint4 *>(ap + a_copy) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
-                    const int n_ks = kt / 16;
+                    const int n_ks = __shfl_sync(0xffffffffu, kt / 16, 0);
                     build_b(0, min(PHASE, R + 1), 0, nd, c0);
                     fence_proxy_async();   // generic-proxy smem writes -> tensor core reads
                     fence_before();
@@ -386,10 +391,10 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
                     fence_after();
                     // phase ph + 1 is built and issued while phase ph runs; its
                     // buffer is free once phase ph - 1 completed
-                    if (tid == 0) {
+                    if (warp == 0) {
                         issue(0, n_ks, idesc, Iss0{}, two);
                         note_issue(0, two);
-                    } else if (ADJ && two && tid == 32) {
+                    } else if (ADJ && two && warp == 1) {
                         issue(0, n_ks, idesc, Iss1{}, two);
                     }
                     int waited = 0;   // phases [0, waited) are known complete
@@ -404,10 +409,10 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
                         fence_before();
                         __syncthreads();
                         fence_after();
-                        if (tid == 0) {
+                        if (warp == 0) {
                             issue(ph + 1, n_ks, idesc, Iss0{}, two);
                             note_issue(ph + 1, two);
-                        } else if (ADJ && two && tid == 32) {
+                        } else if (ADJ && two && warp == 1) {
                             issue(ph + 1, n_ks, idesc, Iss1{}, two);
                         }
                     }
