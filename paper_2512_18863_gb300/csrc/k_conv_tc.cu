@@ -201,8 +201,9 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
         const uint64_t da_hi0 = smem_desc(a_hi0, lbo_a, 128);
         const uint64_t da_lo0 = smem_desc(a_hi0 + (uint32_t)a_copy, lbo_a, 128);
         const uint64_t db0 = smem_desc(smem_u32(bbase), 128, 128);
-        const uint64_t a_ks = (uint64_t)((2u * (uint32_t)lbo_a) >> 4);   // per K step
-        const uint64_t b_ks = (uint64_t)((2u * 128u) >> 4);
+        const uint32_t a_ks = (2u * (uint32_t)lbo_a) >> 4;   // per K step
+        const uint32_t b_ks = (2u * 128u) >> 4;
+        const uint32_t desc_hi = (uint32_t)(da_hi0 >> 32);    // SBO 128 and version: common to all operands
         const uint64_t b_lo_off = (uint64_t)(((uint32_t)Lim::ND * 128u) >> 4);
         uint32_t acc = 0;   // per issuing thread: its accumulator holds a partial sum
         // Phase ph (kernel rows |p| in [ph*PHASE, ...)) reads operand buffer
@@ -226,14 +227,13 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
                 const int sg0 = who ? -1 : ((ap == 0 || two) ? 1 : -1);
                 const int sg1 = who ? -1 : 1;
                 for (int sg = sg0; sg <= sg1; sg += 2) {
-                    const uint64_t row = (uint64_t)(R - sg * ap);      // (row_off >> 4): rows 16 B apart
-                    uint64_t dah = da_hi0 + row, dal = da_lo0 + row;
-                    uint64_t dbh = dbh_row, dbl = dbl_row;
+                    // descriptor low words (start address >> 4 in bits 0-13)
+                    const uint32_t row = (uint32_t)(R - sg * ap);      // rows 16 B apart
+                    uint32_t dah = (uint32_t)da_hi0 + row, dal = (uint32_t)da_lo0 + row;
+                    uint32_t dbh = (uint32_t)dbh_row, dbl = (uint32_t)dbl_row;
                     for (int ks = 0; ks < n_ks; ++ks) {
-                        mma_bf16_warp(dacc, dah, dbh, idesc, acc);
+                        mma3_warp(dacc, dah, dal, dbh, dbl, desc_hi, idesc, acc);
                         acc = 1;
-                        mma_bf16_warp(dacc, dah, dbl, idesc, 1);
-                        mma_bf16_warp(dacc, dal, dbh, idesc, 1);
                         dah += a_ks;
                         dal += a_ks;
                         dbh += b_ks;

@@ -49,19 +49,28 @@ __device__ __forceinline__ void mma_commit(void *mbar)
                  : "memory");
 }
 
-// The same two instructions executed by a whole converged warp and issued by
-// its lane 0 only: the issuing loop then runs warp-uniform (its descriptors
-// are warp-uniform values), which measured faster than a loop inside a
-// one-thread branch.  The commit comes from the lane that issued the MMAs,
-// so it tracks them.
-__device__ __forceinline__ void mma_bf16_warp(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                              uint32_t accumulate)
+// MMA issue and commit executed by a whole converged warp and performed by
+// its lane 0 only: the issuing loop then runs on warp-uniform descriptors,
+// which measured faster than a loop inside a one-thread branch.  The commit
+// comes from the lane that issued the MMAs, so it tracks them.
+//
+// mma3_warp: the three products of one K step of an FP32-accurate product
+// split into BF16 hi + lo parts, D += Ah.Bh (or D = Ah.Bh when accumulate is
+// 0), D += Ah.Bl, D += Al.Bh.  Descriptors are passed as their low words
+// (start address, LBO) and one common high word (SBO, version): all four
+// share SBO, and start addresses stay inside their 14-bit field, so the
+// caller advances them with 32-bit adds.
+__device__ __forceinline__ void mma3_warp(uint32_t tmem_d, uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl,
+                                          uint32_t desc_hi, uint32_t idesc, uint32_t accumulate)
 {
     asm volatile(
-        "{\n\t.reg .pred p, e;\n\t.reg .u32 l;\n\tmov.u32 l, %%laneid;\n\tsetp.eq.u32 e, l, 0;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+        "{\n\t.reg .pred p, t, e;\n\t.reg .u32 l;\n\t.reg .b64 a0, a1, b0, b1;\n\t"
+        "mov.u32 l, %%laneid;\n\tsetp.eq.u32 e, l, 0;\n\tsetp.ne.b32 p, %7, 0;\n\tsetp.ne.b32 t, 1, 0;\n\t"
+        "mov.b64 a0, {%1, %5};\n\tmov.b64 a1, {%2, %5};\n\tmov.b64 b0, {%3, %5};\n\tmov.b64 b1, {%4, %5};\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a0, b0, %6, p;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a0, b1, %6, t;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b0, %6, t;\n\t}\n" ::"r"(tmem_d),
+        "r"(ah), "r"(al), "r"(bh), "r"(bl), "r"(desc_hi), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit_warp(void *mbar)
