@@ -25,14 +25,16 @@
 // adjoint, for column tiles of at most 64 columns, warp 1 issues those of -p
 // into a second accumulator (tensor memory columns 64..127), since one
 // issuing thread delivers an MMA only every ~50 cycles while an M = 64 MMA
-// with N <= 64 takes ~30.  Completion is signalled through one mbarrier per issuer and
-// operand buffer (tcgen05.commit); all waits are bounded and raise
-// PDRT_FLAG_TIMEOUT.  The kernel-row operands are built in phases of PHASE
-// rows (chosen per plan: the deepest phase that keeps the most CTAs per SM)
-// into a double buffer, each phase while the previous phase's MMAs run; with
-// the per direction tile limits three forward or four adjoint CTAs fit on an
-// SM at R = 20 px, and several resident CTAs overlap one another's operand
-// builds with their MMAs.
+// with N <= 64 takes ~30.  The kernel-row operands are built in phases of
+// PHASE rows (chosen per plan: the deepest phase that keeps the most CTAs per
+// SM) into three buffers: while the issuing warps issue phase ph, the other
+// warps build phase ph + 1 into the buffer that phase ph - 2 read, after
+// waiting for its MMAs; one CTA barrier per phase.  Completion is signalled
+// through one mbarrier per issuer and operand buffer (tcgen05.commit); all
+// waits are bounded and raise PDRT_FLAG_TIMEOUT.  With the per direction
+// tile limits three forward or four adjoint CTAs fit on an SM at R = 20 px,
+// and the resident CTAs overlap one another's input-tile builds and
+// epilogues with their MMAs.
 // Boxes wider than one tile are split into output-column tiles of at most
 // MAXN columns and, per column tile, chunks of at most MAXK of the input
 // columns within R of it; the chunks accumulate in tensor memory.  With
@@ -54,6 +56,7 @@ constexpr int kTcM = 128;
 constexpr int kTcThreads = 256;      // 8 warps: two per tensor-memory lane quarter
 constexpr uint32_t kTmemCols = 128;   // >= the largest tile width N, power of two
 constexpr uint32_t kAcc1Col = 64;     // second accumulator (tiles of N <= 64)
+constexpr int kTcBufs = 3;            // kernel-row operand buffers
 
 }  // namespace
 
@@ -66,9 +69,9 @@ struct TcLimits {
     static constexpr int ND = MAXN / 8 + MAXK / 8 - 1;   // Hankel diagonals per kernel row
 };
 
-// shared memory: [0,128) barriers / tmem address / broadcast; kernel rows;
-// input tile hi+lo [2][K/8][rows][16 B]; kernel-row operands, two buffers of
-// `phase` rows x hi+lo x ND core matrices
+// shared memory: [0,128) barriers / tmem address / broadcasts; kernel rows;
+// input tile hi+lo [2][K/8][rows][16 B]; kernel-row operands, three buffers
+// of `phase` rows x hi+lo x ND core matrices
 int conv_tc_smem_bytes(int R, bool adjoint, int phase)
 {
     const int rows = tc_rows(R);
@@ -76,7 +79,7 @@ int conv_tc_smem_bytes(int R, bool adjoint, int phase)
     const int nd = adjoint ? TcLimits<true>::ND : TcLimits<false>::ND;
     const int krow = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
     const int a = 2 * rows * maxk * 2;
-    const int bsz = 2 * phase * 2 * nd * 128;
+    const int bsz = kTcBufs * phase * 2 * nd * 128;
     return 128 + krow + a + bsz;
 }
 
@@ -96,9 +99,11 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
     const Lattice &L = P.lat;
     const int R = P.mach.R;
     const int rows = tc_rows(R);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [buffer * 2 + issuer]
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 32);
-    int *s_item = reinterpret_cast<int *>(smem + 36);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem);   // [buffer * 2 + issuer], 6
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 48);
+    int *s_item = reinterpret_cast<int *>(smem + 52);
+    // a wait gave up: [phase parity] in the phase loop, [2] in its drain
+    volatile int *s_flag = reinterpret_cast<volatile int *>(smem + 56);
     float *krow = reinterpret_cast<float *>(smem + 128);
     const int krow_bytes = ((R + 1) * (2 * R + 1) * 4 + 127) / 128 * 128;
     unsigned char *abase = smem + 128 + krow_bytes;
@@ -117,9 +122,10 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int q = 0; q < 4; ++q)
+        for (int q = 0; q < 2 * kTcBufs; ++q)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[q])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_flag[0] = s_flag[1] = s_flag[2] = 0;
     }
     fence_before();
     __syncthreads();
@@ -127,9 +133,10 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
     // values the issuing loop depends on are made warp-uniform (lane 0's
     // value) so that its descriptor arithmetic stays warp-uniform
     const uint32_t tmem = __shfl_sync(0xffffffffu, *s_tmem, 0);
-    // thread 0 tracks every barrier q in bit q: the parity of its next phase,
-    // and whether a commit to it is outstanding
-    uint32_t parity = 0u, pending = 0u;
+    // every thread tracks, in bit q, the parity of the number of commits to
+    // barrier q so far (cpar) and whether q was ever committed (cused); the
+    // commits are a function of the phase sequence, identical in all threads
+    uint32_t cpar = 0u, cused = 0u;
     bool timed_out = false;
 
     while (!timed_out) {
@@ -165,9 +172,9 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
         int nt = 16, kt = 16, nd = 1, s_end = 0, c0 = 0;
         // Hankel core matrices of kernel rows |p| in [p0, p1) into buffer `buf`:
         // element (r, t) of diagonal d = K(|p|, 8d + r + t + c0), c0 = j0 - s_end + 1
-        auto build_b = [&](int p0, int p1, int buf, const int nd, const int c0) {
+        auto build_b = [&](int p0, int p1, int buf, const int nd, const int c0, int t0, int ts) {
             const int n = (p1 - p0) * nd * 8;
-            for (int idx = tid; idx < n; idx += blockDim.x) {
+            for (int idx = t0; idx < n; idx += ts) {
                 const int pl = idx / (nd * 8), rem = idx - pl * nd * 8, d = rem >> 3, r = rem & 7;
                 const int p = p0 + pl;
                 uint32_t hw[4], lw[4];
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
         const uint64_t b_lo_off = (uint64_t)(((uint32_t)Lim::ND * 128u) >> 4);
         uint32_t acc = 0;   // per issuing thread: its accumulator holds a partial sum
         // Phase ph (kernel rows |p| in [ph*PHASE, ...)) reads operand buffer
-        // ph & 1; each issuer commits to mbar[2 (ph & 1) + issuer].  Issuer 0
+        // ph % 3; each issuer commits to mbar[2 (ph % 3) + issuer].  Issuer 0
         // (warp 0) takes the rows +p into columns [0, N); with two issuers,
         // issuer 1 (warp 1) takes the rows -p into columns [64, 64 + N),
         // otherwise issuer 0 takes both and issuer 1 does nothing.  Each
@@ -216,8 +223,8 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
         // instruction stream bounds the MMA rate, so its loop stays lean)
         auto issue = [&](int ph, const int n_ks, const uint32_t idesc, auto who_c, const bool two) {
             constexpr int who = decltype(who_c)::value;
-            const int p0 = ph * PHASE, p1 = min(p0 + PHASE, R + 1);
-            const uint64_t db_buf = db0 + (uint64_t)(((uint32_t)((ph & 1) * b_buf)) >> 4);
+            const int p0 = ph * PHASE, p1 = min(p0 + PHASE, R + 1), buf = ph % kTcBufs;
+            const uint64_t db_buf = db0 + (uint64_t)(((uint32_t)(buf * b_buf)) >> 4);
             const uint32_t dacc = tmem + (who ? kAcc1Col : 0u);
             for (int ap = (who ? max(p0, 1) : p0); ap < p1; ++ap) {
                 const uint64_t dbh_row = db_buf + (uint64_t)(((uint32_t)((ap - p0) * b_row)) >> 4);
@@ -242,43 +249,44 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
                 }
             }
             // issuer 1 commits only in phases where it issued (rows |p| >= 1)
-            if (who == 0 || p1 > max(p0, 1)) mma_commit_warp(&mbar[2 * (ph & 1) + who]);
+            if (who == 0 || p1 > max(p0, 1)) mma_commit_warp(&mbar[2 * buf + who]);
         };
         using Iss0 = std::integral_constant<int, 0>;
         using Iss1 = std::integral_constant<int, 1>;
-        // warp 0 notes the commits of phase ph (on buffer ph & 1); thread 0
-        // waits on them
-        auto note_issue = [&](int ph, const bool two) {
+        // does issuer 1 commit in phase ph (it takes rows |p| >= 1 only)
+        auto commits1 = [&](int ph, const bool two) {
             const int p0 = ph * PHASE, p1 = min(p0 + PHASE, R + 1);
-            pending |= ((two && p1 > max(p0, 1)) ? 3u : 1u) << (2 * (ph & 1));
+            return two && p1 > max(p0, 1);
         };
-        // bounded wait of thread 0 on buffer sb (the barriers with a commit
-        // outstanding), outcome broadcast to the CTA
-        auto wait_buf = [&](int sb) -> bool {
-            if (tid == 0) {
-                int ok = 1;
-                for (int q = 2 * sb; q < 2 * sb + 2 && ok; ++q) {
-                    if (!((pending >> q) & 1u)) continue;
-                    long long spins = 0;
-                    while (!mbar_try(&mbar[q], (parity >> q) & 1u)) {
-                        if (++spins > (1LL << 28)) {
-                            ok = 0;
-                            break;
-                        }
-                    }
-                    if (ok) {
-                        parity ^= 1u << q;
-                        pending &= ~(1u << q);
+        // all threads note the commits of phase ph
+        auto note_commits = [&](int ph, const bool two) {
+            const uint32_t m = (commits1(ph, two) ? 3u : 1u) << (2 * (ph % kTcBufs));
+            cpar ^= m;
+            cused |= m;
+        };
+        // bounded wait of a warp (its lane 0 polls) for the latest commit to
+        // barrier q
+        auto poll_q = [&](int q) -> bool {
+            int ok = 1;
+            if (lane == 0) {
+                const uint32_t par = ((cpar >> q) & 1u) ^ 1u;
+                long long spins = 0;
+                while (!mbar_try(&mbar[q], par)) {
+                    if (++spins > (1LL << 28)) {
+                        ok = 0;
+                        break;
                     }
                 }
-                *s_item = ok;
             }
-            fence_before();
-            __syncthreads();
-            const int ok = *s_item;
-            __syncthreads();
-            fence_after();
-            return ok != 0;
+            __syncwarp();
+            return __shfl_sync(0xffffffffu, ok, 0) != 0;
+        };
+        // the commits of phase ph (no later phase has reused its buffer)
+        auto poll_phase = [&](int ph, const bool two) -> bool {
+            const int q = 2 * (ph % kTcBufs);
+            bool ok = poll_q(q);
+            if (ok && commits1(ph, two)) ok = poll_q(q + 1);
+            return ok;
         };
         const int ow = bx.out_j1 - bx.out_j0;
         const int n_ct = (ow + Lim::MAXN - 1) / Lim::MAXN;
@@ -384,49 +392,61 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
                         *reinterpret_cast<uint4 *>(ap + a_copy) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                     }
                     const int n_ks = __shfl_sync(0xffffffffu, kt / 16, 0);
-                    build_b(0, min(PHASE, R + 1), 0, nd, c0);
+                    // Three operand buffers: the issuing warps issue phase ph
+                    // from buffer ph % 3 while the other warps build phase ph + 1
+                    // into buffer (ph + 1) % 3, which phase ph - 2 read last
+                    // (its commits are waited on first); one CTA barrier per
+                    // phase.
+                    const int n_iw = two ? 2 : 1;   // issuing warps
+                    build_b(0, min(PHASE, R + 1), 0, nd, c0, tid, kTcThreads);
                     fence_proxy_async();   // generic-proxy smem writes -> tensor core reads
                     fence_before();
                     __syncthreads();
                     fence_after();
-                    // phase ph + 1 is built and issued while phase ph runs; its
-                    // buffer is free once phase ph - 1 completed
-                    if (warp == 0) {
-                        issue(0, n_ks, idesc, Iss0{}, two);
-                        note_issue(0, two);
-                    } else if (ADJ && two && warp == 1) {
-                        issue(0, n_ks, idesc, Iss1{}, two);
-                    }
-                    int waited = 0;   // phases [0, waited) are known complete
-                    for (int ph = 0; ph + 1 < n_ph && !timed_out; ++ph) {
-                        if (ph >= 1) {
-                            if (!wait_buf((ph - 1) & 1)) timed_out = true;
-                            waited = ph;
+                    for (int ph = 0; ph < n_ph; ++ph) {
+                        if (warp == 0) {
+                            issue(ph, n_ks, idesc, Iss0{}, two);
+                        } else if (ADJ && two && warp == 1) {
+                            issue(ph, n_ks, idesc, Iss1{}, two);
+                        } else if (ph + 1 < n_ph) {
+                            if (ph < 2 || poll_phase(ph - 2, two))
+                                build_b((ph + 1) * PHASE, min((ph + 2) * PHASE, R + 1), (ph + 1) % kTcBufs, nd, c0,
+                                        tid - 32 * n_iw, kTcThreads - 32 * n_iw);
+                            else
+                                s_flag[ph & 1] = 1;
                         }
-                        if (timed_out) break;
-                        build_b((ph + 1) * PHASE, min((ph + 2) * PHASE, R + 1), (ph + 1) & 1, nd, c0);
+                        note_commits(ph, two);
                         fence_proxy_async();
                         fence_before();
                         __syncthreads();
                         fence_after();
-                        if (warp == 0) {
-                            issue(ph + 1, n_ks, idesc, Iss0{}, two);
-                            note_issue(ph + 1, two);
-                        } else if (ADJ && two && warp == 1) {
-                            issue(ph + 1, n_ks, idesc, Iss1{}, two);
+                        // a flag is written before the barrier of its own phase
+                        // only and read by every thread before the next barrier,
+                        // so all threads take the same branch
+                        if (s_flag[ph & 1]) {
+                            timed_out = true;
+                            break;
                         }
                     }
-                    for (int ph = waited; ph < n_ph && !timed_out; ++ph)
-                        if (!wait_buf(ph & 1)) timed_out = true;
+                    // every MMA of the chunk complete before the epilogue or the
+                    // next chunk: the phases not yet waited on (the last three)
+                    if (!timed_out) {
+                        for (int ph = max(n_ph - kTcBufs, 0); ph < n_ph; ++ph)
+                            if (!poll_phase(ph, two)) s_flag[2] = 1;
+                        fence_before();
+                        __syncthreads();
+                        fence_after();
+                        if (s_flag[2]) timed_out = true;
+                    }
                 }
                 if (timed_out) {
                     if (tid == 0) {
                         atomicOr(P.flags, (unsigned)PDRT_FLAG_TIMEOUT);
                         // second bounded waits for MMAs still in flight before the
                         // tensor memory is released
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q < 2 * kTcBufs; ++q) {
                             long long spins = 0;
-                            while (((pending >> q) & 1u) && !mbar_try(&mbar[q], (parity >> q) & 1u) &&
+                            while (((cused >> q) & 1u) && !mbar_try(&mbar[q], ((cpar >> q) & 1u) ^ 1u) &&
                                    ++spins < (1LL << 28)) {
                             }
                         }

@@ -32,7 +32,7 @@ constexpr int kConvRows = 32;            // output rows per CTA (one per lane)
 // tensor-core tile limits (output columns N, input columns K per chunk) per
 // direction: the forward has wide outputs and narrow inputs, the adjoint the
 // reverse; wider boxes are split into column tiles and input chunks
-constexpr int kTcFwdMaxN = 128, kTcFwdMaxK = 64;
+constexpr int kTcFwdMaxN = 128, kTcFwdMaxK = 48;
 constexpr int kTcAdjMaxN = 64, kTcAdjMaxK = 48;
 
 enum KernelId {
