@@ -296,7 +296,8 @@ def _reference(args):
 # point and pass, from a one-pass ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum) of the 256x256x160 two-arc plan at R = 20 px: forward
 # 12.03 (output write), adjoint 18.27 (gathered-gradient read + output write).
-# Valid for that workload and this kernel version only.
+# Valid for that workload and this kernel version only (None: not captured
+# for the current kernel, reported as null).
 _TRAFFIC_B_PER_SUPPORT_POINT = {"workload": "pelvis256x256x160_2x178cp_R4cm", "fwd": 12.03, "adj": 18.27}
 
 
@@ -400,7 +401,8 @@ def _gpu(args):
         peak_src = "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
     mma_flops = work.get("mma_flops", 0.0) * args.steps          # tensor FLOPs issued in the timed steps
     traffic = None
-    if w.name == _TRAFFIC_B_PER_SUPPORT_POINT["workload"] and tc_ms > 0.5 * conv_ms:
+    if (_TRAFFIC_B_PER_SUPPORT_POINT and w.name == _TRAFFIC_B_PER_SUPPORT_POINT["workload"]
+            and tc_ms > 0.5 * conv_ms):
         per_point = _TRAFFIC_B_PER_SUPPORT_POINT["fwd"] + _TRAFFIC_B_PER_SUPPORT_POINT["adj"]
         traffic = per_point * work["support_points"] * args.steps / max(conv_launches, 1)
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps}
