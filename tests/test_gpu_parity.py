@@ -120,6 +120,41 @@ def test_gradients_match_oracle(ste, tensor_cores):
     eng.close()
 
 
+def _assert_case(w, tensor_cores, seed):
+    eng = _engine(w, tensor_cores=tensor_cores)
+    model = O.Model(w.phantom, w.machine, w.plan)
+    gpu = eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).cpu().numpy().astype(np.float64)
+    ref = model.dose()
+    assert ref.max() > 0
+    _assert_dose(gpu, ref)
+    g = np.random.default_rng(seed).standard_normal(w.phantom.shape)
+    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
+                  for t in eng.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g))
+    rl, rj, rm = model.dose_grad(g)
+    _assert_grad(dl, rl, "leaves")
+    _assert_grad(dj, rj, "jaws")
+    _assert_grad(dm, rm, "mu")
+    eng.close()
+
+
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_zero_radius_kernel_matches_oracle(tensor_cores):
+    """R = 0: a one-tap lateral kernel (on the tensor cores a single operand
+    phase and one issuer per direction)."""
+    _assert_case(S.small_pelvis(seed=23, n=(18, 32, 32), n_cp=4, r_px=0), tensor_cores, 6)
+
+
+@pytest.mark.parametrize("tensor_cores", [True, False])
+def test_field_wider_than_64_pixels_across_leaf_pairs_matches_oracle(tensor_cores):
+    """A field 18 cm long along the leaf-pair axis on 2.5 mm pixels: the
+    adjoint's output columns exceed 64, so its tensor-core tiles run with one
+    issuing warp and seven building warps."""
+    m = S.machine_model(1011, r_px=3)
+    ph = S.water_phantom((80, 32, 32), (2.5, 2.5, 2.5))
+    plan = S.static_field(m, gantry_deg=30.0, half_x=20.0, half_y=90.0)
+    _assert_case(S.Workload("wide_v", ph, m, plan), tensor_cores, 7)
+
+
 def test_autograd_function_matches_oracle():
     """DoseFn inside a torch graph: quadratic objective on the PTV and an OAR."""
     w = S.small_pelvis(seed=22, n=(20, 36, 36), n_cp=4, r_px=5)
