@@ -84,12 +84,12 @@ int conv_tc_smem_bytes(int R, bool adjoint, int phase)
 }
 
 // Occupancy: the forward at most 80 registers per thread, so three CTAs of
-// 256 threads fit the register file (its shared memory allows three per SM);
-// the adjoint at most 64, four CTAs (its 48-column input chunks keep the
-// shared memory at four per SM, and four x 128 tensor-memory columns fill the
-// 512).  More resident CTAs overlap one CTA's operand build with another's
-// MMAs and add issuing threads: the adjoint ran 17 % faster at four CTAs
-// than at two.
+// 256 threads fit the register file (its shared memory with three operand
+// buffers allows three per SM); the adjoint at most 64, four CTAs (its
+// 48-column input chunks keep the shared memory at four per SM, and four x
+// 128 tensor-memory columns fill the 512).  More resident CTAs overlap one
+// CTA's input-tile build and epilogue with another's MMAs and add issuing
+// warps: the adjoint ran 17 % faster at four CTAs than at two.
 template <bool ADJ>
 __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, int b0, int nb,
                                                            unsigned int *__restrict__ counter)
@@ -212,14 +212,14 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
         const uint32_t b_ks = (2u * 128u) >> 4;
         const uint32_t desc_hi = (uint32_t)(da_hi0 >> 32);    // SBO 128 and version: common to all operands
         const uint64_t b_lo_off = (uint64_t)(((uint32_t)Lim::ND * 128u) >> 4);
-        uint32_t acc = 0;   // per issuing thread: its accumulator holds a partial sum
+        uint32_t acc = 0;   // per issuing warp: its accumulator holds a partial sum
         // Phase ph (kernel rows |p| in [ph*PHASE, ...)) reads operand buffer
         // ph % 3; each issuer commits to mbar[2 (ph % 3) + issuer].  Issuer 0
         // (warp 0) takes the rows +p into columns [0, N); with two issuers,
         // issuer 1 (warp 1) takes the rows -p into columns [64, 64 + N),
         // otherwise issuer 0 takes both and issuer 1 does nothing.  Each
         // issuer's lane 0 executes its MMAs and commits.
-        // (the issuer is a compile-time constant: the issuing thread's
+        // (the issuer is a compile-time constant: the issuing warp's
         // instruction stream bounds the MMA rate, so its loop stays lean)
         auto issue = [&](int ph, const int n_ks, const uint32_t idesc, auto who_c, const bool two) {
             constexpr int who = decltype(who_c)::value;
