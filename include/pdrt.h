@@ -65,7 +65,7 @@ typedef enum {
     PDRT_ESHAPE = 2,   /* inconsistent sizes */
     PDRT_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
     PDRT_ENOMEM = 4,   /* device or host allocation failed */
-    PDRT_EDEVICE = 5   /* the device does not support this build (needs sm_103a) */
+    PDRT_EDEVICE = 5   /* the device is not sm_103a, the only architecture the library is compiled for */
 } pdrt_status;
 
 /* Device-detected input problems, reported by pdrt_plan_status. */

@@ -30,7 +30,7 @@ def test_two_gloo_replicas_take_the_slowest_time():
     s.bind(("127.0.0.1", 0))
     port = s.getsockname()[1]
     s.close()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a threaded process
     out = mgr.dict()
     mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
     assert out[0][0] == out[1][0] == 150.0
