@@ -191,8 +191,9 @@ void pdrt_grid_destroy(pdrt_grid_t g);
  *                    memory, between 1 and 32 GiB); it sets how many control
  *                    points one pass processes (passes are balanced).
  * The plan owns all device scratch the forward and backward passes need.
- * Errors: EINVAL (bad values; kernel radius above PDRT_MAX_RADIUS_PX;
- * SID not larger than the grid's reach from the isocentre), ENOMEM, ECUDA.
+ * Errors: ESHAPE (n_cp < 1: an arc needs a control point), EINVAL (bad
+ * values; kernel radius above PDRT_MAX_RADIUS_PX; SID not larger than the
+ * grid's reach from the isocentre), ENOMEM, ECUDA.
  */
 pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
                              const double *gantry_deg_host, const double iso_mm[3],

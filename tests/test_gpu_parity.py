@@ -255,6 +255,43 @@ def test_tensor_and_simt_paths_match_oracle_on_arc_subset():
         _assert_dose(d.astype(np.float64), ref)
 
 
+def test_plan_without_control_points_is_rejected():
+    """An arc with no control points is a shape error of the upload (ESHAPE),
+    not an empty dose."""
+    from paper_2512_18863_gb300 import _lib
+    w = S.small_pelvis(n=(16, 24, 24), n_cp=1, r_px=3)
+    with pytest.raises(_lib.PdrtError) as e:
+        DoseEngine(w.phantom, w.machine, np.zeros(0), w.plan.iso)
+    assert e.value.status == 2
+
+
+def test_plan_of_another_grid_is_rejected():
+    """A plan handle is bound to the grid it was uploaded for: forward and
+    backward with another grid's handle fail with EINVAL before any launch,
+    and the engines stay usable."""
+    from paper_2512_18863_gb300 import _lib
+    w = S.small_pelvis(n=(16, 24, 24), n_cp=2, r_px=3)
+    a, b = _engine(w), _engine(w)
+    leaves, jaws, mu = a._params(w.plan.leaves, w.plan.jaws, w.plan.mu)
+    out = torch.empty(a.shape, dtype=torch.float32, device=a.device)
+    stream = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(_lib.PdrtError) as e:
+        _lib.pdrt_dose_forward(a._grid, b._plan, leaves.data_ptr(), jaws.data_ptr(),
+                               mu.data_ptr(), out.data_ptr(), stream)
+    assert e.value.status == 1
+    g = torch.ones(a.shape, dtype=torch.float32, device=a.device)
+    grads = [torch.empty_like(t) for t in (leaves, jaws, mu)]
+    with pytest.raises(_lib.PdrtError) as e:
+        _lib.pdrt_dose_backward(b._grid, a._plan, leaves.data_ptr(), jaws.data_ptr(),
+                                mu.data_ptr(), g.data_ptr(), *(t.data_ptr() for t in grads), stream)
+    assert e.value.status == 1
+    da = a.forward(w.plan.leaves, w.plan.jaws, w.plan.mu)
+    db = b.forward(w.plan.leaves, w.plan.jaws, w.plan.mu)
+    assert torch.equal(da, db) and float(da.max()) > 0
+    a.close()
+    b.close()
+
+
 def test_nan_input_is_flagged():
     w = S.small_pelvis(n=(16, 24, 24), n_cp=2, r_px=3)
     eng = _engine(w)
@@ -337,6 +374,27 @@ def test_full_size_8cm_kernel_sampled_against_oracle():
     g = np.random.default_rng(12).standard_normal(sub.phantom.shape).astype(np.float32)
     eng = _engine(sub)
     assert eng.info["tensor_cores"] == 1
+    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
+                  for t in eng.backward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu, g))
+    eng.close()
+    rl, rj, rm = mod.dose_grad(g.astype(np.float64))
+    _assert_grad(dl, rl, "leaves")
+    _assert_grad(dj, rj, "jaws")
+    _assert_grad(dm, rm, "mu")
+
+
+def test_full_size_2cm_kernel_sampled_against_oracle():
+    """R = 10 px (2 cm at 2 mm), the small end of the kernel-radius sweep:
+    full grid, two control points of the two-arc plan (one per arc), dose and
+    gradients against the oracle."""
+    w = S.pelvis_two_arc_256(r_cm=2.0)
+    assert w.machine.r_px == 10
+    sub = _subplan(w, np.array([30, 300]))
+    gpu = _gpu_dose(sub)
+    mod = O.Model(sub.phantom, sub.machine, sub.plan)
+    _assert_dose(gpu, mod.dose())
+    g = np.random.default_rng(13).standard_normal(sub.phantom.shape).astype(np.float32)
+    eng = _engine(sub)
     dl, dj, dm = (t.cpu().numpy().astype(np.float64)
                   for t in eng.backward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu, g))
     eng.close()
