@@ -107,6 +107,43 @@ def test_wepl_slab_closed_form(gantry, axis, sign):
     assert z[kk[0]] == pytest.approx(z[kk[1]], abs=1e-12) == pytest.approx(z[kk[2]], abs=1e-12)
 
 
+@pytest.mark.parametrize("gantry", [30.0, 45.0, 137.0, 210.0, 300.0])
+def test_wepl_increments_in_a_linear_density_field(gantry):
+    """Oblique central rays (Sec. 2.2.4).  HU linear in x and y within
+    [0, 1000] gives a density linear in position (the calibration curve is
+    linear there), and trilinear interpolation reproduces a linear function
+    exactly inside the hull of the voxel centres.  So for two consecutive
+    beam slices sampled inside that hull the midpoint sum increases by
+    dw (rho(p_k) + rho(p_k+1)) / 2, with p_k = iso + w_k e_w and
+    e_w = (sin g, cos g, 0).  A wrong step length, ray direction or axis
+    assignment at a non-axial angle breaks this."""
+    n, s = 41, 2.0
+    half = n // 2
+    ph = _phantom((3, n, n), (s, s, s), lambda X, Y, Z: 500.0 + 10.0 * (X - half) + 5.0 * (Y - half))
+    m = S.machine_model(4, r_px=2)
+    mod = O.Model(ph, m, S.static_field(m, gantry_deg=gantry))
+    z = mod.wepl(0)
+    lat = mod.lattice
+    dw = lat["du"]
+    g = np.deg2rad(gantry)
+    ew = np.array([np.sin(g), np.cos(g)])
+
+    def rho(p):   # RED = 1 + 0.6 HU / 1000, HU = 500 + 5 x + 2.5 y (x, y in mm)
+        return 1.0 + 0.6e-3 * (500.0 + 5.0 * p[0] + 2.5 * p[1])
+
+    lim = half * s - 1e-9
+    checked = 0
+    for k in range(lat["nw"] - 1):
+        p0 = (k - lat["cw"]) * dw * ew
+        p1 = (k + 1 - lat["cw"]) * dw * ew
+        if max(np.abs(p0).max(), np.abs(p1).max()) > lim:
+            continue
+        exp = dw * 0.5 * (rho(p0) + rho(p1))
+        assert z[k + 1] - z[k] == pytest.approx(exp, rel=1e-12), (k, p0)
+        checked += 1
+    assert checked >= 20
+
+
 # --------------------------------------------------------------------------
 # T1: open-field water depth dose = cal MU T(z) (SID/d)^2 on the central axis
 # (Sec. 2.2.3 inverse square, Sec. 2.2.4 depth, Sec. 2.2.6 kernel unit sum,
