@@ -41,6 +41,27 @@ def test_overlap_golden_values():
         assert O.overlap(d, lo, hi, D) == pytest.approx(exp, abs=1e-15)
 
 
+def test_projection_golden_values():
+    """Sec. 2.2.1: hand-derived projections of leaf and jaw pairs (both use
+    the same centre / width projection, with their own w_min and F), and
+    MU^ = max(MU, eps)."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "projection_eq.txt"), comments="#")
+    w = S.small_pelvis(n=(8, 12, 12), n_cp=1, r_px=1)
+    for a, b, wmin, F, ea, eb in rows:
+        m = S.Machine(**{**w.machine.__dict__, "wmin_leaf": wmin, "f_leaf": F,
+                         "wmin_jaw": wmin, "f_jaw": F, "eps_mu": 0.01})
+        mod = O.Model(w.phantom, m, w.plan)
+        lv = w.plan.leaves.copy()
+        lv[0, 7] = (a, b)
+        jw = np.array([[a, b, b - 400.0, b + 400.0]])
+        lv_p, jw_p, _ = mod.project(0, lv, jw, w.plan.mu)
+        assert tuple(lv_p[7]) == pytest.approx((ea, eb), abs=1e-12)
+        assert tuple(jw_p[:2]) == pytest.approx((ea, eb), abs=1e-12)
+    for mu, exp in ((0.004, 0.01), (-1.0, 0.01), (0.01, 0.01), (2.0, 2.0)):
+        _, _, mu_p = mod.project(0, w.plan.leaves, w.plan.jaws, np.array([mu]))
+        assert mu_p == exp
+
+
 def test_overlap_partition_of_unity():
     """T7: sum_a f(u_a; l, r) D = r - l for any l < r inside the lattice."""
     rng = np.random.default_rng(0)
