@@ -77,7 +77,9 @@ __device__ __forceinline__ MagTap mag_taps(int p, float c, const MagSlice &e, in
 // pixel rows and 16 pixel columns (they are separable), then each pixel sums
 //   sum_j wc(c, j) sum_i wa(a, i) h'(i, j)
 // slice by slice, j then i in increasing order (non-zero terms only).
-__global__ void __launch_bounds__(256) k_mag_T(PlanDev P, int b0)
+// The kernel waits mostly on its h' loads, so it is bounded to 32 registers
+// for eight resident CTAs (64 warps) per SM instead of six.
+__global__ void __launch_bounds__(256, 8) k_mag_T(PlanDev P, int b0)
 {
     const Lattice &L = P.lat;
     const int bl = blockIdx.x, b = b0 + bl;
