@@ -107,3 +107,25 @@ def test_network_parameter_count_and_host_checks():
     with pytest.raises(_lib.PdrtError):
         _lib.pdrt_bev_project(0, 4, 4, 4, (1.0, 1.0, 1.0), (0, 0, 0), (0, 0, 0), 1000.0, [0.0], 64,
                               2.5, 50.0, 1.0, 0, 0)
+
+
+@pytest.mark.skipif(__import__("torch").cuda.is_available(),
+                    reason="host-only check with placeholder device pointers; "
+                           "the GPU test of the entry point covers a real device")
+def test_static_entry_point_rejects_on_the_host():
+    """pdrt_cp_dose_static checks its arguments and its scratch need on the
+    host before any CUDA call: NULL buffers are EINVAL, and a grid whose
+    scratch exceeds PDRT_STATIC_SCRATCH_BYTES is EINVAL with the size needed."""
+    from paper_2512_18863_gb300 import synth as S
+    m = _lib.machine_struct(S.machine_model(5, r_px=10))
+    fake = 256   # never dereferenced: every call below is rejected on the host
+    with pytest.raises(_lib.PdrtError) as e:
+        _lib.pdrt_cp_dose_static(0, 64, 64, 64, 2.0, 2.0, 2.0, (-64.0, -64.0, -64.0), (0, 0, 0),
+                                 0.0, m, fake, fake, fake, fake, 0)
+    assert e.value.status == 1
+    with pytest.raises(_lib.PdrtError) as e:
+        _lib.pdrt_cp_dose_static(fake, 1024, 1024, 512, 1.0, 1.0, 1.0, (-512.0, -512.0, -256.0),
+                                 (0, 0, 0), 30.0, m, fake, fake, fake, fake, 0)
+    assert e.value.status == 1
+    msg = _lib.pdrt_last_error()
+    assert "MiB" in msg and "PDRT_STATIC_SCRATCH_BYTES" in msg
