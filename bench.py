@@ -148,7 +148,7 @@ def _objective_grad(D, masks, torch):
 
 
 class _Clocks:
-    """nvidia-smi sampling (200 ms) while the timed region runs."""
+    """nvidia-smi sampling (every 100 ms) while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -160,7 +160,7 @@ class _Clocks:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(gpu_index), "-lms", "200"], stdout=self.fh,
+                                          "-i", str(gpu_index), "-lms", "100"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
