@@ -371,6 +371,32 @@ def test_fluence_area_closed_forms():
 # --------------------------------------------------------------------------
 # T8: brute force on a 16^3 grid
 # --------------------------------------------------------------------------
+def test_convolution_is_the_same_size_zero_padded_convolution_per_slice():
+    """Sec. 2.2.6: beam slice k's lateral dose is T(z_k) times the 'same'-size
+    2-D convolution, zero padded at the lattice edge, of that slice's fluence
+    with that slice's kernel; scipy.signal.convolve2d computes it
+    independently.  The lattice has du != dv (3 and 2 mm), the fluence is
+    random, non-negative and fills the lattice to its edges, some slices are
+    empty, and the depths change the kernel from slice to slice."""
+    from scipy.signal import convolve2d
+    ph = _phantom((6, 9, 9), (3.0, 3.0, 2.0))
+    m = S.machine_model(8, r_px=4)
+    mod = O.Model(ph, m, S.static_field(m))
+    nw, nv, nu = mod.vol_shape()
+    R = m.r_px
+    rng = np.random.default_rng(5)
+    Phi = rng.random((nw, nv, nu))
+    Phi[::4] = 0.0
+    z = np.linspace(5.0, 250.0, nw)
+    for brute in (False, True):
+        got = mod.conv(z, Phi, brute=brute)
+        for k in range(nw):
+            K = mod.kernel(z[k])                 # [u offset][v offset]
+            assert K[R, R + 1] > K[R + 1, R]     # a 2 mm step (v) is nearer than 3 mm (u)
+            exp = mod.depth_dose(z[k]) * convolve2d(Phi[k], K.T, mode="same")
+            np.testing.assert_allclose(got[k], exp, rtol=1e-12, atol=1e-15)
+
+
 def test_brute_force_16cube():
     w = S.small_pelvis(n=(16, 16, 16), spacing=4.0, n_cp=3, r_px=3, ptv_radii=(12.0, 10.0, 12.0))
     mod = O.Model(w.phantom, w.machine, w.plan)
