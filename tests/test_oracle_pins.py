@@ -397,6 +397,32 @@ def test_convolution_is_the_same_size_zero_padded_convolution_per_slice():
             np.testing.assert_allclose(got[k], exp, rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("gantry", [0.0, 37.0, 251.0])
+def test_gather_is_trilinear_sampling_with_zero_outside(gantry):
+    """Sec. 2.2.7: voxel x receives the beam-frame dose sampled trilinearly at
+    its beam coordinates (u, v, w) = ((x - iso).e_u, (x - iso).e_v,
+    (x - iso).e_w) in lattice units; scipy.ndimage.map_coordinates (order 1,
+    zero outside) samples the same points independently.  The isocentre is
+    off the grid centre and sx != sz."""
+    from scipy.ndimage import map_coordinates
+    ph = _phantom((7, 12, 10), (3.0, 3.0, 2.0), iso_index=(3, 7, 2))
+    m = S.machine_model(8, r_px=2)
+    mod = O.Model(ph, m, S.static_field(m, gantry_deg=gantry))
+    lat = mod.lattice
+    Dp = np.random.default_rng(6).random(mod.vol_shape())
+    got = mod.gather(0, Dp, scale=1.7)
+    nz, ny, nx = ph.hu.shape
+    Z, Y, X = np.meshgrid(*(o + s * np.arange(n) for o, s, n in
+                            zip(ph.origin[::-1], ph.spacing[::-1], (nz, ny, nx))), indexing="ij")
+    g = np.deg2rad(gantry)
+    u = X * np.cos(g) - Y * np.sin(g)
+    w = X * np.sin(g) + Y * np.cos(g)
+    coords = np.stack([w / lat["du"] + lat["cw"], Z / lat["dv"] + lat["cv"], u / lat["du"] + lat["cu"]])
+    exp = 1.7 * map_coordinates(Dp, coords.reshape(3, -1), order=1, mode="grid-constant",
+                                cval=0.0).reshape(nz, ny, nx)
+    np.testing.assert_allclose(got, exp, rtol=1e-12, atol=1e-14)
+
+
 def test_brute_force_16cube():
     w = S.small_pelvis(n=(16, 16, 16), spacing=4.0, n_cp=3, r_px=3, ptv_radii=(12.0, 10.0, 12.0))
     mod = O.Model(w.phantom, w.machine, w.plan)
