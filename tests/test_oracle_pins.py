@@ -423,6 +423,30 @@ def test_gather_is_trilinear_sampling_with_zero_outside(gantry):
     np.testing.assert_allclose(got, exp, rtol=1e-12, atol=1e-14)
 
 
+def test_fluence_volume_is_magnified_bilinear_sampling():
+    """Sec. 2.2.3: Phi_k at lattice point (i, j) is (SID/d_k)^2 times the
+    fluence map sampled bilinearly at the iso-plane point (SID/d_k) times the
+    point's offset from the central axis, zero outside the map, with
+    d_k = SID + w_k; scipy.ndimage.map_coordinates (order 1, zero outside)
+    samples it independently.  A short SID makes m range well above and below
+    1, so samples fall outside the map near its edges."""
+    from scipy.ndimage import map_coordinates
+    ph = _phantom((5, 11, 11), (3.0, 3.0, 2.0))
+    m = S.machine_model(8, r_px=2)
+    m.sid = 120.0
+    mod = O.Model(ph, m, S.static_field(m))
+    lat = mod.lattice
+    F = np.random.default_rng(7).random((lat["nv"], lat["nu"]))
+    Phi = mod.magnify(F)
+    jj, ii = np.meshgrid(np.arange(lat["nv"]), np.arange(lat["nu"]), indexing="ij")
+    for k in range(lat["nw"]):
+        mk = m.sid / (m.sid + (k - lat["cw"]) * lat["du"])
+        coords = np.stack([mk * (jj - lat["cv"]) + lat["cv"], mk * (ii - lat["cu"]) + lat["cu"]])
+        exp = mk ** 2 * map_coordinates(F, coords.reshape(2, -1), order=1, mode="grid-constant",
+                                        cval=0.0).reshape(F.shape)
+        np.testing.assert_allclose(Phi[k], exp, rtol=1e-12, atol=1e-14)
+
+
 def test_brute_force_16cube():
     w = S.small_pelvis(n=(16, 16, 16), spacing=4.0, n_cp=3, r_px=3, ptv_radii=(12.0, 10.0, 12.0))
     mod = O.Model(w.phantom, w.machine, w.plan)
