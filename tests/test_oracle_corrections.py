@@ -111,6 +111,28 @@ def test_collimator_rotation_of_a_radial_map_within_interpolation_bound():
     assert np.abs(G - F)[inner].max() > 0.0
 
 
+@pytest.mark.parametrize("coll", [23.0, -61.0, 145.0])
+def test_collimator_rotation_is_bilinear_resampling(coll):
+    """A feature at s appears at R(coll) s, so pixel x reads the corrected map
+    at R(coll)^-1 x, in mm (pixels 2 x 2.5 mm here), bilinearly, zero
+    outside the lattice; scipy.ndimage.map_coordinates (order 1, zero
+    outside) resamples the same points independently."""
+    from scipy.ndimage import map_coordinates
+    mod, _ = _model(pen_u=0.0, pen_v=0.0, coll=coll, sz=2.5)
+    L = mod.lattice
+    assert L["du"] != L["dv"]
+    F = np.random.default_rng(9).random((L["nv"], L["nu"]))
+    G = mod.rotate(F)
+    t = math.radians(coll)
+    Rinv = np.linalg.inv(np.array([[math.cos(t), -math.sin(t)], [math.sin(t), math.cos(t)]]))
+    c, a = np.meshgrid(np.arange(L["nv"]), np.arange(L["nu"]), indexing="ij")
+    uv = np.stack([(a - L["cu"]) * L["du"], (c - L["cv"]) * L["dv"]]).reshape(2, -1)
+    us, vs = Rinv @ uv
+    coords = np.stack([vs / L["dv"] + L["cv"], us / L["du"] + L["cu"]])
+    exp = map_coordinates(F, coords, order=1, mode="grid-constant", cval=0.0).reshape(F.shape)
+    np.testing.assert_allclose(G, exp, rtol=1e-12, atol=1e-14)
+
+
 def test_collimator_rotation_dot_product():
     mod, _ = _model(coll=23.0)
     L = mod.lattice
