@@ -165,6 +165,35 @@ def test_wepl_increments_in_a_linear_density_field(gantry):
     assert checked >= 20
 
 
+@pytest.mark.parametrize("gantry", [0.0, 23.0, 118.0, 301.0])
+def test_wepl_is_the_midpoint_sum_of_trilinear_samples(gantry):
+    """Sec. 2.2.4 at any angle in any density: the depth of beam slice k is
+    dw (sum_{m<k} rho_m + rho_k / 2), rho_m the density sampled trilinearly
+    (zero outside the grid) at the slice centre p_m = iso + w_m e_w on the
+    central ray; scipy.ndimage.map_coordinates samples the same points and
+    numpy's cumulative sum adds them.  Random HU, an off-centre isocentre
+    between voxel centres in z, and sx != sz."""
+    from scipy.ndimage import map_coordinates
+    n = (9, 17, 15)
+    rng = np.random.default_rng(11)
+    ph = _phantom(n, (2.0, 2.0, 3.0), lambda X, Y, Z: rng.uniform(-1000.0, 3000.0, X.shape),
+                  iso_index=(6, 9, 4))
+    red = np.interp(ph.hu.astype(np.float64), S.HU_TO_RED[:, 0], S.HU_TO_RED[:, 1])
+    m = S.machine_model(4, r_px=2)
+    iso = (1.0, -0.5, 1.2)
+    mod = O.Model(ph, m, S.static_field(m, gantry_deg=gantry, iso=iso))
+    z = mod.wepl(0)
+    lat = mod.lattice
+    g = np.deg2rad(gantry)
+    w = (np.arange(lat["nw"]) - lat["cw"]) * lat["du"]
+    pts = np.stack([np.full_like(w, iso[2]), iso[1] + w * np.cos(g), iso[0] + w * np.sin(g)])
+    idx = (pts - np.array(ph.origin[::-1])[:, None]) / np.array(ph.spacing[::-1])[:, None]
+    rho = map_coordinates(red, idx, order=1, mode="grid-constant", cval=0.0)
+    exp = lat["du"] * (np.concatenate([[0.0], np.cumsum(rho)[:-1]]) + 0.5 * rho)
+    np.testing.assert_allclose(z, exp, rtol=1e-12, atol=1e-12)
+    assert rho.max() > 0 and (rho == 0).any()      # the ray enters from outside the grid
+
+
 # --------------------------------------------------------------------------
 # T1: open-field water depth dose = cal MU T(z) (SID/d)^2 on the central axis
 # (Sec. 2.2.3 inverse square, Sec. 2.2.4 depth, Sec. 2.2.6 kernel unit sum,
