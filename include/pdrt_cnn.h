@@ -51,28 +51,34 @@ pdrt_status pdrt_cnn_create(pdrt_cnn_t *out, int32_t batch_max, pdrt_stream_t st
 void pdrt_cnn_destroy(pdrt_cnn_t net);
 
 /* Copies the FP32 parameter vector from device memory (params_dev, caller
- * owned, pdrt_cnn_param_count floats) and resets the Adam state and step. */
+ * owned, pdrt_cnn_param_count floats) and resets the Adam state and step.
+ * Errors (here and in every call below that takes a handle): EINVAL (NULL
+ * handle or buffer, or the current device is not the handle's), ECUDA. */
 pdrt_status pdrt_cnn_set_params(pdrt_cnn_t net, const float *params_dev, pdrt_stream_t stream);
 /* Copies the FP32 master parameters to params_dev (caller owned). */
 pdrt_status pdrt_cnn_get_params(pdrt_cnn_t net, float *params_dev, pdrt_stream_t stream);
 
 /* Forward pass of n <= batch_max samples.  x_dev: BF16 bits [n][64][64][3];
  * y_dev: FP32 [n][121] (caller owned, overwritten).  The activations stay in
- * the handle for a following pdrt_cnn_backward of the same n. */
+ * the handle for a following pdrt_cnn_backward of the same n.
+ * Errors: ESHAPE (n outside 1..batch_max). */
 pdrt_status pdrt_cnn_forward(pdrt_cnn_t net, const uint16_t *x_dev, int32_t n, float *y_dev,
                              pdrt_stream_t stream);
 
 /* Backward pass of the last forward for an upstream gradient dy_dev FP32
  * [n][121] (rounded to BF16 like every backward operand); writes the FP32
  * parameter gradient to grads_dev (pdrt_cnn_param_count floats, caller owned)
- * or, if grads_dev is NULL, keeps it in the handle only. */
+ * or, if grads_dev is NULL, keeps it in the handle only.
+ * Errors: ESHAPE (n is not the last forward's batch). */
 pdrt_status pdrt_cnn_backward(pdrt_cnn_t net, int32_t n, const float *dy_dev, float *grads_dev,
                               pdrt_stream_t stream);
 
 /* One training step: forward, mean-squared error against target_dev FP32
  * [n][121], backward and an Adam update (beta1 0.9, beta2 0.999, eps 1e-8)
  * with learning rate lr.  loss_dev (1 FP32, caller owned, may be NULL)
- * receives the batch loss before the update. */
+ * receives the batch loss before the update.
+ * Errors: ESHAPE (n outside 1..batch_max), EINVAL (lr not positive and
+ * finite). */
 pdrt_status pdrt_cnn_train_step(pdrt_cnn_t net, const uint16_t *x_dev, const float *target_dev,
                                 int32_t n, float lr, float *loss_dev, pdrt_stream_t stream);
 
