@@ -238,22 +238,27 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
  */
 pdrt_status pdrt_plan_set_tensor_cores(pdrt_plan_t p, int32_t enable);
 
-/* Lattice and scratch sizes of a plan (host only, no device work). */
+/* Lattice and scratch sizes of a plan (host only, no device work).
+ * Errors: EINVAL (NULL argument). */
 pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out);
 
 /*
  * Synchronises `stream`, returns the device-detected input flags
  * (PDRT_FLAG_*) raised since the previous call, and clears them.
+ * Errors: EINVAL (NULL argument), ECUDA (the synchronisation or the flag
+ * copy failed, e.g. an earlier kernel of the stream faulted).
  */
 pdrt_status pdrt_plan_status(pdrt_plan_t p, pdrt_stream_t stream, uint32_t *flags_out);
 
-/* Synchronises `stream` and returns the work counters of the last call. */
+/* Synchronises `stream` and returns the work counters of the last call.
+ * Errors: EINVAL (NULL argument), ECUDA. */
 pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out);
 
 /*
  * Per-kernel timing with CUDA events recorded on the launch stream around
  * every kernel the plan launches.  enable != 0 starts (and clears) a
  * measurement; pdrt_profile_read synchronises `stream` and returns the sums.
+ * Errors: EINVAL (NULL argument), ECUDA (event creation, synchronisation).
  */
 pdrt_status pdrt_profile_enable(pdrt_plan_t p, int32_t enable);
 pdrt_status pdrt_profile_read(pdrt_plan_t p, pdrt_stream_t stream, pdrt_profile *out);
@@ -298,6 +303,7 @@ pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int32_t ny, in
  * Control points per pass (1 .. the count chosen at upload; the scratch was
  * sized for that count).  Fewer points per pass keep each pass's beam-frame
  * dose closer to L2; more points mean fewer launches.  Host only.
+ * Errors: EINVAL (NULL plan, chunk_cp outside 1 .. the upload's count).
  */
 pdrt_status pdrt_plan_set_chunk(pdrt_plan_t p, int32_t chunk_cp);
 
@@ -353,7 +359,8 @@ pdrt_status pdrt_batch_create(pdrt_batch_t *out, int32_t n, const pdrt_grid_t *g
                               float *const *dmu_dev, int32_t n_branches, pdrt_stream_t stream);
 pdrt_status pdrt_batch_launch(pdrt_batch_t b, pdrt_stream_t stream);
 /* Synchronises `stream`; ms_out[i] = completion time of plan i in the last
- * launch, measured from the start of that launch (CUDA events in the graph). */
+ * launch, measured from the start of that launch (CUDA events in the graph).
+ * Errors: EINVAL (NULL argument), ECUDA (no launch yet, or a fault). */
 pdrt_status pdrt_batch_plan_times(pdrt_batch_t b, pdrt_stream_t stream, float *ms_out);
 /* Number of kernel nodes in the batch's graph (kernels run per launch). */
 int64_t pdrt_batch_kernels(pdrt_batch_t b);
