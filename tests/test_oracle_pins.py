@@ -224,6 +224,35 @@ def _pencil_model(gantry, jaws, sz=3.0, a=0.2, r_px=6):
     return O.Model(ph, m, plan), m
 
 
+def test_kernel_parameters_and_unit_sum_over_depth():
+    """Sec. 2.2.5 reading: decay rates a_c(z) and raw weights w_c(z) are
+    quadratics in depth (numpy's polyval evaluates them), a_c floored at
+    1e-4 / mm, raw weights floored at 0 and normalised to sum 1; every
+    component is normalised over the (2R+1)^2 window, so the kernel sums to 1
+    at every depth, and it depends on the radius only (symmetric under
+    p -> -p, q -> -q and, with square pixels, p <-> q)."""
+    from numpy.polynomial import polynomial as Pn
+    ph = _phantom((5, 9, 9), (2.0, 2.0, 2.0))
+    m = S.machine_model(12, r_px=6)
+    m.alpha[2] = (0.02, -2e-4, 0.0)           # decays to the floor beyond 100 mm
+    m.beta[1] = (0.2, -2e-3, 0.0)             # raw weight clamps to 0 beyond 100 mm
+    mod = O.Model(ph, m, S.static_field(m))
+    R = m.r_px
+    for z in (0.0, 35.0, 99.0, 150.0, 300.0):
+        a, w = mod.kernel_params(z)
+        a_exp = np.maximum([Pn.polyval(z, m.alpha[c]) for c in range(3)], 1e-4)
+        wr = np.maximum([Pn.polyval(z, m.beta[c]) for c in range(3)], 0.0)
+        np.testing.assert_allclose(a, a_exp, rtol=1e-14)
+        np.testing.assert_allclose(w, wr / wr.sum(), rtol=1e-14)
+        K = mod.kernel(z)
+        assert K.sum() == pytest.approx(1.0, abs=1e-13)
+        np.testing.assert_allclose(K, K[::-1, :], rtol=1e-14)
+        np.testing.assert_allclose(K, K[:, ::-1], rtol=1e-14)
+        np.testing.assert_allclose(K, K.T, rtol=1e-14)
+        assert K[R, R] == K.max() and K[R, R + 1] > K[R + 1, R + 1] > K[R, R + 2]
+    assert mod.kernel_params(150.0)[0][2] == 1e-4 and mod.kernel_params(150.0)[1][1] == 0.0
+
+
 def test_pencil_kernel_shape_and_unit_sum():
     """Sec. 2.2.5/2.2.6: a one-pixel field at the isocentre plane (m = 1, C = 1)
     gives D = cal MU T(z_iso) K(p,q); a single-exponential kernel must then fall
