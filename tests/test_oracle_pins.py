@@ -224,6 +224,20 @@ def _pencil_model(gantry, jaws, sz=3.0, a=0.2, r_px=6):
     return O.Model(ph, m, plan), m
 
 
+def test_depth_dose_is_the_clamped_linear_interpolation_of_the_table():
+    """Reading of the depth dose (Sec. 2.4): T(z) interpolates the table
+    linearly and is clamped at both ends; numpy's interp (which clamps the
+    same way) gives the same values, on a table with a 2.5 mm step."""
+    ph = _phantom((5, 9, 9), (2.0, 2.0, 2.0))
+    m = S.machine_model(13, r_px=2, n_t=41, dz_t=2.5)
+    mod = O.Model(ph, m, S.static_field(m))
+    zs = np.concatenate([[-5.0, 0.0, 1e-9], np.random.default_rng(2).uniform(0.0, 100.0, 50),
+                         [97.5, 99.99, 100.0, 250.0]])
+    exp = np.interp(zs, np.arange(41) * 2.5, m.t_table)
+    got = np.array([mod.depth_dose(z) for z in zs])
+    np.testing.assert_allclose(got, exp, rtol=1e-14, atol=1e-15)
+
+
 def test_kernel_parameters_and_unit_sum_over_depth():
     """Sec. 2.2.5 reading: decay rates a_c(z) and raw weights w_c(z) are
     quadratics in depth (numpy's polyval evaluates them), a_c floored at
