@@ -283,14 +283,17 @@ pdrt_status pdrt_profile_read(pdrt_plan_t p, pdrt_stream_t stream, pdrt_profile 
  * PDRT_STATIC_SCRATCH_BYTES inside the library, held by every GPU that loads
  * the library until the process exits.  The first call made with a device
  * current looks up that array's device address (cudaGetSymbolAddress) and
- * prepares the kernels for that device; make that first call before any
- * stream capture.  Every call shares the array, which keeps the last call's
- * contents (counters are cleared at the start of each call); calls that can
- * overlap on the GPU (other streams, other host threads) race on it.
- * Synchronous: returns once the dose is written (the stream is synchronised).
- * Errors: EINVAL (bad arguments; a grid whose scratch would exceed
- * PDRT_STATIC_SCRATCH_BYTES, with the needed size in the message), EDEVICE,
- * ECUDA.  Calls no cudaMalloc/cudaFree.
+ * prepares the kernels for that device.  Every call shares the array, which
+ * keeps the last call's contents (counters and flags are cleared at the start
+ * of each call); calls that can overlap on the GPU (other streams, other host
+ * threads) race on it.
+ * Synchronous: the call copies host tables, synchronises `stream` and reads
+ * the device flags back before it returns, so it cannot be recorded into a
+ * stream capture.
+ * Errors: EINVAL (bad arguments; nz > 32767; a grid whose scratch would
+ * exceed PDRT_STATIC_SCRATCH_BYTES, with the needed size in the message; a
+ * NaN or infinite leaf, jaw or MU value found on the device, in which case
+ * the dose is not valid), EDEVICE, ECUDA.  Calls no cudaMalloc/cudaFree.
  */
 #define PDRT_STATIC_SCRATCH_BYTES (64u << 20)
 pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int32_t ny, int32_t nz,

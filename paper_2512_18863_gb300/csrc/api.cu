@@ -123,10 +123,12 @@ cudaError_t timed(pdrt_plan_t p, int kid, cudaStream_t s, F &&launch)
 
 bool is_fin(double x) { return std::isfinite(x); }
 
+}  // namespace
+
 // u-range [lo, hi) of the beam lattice points of slice k that some voxel's
 // bilinear stencil can touch: the rotated grid rectangle in (fu, fw) index
 // space clipped to the band fw in [k-1, k+1], widened by one point.
-void needed_range(const double fu[4], const double fw[4], int k, int nu, int &lo, int &hi)
+void pdrt::needed_u_range(const double fu[4], const double fw[4], int k, int nu, int &lo, int &hi)
 {
     double umin = 1e300, umax = -1e300;
     const double b0 = k - 1.0, b1 = k + 1.0;
@@ -158,8 +160,6 @@ void needed_range(const double fu[4], const double fw[4], int k, int nu, int &lo
     hi = std::min((int)floor(umax) + 3, nu);
     if (hi < lo) hi = lo;
 }
-
-}  // namespace
 
 // Hooks for entry points defined in other translation units.
 void pdrt::internal_set_error(const char *msg) { g_last_error = msg ? msg : ""; }
@@ -401,7 +401,7 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
         long long so = 0, sa = 0;
         for (int k = 0; k < L.nw; ++k) {
             int lo, hi;
-            needed_range(fu, fw, k, L.nu, lo, hi);
+            needed_u_range(fu, fw, k, L.nu, lo, hi);
             ukr[(size_t)b * L.nw + k] = make_int2(lo, hi);
             if (hi > lo) {
                 so += (long long)(hi - lo) * L.nv;

@@ -13,11 +13,13 @@
 //
 // The array is held by every GPU that loads the library until the process
 // exits.  Its device address is obtained once per device with
-// cudaGetSymbolAddress on the first call made with that device current; that
-// first call should come before any stream capture.  Every call shares the
-// array and it keeps the previous call's contents: the counters and flags
-// are cleared at the start of each call, and calls that can overlap on the
-// GPU (two streams, two host threads) race on it.
+// cudaGetSymbolAddress on the first call made with that device current.
+// Every call shares the array and it keeps the previous call's contents: the
+// counters and flags are cleared at the start of each call, and calls that
+// can overlap on the GPU (two streams, two host threads) race on it.  The
+// call is synchronous: it copies pageable host tables to the array,
+// synchronises the stream and reads the device flags back before returning,
+// so none of its calls can be recorded into a stream capture.
 #include <math.h>
 #include <string.h>
 
@@ -52,37 +54,6 @@ pdrt_status cuda_err(cudaError_t e, const char *what)
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// u-range [lo, hi) of slice k touched by some voxel's bilinear stencil: the
-// rotated grid rectangle in (fu, fw) index space clipped to fw in [k-1, k+1],
-// widened by one point on each side.
-void slice_u_range(const double fu[4], const double fw[4], int k, int nu, int &lo, int &hi)
-{
-    double umin = 1e300, umax = -1e300;
-    for (int e = 0; e < 4; ++e) {
-        const int f = (e + 1) & 3;
-        const double w0 = fw[e], w1 = fw[f], u0 = fu[e], u1 = fu[f];
-        double tlo = 0.0, thi = 1.0;
-        if (fabs(w1 - w0) < 1e-12) {
-            if (w0 < k - 1.0 || w0 > k + 1.0) continue;
-        } else {
-            const double t0 = (k - 1.0 - w0) / (w1 - w0), t1 = (k + 1.0 - w0) / (w1 - w0);
-            tlo = std::max(0.0, std::min(t0, t1));
-            thi = std::min(1.0, std::max(t0, t1));
-            if (tlo > thi) continue;
-        }
-        for (double t : {tlo, thi}) {
-            umin = std::min(umin, u0 + t * (u1 - u0));
-            umax = std::max(umax, u0 + t * (u1 - u0));
-        }
-    }
-    if (umin > umax) {
-        lo = hi = 0;
-        return;
-    }
-    lo = std::max((int)floor(umin) - 1, 0);
-    hi = std::max(std::min((int)floor(umax) + 3, nu), lo);
-}
 
 }  // namespace
 
@@ -133,6 +104,8 @@ extern "C" pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int
     L.du = (float)sx;
     L.dv = (float)sz;
     if (!(m->sid_mm > (H + 2) * sx)) return err(PDRT_EINVAL, "SID must exceed the grid's reach");
+    // the gather's slice records pack the v bounds of a box in 16 bits each
+    if (L.nv > 32767) return err(PDRT_EINVAL, "grid too large: nz must be at most 32767");
 
     MachineDev M;
     memset(&M, 0, sizeof(M));
@@ -178,7 +151,7 @@ extern "C" pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int
     long long cap_o = 1;
     for (int k = 0; k < L.nw; ++k) {
         int lo, hi;
-        slice_u_range(fu, fw, k, L.nu, lo, hi);
+        needed_u_range(fu, fw, k, L.nu, lo, hi);
         ukr[k] = make_int2(lo, hi);
         cap_o += (long long)(hi - lo) * L.nv;
     }
@@ -292,5 +265,14 @@ extern "C" pdrt_status pdrt_cp_dose_static(const float *red_dev, int32_t nx, int
     internal_count_launch();
     // the pageable sources above must stay valid until their copies are staged
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_err(e, "stream sync");
+    // device-detected input problems of this call (cleared at its start)
+    unsigned flags = 0;
+    if ((e = cudaMemcpy(&flags, base + o_flags, sizeof(flags), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_err(e, "flag read-back");
+    if (flags & PDRT_FLAG_NAN_INPUT)
+        return err(PDRT_EINVAL, "a leaf, jaw or MU value is NaN or infinite (PDRT_FLAG_NAN_INPUT)");
+    if (flags & PDRT_FLAG_CAPACITY)
+        return err(PDRT_EINVAL, "a beam slice exceeded the scratch bound and was dropped (PDRT_FLAG_CAPACITY)");
+    if (flags) return err(PDRT_EINVAL, "device flag raised during the call");
     return PDRT_OK;
 }

@@ -295,6 +295,11 @@ inline cudaError_t allow_full_smem(Kern kern)
     return e;
 }
 int conv_tc_smem_bytes(int R, bool adjoint, int phase);
+// u-range [lo, hi) of beam slice k needed by some voxel of the grid whose
+// corners map to lattice indices (fu[c], fw[c]) (host; one definition for the
+// plan upload and the allocation-free entry point, so both size their regions
+// identically)
+void needed_u_range(const double fu[4], const double fw[4], int k, int nu, int &lo, int &hi);
 void internal_set_error(const char *msg);   // sets pdrt_last_error() for this thread
 void internal_count_launch();                // counts one launch in pdrt_launch_count()
 

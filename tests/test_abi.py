@@ -129,3 +129,9 @@ def test_static_entry_point_rejects_on_the_host():
     assert e.value.status == 1
     msg = _lib.pdrt_last_error()
     assert "MiB" in msg and "PDRT_STATIC_SCRATCH_BYTES" in msg
+    # a tall, narrow grid (nz > 32767) fits the scratch but not the gather's
+    # 16-bit packing of the v bounds: EINVAL before any device work
+    with pytest.raises(_lib.PdrtError) as e:
+        _lib.pdrt_cp_dose_static(fake, 4, 4, 40000, 2.0, 2.0, 1.0, (-4.0, -4.0, -20000.0),
+                                 (0, 0, 0), 0.0, m, fake, fake, fake, fake, 0)
+    assert e.value.status == 1 and "32767" in _lib.pdrt_last_error()

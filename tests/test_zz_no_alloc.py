@@ -55,6 +55,42 @@ def test_static_scratch_dose_matches_plan_forward_twice():
         assert np.abs(got - ref).max() <= DOSE_TOL * ref.max()
 
 
+def test_static_scratch_dose_with_fluence_corrections():
+    """The corrections path (penumbra blurs, off-axis profile, collimator
+    rotation) uses two more carve-outs of the static array; its dose matches
+    the plan forward on a one-point plan, on two calls in a row."""
+    w = S.small_pelvis(seed=33, n=(24, 44, 44), spacing=3.0, n_cp=2, r_px=6)
+    S.with_corrections(w.machine, seed=7, collimator_deg=23.0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    red = torch.tensor(_red(w.phantom), device=dev)
+    out = torch.empty(w.phantom.shape, dtype=torch.float32, device=dev)
+    for b in (0, 1):
+        got = _static_dose(w, b, red, out)
+        eng = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg[b:b + 1], w.plan.iso)
+        ref = eng.forward(w.plan.leaves[b:b + 1], w.plan.jaws[b:b + 1], w.plan.mu[b:b + 1])
+        ref = ref.cpu().numpy().astype(np.float64)
+        eng.close()
+        assert ref.max() > 0
+        assert np.abs(got - ref).max() <= DOSE_TOL * ref.max()
+
+
+def test_static_scratch_reports_nan_input():
+    """A NaN MU raises the device's input flag; the call reads it back and
+    returns EINVAL instead of a silently wrong dose.  The next valid call
+    succeeds (the flags are cleared at the start of each call)."""
+    w = S.small_pelvis(seed=34, n=(16, 32, 32), spacing=3.0, n_cp=1, r_px=4)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    red = torch.tensor(_red(w.phantom), device=dev)
+    out = torch.empty(w.phantom.shape, dtype=torch.float32, device=dev)
+    good_mu = w.plan.mu.copy()
+    w.plan.mu[0] = np.nan
+    with pytest.raises(_lib.PdrtError) as e:
+        _static_dose(w, 0, red, out)
+    assert e.value.status == 1 and "NaN" in str(e.value)
+    w.plan.mu[:] = good_mu
+    assert _static_dose(w, 0, red, out).max() > 0
+
+
 def test_static_scratch_rejects_oversized_grid():
     w = S.small_pelvis(seed=32, n=(16, 16, 16), spacing=3.0, n_cp=1, r_px=4)
     dev = torch.device("cuda", torch.cuda.current_device())
