@@ -70,8 +70,7 @@ def lib():
             L.orc_overlap.argtypes = [D, D, D, D]
             L.orc_depth_dose.restype = D
             L.orc_hu_to_red_1.restype = D
-            L.orc_calibration.restype = D
-            L.orc_calibration.argtypes = [D, D]
+            L.orc_calibrate.restype = C.c_int
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -83,6 +82,36 @@ def _p(a: np.ndarray):
 
 def _f64(a):
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _plan_struct(machine, gantry, iso, cal):
+    """OrcPlan of a machine + gantry angles (the arrays it points to are kept
+    on the returned structure)."""
+    pl = OrcPlan()
+    pl._keep = (gantry, _f64(machine.leaf_bounds), _f64(machine.t_table))
+    pl.n_cp = len(gantry)
+    pl.gantry_deg = _p(gantry)
+    pl.iso[:] = list(_f64(iso))
+    pl.sid = machine.sid
+    pl.n_pairs = len(pl._keep[1]) - 1
+    pl.leaf_bounds = _p(pl._keep[1])
+    pl.tau, pl.wmin_leaf, pl.wmin_jaw = machine.tau, machine.wmin_leaf, machine.wmin_jaw
+    pl.f_leaf, pl.f_jaw, pl.eps_mu = machine.f_leaf, machine.f_jaw, machine.eps_mu
+    pl.r_px = int(machine.r_px)
+    for c in range(3):
+        for k in range(3):
+            pl.alpha[c][k] = float(machine.alpha[c][k])
+            pl.beta[c][k] = float(machine.beta[c][k])
+    pl.n_t = len(pl._keep[2])
+    pl.dz_t = machine.dz_t
+    pl.t_table = _p(pl._keep[2])
+    pl.cal = float(cal)
+    pl.ste = int(machine.ste)
+    pl.pen_fwhm_u = float(getattr(machine, "pen_fwhm_u", 0.0))
+    pl.pen_fwhm_v = float(getattr(machine, "pen_fwhm_v", 0.0))
+    pl.oap[:] = [float(x) for x in getattr(machine, "off_axis", (1.0, 0.0, 0.0))]
+    pl.coll_deg = float(getattr(machine, "collimator_deg", 0.0))
+    return pl
 
 
 class Model:
@@ -103,31 +132,11 @@ class Model:
         g.red = _p(self.red)
         self.grid = g
         self._gantry = _f64(plan.gantry_deg)
-        self._lb = _f64(machine.leaf_bounds)
-        self._tt = _f64(machine.t_table)
-        pl = OrcPlan()
-        pl.n_cp = len(self._gantry)
-        pl.gantry_deg = _p(self._gantry)
-        pl.iso[:] = list(_f64(plan.iso))
-        pl.sid = machine.sid
-        pl.n_pairs = len(self._lb) - 1
-        pl.leaf_bounds = _p(self._lb)
-        pl.tau, pl.wmin_leaf, pl.wmin_jaw = machine.tau, machine.wmin_leaf, machine.wmin_jaw
-        pl.f_leaf, pl.f_jaw, pl.eps_mu = machine.f_leaf, machine.f_jaw, machine.eps_mu
-        pl.r_px = int(machine.r_px)
-        for c in range(3):
-            for k in range(3):
-                pl.alpha[c][k] = float(machine.alpha[c][k])
-                pl.beta[c][k] = float(machine.beta[c][k])
-        pl.n_t = len(self._tt)
-        pl.dz_t = machine.dz_t
-        pl.t_table = _p(self._tt)
-        pl.cal = machine.cal
-        pl.ste = int(machine.ste)
-        pl.pen_fwhm_u = float(getattr(machine, "pen_fwhm_u", 0.0))
-        pl.pen_fwhm_v = float(getattr(machine, "pen_fwhm_v", 0.0))
-        pl.oap[:] = [float(x) for x in getattr(machine, "off_axis", (1.0, 0.0, 0.0))]
-        pl.coll_deg = float(getattr(machine, "collimator_deg", 0.0))
+        cal = machine.cal
+        if cal is None:   # calibrate to the reference conditions of Sec. 2.4
+            cal = calibrate(machine, phantom.spacing[0], phantom.spacing[2])
+        self.cal = float(cal)
+        pl = _plan_struct(machine, self._gantry, plan.iso, cal=self.cal)
         self.cplan = pl
         L = OrcLattice()
         lib().orc_lattice_of(C.byref(g), C.byref(pl), C.byref(L))
@@ -290,8 +299,21 @@ def hu_to_red(hu, pts):
     return out
 
 
-def calibration(ref_dose_per_mu, gy_per_mu):
-    return lib().orc_calibration(float(ref_dose_per_mu), float(gy_per_mu))
+def calibrate(machine, sxy, sz, ref_mu=None, ref_gy=None, details=False):
+    """Output calibration of Sec. 2.4 (orc_calibrate): the factor cal that
+    makes ref_mu MU of the 10 x 10 cm reference field give ref_gy Gy at 10 cm
+    depth in water (SSD = SID - 100 mm) on a grid of the given pitch.  With
+    details=True also returns the reference slice's WEPL and dose per MU."""
+    ref_mu = float(getattr(machine, "cal_ref_mu", 100.0) if ref_mu is None else ref_mu)
+    ref_gy = float(getattr(machine, "cal_ref_gy", 1.0) if ref_gy is None else ref_gy)
+    gantry = _f64([0.0])
+    pl = _plan_struct(machine, gantry, (0.0, 0.0, 0.0), cal=1.0)
+    cal, zr, dpm = D(), D(), D()
+    rc = lib().orc_calibrate(C.byref(pl), D(float(sxy)), D(float(sz)), D(ref_mu), D(ref_gy),
+                             C.byref(cal), C.byref(zr), C.byref(dpm))
+    if rc:
+        raise RuntimeError(f"orc_calibrate failed: {rc}")
+    return (cal.value, zr.value, dpm.value) if details else cal.value
 
 
 def num_threads():

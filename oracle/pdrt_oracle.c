@@ -24,7 +24,8 @@
  * magnification of a sharp field edge, MU linearity, abutting half fields,
  * closed-MLC leakage, 90-degree rotation symmetry, fluence partition of unity,
  * brute force on a 16^3 grid, adjoint dot products and central finite
- * differences.  No function here is "parity unpinned".
+ * differences, and the output calibration against the depth-dose table at the
+ * reference depth.  No function here is "parity unpinned".
  *
  * Layouts (x fastest / last index fastest):
  *   red, dose, dose gradient : [nz][ny][nx]
@@ -1020,12 +1021,96 @@ int orc_dose_grad(const orc_grid *g, const orc_plan *p, const double *leaves, co
     return ORC_OK;
 }
 
-/* Output calibration (Sec. 2.4): the factor that turns the dose of 1 MU of
- * the reference field at the reference point into the requested Gy/MU.
- * ref_dose_per_mu is a forward dose per MU computed with cal = 1. */
-double orc_calibration(double ref_dose_per_mu, double gy_per_mu)
+/* ------------------------------------------------------------------------ */
+/* Output calibration (Sec. 2.4): the factor cal that makes ref_mu MU of the  */
+/* reference field give ref_gy Gy at the reference point of a virtual water   */
+/* phantom.  The paper names the reference conditions (10 cm x 10 cm field,   */
+/* 10 cm depth in water, SSD 90 cm) and says the dose there is computed with  */
+/* the beam model and the scaling factor adjusted; the discrete set-up is a   */
+/* reading:                                                                   */
+/*   - the reference point is the isocentre, 100 mm below the water surface   */
+/*     on the central axis, gantry 0 (SSD = SID - 100 mm: 90 cm at SID 1 m);  */
+/*   - the field is 100 mm x 100 mm at the isocentre plane: jaws (-50, 50,    */
+/*     -50, 50) and every leaf pair at (-50, 50); collimator 0; the beam      */
+/*     model's penumbra and off-axis profile apply;                           */
+/*   - voxels sxy x sxy x sz (the patient grid's pitch, so the kernel's pixel  */
+/*     radius means the same), the isocentre on a voxel centre; a voxel row   */
+/*     whose centre is y holds the water fraction of its extent              */
+/*     clamp((y + sxy/2 + 100) / sxy, 0, 1) as relative electron density, so   */
+/*     the midpoint depth sum (Sec. 2.2.4) at the isocentre is 100 mm exactly  */
+/*     at any pitch;                                                          */
+/*   - the grid reaches sqrt(2) R + penumbra half-window + 2 pixels beyond    */
+/*     the central axis in x and z, 100 mm + 2 voxels above the isocentre and */
+/*     2 voxels below it, so every pixel the isocentre's dose reads is on the */
+/*     lattice.                                                               */
+/* cal = ref_gy / D(isocentre) with D computed at cal = 1.  Also returns the  */
+/* WEPL of the reference slice and D per MU.                                  */
+/* ------------------------------------------------------------------------ */
+int orc_calibrate(const orc_plan *machine, double sxy, double sz, double ref_mu, double ref_gy,
+                  double *cal_out, double *z_ref_out, double *dose_per_mu_out)
 {
-    return gy_per_mu / ref_dose_per_mu;
+    if (!(sxy > 0) || !(sz > 0) || !(ref_mu > 0) || !(ref_gy > 0)) return ORC_EINVAL;
+    const int R = machine->r_px;
+    const double rad_mm = R * sqrt(sxy * sxy + sz * sz);
+    const int hx = (int)ceil(rad_mm / sxy) + orc_penumbra_radius(machine->pen_fwhm_u, sxy) + 2;
+    const int hz = (int)ceil(rad_mm / sz) + orc_penumbra_radius(machine->pen_fwhm_v, sz) + 2;
+    const int n_above = (int)ceil(100.0 / sxy + 0.5) + 2;   /* rows above the isocentre */
+    const int nx = 2 * hx + 1, nz = 2 * hz + 1, ny = n_above + 1 + 2;
+    double *red = (double *)malloc(sizeof(double) * (size_t)nx * ny * nz);
+    double *dose = (double *)malloc(sizeof(double) * (size_t)nx * ny * nz);
+    double *leaves = (double *)malloc(sizeof(double) * 2 * (machine->n_pairs > 0 ? machine->n_pairs : 1));
+    double *z = NULL;
+    if (!red || !dose || !leaves) {
+        free(red); free(dose); free(leaves);
+        return ORC_ENOMEM;
+    }
+    for (int j = 0; j < ny; ++j) {
+        double y = (j - n_above) * sxy;   /* row centre, mm; isocentre row j = n_above */
+        double f = (y + 0.5 * sxy + 100.0) / sxy;
+        f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+        for (int k = 0; k < nz; ++k)
+            for (int i = 0; i < nx; ++i) red[((size_t)k * ny + j) * nx + i] = f;
+    }
+    orc_grid g;
+    g.nx = nx; g.ny = ny; g.nz = nz;
+    g.sx = sxy; g.sy = sxy; g.sz = sz;
+    g.origin[0] = -hx * sxy; g.origin[1] = -n_above * sxy; g.origin[2] = -hz * sz;
+    g.red = red;
+    orc_plan p = *machine;
+    double gantry = 0.0;
+    p.n_cp = 1;
+    p.gantry_deg = &gantry;
+    p.iso[0] = p.iso[1] = p.iso[2] = 0.0;
+    p.cal = 1.0;
+    p.coll_deg = 0.0;
+    for (int i = 0; i < p.n_pairs; ++i) {
+        leaves[2 * i] = -50.0;
+        leaves[2 * i + 1] = 50.0;
+    }
+    double jaws[4] = {-50.0, 50.0, -50.0, 50.0};
+    int rc = orc_dose(&g, &p, leaves, jaws, &ref_mu, dose, 0);
+    if (rc == ORC_OK) {
+        double d_ref = dose[((size_t)hz * ny + n_above) * nx + hx];
+        if (!(d_ref > 0)) {
+            rc = ORC_EINVAL;
+        } else {
+            *cal_out = ref_gy / d_ref;
+            if (dose_per_mu_out) *dose_per_mu_out = d_ref / ref_mu;
+            if (z_ref_out) {
+                orc_lattice L;
+                orc_lattice_of(&g, &p, &L);
+                z = (double *)malloc(sizeof(double) * L.nw);
+                if (!z) {
+                    rc = ORC_ENOMEM;
+                } else {
+                    orc_wepl(&g, &p, &L, 0, z);
+                    *z_ref_out = z[(int)L.cw];
+                }
+            }
+        }
+    }
+    free(red); free(dose); free(leaves); free(z);
+    return rc;
 }
 
 int orc_num_threads(void)
