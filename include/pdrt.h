@@ -230,6 +230,34 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
                                float *dmu_dev, pdrt_stream_t stream);
 
 /*
+ * Output calibration (Sec. 2.4): the paper normalises the output so that a
+ * set number of reference MU gives 1 Gy at reference conditions (10 cm x 10 cm
+ * field, 10 cm depth in water, SSD 90 cm), computing the dose in a virtual
+ * water phantom.  This call runs that forward with the engine's kernels and
+ * returns cal = ref_gy / D_ref, D_ref being the dose of ref_mu MU of the
+ * reference field at the reference point with cal = 1; pass the result as
+ * pdrt_machine.cal of the plans.
+ * Reading of the discrete set-up: the reference point is the isocentre,
+ * 100 mm below the water surface on the central axis at gantry 0 (SSD = SID -
+ * 100 mm, i.e. 90 cm at SID 1 m); the field is 100 x 100 mm at the isocentre
+ * plane (jaws and every leaf pair at +-50 mm, collimator 0; the model's
+ * transmission, penumbra and off-axis profile apply); voxels sxy x sxy x sz,
+ * the patient grid's pitch, so that kernel_radius_px means the same; the
+ * isocentre on a voxel centre; a voxel row holds the water fraction of its
+ * extent as density, so that the midpoint depth at the isocentre is exactly
+ * 100 mm; the grid reaches every lattice pixel the isocentre's dose reads.
+ *   m        beam model (host; its cal and collimator_deg are ignored).
+ *   sxy, sz  voxel pitch in-plane and along z (mm).
+ *   ref_mu, ref_gy  the reference MU and the dose they must give (e.g. 100, 1).
+ *   cal_out  receives the factor (host).
+ * Allocates and frees temporary device memory and synchronises `stream`.
+ * Errors: EINVAL (NULL, non-positive values, bad beam model, or a model that
+ * gives no dose at the reference point), ENOMEM, ECUDA, EDEVICE.
+ */
+pdrt_status pdrt_calibrate(const pdrt_machine *m, double sxy, double sz, double ref_mu,
+                           double ref_gy, double *cal_out, pdrt_stream_t stream);
+
+/*
  * Route the per-slice convolution (Sec. 2.2.6) to the tensor cores (enable = 1,
  * the default: BF16 three-term split, FP32 accumulation, every slice tiled)
  * or to the FP32 SIMT kernel (enable = 0).  Host only.

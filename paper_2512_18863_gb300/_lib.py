@@ -89,6 +89,8 @@ _SIG = {
     "pdrt_cp_dose_static": (C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.c_double, C.POINTER(pdrt_machine), _VP, _VP, _VP, _VP, _VP]),
+    "pdrt_calibrate": (C.c_int, [C.POINTER(pdrt_machine), C.c_double, C.c_double, C.c_double,
+                                 C.c_double, C.POINTER(C.c_double), _VP]),
     "pdrt_plan_set_chunk": (C.c_int, [_VP, C.c_int32]),
     "pdrt_plan_set_tc_phase": (C.c_int, [_VP, C.c_int32, C.c_int32]),
     "pdrt_plan_autotune": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
@@ -253,6 +255,14 @@ def pdrt_cp_dose_static(red_dev_ptr, nx, ny, nz, sx, sy, sz, origin_mm, iso_mm, 
                                       _VP(jaws_ptr), _VP(mu_ptr), _VP(dose_ptr), _VP(stream)))
 
 
+def pdrt_calibrate(machine: pdrt_machine, sxy, sz, ref_mu, ref_gy, stream) -> float:
+    """Output calibration factor of Sec. 2.4 computed by the library's kernels."""
+    cal = C.c_double()
+    _check(load().pdrt_calibrate(C.byref(machine), float(sxy), float(sz), float(ref_mu),
+                                 float(ref_gy), C.byref(cal), _VP(stream)))
+    return cal.value
+
+
 def pdrt_plan_set_chunk(plan, chunk_cp):
     _check(load().pdrt_plan_set_chunk(_VP(plan), int(chunk_cp)))
 
@@ -305,8 +315,10 @@ def pdrt_batch_destroy(batch):
     load().pdrt_batch_destroy(_VP(batch))
 
 
-def machine_struct(machine) -> pdrt_machine:
-    """Fill pdrt_machine from a synth.Machine-like object."""
+def machine_struct(machine, cal=None) -> pdrt_machine:
+    """Fill pdrt_machine from a synth.Machine-like object.  cal overrides the
+    machine's output factor; a machine without one (cal None: calibrate) needs
+    it given."""
     m = pdrt_machine()
     lb = list(machine.leaf_bounds)
     if len(lb) - 1 > MAX_PAIRS:
@@ -333,7 +345,10 @@ def machine_struct(machine) -> pdrt_machine:
     m.depth_step_mm = float(machine.dz_t)
     for i, x in enumerate(tt):
         m.depth_dose[i] = float(x)
-    m.cal = float(machine.cal)
+    cal = machine.cal if cal is None else cal
+    if cal is None:
+        raise ValueError("the machine has no output factor: calibrate it (pdrt_calibrate) and pass cal")
+    m.cal = float(cal)
     m.ste = int(machine.ste)
     m.pen_fwhm_u_mm = float(getattr(machine, "pen_fwhm_u", 0.0))
     m.pen_fwhm_v_mm = float(getattr(machine, "pen_fwhm_v", 0.0))

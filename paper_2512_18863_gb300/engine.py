@@ -24,6 +24,19 @@ def _f32(x, device):
     return t.contiguous()
 
 
+def calibrate(machine, sxy, sz, ref_mu=None, ref_gy=None) -> float:
+    """Output calibration of Sec. 2.4 by the library (pdrt_calibrate): the
+    factor that makes ref_mu MU of the 10 x 10 cm reference field give ref_gy
+    Gy at 10 cm depth in water on a grid of pitch (sxy, sxy, sz).  Defaults:
+    the machine's cal_ref_mu / cal_ref_gy, else 100 MU -> 1 Gy."""
+    if not torch.cuda.is_available():
+        raise RuntimeError("calibrate needs a CUDA device (GB300, sm_103a); no CPU path exists")
+    ref_mu = float(getattr(machine, "cal_ref_mu", 100.0) if ref_mu is None else ref_mu)
+    ref_gy = float(getattr(machine, "cal_ref_gy", 1.0) if ref_gy is None else ref_gy)
+    return _lib.pdrt_calibrate(_lib.machine_struct(machine, cal=1.0), sxy, sz, ref_mu, ref_gy,
+                               _stream_ptr())
+
+
 class DoseEngine:
     """One CT grid + one VMAT geometry (gantry angles, isocentre, beam model).
 
@@ -50,7 +63,12 @@ class DoseEngine:
             self._grid = _lib.pdrt_grid_create(hu.data_ptr(), nx, ny, nz, sx, sy, sz,
                                                list(phantom.origin), np.asarray(phantom.hu_to_red),
                                                _stream_ptr())
-            self._machine = _lib.machine_struct(machine)
+            # output factor: the machine's, or the calibration of Sec. 2.4
+            # on this grid's pitch when the machine leaves it open (None)
+            self.cal = machine.cal
+            if self.cal is None:
+                self.cal = calibrate(machine, sx, sz)
+            self._machine = _lib.machine_struct(machine, cal=self.cal)
             self._plan = _lib.pdrt_plan_upload(self._grid, list(np.asarray(gantry_deg, float)),
                                                list(np.asarray(iso, float)), self._machine,
                                                scratch_budget_bytes, _stream_ptr())

@@ -14,6 +14,7 @@ same objects, so the two sides always see identical inputs.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+from typing import Optional
 
 import numpy as np
 
@@ -47,7 +48,12 @@ class Machine:
     f_leaf: float = 150.0
     f_jaw: float = 200.0
     eps_mu: float = 0.01
-    cal: float = 1.0
+    # output factor (Sec. 2.4); None: calibrated on the dose grid's pitch so
+    # that cal_ref_mu MU of the 10 x 10 cm reference field give cal_ref_gy Gy
+    # at 10 cm depth in water (the engine and the oracle each compute it)
+    cal: Optional[float] = 1.0
+    cal_ref_mu: float = 100.0
+    cal_ref_gy: float = 1.0
     ste: int = 1
     # fluence corrections of Sec. 2.2.2 beyond transmission: source penumbra
     # FWHM along leaf travel (u) and across leaf pairs / Y jaws (v), mm (0 =
@@ -283,12 +289,14 @@ def arc_angles(n_cp: int, reverse=False) -> np.ndarray:
 # ----------------------------------------------------------------------------
 def water_static_64(seed=1000) -> Workload:
     m = machine_model(seed, r_px=8)
+    m.cal = None   # calibrated to the reference conditions of Sec. 2.4
     ph = water_phantom((64, 64, 64), (2.5, 2.5, 2.5))
     return Workload("water64_static_10x10", ph, m, static_field(m))
 
 
 def pelvis_arc_128(seed=1001, n_cp=178, r_cm=4.0) -> Workload:
     m = machine_model(seed, r_px=int(round(r_cm * 10.0 / 3.0)))
+    m.cal = None   # calibrated to the reference conditions of Sec. 2.4
     ph = pelvis_phantom((96, 128, 128), (3.0, 3.0, 3.0), seed=seed)
     pl = arc_plan(m, arc_angles(n_cp), seed=seed)
     return Workload(f"pelvis128x128x96_arc{n_cp}_R{r_cm:g}cm", ph, m, pl)
@@ -297,6 +305,7 @@ def pelvis_arc_128(seed=1001, n_cp=178, r_cm=4.0) -> Workload:
 def pelvis_two_arc_256(seed=1002, n_cp_arc=178, r_cm=4.0, shape=(160, 256, 256),
                        spacing=2.0) -> Workload:
     m = machine_model(seed, r_px=int(round(r_cm * 10.0 / spacing)))
+    m.cal = None   # calibrated to the reference conditions of Sec. 2.4
     ph = pelvis_phantom(shape, (spacing,) * 3, seed=seed)
     ang = np.concatenate([arc_angles(n_cp_arc), arc_angles(n_cp_arc, reverse=True)])
     pl = arc_plan(m, ang, seed=seed)
@@ -309,6 +318,7 @@ def paper_table_arc(seed=1006) -> Workload:
     105 x 224 x 224 grid with a 55-pixel lateral kernel (R = 27 px); voxel
     size 2.5 mm in-plane, 3 mm between slices (not stated there)."""
     m = machine_model(seed, r_px=27)
+    m.cal = None   # calibrated to the reference conditions of Sec. 2.4
     ph = pelvis_phantom((105, 224, 224), (2.5, 2.5, 3.0), seed=seed)
     pl = arc_plan(m, arc_angles(180), seed=seed)
     return Workload("pelvis224x224x105_arc180_K55", ph, m, pl)
@@ -334,6 +344,7 @@ def uneven_batch(n_plans=32, seed=1003, r_cm=4.0):
         sp = float(rng.choice([2.0, 2.5, 3.0]))
         n_cp = int(rng.integers(90, 357))
         m = machine_model(seed + 10 * q, r_px=int(round(r_cm * 10.0 / sp)))
+        m.cal = None   # calibrated to the reference conditions of Sec. 2.4
         ph = pelvis_phantom((nz, ny, nx), (sp, sp, sp), seed=seed + q)
         if n_cp > 178:
             ang = np.concatenate([arc_angles(n_cp // 2), arc_angles(n_cp - n_cp // 2, reverse=True)])

@@ -56,7 +56,8 @@ def test_water_static_10x10_matches_oracle_and_closed_form(tensor_cores):
     iy = np.arange(64)
     T = np.interp((iy + 0.5) * 2.5, np.arange(len(w.machine.t_table)) * w.machine.dz_t,
                   w.machine.t_table)
-    closed = w.machine.cal * 100.0 * T * (1000.0 / (1000.0 + (iy - 32) * 2.5)) ** 2
+    cal = O.calibrate(w.machine, 2.5, 2.5)        # the workload's output factor (Sec. 2.4)
+    closed = cal * 100.0 * T * (1000.0 / (1000.0 + (iy - 32) * 2.5)) ** 2
     np.testing.assert_allclose(gpu[32, :, 32], closed, rtol=2e-5)
 
 

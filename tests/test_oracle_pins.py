@@ -206,7 +206,7 @@ def test_open_field_depth_dose_closed_form():
     iy = np.arange(64)
     depth = (iy + 0.5) * 2.5
     d = 1000.0 + (iy - 32) * 2.5
-    exp = w.machine.cal * 100.0 * _depth_dose_np(w.machine, depth) * (1000.0 / d) ** 2
+    exp = mod.cal * 100.0 * _depth_dose_np(w.machine, depth) * (1000.0 / d) ** 2
     np.testing.assert_allclose(D[32, :, 32], exp, rtol=1e-12)
 
 
