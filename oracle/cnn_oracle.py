@@ -30,6 +30,8 @@ Only tests/ and the benchmark's baseline leg may import this module.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 N_OUT = 121          # 60 leaf pairs x (left, right) + MU
@@ -146,30 +148,44 @@ def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 def bev_project(bits, spacing, origin, iso, sid, gantry_deg, side, pitch, reach, step):
     """Beam's-eye-view projection of a uint8 bit-mask volume bits [nz][ny][nx]
     (the network input): for each gantry angle g and BEV pixel (py, px), the
-    ray from the source S = iso - sid e_w through iso + u e_u + v e_v, with
+    ray from the source S = iso - sid e_w through P = iso + u e_u + v e_v, with
     e_w = (sin g, cos g, 0), e_u = (cos g, -sin g, 0), e_v = (0, 0, 1),
     u = (px - (side-1)/2) pitch, v = (py - (side-1)/2) pitch, is sampled at
     depths w = -reach, -reach + step, ... (n = floor(2 reach / step) + 1
-    samples) beyond the isocentre plane, i.e. at S + (sid + w) / sid
-    (iso + u e_u + v e_v - S); channel s is 1 where a sample's nearest voxel
-    has bit s.  Returns float64 [n_cp][side][side][3]."""
+    samples) beyond the isocentre plane, i.e. at X = S + t (P - S) with
+    t = (sid + w) / sid; channel s is 1 where a sample's nearest voxel
+    round((X - origin) / spacing) has bit s.  Returns float64
+    [n_cp][side][side][3].
+
+    The nearest-voxel index is an integer decided by floating point, so it is
+    taken in the kernel's precision: FP32, each operation rounded to nearest
+    (numpy float32 arithmetic is IEEE single precision), in this order:
+    S = (iso_x - sid sn, iso_y - sid cs, iso_z); P - S = (u cs + sid sn,
+    -(u sn) + sid cs, v); X = S + t (P - S) per axis; index = rint((X - o) / s)
+    with ties to even.  cs and sn are cos and sin of (g pi / 180) in double,
+    then rounded to FP32."""
+    f = np.float32
     nz, ny, nx = bits.shape
     out = np.zeros((len(gantry_deg), side, side, 3))
-    half = 0.5 * (side - 1)
-    pu = (np.arange(side) - half) * pitch
-    U, V = np.meshgrid(pu, pu)                      # [py][px]
-    n_steps = int(2.0 * reach / step) + 1
-    for b, g in enumerate(np.deg2rad(np.asarray(gantry_deg, dtype=np.float64))):
-        ew = np.array([np.sin(g), np.cos(g), 0.0])
-        eu = np.array([np.cos(g), -np.sin(g), 0.0])
-        ev = np.array([0.0, 0.0, 1.0])
-        S = np.asarray(iso, dtype=np.float64) - sid * ew
-        P = np.asarray(iso, dtype=np.float64)[None, None, :] + U[..., None] * eu + V[..., None] * ev
+    half = f(0.5) * f(side - 1)
+    idx_pix = np.arange(side, dtype=np.float32)
+    pu = (idx_pix - half) * f(pitch)                    # float32 ops, rounded per step
+    U, V = np.meshgrid(pu, pu)                          # [py][px]
+    n_steps = int(np.floor(2.0 * reach / step)) + 1
+    sid32, reach32, step32 = f(sid), f(reach), f(step)
+    o32 = [f(origin[d]) for d in range(3)]
+    s32 = [f(spacing[d]) for d in range(3)]
+    iso32 = [f(iso[d]) for d in range(3)]
+    for b, g in enumerate(gantry_deg):
+        ang = float(g) * math.pi / 180.0
+        cs, sn = f(math.cos(ang)), f(math.sin(ang))
+        S = (iso32[0] - sid32 * sn, iso32[1] - sid32 * cs, iso32[2])
+        Dv = (U * cs + sid32 * sn, -(U * sn) + sid32 * cs, V)
         acc = np.zeros((side, side), dtype=np.uint8)
         for q in range(n_steps):
-            w = -reach + q * step
-            X = S + (sid + w) / sid * (P - S)
-            idx = [np.rint((X[..., d] - origin[d]) / spacing[d]).astype(np.int64) for d in range(3)]
+            w = -reach32 + f(q) * step32
+            t = (sid32 + w) / sid32
+            idx = [np.rint((S[d] + t * Dv[d] - o32[d]) / s32[d]).astype(np.int64) for d in range(3)]
             ok = ((idx[0] >= 0) & (idx[0] < nx) & (idx[1] >= 0) & (idx[1] < ny)
                   & (idx[2] >= 0) & (idx[2] < nz))
             vals = np.zeros((side, side), dtype=np.uint8)

@@ -428,6 +428,17 @@ __global__ void k_cast_bf16(const float *__restrict__ p, __nv_bfloat16 *__restri
 // iso + u e_u + v e_v is sampled every `step` mm of depth over +-reach around
 // the isocentre plane; channel s is 1 if any sample's nearest voxel carries
 // bit s of the mask volume.  Output BF16 [n_cp][side][side][3].
+// The sample position decides an integer (the voxel index), so it is taken in
+// FP32 with every operation rounded to nearest and in a fixed order (explicit
+// _rn intrinsics: no contraction into FMAs), which a reference can reproduce
+// bit for bit:
+//   half = (side - 1) / 2; u = (px - half) * pitch; v = (py - half) * pitch
+//   sxp = ix - sid * sn; syp = iy - sid * cs; szp = iz      (source)
+//   dx = u * cs + sid * sn; dy = -(u * sn) + sid * cs; dz = v
+//   w = -reach + q * step; t = (sid + w) / sid   (q = 0 .. n_steps - 1)
+//   x = sxp + t * dx (likewise y, z); index = rint((x - ox) / sx), ties to even
+// with n_steps = floor(2 reach / step) + 1 computed on the host in double and
+// cs, sn = (float) cos / sin of (gantry_deg * pi / 180) in double.
 struct BevGeo {
     int nx, ny, nz;
     float sx, sy, sz;
@@ -435,7 +446,13 @@ struct BevGeo {
     float ix, iy, iz;      // isocentre, mm
     float sid, pitch, reach, step;
     int side;
+    int n_steps;
 };
+
+__device__ __forceinline__ int bev_index(float x, float o, float s)
+{
+    return __float2int_rn(__fdiv_rn(__fsub_rn(x, o), s));
+}
 
 __global__ void k_bev(const uint8_t *__restrict__ masks, BevGeo G, const float2 *__restrict__ cs_sn,
                       __nv_bfloat16 *__restrict__ out)
@@ -446,19 +463,22 @@ __global__ void k_bev(const uint8_t *__restrict__ masks, BevGeo G, const float2 
     const int py = pix / G.side, px = pix - py * G.side;
     const float cs = cs_sn[b].x, sn = cs_sn[b].y;
     const float half = 0.5f * (float)(G.side - 1);
-    const float u = ((float)px - half) * G.pitch, v = ((float)py - half) * G.pitch;
+    const float u = __fmul_rn(__fsub_rn((float)px, half), G.pitch);
+    const float v = __fmul_rn(__fsub_rn((float)py, half), G.pitch);
     // e_w = (sn, cs, 0), e_u = (cs, -sn, 0), e_v = (0, 0, 1)
-    const float sxp = G.ix - G.sid * sn, syp = G.iy - G.sid * cs, szp = G.iz;   // source
-    const float dx = u * cs + G.sid * sn, dy = -u * sn + G.sid * cs, dz = v;     // source -> iso-plane point
+    const float sxp = __fsub_rn(G.ix, __fmul_rn(G.sid, sn));
+    const float syp = __fsub_rn(G.iy, __fmul_rn(G.sid, cs));
+    const float szp = G.iz;
+    const float dx = __fadd_rn(__fmul_rn(u, cs), __fmul_rn(G.sid, sn));
+    const float dy = __fadd_rn(-__fmul_rn(u, sn), __fmul_rn(G.sid, cs));
+    const float dz = v;
     unsigned bits = 0u;
-    const int n_steps = (int)(2.f * G.reach / G.step) + 1;
-    for (int q = 0; q < n_steps; ++q) {
-        const float w = -G.reach + q * G.step;                  // depth beyond the isocentre plane
-        const float t = (G.sid + w) / G.sid;
-        const float x = sxp + t * dx, y = syp + t * dy, z = szp + t * dz;
-        const int ix = __float2int_rn((x - G.ox) / G.sx);
-        const int iy = __float2int_rn((y - G.oy) / G.sy);
-        const int iz = __float2int_rn((z - G.oz) / G.sz);
+    for (int q = 0; q < G.n_steps; ++q) {
+        const float w = __fadd_rn(-G.reach, __fmul_rn((float)q, G.step));   // depth beyond the isocentre plane
+        const float t = __fdiv_rn(__fadd_rn(G.sid, w), G.sid);
+        const int ix = bev_index(__fadd_rn(sxp, __fmul_rn(t, dx)), G.ox, G.sx);
+        const int iy = bev_index(__fadd_rn(syp, __fmul_rn(t, dy)), G.oy, G.sy);
+        const int iz = bev_index(__fadd_rn(szp, __fmul_rn(t, dz)), G.oz, G.sz);
         if (ix < 0 || ix >= G.nx || iy < 0 || iy >= G.ny || iz < 0 || iz >= G.nz) continue;
         bits |= masks[((long long)iz * G.ny + iy) * G.nx + ix];
     }
@@ -931,6 +951,7 @@ pdrt_status pdrt_bev_project(const uint8_t *masks_dev, int32_t nx, int32_t ny, i
     G.ix = (float)iso_mm[0]; G.iy = (float)iso_mm[1]; G.iz = (float)iso_mm[2];
     G.sid = (float)sid_mm; G.pitch = (float)pitch_mm; G.reach = (float)reach_mm; G.step = (float)step_mm;
     G.side = side;
+    G.n_steps = (int)floor(2.0 * reach_mm / step_mm) + 1;
     std::vector<float2> h(n_cp);
     for (int b = 0; b < n_cp; ++b) {
         const double g = gantry_deg[b] * M_PI / 180.0;
