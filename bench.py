@@ -49,7 +49,7 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--corrections", action="store_true",
                     help="penumbra, off-axis profile and collimator rotation on (Sec. 2.2.2)")
-    ap.add_argument("--warm-cases", type=int, default=6,
+    ap.add_argument("--warm-cases", type=int, default=20,
                     help="held-out phantoms for the warm-versus-plain figure (0 = skip)")
     ap.add_argument("--workload", default="pelvis256",
                     choices=["pelvis256", "pelvis128", "water64", "paper180", "batch32", "optimise"],

@@ -353,31 +353,43 @@ def assess(case: Case, prop):
 
 
 def evaluate(net: WarmStartNet, seeds, n_iter=N_ITER):
-    """Warm versus plain on held-out phantoms.  The plain optimiser runs
-    n_iter evaluations from the open-field start; its best objective J* is the
-    target.  The warm start costs one evaluation to assess the proposal
-    (assess: objective with the best global MU scale) against the open-field
-    start (the fallback when the proposal is worse), then optimises until
-    J <= J* (at most n_iter more evaluations)."""
+    """Warm versus plain on held-out phantoms, with a control that isolates
+    what the network adds.  Three arms per phantom:
+      plain    the plain optimiser, n_iter evaluations from the open-field
+               start; its best objective J* is the target and plain_evals
+               the evaluations it took to reach it;
+      control  the open-field start through the same one-evaluation MU
+               assessment as the proposal (assess: best global MU scale),
+               then the optimiser until J <= J*;
+      warm     the network's proposal through the assessment; the engine
+               keeps the better of it and the assessed open-field start (so
+               the warm arm pays two assessments), then optimises until
+               J <= J* (at most n_iter more evaluations).
+    warm / plain is the spec comparison; warm / control is the
+    network's own gain (same line search, other start)."""
     rows = []
     for sd in seeds:
         c = make_case(int(sd))
         plain = plain_optimise(c, n_iter)
         j_star = min(plain.history)
         plain_evals = int(np.argmin(plain.history)) + 1
-        prop, j_prop, alpha = assess(c, propose(net, c))
         j_open = plain.history[0]
-        start = prop if j_prop <= j_open else c.open_init
+        open_s, j_open_s, alpha_open = assess(c, c.open_init)
+        ctrl = optimise(c.engine, c.masks, c.presc, open_s, n_iter=n_iter, lr=OPT_LR, lr_mu=OPT_LR_MU,
+                        objective="quadratic", target=j_star)
+        prop, j_prop, alpha = assess(c, propose(net, c))
+        fallback = j_prop > j_open_s
+        start = open_s if fallback else prop
         warm = optimise(c.engine, c.masks, c.presc, start, n_iter=n_iter, lr=OPT_LR, lr_mu=OPT_LR_MU,
                         objective="quadratic", target=j_star)
-        reached = min(warm.history) <= j_star
         D_p = c.engine.forward(plain.leaves, plain.jaws, plain.mu)
         D_w = c.engine.forward(warm.leaves, warm.jaws, warm.mu)
         rows.append({
-            "seed": int(sd), "j_open": j_open, "j_proposal": j_prop, "j_star": j_star,
-            "mu_scale": float(alpha),
-            "fallback": bool(j_prop > j_open), "plain_evals": plain_evals,
-            "warm_evals": 1 + warm.dose_evals, "reached": bool(reached),
+            "seed": int(sd), "j_open": j_open, "j_open_scaled": j_open_s, "j_proposal": j_prop,
+            "j_star": j_star, "mu_scale": float(alpha), "mu_scale_open": float(alpha_open),
+            "fallback": bool(fallback), "plain_evals": plain_evals,
+            "control_evals": 1 + ctrl.dose_evals, "control_reached": bool(min(ctrl.history) <= j_star),
+            "warm_evals": 2 + warm.dose_evals, "reached": bool(min(warm.history) <= j_star),
             "dose_diff_rel": float((D_w - D_p).abs().max() / D_p.max()),
         })
         c.engine.close()
@@ -386,14 +398,23 @@ def evaluate(net: WarmStartNet, seeds, n_iter=N_ITER):
 
 def summarise(rows) -> dict:
     r = np.array([x["warm_evals"] / x["plain_evals"] for x in rows])
+    rc = np.array([x["warm_evals"] / x["control_evals"] for x in rows])
+    cp = np.array([x["control_evals"] / x["plain_evals"] for x in rows])
     return {"cases": len(rows), "median_eval_ratio": float(np.median(r)),
             "mean_eval_ratio": float(np.mean(r)),
             "frac_at_most_half": float(np.mean(r <= 0.5)),
+            "median_warm_over_control": float(np.median(rc)),
+            "mean_warm_over_control": float(np.mean(rc)),
+            "median_control_over_plain": float(np.median(cp)),
             "reached": int(sum(x["reached"] for x in rows)),
+            "control_reached": int(sum(x["control_reached"] for x in rows)),
             "fallbacks": int(sum(x["fallback"] for x in rows)),
             "median_plain_evals": float(np.median([x["plain_evals"] for x in rows])),
+            "median_control_evals": float(np.median([x["control_evals"] for x in rows])),
             "median_warm_evals": float(np.median([x["warm_evals"] for x in rows])),
             "median_proposal_over_open": float(np.median([x["j_proposal"] / x["j_open"] for x in rows])),
+            "median_proposal_over_scaled_open": float(np.median([x["j_proposal"] / x["j_open_scaled"]
+                                                                 for x in rows])),
             "median_dose_diff_rel": float(np.median([x["dose_diff_rel"] for x in rows]))}
 
 

@@ -2,12 +2,19 @@
 
 The engine computes the factor with its own kernels (grid creation, plan
 upload, one forward in the virtual water phantom); the oracle computes it in
-FP64 from the same written reference conditions.  They agree to 1e-5
-relative at every kernel radius of the configurations (2, 4, 8 cm at 2 mm;
+FP64 from the same written reference conditions.  They agree to 5e-5
+relative (see below) at every kernel radius of the configurations (2, 4, 8 cm at 2 mm;
 4 cm at 3 mm; 2 cm at 2.5 mm), with the fluence corrections on, and at a
 pitch whose water surface cuts a voxel row.  A workload whose machine leaves
 cal open is calibrated by the engine and matches the oracle's dose on its
 own calibration.
+
+Tolerance: the factor is ref_gy over one dose value, so its relative error is
+that of the dose at the reference point.  That dose is a sum of non-negative
+products (fluence x kernel tap); the tensor-core convolution carries each
+product with a relative error below 3 x 2^-16 (BF16 hi/lo split, the lo x lo
+term dropped) and FP32 sums add ~1e-6, so the two factors agree to 5e-5
+relative.
 """
 import numpy as np
 import pytest
@@ -20,7 +27,7 @@ from paper_2512_18863_gb300.engine import DoseEngine, calibrate
 
 pytestmark = pytest.mark.gpu
 
-CAL_TOL = 1e-5
+CAL_TOL = 5e-5
 
 
 @pytest.mark.parametrize("r_px,pitch,sz", [(10, 2.0, 2.0), (20, 2.0, 2.0), (40, 2.0, 2.0),

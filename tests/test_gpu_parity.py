@@ -333,76 +333,42 @@ def _subplan(w, sel):
                              w.plan.jaws[sel], w.plan.mu[sel]))
 
 
-def test_full_size_forward_sampled_against_oracle(c3):
-    """Oracle on 2 control points at full grid size vs the GPU on the same two;
-    the full 356-CP dose equals the sum of its two arcs (linearity, any size)."""
-    sel = np.array([45, 250])
-    sub = _subplan(c3, sel)
-    gpu = _gpu_dose(sub)
-    ref = O.Model(sub.phantom, sub.machine, sub.plan).dose()
-    _assert_dose(gpu, ref)
+@pytest.mark.parametrize("r_cm,n_sample", [(2.0, 12), (4.0, 12), (8.0, 8)])
+def test_full_size_sampled_against_oracle(r_cm, n_sample):
+    """Every kernel radius of the two-arc configuration at full grid size
+    (256 x 256 x 160 at 2 mm): n_sample control points spread evenly over
+    both arcs (the second arc runs backwards), the GPU in the benchmark's
+    launch configuration (tensor cores, default schedule) against the oracle:
+    the dose and all three gradient classes of <g, D> for a random g."""
+    w = S.pelvis_two_arc_256(r_cm=r_cm)
+    assert w.machine.r_px == int(round(r_cm * 5))
+    sel = np.unique(np.linspace(3, w.plan.n_cp - 4, n_sample).round().astype(int))
+    assert len(sel) == n_sample and sel.min() < 178 <= sel.max()
+    sub = _subplan(w, sel)
+    eng = _engine(sub)
+    assert eng.info["tensor_cores"] == 1
+    gpu = eng.forward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu).cpu().numpy().astype(np.float64)
+    g = np.random.default_rng(int(r_cm * 10)).standard_normal(sub.phantom.shape).astype(np.float32)
+    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
+                  for t in eng.backward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu, g))
+    cal = eng.cal
+    eng.close()
+    mod = O.Model(sub.phantom, sub.machine, sub.plan)
+    assert abs(cal - mod.cal) <= 1e-5 * mod.cal
+    _assert_dose(gpu, mod.dose())
+    rl, rj, rm = mod.dose_grad(g.astype(np.float64))
+    _assert_grad(dl, rl, "leaves")
+    _assert_grad(dj, rj, "jaws")
+    _assert_grad(dm, rm, "mu")
+
+
+def test_full_size_arc_sum_is_linear(c3):
+    """The whole 356-CP dose equals the sum of its two arcs (linearity of
+    Eq. D_total; holds at any size, checked GPU against GPU)."""
     full = _gpu_dose(c3)
     a = _gpu_dose(_subplan(c3, np.arange(178)))
     b = _gpu_dose(_subplan(c3, np.arange(178, 356)))
     np.testing.assert_allclose(full, a + b, rtol=0, atol=1e-5 * full.max())
-
-
-def test_full_size_gradient_sampled_against_oracle(c3):
-    sel = np.array([100])
-    sub = _subplan(c3, sel)
-    rng = np.random.default_rng(9)
-    g = rng.standard_normal(sub.phantom.shape).astype(np.float32)
-    eng = _engine(sub)
-    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
-                  for t in eng.backward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu, g))
-    rl, rj, rm = O.Model(sub.phantom, sub.machine, sub.plan).dose_grad(g.astype(np.float64))
-    _assert_grad(dl, rl, "leaves")
-    _assert_grad(dj, rj, "jaws")
-    _assert_grad(dm, rm, "mu")
-    eng.close()
-
-
-def test_full_size_8cm_kernel_sampled_against_oracle():
-    """R = 40 px (8 cm at 2 mm): output and input boxes wider than one
-    tensor-core tile (column tiles and input-column chunks), full grid, one
-    control point: dose and gradients against the oracle."""
-    w = S.pelvis_two_arc_256(r_cm=8.0)
-    sub = _subplan(w, np.array([60]))
-    gpu = _gpu_dose(sub)
-    mod = O.Model(sub.phantom, sub.machine, sub.plan)
-    ref = mod.dose()
-    _assert_dose(gpu, ref)
-    g = np.random.default_rng(12).standard_normal(sub.phantom.shape).astype(np.float32)
-    eng = _engine(sub)
-    assert eng.info["tensor_cores"] == 1
-    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
-                  for t in eng.backward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu, g))
-    eng.close()
-    rl, rj, rm = mod.dose_grad(g.astype(np.float64))
-    _assert_grad(dl, rl, "leaves")
-    _assert_grad(dj, rj, "jaws")
-    _assert_grad(dm, rm, "mu")
-
-
-def test_full_size_2cm_kernel_sampled_against_oracle():
-    """R = 10 px (2 cm at 2 mm), the small end of the kernel-radius sweep:
-    full grid, two control points of the two-arc plan (one per arc), dose and
-    gradients against the oracle."""
-    w = S.pelvis_two_arc_256(r_cm=2.0)
-    assert w.machine.r_px == 10
-    sub = _subplan(w, np.array([30, 300]))
-    gpu = _gpu_dose(sub)
-    mod = O.Model(sub.phantom, sub.machine, sub.plan)
-    _assert_dose(gpu, mod.dose())
-    g = np.random.default_rng(13).standard_normal(sub.phantom.shape).astype(np.float32)
-    eng = _engine(sub)
-    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
-                  for t in eng.backward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu, g))
-    eng.close()
-    rl, rj, rm = mod.dose_grad(g.astype(np.float64))
-    _assert_grad(dl, rl, "leaves")
-    _assert_grad(dj, rj, "jaws")
-    _assert_grad(dm, rm, "mu")
 
 
 def test_full_size_gradient_vs_central_differences(c3):
