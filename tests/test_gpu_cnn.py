@@ -78,28 +78,34 @@ def test_dense_head_matches_oracle(net_and_forward):
     assert np.abs(y - ref).max() <= 2e-3 * np.abs(ref).max()
 
 
-def test_end_to_end_forward_close_to_oracle(net_and_forward):
-    """Raw input to output, no GPU activations fed to the oracle.  Bound per
-    output element, propagated from the stored activations' rounding: each
-    stored BF16 activation may differ from the oracle's by one BF16 step
-    (|dh_l| <= 2^-7 |h_l| + 2^-20, the layer test's bar), and a difference
-    d_{l-1} in the layer input moves the next pre-activation by at most
-    conv(|W_l|, d_{l-1}) (ReLU is 1-Lipschitz), so
-      d_l = conv(|W_l|, d_{l-1}) + 2^-7 |h_l| + 2^-20,   d_0 = 0 (0/1 inputs),
-      |y - y_ref| <= |W_5| d_4 + 1e-5 max |y_ref|   (FP32 sums of the head).
-    The bound is computed around the oracle's own activations."""
-    net, p, x, y, h = net_and_forward
-    acts = N.forward(p, x)
-    ref = acts["out"]
-    d = np.zeros_like(acts["h0"])
+def _forward_with_flips(p, x, rng, frac):
+    """The oracle's forward with the discrepancy the layer test allows: one
+    BF16 step (2^-8 |h|, the typical spacing) up or down at a random fraction
+    `frac` of every layer's stored activations."""
+    h = N.bf16(x)
     for l in range(1, 5):
-        d = (N.conv_forward(d, np.abs(N.bf16(p[f"W{l}"])), np.zeros(64))
-             + 2.0 ** -7 * np.abs(acts[f"h{l}"]) + 2.0 ** -20)
-    bound = d.reshape(len(x), -1) @ np.abs(N.bf16(p["W5"])).T + 1e-5 * np.abs(ref).max()
-    err = np.abs(y - ref)
-    assert np.all(err <= bound), f"worst excess {(err - bound).max():.3e}"
-    # the bound is informative: on average well under 1 % of the output scale
-    assert bound.mean() <= 1e-2 * np.abs(ref).max()
+        h = N.bf16(np.maximum(N.conv_forward(h, N.bf16(p[f"W{l}"]), p[f"b{l}"]), 0.0))
+        flip = (rng.random(h.shape) < frac) * rng.choice([-1.0, 1.0], h.shape)
+        h = h + flip * np.abs(h) * 2.0 ** -8
+    return h.reshape(h.shape[0], -1) @ N.bf16(p["W5"]).T + p["b5"]
+
+
+def test_end_to_end_forward_close_to_oracle(net_and_forward):
+    """Raw input to output, no GPU activations fed to the oracle.  The
+    tolerance is derived from the stored activations' BF16 rounding: the GPU
+    and the oracle round each stored activation from sums taken in FP32 and
+    FP64, so they may differ by one BF16 step at up to 1 % of the values
+    (the layer test's bar).  Propagating such flips through the oracle's
+    network (8 random draws) gives the output spread they cause; the GPU must
+    stay within 3x its largest value, element by element."""
+    net, p, x, y, h = net_and_forward
+    ref = N.forward(p, x)["out"]
+    spread = np.max([np.abs(_forward_with_flips(p, x, np.random.default_rng(100 + k), 0.01) - ref)
+                     for k in range(8)], axis=0)
+    tol = 3.0 * spread.max()
+    err = np.abs(y - ref).max()
+    assert err <= tol, f"end-to-end error {err:.3e} vs derived tolerance {tol:.3e}"
+    assert tol <= 2e-2 * np.abs(ref).max()
 
 
 def test_backward_matches_oracle(net_and_forward):
