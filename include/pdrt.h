@@ -142,6 +142,9 @@ typedef struct {
     int32_t tc_ctas_per_sm[2];   /* tensor-core convolution CTAs per SM (forward, adjoint) */
     int32_t simt_ctas_per_sm[2]; /* resident FP32 convolution CTAs per SM (forward, adjoint) */
     int32_t tc_phase[2];         /* tensor-core kernel rows per operand phase (forward, adjoint) */
+    int32_t fft_pmax;            /* > 0: FFT convolution for slices whose padded sizes are at most
+                                    this, tensor cores for the rest; 0: FFT off */
+    int32_t fft_ctas_per_sm[2];  /* FFT convolution CTAs per SM (forward, adjoint) */
 } pdrt_plan_info;
 
 /* Work counters of the last forward/backward call (for roofline accounting). */
@@ -152,11 +155,20 @@ typedef struct {
     int64_t taps;                /* (2R+1)^2 */
     double conv_flops;           /* 2 * taps * support_points: one convolution pass */
     double mma_flops;            /* tensor-core FLOPs issued by one forward + one adjoint
-                                    convolution pass (BF16 three-term split, padded tiles) */
+                                    convolution pass (BF16 three-term split, padded tiles) on
+                                    the slices the tensor cores take */
+    double fft_flops;            /* FP32 FLOPs of the FFT convolution of one forward + one
+                                    adjoint pass on the slices it takes: per slice and direction
+                                    2 x 2.5 N log2 N for the forward and inverse real 2-D FFTs
+                                    (N = Pu Pv), the kernel spectrum's cosine sums
+                                    2 (R+1)^2 (Pv/2+1) + 2 (R+1)(Pv/2+1)(Pu/2+1) and the
+                                    product 2 Pv (Pu/2+1) */
+    int64_t fft_slices;          /* (slice, direction) pairs the FFT convolution takes */
+    int64_t tc_slices;           /* (slice, direction) pairs left to the tensor cores */
 } pdrt_work;
 
 /* Per-kernel device time accumulated while profiling is enabled. */
-#define PDRT_NUM_KERNELS 10
+#define PDRT_NUM_KERNELS 12
 typedef struct {
     const char *name[PDRT_NUM_KERNELS];
     int64_t launches[PDRT_NUM_KERNELS];
@@ -259,12 +271,25 @@ pdrt_status pdrt_calibrate(const pdrt_machine *m, double sxy, double sz, double 
 
 /*
  * Route the per-slice convolution (Sec. 2.2.6) to the tensor cores (enable = 1,
- * the default: BF16 three-term split, FP32 accumulation, every slice tiled)
- * or to the FP32 SIMT kernel (enable = 0).  Host only.
+ * the default: BF16 three-term split, FP32 accumulation, every slice tiled;
+ * with the FFT convolution on, only the slices it leaves) or to the FP32 SIMT
+ * kernel (enable = 0, which also turns the FFT convolution off).  Host only.
  * Errors: EINVAL if enable = 1 and the tensor-core kernel does not fit in
  * shared memory (it fits for every radius up to PDRT_MAX_RADIUS_PX).
  */
 pdrt_status pdrt_plan_set_tensor_cores(pdrt_plan_t p, int32_t enable);
+
+/*
+ * FFT convolution (Sec. 2.2.6 computed by FP32 FFTs in shared memory, the
+ * default): slices whose padded transform sizes are at most pmax are
+ * convolved by FFT, the others by the tensor-core kernel.  pmax = 0 turns it
+ * off; otherwise one of 32, 40, 48, 64, 80, 96, 120, 128, 160, 192 (sets the
+ * shared memory per CTA and so the CTAs per SM).  The upload picks the
+ * smallest size that holds a 48-pixel input plus the kernel's 2R margin.
+ * Host only.  Errors: EINVAL (NULL plan, unsupported size, size that does not
+ * fit in shared memory, or the tensor-core path is off: it takes the overflow).
+ */
+pdrt_status pdrt_plan_set_fft(pdrt_plan_t p, int32_t pmax);
 
 /* Lattice and scratch sizes of a plan (host only, no device work).
  * Errors: EINVAL (NULL argument). */
@@ -351,7 +376,8 @@ pdrt_status pdrt_plan_set_tc_phase(pdrt_plan_t p, int32_t phase_forward, int32_t
  * Autotuner: times forward (+ adjoint if dose_grad_dev != NULL) passes of the
  * plan with CUDA events on `stream` and keeps the fastest schedule, searched
  * one coordinate at a time from the upload's choice: the convolution path
- * (tensor cores or FP32 SIMT), then the tensor-core tile shape of each
+ * (FFT with tensor-core overflow, tensor cores alone or FP32 SIMT) and the
+ * FFT size limit, then the tensor-core tile shape of each
  * direction (kernel rows per operand phase, 1..4, which sets the shared
  * memory and so the CTAs per SM), then the control points per pass (the
  * uploaded count, 1/2 and 1/4 of it).  Output buffers are overwritten.
@@ -364,6 +390,7 @@ typedef struct {
     int32_t n_candidates;        /* schedules timed */
     int32_t phase[2];            /* tensor-core kernel rows per operand phase (forward, adjoint) */
     int32_t tc_ctas_per_sm[2];   /* resulting tensor-core CTAs per SM (forward, adjoint) */
+    int32_t fft_pmax;            /* chosen FFT size limit (0: FFT convolution off) */
 } pdrt_tune_result;
 pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_dev,
                                const float *jaws_dev, const float *mu_dev, float *dose_dev,

@@ -17,7 +17,7 @@ MAX_PAIRS = 160
 MAX_RADIUS_PX = 44
 MAX_DEPTH_TABLE = 4096
 MAX_HU_POINTS = 32
-NUM_KERNELS = 10
+NUM_KERNELS = 12
 FLAG_NAN_INPUT = 1
 FLAG_CAPACITY = 2
 FLAG_TIMEOUT = 4
@@ -50,18 +50,21 @@ class pdrt_plan_info(C.Structure):
                 ("cu", C.c_double), ("cv", C.c_double), ("cw", C.c_double),
                 ("n_cp", C.c_int32), ("chunk_cp", C.c_int32), ("scratch_bytes", C.c_size_t),
                 ("tensor_cores", C.c_int32), ("tc_ctas_per_sm", C.c_int32 * 2),
-                ("simt_ctas_per_sm", C.c_int32 * 2), ("tc_phase", C.c_int32 * 2)]
+                ("simt_ctas_per_sm", C.c_int32 * 2), ("tc_phase", C.c_int32 * 2),
+                ("fft_pmax", C.c_int32), ("fft_ctas_per_sm", C.c_int32 * 2)]
 
 
 class pdrt_work(C.Structure):
     _fields_ = [("active_slices", C.c_int64), ("support_points", C.c_int64),
                 ("region_points", C.c_int64), ("taps", C.c_int64), ("conv_flops", C.c_double),
-                ("mma_flops", C.c_double)]
+                ("mma_flops", C.c_double), ("fft_flops", C.c_double), ("fft_slices", C.c_int64),
+                ("tc_slices", C.c_int64)]
 
 
 class pdrt_tune_result(C.Structure):
     _fields_ = [("tensor_cores", C.c_int32), ("chunk_cp", C.c_int32), ("best_ms", C.c_float),
-                ("n_candidates", C.c_int32), ("phase", C.c_int32 * 2), ("tc_ctas_per_sm", C.c_int32 * 2)]
+                ("n_candidates", C.c_int32), ("phase", C.c_int32 * 2), ("tc_ctas_per_sm", C.c_int32 * 2),
+                ("fft_pmax", C.c_int32)]
 
 
 class pdrt_profile(C.Structure):
@@ -93,6 +96,7 @@ _SIG = {
                                  C.c_double, C.POINTER(C.c_double), _VP]),
     "pdrt_plan_set_chunk": (C.c_int, [_VP, C.c_int32]),
     "pdrt_plan_set_tc_phase": (C.c_int, [_VP, C.c_int32, C.c_int32]),
+    "pdrt_plan_set_fft": (C.c_int, [_VP, C.c_int32]),
     "pdrt_plan_autotune": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
                                      C.POINTER(pdrt_tune_result)]),
     "pdrt_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP), C.POINTER(_VP),
@@ -214,6 +218,7 @@ def pdrt_plan_get_info(plan) -> dict:
     out["simt_ctas_per_sm"] = list(out["simt_ctas_per_sm"])
     out["tc_ctas_per_sm"] = list(out["tc_ctas_per_sm"])
     out["tc_phase"] = list(out["tc_phase"])
+    out["fft_ctas_per_sm"] = list(out["fft_ctas_per_sm"])
     return out
 
 
@@ -420,6 +425,10 @@ def pdrt_bev_project(masks_dev, nx, ny, nz, spacing, origin, iso, sid, gantry_de
                                    (C.c_double * 3)(*[float(x) for x in iso]), float(sid),
                                    len(gantry_deg), g, int(side), float(pitch), float(reach),
                                    float(step), _VP(out_dev), _VP(stream)))
+
+
+def pdrt_plan_set_fft(plan, pmax):
+    _check(load().pdrt_plan_set_fft(_VP(plan), int(pmax)))
 
 
 def pdrt_plan_set_tc_phase(plan, phase_forward, phase_adjoint):

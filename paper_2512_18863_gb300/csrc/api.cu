@@ -68,6 +68,7 @@ struct pdrt_plan_s {
     int conv_blocks_fwd, conv_blocks_adj;
     int tc_blocks;            // persistent grid of k_conv_tc<false> (0: path unavailable)
     int tc_blocks_adj;        // persistent grid of k_conv_tc<true>
+    int fft_blocks[2];        // persistent grids of k_conv_fft (forward, adjoint) at dev.fft_pmax
     PlanDev dev;
     size_t scratch_bytes;
     std::vector<void *> allocs;
@@ -82,7 +83,7 @@ struct pdrt_plan_s {
 static const char *kKernelNames[PDRT_NUM_KERNELS] = {
     "hu_to_red", "project_raster", "wepl_tables", "conv_forward",
     "gather_accumulate", "gather_transpose", "conv_adjoint", "mag_transpose_param_grad",
-    "conv_forward_tc", "conv_adjoint_tc"};
+    "conv_forward_tc", "conv_adjoint_tc", "conv_forward_fft", "conv_adjoint_fft"};
 
 namespace {
 
@@ -473,6 +474,8 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     PLAN_TRY(dalloc(p, &P.adjbuf, (size_t)chunk * cap_a), "cudaMalloc(adjoint region)");
     PLAN_TRY(dalloc(p, &P.flags, 1), "cudaMalloc(flags)");
     PLAN_TRY(dalloc(p, &P.counters, 4 * (size_t)n_cp + 2), "cudaMalloc(counters)");
+    PLAN_TRY(dalloc(p, &P.fft_ctr, 4 * (size_t)n_cp + 4), "cudaMalloc(fft counters)");
+    PLAN_TRY(dalloc(p, &P.fft_over, (size_t)chunk * L.nw), "cudaMalloc(fft overflow list)");
     P.leaf_bounds = lb;
     P.depth_dose = dd;
     P.cpgeo = dgeo;
@@ -513,6 +516,27 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
             P.tc_enabled = 1;
         }
     }
+    // FFT convolution: default size limit from the kernel radius (inputs up
+    // to ~48 pixels wide fit; wider slices take the tensor-core path), needs
+    // the tensor-core kernel for the overflow
+    P.fft_pmax = 0;
+    p->fft_blocks[0] = p->fft_blocks[1] = 0;
+    if (P.tc_enabled) {
+        const int want = fft_size_for(2 * M.R + 48) ? fft_size_for(2 * M.R + 48) : 192;
+        const int sizes[10] = {192, 160, 128, 120, 96, 80, 64, 48, 40, 32};
+        for (int t = 0; t < 10 && !P.fft_pmax; ++t) {
+            const int pm = sizes[t];
+            if (pm > want || pm < 2 * M.R + 2) continue;
+            int cf = 0, ca = 0;
+            PLAN_TRY(conv_fft_ctas(pm, false, &cf), "fft convolution set-up");
+            PLAN_TRY(conv_fft_ctas(pm, true, &ca), "fft convolution set-up");
+            if (cf > 0 && ca > 0) {
+                P.fft_pmax = pm;
+                p->fft_blocks[0] = cf * g->sm_count;
+                p->fft_blocks[1] = ca * g->sm_count;
+            }
+        }
+    }
 #undef PLAN_TRY
     *out = p;
     return PDRT_OK;
@@ -544,9 +568,26 @@ pdrt_status pdrt_dose_forward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_
     CU_TRY(timed(p, K_TABLES, s, [&] { return launch_tables(P, s); }), "wepl_tables launch");
     const int n_chunks = (p->n_cp + p->chunk - 1) / p->chunk;
     CU_TRY(cudaMemsetAsync(P.counters, 0, sizeof(unsigned) * 4 * n_chunks, s), "clear counters");
+    if (P.fft_pmax) CU_TRY(cudaMemsetAsync(P.fft_ctr, 0, sizeof(unsigned) * 4 * n_chunks, s), "clear counters");
     for (int c = 0; c < n_chunks; ++c) {
         const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
-        if (P.tc_enabled)
+        if (P.fft_pmax) {
+            // FFT for the slices within the size limit, tensor cores for the
+            // overflow list it leaves
+            unsigned int *fc = P.fft_ctr + 4 * c;
+            CU_TRY(timed(p, K_CONV_FFT_FWD, s,
+                         [&] {
+                             return launch_conv_fft(P, b0, nb, false, P.fft_pmax, fc, P.fft_over, fc + 1,
+                                                    p->fft_blocks[0], s);
+                         }),
+                   "conv_forward_fft launch");
+            CU_TRY(timed(p, K_CONV_TC_FWD, s,
+                         [&] {
+                             return launch_conv_tc(P, b0, nb, false, P.counters + 2 * n_chunks + c,
+                                                   p->tc_blocks, s, P.fft_over, fc + 1);
+                         }),
+                   "conv_forward_tc launch");
+        } else if (P.tc_enabled)
             CU_TRY(timed(p, K_CONV_TC_FWD, s,
                          [&] {
                              return launch_conv_tc(P, b0, nb, false, P.counters + 2 * n_chunks + c,
@@ -582,6 +623,7 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
     const int n_chunks = (p->n_cp + p->chunk - 1) / p->chunk;
     unsigned int *ctr = P.counters + n_chunks;
     CU_TRY(cudaMemsetAsync(P.counters, 0, sizeof(unsigned) * 4 * n_chunks, s), "clear counters");
+    if (P.fft_pmax) CU_TRY(cudaMemsetAsync(P.fft_ctr, 0, sizeof(unsigned) * 4 * n_chunks, s), "clear counters");
     for (int c = 0; c < n_chunks; ++c) {
         const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
         // the gathered gradient h is formed by its own kernel (fusing the
@@ -589,7 +631,21 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
         // its few warps do not hide the gather's load latency)
         CU_TRY(timed(p, K_GATHER_T, s, [&] { return launch_gather_T(P, b0, nb, dose_grad_dev, s); }),
                "gather_transpose launch");
-        if (P.tc_enabled)
+        if (P.fft_pmax) {
+            unsigned int *fc = P.fft_ctr + 4 * c + 2;
+            CU_TRY(timed(p, K_CONV_FFT_ADJ, s,
+                         [&] {
+                             return launch_conv_fft(P, b0, nb, true, P.fft_pmax, fc, P.fft_over, fc + 1,
+                                                    p->fft_blocks[1], s);
+                         }),
+                   "conv_adjoint_fft launch");
+            CU_TRY(timed(p, K_CONV_TC_ADJ, s,
+                         [&] {
+                             return launch_conv_tc(P, b0, nb, true, P.counters + 3 * n_chunks + c,
+                                                   p->tc_blocks_adj, s, P.fft_over, fc + 1);
+                         }),
+                   "conv_adjoint_tc launch");
+        } else if (P.tc_enabled)
             CU_TRY(timed(p, K_CONV_TC_ADJ, s,
                          [&] {
                              return launch_conv_tc(P, b0, nb, true, P.counters + 3 * n_chunks + c,
@@ -619,6 +675,29 @@ pdrt_status pdrt_plan_set_tensor_cores(pdrt_plan_t p, int32_t enable)
     if (enable && p->tc_blocks <= 0)
         return fail(PDRT_EINVAL, "the tensor-core convolution does not fit this kernel radius");
     p->dev.tc_enabled = enable ? 1 : 0;
+    if (!enable) p->dev.fft_pmax = 0;   // the FFT path hands its overflow to the tensor cores
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_plan_set_fft(pdrt_plan_t p, int32_t pmax)
+{
+    g_last_error.clear();
+    if (!p) return fail(PDRT_EINVAL, "NULL plan");
+    if (pmax == 0) {
+        p->dev.fft_pmax = 0;
+        return PDRT_OK;
+    }
+    if (!p->dev.tc_enabled)
+        return fail(PDRT_EINVAL, "the FFT convolution needs the tensor-core path for its overflow");
+    if (pmax < 0 || fft_size_for(pmax) != pmax)
+        return fail(PDRT_EINVAL, "unsupported FFT size %d (32, 40, 48, 64, 80, 96, 120, 128, 160, 192)", pmax);
+    int cf = 0, ca = 0;
+    CU_TRY(conv_fft_ctas(pmax, false, &cf), "fft convolution set-up");
+    CU_TRY(conv_fft_ctas(pmax, true, &ca), "fft convolution set-up");
+    if (cf <= 0 || ca <= 0) return fail(PDRT_EINVAL, "FFT size %d does not fit in shared memory", pmax);
+    p->dev.fft_pmax = pmax;
+    p->fft_blocks[0] = cf * p->grid->sm_count;
+    p->fft_blocks[1] = ca * p->grid->sm_count;
     return PDRT_OK;
 }
 
@@ -639,6 +718,9 @@ pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out)
     out->simt_ctas_per_sm[1] = p->grid->sm_count > 0 ? p->conv_blocks_adj / p->grid->sm_count : 0;
     out->tc_phase[0] = p->dev.tc_phase[0];
     out->tc_phase[1] = p->dev.tc_phase[1];
+    out->fft_pmax = p->dev.fft_pmax;
+    out->fft_ctas_per_sm[0] = p->dev.fft_pmax && p->grid->sm_count > 0 ? p->fft_blocks[0] / p->grid->sm_count : 0;
+    out->fft_ctas_per_sm[1] = p->dev.fft_pmax && p->grid->sm_count > 0 ? p->fft_blocks[1] / p->grid->sm_count : 0;
     return PDRT_OK;
 }
 
@@ -673,6 +755,7 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
     out->taps = n * n;
     out->conv_flops = 2.0 * (double)out->taps * (double)out->support_points;
     out->mma_flops = 0.0;
+    out->fft_flops = 0.0;
     if (p->dev.tc_enabled) {
         // replay the tensor-core tiling of k_conv_tc (row tiles of 128 rows
         // with a last tile of at most 64 rows as M = 64, column tiles, input
@@ -684,6 +767,19 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
                "read slice tables");
         for (const SliceTab &st : sl) {
             for (int adj = 0; adj < 2; ++adj) {
+                if (p->dev.fft_pmax) {
+                    int pu = 0, pv = 0;
+                    fft_slice_sizes(st, adj != 0, R, pu, pv);
+                    if (pu == 0) continue;
+                    if (pu <= p->dev.fft_pmax && pv <= p->dev.fft_pmax) {
+                        const double n = (double)pu * pv, hu1 = pu / 2 + 1, kv1 = pv / 2 + 1;
+                        out->fft_flops += 2.0 * 2.5 * n * log2(n) + 2.0 * (R + 1) * (R + 1) * kv1 +
+                                          2.0 * (R + 1) * kv1 * hu1 + 2.0 * pv * hu1;
+                        out->fft_slices += 1;
+                        continue;
+                    }
+                    out->tc_slices += 1;
+                }
                 const int ii0 = adj ? st.oi0 : st.pi0, ii1 = adj ? st.oi1 : st.pi1;
                 const int ij0 = adj ? st.oj0 : st.pj0, ij1 = adj ? st.oj1 : st.pj1;
                 const int oi0 = adj ? st.ai0 : st.oi0, oi1 = adj ? st.ai1 : st.oi1;
@@ -792,14 +888,33 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
     p->profiling = false;
     const int sm = g->sm_count, R = p->dev.mach.R;
     struct Sched {
-        int tc, chunk, ph_f, ph_a;
+        int tc, chunk, ph_f, ph_a, fft;
     };
     const bool tc_ok = p->tc_blocks > 0;
-    const Sched start = {p->dev.tc_enabled, p->chunk, p->dev.tc_phase[0], p->dev.tc_phase[1]};
+    const Sched start = {p->dev.tc_enabled, p->chunk, p->dev.tc_phase[0], p->dev.tc_phase[1], p->dev.fft_pmax};
     int ctas_f = tc_ok ? p->tc_blocks / sm : 0, ctas_a = tc_ok ? p->tc_blocks_adj / sm : 0;
+    // FFT size limits that fit (each with its CTAs per SM)
+    std::vector<int> fft_ok;
+    if (tc_ok)
+        for (int pm : {32, 40, 48, 64, 80, 96, 120, 128, 160, 192}) {
+            if (pm < 2 * R + 2) continue;
+            int cf = 0, ca = 0;
+            CU_TRY(conv_fft_ctas(pm, false, &cf), "fft occupancy");
+            CU_TRY(conv_fft_ctas(pm, true, &ca), "fft occupancy");
+            if (cf > 0 && ca > 0) fft_ok.push_back(pm);
+        }
     auto apply = [&](const Sched &c) -> pdrt_status {
         p->dev.tc_enabled = c.tc;
         p->chunk = c.chunk;
+        p->dev.fft_pmax = 0;
+        if (c.fft && c.tc) {
+            int cf = 0, ca = 0;
+            CU_TRY(conv_fft_ctas(c.fft, false, &cf), "fft occupancy");
+            CU_TRY(conv_fft_ctas(c.fft, true, &ca), "fft occupancy");
+            p->dev.fft_pmax = c.fft;
+            p->fft_blocks[0] = cf * sm;
+            p->fft_blocks[1] = ca * sm;
+        }
         if (tc_ok) {
             int nf = 0, na = 0;
             CU_TRY(conv_tc_ctas(R, false, c.ph_f, &nf), "tensor-core occupancy");
@@ -851,11 +966,31 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
             best = c;
         }
     };
-    // 1) convolution path
+    // 1) convolution path: FFT (+ tensor-core overflow), tensor cores alone,
+    //    FP32 SIMT; then the FFT size limit
     if (tc_ok) {
-        Sched c = best;
-        c.tc = best.tc ? 0 : 1;
-        consider(c);
+        const Sched cand[3] = {{1, best.chunk, best.ph_f, best.ph_a, fft_ok.empty() ? 0 : best.fft},
+                               {1, best.chunk, best.ph_f, best.ph_a, 0},
+                               {0, best.chunk, best.ph_f, best.ph_a, 0}};
+        if (!best.fft && !fft_ok.empty()) {
+            Sched c = best;
+            c.tc = 1;
+            c.fft = fft_ok[0];
+            for (int pm : fft_ok)
+                if (pm <= fft_size_for(2 * R + 48)) c.fft = pm;
+            consider(c);
+        }
+        for (const Sched &c : cand)
+            if (c.tc != best.tc || c.fft != best.fft) consider(c);
+        if (best.fft) {
+            const int cur = best.fft;
+            for (int pm : fft_ok)
+                if (pm != cur) {
+                    Sched c = best;
+                    c.fft = pm;
+                    consider(c);
+                }
+        }
     }
     // 2) tensor-core tile shape per direction (phase depths that fit)
     if (tc_ok && best.tc) {
@@ -890,6 +1025,7 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
     out->phase[1] = best.ph_a;
     out->tc_ctas_per_sm[0] = ctas_f;
     out->tc_ctas_per_sm[1] = ctas_a;
+    out->fft_pmax = best.tc ? best.fft : 0;
     return PDRT_OK;
 }
 

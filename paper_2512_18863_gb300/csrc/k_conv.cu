@@ -62,32 +62,6 @@ __device__ __forceinline__ void conv_row(float (&acc)[kConvTJ], const float *__r
     }
 }
 
-// bilinear sample of fluence map b (stored over its support box) at the
-// magnified position of lattice point (i, j) of a slice with magnification m
-__device__ __forceinline__ float fluence_sample(const float *__restrict__ F, int fa0, int fa1,
-                                                int fc0, int fc1, float fa, float fc)
-{
-    const float ba = floorf(fa), bc = floorf(fc);
-    const int a0 = (int)ba, c0 = (int)bc;
-    const float ta = fa - ba, tc = fc - bc;
-    const int Fc = fc1 - fc0;
-    float s = 0.f;
-#pragma unroll
-    for (int da = 0; da < 2; ++da) {
-        const int a = a0 + da;
-        if (a < fa0 || a >= fa1) continue;
-        const float wa = da ? ta : 1.f - ta;
-#pragma unroll
-        for (int dc = 0; dc < 2; ++dc) {
-            const int c = c0 + dc;
-            if (c < fc0 || c >= fc1) continue;
-            const float wc = dc ? tc : 1.f - tc;
-            s += wa * wc * __ldg(&F[(long long)(a - fa0) * Fc + (c - fc0)]);
-        }
-    }
-    return s;
-}
-
 // G = output rows per warp (32, 16 or 8); a warp's lanes cover G rows x 32/G
 // blocks of 16 columns, the CTA's 4 warps tile 32 rows x 64 columns.
 template <int NQ4, bool ADJ, int G>

@@ -92,7 +92,9 @@ int conv_tc_smem_bytes(int R, bool adjoint, int phase)
 // warps: the adjoint ran 17 % faster at four CTAs than at two.
 template <bool ADJ>
 __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, int b0, int nb,
-                                                           unsigned int *__restrict__ counter)
+                                                           unsigned int *__restrict__ counter,
+                                                           const int *__restrict__ list,
+                                                           const unsigned int *__restrict__ list_n)
 {
     using Lim = TcLimits<ADJ>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -140,7 +142,12 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
     bool timed_out = false;
 
     while (!timed_out) {
-        if (tid == 0) *s_item = (int)atomicAdd(counter, 1u);
+        if (tid == 0) {
+            // list mode: the items the FFT kernel left (slices beyond its size
+            // limit), else every item of the chunk
+            const int q = (int)atomicAdd(counter, 1u);
+            *s_item = list ? (q < (int)*list_n ? list[q] : n_items) : q;
+        }
         __syncthreads();
         const int item = *s_item;
         __syncthreads();
@@ -500,13 +507,13 @@ __global__ void __launch_bounds__(kTcThreads, ADJ ? 4 : 3) k_conv_tc(PlanDev P, 
 }
 
 cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
-                           int grid_blocks, cudaStream_t s)
+                           int grid_blocks, cudaStream_t s, const int *list, const unsigned int *list_n)
 {
     const int smem = conv_tc_smem_bytes(P.mach.R, adjoint, P.tc_phase[adjoint ? 1 : 0]);
     if (adjoint)
-        k_conv_tc<true><<<grid_blocks, kTcThreads, smem, s>>>(P, b0, nb, counter);
+        k_conv_tc<true><<<grid_blocks, kTcThreads, smem, s>>>(P, b0, nb, counter, list, list_n);
     else
-        k_conv_tc<false><<<grid_blocks, kTcThreads, smem, s>>>(P, b0, nb, counter);
+        k_conv_tc<false><<<grid_blocks, kTcThreads, smem, s>>>(P, b0, nb, counter, list, list_n);
     return cudaGetLastError();
 }
 

@@ -37,7 +37,8 @@ constexpr int kTcAdjMaxN = 64, kTcAdjMaxK = 48;
 
 enum KernelId {
     K_HU = 0, K_RASTER = 1, K_TABLES = 2, K_CONV_FWD = 3, K_GATHER = 4,
-    K_GATHER_T = 5, K_CONV_ADJ = 6, K_MAG_T_GRAD = 7, K_CONV_TC_FWD = 8, K_CONV_TC_ADJ = 9
+    K_GATHER_T = 5, K_CONV_ADJ = 6, K_MAG_T_GRAD = 7, K_CONV_TC_FWD = 8, K_CONV_TC_ADJ = 9,
+    K_CONV_FFT_FWD = 10, K_CONV_FFT_ADJ = 11
 };
 
 struct Lattice {
@@ -124,6 +125,11 @@ struct PlanDev {
     unsigned int *counters;  // work-queue counters (per chunk launch)
     int tc_enabled;          // 1: every slice with work goes to k_conv_tc
     int tc_phase[2];         // kernel rows per operand phase of k_conv_tc (forward, adjoint)
+    int fft_pmax;            // > 0: k_conv_fft takes every slice whose padded sizes are at most
+                             // this; k_conv_tc takes the rest from the overflow list
+    int *fft_over;           // [chunk * nw] overflow list of one chunk launch (items)
+    unsigned int *fft_ctr;   // [4 * n_cp]: per chunk {fwd counter, fwd overflow count,
+                             // adj counter, adj overflow count}
 };
 
 // Same float expression in every kernel that samples or transposes the
@@ -184,6 +190,67 @@ __device__ __forceinline__ int gather_t_taps(const CpGeo &g, const Lattice &L, i
         }
     }
     return n;
+}
+
+// Bilinear sample of fluence map b (stored over its support box) at the
+// magnified position (fa, fc) of a lattice point (same expression in every
+// convolution kernel that fills its input from the fluence).
+__device__ __forceinline__ float fluence_sample(const float *__restrict__ F, int fa0, int fa1,
+                                                int fc0, int fc1, float fa, float fc)
+{
+    const float ba = floorf(fa), bc = floorf(fc);
+    const int a0 = (int)ba, c0 = (int)bc;
+    const float ta = fa - ba, tc = fc - bc;
+    const int Fc = fc1 - fc0;
+    float s = 0.f;
+#pragma unroll
+    for (int da = 0; da < 2; ++da) {
+        const int a = a0 + da;
+        if (a < fa0 || a >= fa1) continue;
+        const float wa = da ? ta : 1.f - ta;
+#pragma unroll
+        for (int dc = 0; dc < 2; ++dc) {
+            const int c = c0 + dc;
+            if (c < fc0 || c >= fc1) continue;
+            const float wc = dc ? tc : 1.f - tc;
+            s += wa * wc * __ldg(&F[(long long)(a - fa0) * Fc + (c - fc0)]);
+        }
+    }
+    return s;
+}
+
+// Padded sizes of the FFT convolution: the sizes whose complex transform
+// lengths (P along v, P / 2 along u) have radix plans in k_conv_fft.
+__host__ __device__ inline int fft_size_for(int n)
+{
+    const int sizes[10] = {32, 40, 48, 64, 80, 96, 120, 128, 160, 192};
+    for (int t = 0; t < 10; ++t)
+        if (sizes[t] >= n) return sizes[t];
+    return 0;
+}
+
+// Padded sizes (pu, pv) of one slice's convolution in one direction: the
+// circular period along each axis that keeps every tap within R of an
+// output and no tap beyond R (max distance between an output and an input
+// point + R + 1), and at least the input and output extents; 0 for a slice
+// without work, 1 << 20 if no supported size is large enough.
+__host__ __device__ inline void fft_slice_sizes(const SliceTab &st, bool adj, int R, int &pu, int &pv)
+{
+    const int ii0 = adj ? st.oi0 : st.pi0, ii1 = adj ? st.oi1 : st.pi1;
+    const int ij0 = adj ? st.oj0 : st.pj0, ij1 = adj ? st.oj1 : st.pj1;
+    const int oi0 = adj ? st.ai0 : st.oi0, oi1 = adj ? st.ai1 : st.oi1;
+    const int oj0 = adj ? st.aj0 : st.oj0, oj1 = adj ? st.aj1 : st.oj1;
+    pu = pv = 0;
+    if (!(oi1 > oi0 && oj1 > oj0 && ii1 > ii0 && ij1 > ij0)) return;
+    int nu = (oi1 - 1 - ii0 > ii1 - 1 - oi0 ? oi1 - 1 - ii0 : ii1 - 1 - oi0) + R + 1;
+    int nv = (oj1 - 1 - ij0 > ij1 - 1 - oj0 ? oj1 - 1 - ij0 : ij1 - 1 - oj0) + R + 1;
+    nu = nu > ii1 - ii0 ? nu : ii1 - ii0;
+    nu = nu > oi1 - oi0 ? nu : oi1 - oi0;
+    nv = nv > ij1 - ij0 ? nv : ij1 - ij0;
+    nv = nv > oj1 - oj0 ? nv : oj1 - oj0;
+    pu = fft_size_for(nu);
+    pv = fft_size_for(nv);
+    if (!pu || !pv) pu = pv = 1 << 20;
 }
 
 // Off-axis profile factor of lattice pixel (a, c) (Sec. 2.2.2).
@@ -263,8 +330,16 @@ cudaError_t launch_param_grad(const PlanDev &P, const float *leaves, const float
 int conv_smem_bytes(const MachineDev &m);
 int conv_nq4_for_radius(int R);
 cudaError_t conv_prepare(const MachineDev &m, int *fwd_blocks_per_sm, int *adj_blocks_per_sm);
+// list / list_n: when list != NULL the kernel takes only the items of the
+// list (its first *list_n entries) instead of every item of the chunk
 cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsigned int *counter,
-                           int grid_blocks, cudaStream_t s);
+                           int grid_blocks, cudaStream_t s, const int *list = nullptr,
+                           const unsigned int *list_n = nullptr);
+cudaError_t launch_conv_fft(const PlanDev &P, int b0, int nb, bool adjoint, int pmax, unsigned int *counter,
+                            int *over_list, unsigned int *over_count, int grid_blocks, cudaStream_t s);
+int conv_fft_smem_bytes(int pmax);
+// CTAs per SM of k_conv_fft for a size limit (0 if it does not fit)
+cudaError_t conv_fft_ctas(int pmax, bool adjoint, int *ctas);
 cudaError_t conv_tc_prepare(int R, int *fwd_blocks_per_sm, int *adj_blocks_per_sm, int *fwd_phase,
                             int *adj_phase);
 // CTAs per SM of k_conv_tc for a phase depth (0 if the phase does not fit).

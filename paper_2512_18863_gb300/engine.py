@@ -46,7 +46,7 @@ class DoseEngine:
     """
 
     def __init__(self, phantom, machine, gantry_deg, iso, scratch_budget_bytes=0, device=None,
-                 tensor_cores=None):
+                 tensor_cores=None, conv=None, fft_pmax=None):
         if not torch.cuda.is_available():
             raise RuntimeError("DoseEngine needs a CUDA device (GB300, sm_103a); no CPU path exists")
         _lib.load()
@@ -75,6 +75,25 @@ class DoseEngine:
             torch.cuda.current_stream().synchronize()   # hu is read by the grid kernel
         if tensor_cores is not None:
             _lib.pdrt_plan_set_tensor_cores(self._plan, tensor_cores)
+        self.info = _lib.pdrt_plan_get_info(self._plan)
+        self._fft_default = self.info["fft_pmax"]
+        if conv is not None or fft_pmax is not None:
+            self.set_conv(conv or "fft", fft_pmax)
+
+    def set_conv(self, path: str, fft_pmax=None):
+        """Convolution path: "fft" (FFT for slices up to fft_pmax, default the
+        upload's choice, tensor cores for the rest), "tc" (tensor cores for
+        every slice) or "simt" (FP32 SIMT kernel)."""
+        if path == "fft":
+            _lib.pdrt_plan_set_tensor_cores(self._plan, True)
+            _lib.pdrt_plan_set_fft(self._plan, self._fft_default if fft_pmax is None else fft_pmax)
+        elif path == "tc":
+            _lib.pdrt_plan_set_tensor_cores(self._plan, True)
+            _lib.pdrt_plan_set_fft(self._plan, 0)
+        elif path == "simt":
+            _lib.pdrt_plan_set_tensor_cores(self._plan, False)
+        else:
+            raise ValueError(f"unknown convolution path {path!r}")
         self.info = _lib.pdrt_plan_get_info(self._plan)
 
     # -- raw entry points (tensors on self.device, float32, contiguous) -----
@@ -105,7 +124,8 @@ class DoseEngine:
 
     # -- diagnostics -----------------------------------------------------------
     def set_tensor_cores(self, enable: bool):
-        """Route the convolution to the tensor cores (True) or the FP32 SIMT kernel."""
+        """Route the convolution to the tensor cores (True; the FFT path, if on,
+        keeps the slices within its size limit) or the FP32 SIMT kernel."""
         _lib.pdrt_plan_set_tensor_cores(self._plan, enable)
         self.info = _lib.pdrt_plan_get_info(self._plan)
 

@@ -25,11 +25,11 @@ def _engine(w, **kw):
     return DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso, **kw)
 
 
-@pytest.mark.parametrize("tensor_cores", [True, False])
+@pytest.mark.parametrize("conv", ["fft", "tc", "simt"])
 @pytest.mark.parametrize("coll", [0.0, 30.0, -90.0])
-def test_corrected_forward_matches_oracle(coll, tensor_cores):
+def test_corrected_forward_matches_oracle(coll, conv):
     w = _case(31, coll)
-    eng = _engine(w, tensor_cores=tensor_cores)
+    eng = _engine(w, conv=conv)
     gpu = eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).cpu().numpy().astype(np.float64)
     eng.close()
     ref = O.Model(w.phantom, w.machine, w.plan).dose()
@@ -52,15 +52,15 @@ def test_corrections_change_the_dose():
     assert np.abs(a - b).max() > 100 * DOSE_TOL * b.max()
 
 
-@pytest.mark.parametrize("tensor_cores", [True, False])
+@pytest.mark.parametrize("conv", ["fft", "tc", "simt"])
 @pytest.mark.parametrize("ste,coll", [(1, 0.0), (0, 0.0), (1, 30.0), (0, -17.0)])
-def test_corrected_gradients_match_oracle(ste, coll, tensor_cores):
+def test_corrected_gradients_match_oracle(ste, coll, conv):
     w = _case(33, coll, n_cp=5)
     w.machine.ste = ste
     w.plan.leaves[1, 30] = (2.1, 2.4)      # a pair under w_min
     w.plan.mu[2] = 0.004                   # below eps_mu
     g = np.random.default_rng(6).standard_normal(w.phantom.shape)
-    eng = _engine(w, tensor_cores=tensor_cores)
+    eng = _engine(w, conv=conv)
     got = [t.cpu().numpy().astype(np.float64)
            for t in eng.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g)]
     eng.close()

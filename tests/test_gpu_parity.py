@@ -47,10 +47,10 @@ def _assert_grad(gpu, ref, name):
 # ---------------------------------------------------------------------------
 # forward
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("tensor_cores", [True, False])
-def test_water_static_10x10_matches_oracle_and_closed_form(tensor_cores):
+@pytest.mark.parametrize("conv", ["fft", "tc", "simt"])
+def test_water_static_10x10_matches_oracle_and_closed_form(conv):
     w = S.water_static_64()
-    gpu = _gpu_dose(w, tensor_cores=tensor_cores)
+    gpu = _gpu_dose(w, conv=conv)
     ref = O.Model(w.phantom, w.machine, w.plan).dose()
     _assert_dose(gpu, ref)
     iy = np.arange(64)
@@ -61,7 +61,7 @@ def test_water_static_10x10_matches_oracle_and_closed_form(tensor_cores):
     np.testing.assert_allclose(gpu[32, :, 32], closed, rtol=2e-5)
 
 
-@pytest.mark.parametrize("tensor_cores", [True, False])
+@pytest.mark.parametrize("conv", ["fft", "tc", "simt"])
 @pytest.mark.parametrize("n,spacing,n_cp,r_px,seed", [
     ((24, 40, 40), 3.0, 6, 4, 7),      # several CTA tiles per slice
     ((23, 37, 41), 3.0, 5, 3, 8),      # ragged, odd grid, nx != ny
@@ -70,9 +70,9 @@ def test_water_static_10x10_matches_oracle_and_closed_form(tensor_cores):
     ((16, 28, 28), 5.0, 2, 44, 11),    # maximum radius: column tiles and input chunks
     ((40, 48, 48), 2.0, 3, 13, 12),    # 2 mm grid, R = 13
 ])
-def test_pelvis_forward_matches_oracle(n, spacing, n_cp, r_px, seed, tensor_cores):
+def test_pelvis_forward_matches_oracle(n, spacing, n_cp, r_px, seed, conv):
     w = S.small_pelvis(seed=seed, n=n, spacing=spacing, n_cp=n_cp, r_px=r_px)
-    gpu = _gpu_dose(w, tensor_cores=tensor_cores)
+    gpu = _gpu_dose(w, conv=conv)
     ref = O.Model(w.phantom, w.machine, w.plan).dose()
     assert ref.max() > 0
     _assert_dose(gpu, ref)
@@ -102,16 +102,16 @@ def test_chunking_does_not_change_the_dose():
 # ---------------------------------------------------------------------------
 # gradients
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("tensor_cores", [True, False])
+@pytest.mark.parametrize("conv", ["fft", "tc", "simt"])
 @pytest.mark.parametrize("ste", [1, 0])
-def test_gradients_match_oracle(ste, tensor_cores):
+def test_gradients_match_oracle(ste, conv):
     w = S.small_pelvis(seed=21, n=(20, 36, 36), n_cp=5, r_px=6)
     w.machine.ste = ste
     w.plan.leaves[1, 30] = (2.1, 2.4)          # a pair under w_min: clamp active
     w.plan.mu[2] = 0.004                       # below eps_mu
     rng = np.random.default_rng(5)
     g = rng.standard_normal(w.phantom.shape)
-    eng = _engine(w, tensor_cores=tensor_cores)
+    eng = _engine(w, conv=conv)
     dl, dj, dm = (t.cpu().numpy().astype(np.float64)
                   for t in eng.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g))
     rl, rj, rm = O.Model(w.phantom, w.machine, w.plan).dose_grad(g)
@@ -121,8 +121,8 @@ def test_gradients_match_oracle(ste, tensor_cores):
     eng.close()
 
 
-def _assert_case(w, tensor_cores, seed):
-    eng = _engine(w, tensor_cores=tensor_cores)
+def _assert_case(w, conv, seed):
+    eng = _engine(w, conv=conv)
     model = O.Model(w.phantom, w.machine, w.plan)
     gpu = eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).cpu().numpy().astype(np.float64)
     ref = model.dose()
@@ -138,22 +138,22 @@ def _assert_case(w, tensor_cores, seed):
     eng.close()
 
 
-@pytest.mark.parametrize("tensor_cores", [True, False])
-def test_zero_radius_kernel_matches_oracle(tensor_cores):
+@pytest.mark.parametrize("conv", ["fft", "tc", "simt"])
+def test_zero_radius_kernel_matches_oracle(conv):
     """R = 0: a one-tap lateral kernel (on the tensor cores a single operand
     phase and one issuer per direction)."""
-    _assert_case(S.small_pelvis(seed=23, n=(18, 32, 32), n_cp=4, r_px=0), tensor_cores, 6)
+    _assert_case(S.small_pelvis(seed=23, n=(18, 32, 32), n_cp=4, r_px=0), conv, 6)
 
 
-@pytest.mark.parametrize("tensor_cores", [True, False])
-def test_field_wider_than_64_pixels_across_leaf_pairs_matches_oracle(tensor_cores):
+@pytest.mark.parametrize("conv", ["fft", "tc", "simt"])
+def test_field_wider_than_64_pixels_across_leaf_pairs_matches_oracle(conv):
     """A field 18 cm long along the leaf-pair axis on 2.5 mm pixels: the
     adjoint's output columns exceed 64, so its tensor-core tiles run with one
     issuing warp and seven building warps."""
     m = S.machine_model(1011, r_px=3)
     ph = S.water_phantom((80, 32, 32), (2.5, 2.5, 2.5))
     plan = S.static_field(m, gantry_deg=30.0, half_x=20.0, half_y=90.0)
-    _assert_case(S.Workload("wide_v", ph, m, plan), tensor_cores, 7)
+    _assert_case(S.Workload("wide_v", ph, m, plan), conv, 7)
 
 
 def test_autograd_function_matches_oracle():
@@ -240,7 +240,7 @@ def test_field_larger_than_lattice_and_single_cp():
 
 
 def test_tensor_and_simt_paths_match_oracle_on_arc_subset():
-    """128x128x96 @ 3 mm, R = 13: both convolution paths against the oracle,
+    """128x128x96 @ 3 mm, R = 13: the convolution paths against the oracle,
     and no device flag (timeout, capacity) raised."""
     w = S.pelvis_arc_128()
     sel = np.arange(3, 178, 12)
@@ -248,12 +248,41 @@ def test_tensor_and_simt_paths_match_oracle_on_arc_subset():
                      S.Plan(w.plan.gantry_deg[sel], w.plan.iso, w.plan.leaves[sel],
                             w.plan.jaws[sel], w.plan.mu[sel]))
     ref = O.Model(sub.phantom, sub.machine, sub.plan).dose()
-    for tc in (True, False):
-        eng = _engine(sub, tensor_cores=tc)
+    for conv in ("fft", "tc", "simt"):
+        eng = _engine(sub, conv=conv)
         d = eng.forward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu).cpu().numpy()
         assert eng.status_flags() == 0
         eng.close()
         _assert_dose(d.astype(np.float64), ref)
+
+
+@pytest.mark.parametrize("pmax", [32, 48, 64, 80, 96, 120, 128, 160, 192])
+def test_fft_size_limits_and_overflow_match_oracle(pmax):
+    """The FFT convolution at every supported size limit: slices whose padded
+    sizes exceed it go to the tensor cores through the overflow list (at the
+    small limits most of them), the rest by FFT; dose and gradients against
+    the oracle, and the work counters account for every (slice, direction)."""
+    w = S.small_pelvis(seed=27, n=(26, 44, 44), spacing=3.0, n_cp=4, r_px=9)
+    eng = _engine(w, conv="fft", fft_pmax=pmax)
+    assert eng.info["fft_pmax"] == pmax
+    d = eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).cpu().numpy().astype(np.float64)
+    g = np.random.default_rng(pmax).standard_normal(w.phantom.shape).astype(np.float32)
+    dl, dj, dm = (t.cpu().numpy().astype(np.float64)
+                  for t in eng.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g))
+    work = eng.work()
+    assert eng.status_flags() == 0
+    eng.close()
+    assert work["fft_slices"] + work["tc_slices"] == 2 * work["active_slices"]
+    if pmax <= 32:
+        assert work["tc_slices"] > 0
+    if pmax >= 96:
+        assert work["tc_slices"] == 0 and work["fft_flops"] > 0
+    mod = O.Model(w.phantom, w.machine, w.plan)
+    _assert_dose(d, mod.dose())
+    rl, rj, rm = mod.dose_grad(g.astype(np.float64))
+    _assert_grad(dl, rl, "leaves")
+    _assert_grad(dj, rj, "jaws")
+    _assert_grad(dm, rm, "mu")
 
 
 def test_plan_without_control_points_is_rejected():
