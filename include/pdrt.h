@@ -286,8 +286,9 @@ pdrt_status pdrt_plan_set_tensor_cores(pdrt_plan_t p, int32_t enable);
  * off; otherwise one of 32, 40, 48, 64, 80, 96, 120, 128, 160, 192 (sets the
  * shared memory per CTA and so the CTAs per SM).  The upload picks the
  * smallest size that holds a 48-pixel input plus the kernel's 2R margin.
- * Host only.  Errors: EINVAL (NULL plan, unsupported size, size that does not
- * fit in shared memory, or the tensor-core path is off: it takes the overflow).
+ * Host only.  Errors: EINVAL (NULL plan, unsupported size, size below
+ * 2 kernel_radius_px + 2, size that does not fit in shared memory, or the
+ * tensor-core path is off: it takes the overflow).
  */
 pdrt_status pdrt_plan_set_fft(pdrt_plan_t p, int32_t pmax);
 

@@ -691,6 +691,9 @@ pdrt_status pdrt_plan_set_fft(pdrt_plan_t p, int32_t pmax)
         return fail(PDRT_EINVAL, "the FFT convolution needs the tensor-core path for its overflow");
     if (pmax < 0 || fft_size_for(pmax) != pmax)
         return fail(PDRT_EINVAL, "unsupported FFT size %d (32, 40, 48, 64, 80, 96, 120, 128, 160, 192)", pmax);
+    if (pmax < 2 * p->dev.mach.R + 2)
+        return fail(PDRT_EINVAL, "FFT size %d is below 2 R + 2 = %d for this kernel radius", pmax,
+                    2 * p->dev.mach.R + 2);
     int cf = 0, ca = 0;
     CU_TRY(conv_fft_ctas(pmax, false, &cf), "fft convolution set-up");
     CU_TRY(conv_fft_ctas(pmax, true, &ca), "fft convolution set-up");

@@ -33,6 +33,8 @@
 // takes next.
 #include <math.h>
 
+#include <algorithm>
+
 #include "pdrt_impl.cuh"
 
 namespace pdrt {
@@ -46,7 +48,8 @@ struct Radices {
     int r[3];
 };
 
-// radix passes of a complex transform length (first pass first)
+// radix passes of a complex transform length (first pass first): every
+// supported length in at most two passes
 __host__ __device__ inline Radices radices_of(int n)
 {
     switch (n) {
@@ -56,14 +59,14 @@ __host__ __device__ inline Radices radices_of(int n)
     case 32: return {2, {8, 4, 1}};
     case 40: return {2, {8, 5, 1}};
     case 48: return {2, {16, 3, 1}};
-    case 60: return {3, {4, 3, 5}};
+    case 60: return {2, {12, 5, 1}};
     case 64: return {2, {8, 8, 1}};
     case 80: return {2, {16, 5, 1}};
-    case 96: return {3, {16, 3, 2}};
-    case 120: return {3, {8, 3, 5}};
+    case 96: return {2, {16, 6, 1}};
+    case 120: return {2, {12, 10, 1}};
     case 128: return {2, {16, 8, 1}};
-    case 160: return {3, {16, 5, 2}};
-    case 192: return {3, {16, 4, 3}};
+    case 160: return {2, {16, 10, 1}};
+    case 192: return {2, {16, 12, 1}};
     default: return {0, {1, 1, 1}};
     }
 }
@@ -182,14 +185,65 @@ __device__ __forceinline__ void dft5(float2 *v)
 }
 
 template <int R, int S>
+__device__ __forceinline__ void dft(float2 *v);
+
+// Composite length A B (Cooley-Tukey in registers): with n = B n1 + n2 and
+// k = k1 + A k2, a DFT of length A over n1 for every n2, the twiddle
+// exp(S 2 pi i n2 k1 / (A B)), then a DFT of length B over n2 for every k1.
+// w[n2 * A + k1] holds that twiddle (cos, sin of 2 pi n2 k1 / (A B)).
+template <int A, int B, int S>
+__device__ __forceinline__ void dft_ct(float2 *v, const float (*w)[2])
+{
+    float2 u[B][A];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+        for (int n1 = 0; n1 < A; ++n1) u[n2][n1] = v[B * n1 + n2];
+        dft<A, S>(u[n2]);
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1)
+            if (n2 > 0) u[n2][k1] = cmul(u[n2][k1], make_float2(w[n2 * A + k1][0], S * w[n2 * A + k1][1]));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+        float2 c[B];
+#pragma unroll
+        for (int n2 = 0; n2 < B; ++n2) c[n2] = u[n2][k1];
+        dft<B, S>(c);
+#pragma unroll
+        for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = c[k2];
+    }
+}
+
+template <int R, int S>
 __device__ __forceinline__ void dft(float2 *v)
 {
     if constexpr (R == 2) dft2<S>(v[0], v[1]);
     else if constexpr (R == 3) dft3<S>(v[0], v[1], v[2]);
     else if constexpr (R == 4) dft4<S>(v[0], v[1], v[2], v[3]);
     else if constexpr (R == 5) dft5<S>(v);
-    else if constexpr (R == 8) dft8<S>(v);
-    else dft16<S>(v);
+    else if constexpr (R == 6) {
+        // A = 2, B = 3: twiddles 2 pi n2 / 6 for k1 = 1
+        const float w[6][2] = {{1.f, 0.f}, {1.f, 0.f}, {1.f, 0.f}, {0.5f, 0.86602540378443865f},
+                               {1.f, 0.f}, {-0.5f, 0.86602540378443865f}};
+        dft_ct<2, 3, S>(v, w);
+    } else if constexpr (R == 8) dft8<S>(v);
+    else if constexpr (R == 10) {
+        // A = 2, B = 5: twiddles 2 pi n2 / 10 for k1 = 1
+        const float w[10][2] = {{1.f, 0.f}, {1.f, 0.f},
+                                {1.f, 0.f}, {0.80901699437494742f, 0.58778525229247313f},
+                                {1.f, 0.f}, {0.30901699437494742f, 0.95105651629515357f},
+                                {1.f, 0.f}, {-0.30901699437494742f, 0.95105651629515357f},
+                                {1.f, 0.f}, {-0.80901699437494742f, 0.58778525229247313f}};
+        dft_ct<2, 5, S>(v, w);
+    } else if constexpr (R == 12) {
+        // A = 4, B = 3: twiddles 2 pi n2 k1 / 12
+        const float c30 = 0.86602540378443865f;
+        const float w[12][2] = {{1.f, 0.f}, {1.f, 0.f}, {1.f, 0.f}, {1.f, 0.f},
+                                {1.f, 0.f}, {c30, 0.5f}, {0.5f, c30}, {0.f, 1.f},
+                                {1.f, 0.f}, {0.5f, c30}, {-0.5f, c30}, {-1.f, 0.f}};
+        dft_ct<4, 3, S>(v, w);
+    } else dft16<S>(v);
 }
 
 // Per-slice geometry of the transforms, shared by all threads of the CTA.
@@ -199,6 +253,26 @@ struct FftGeom {
     int n_rows_in;           // input rows (rows 0..n_rows_in-1 of S)
     int out_row0, n_rows_out;// output rows: S rows (out_row0 + t) % pv
 };
+
+// Division by a small positive divisor d (< 2^16) of x < 2^16 by a multiply
+// high: with m = ceil(2^32 / d), floor(x m / 2^32) = floor(x / d) because the
+// error term x (m - 2^32 / d) / 2^32 < 2^-16 < 1 / d cannot reach the next
+// integer.
+struct FastDiv {
+    unsigned m;
+    int d;
+};
+__device__ __forceinline__ FastDiv fast_div(int d)
+{
+    FastDiv f;
+    f.d = d;
+    f.m = d > 1 ? (unsigned)(0xFFFFFFFFull / (unsigned)d) + 1u : 0u;
+    return f;
+}
+__device__ __forceinline__ int operator/(int x, const FastDiv &f)
+{
+    return f.d == 1 ? x : (int)__umulhi((unsigned)x, f.m);
+}
 
 // One radix-R pass over a batch of transforms.
 //   COLS = false: transforms are S rows row(t) = (row0 + t) % pv, t < n_tr,
@@ -219,16 +293,18 @@ __device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &
     const int per_tr = N / R;
     const int total = n_tr * per_tr;
     const int tstep = (N / L) * tmul;
+    const FastDiv div_tr = fast_div(COLS ? n_tr : per_tr), div_m = fast_div(M);
     for (int b = threadIdx.x; b < total; b += kFftThreads) {
+        const int q0 = b / div_tr;
         int tr, t;
         if (COLS) {
-            tr = b % n_tr;
-            t = b / n_tr;
+            t = q0;
+            tr = b - q0 * n_tr;
         } else {
-            tr = b / per_tr;
-            t = b - tr * per_tr;
+            tr = q0;
+            t = b - q0 * per_tr;
         }
-        const int blk = t / M, j = t - blk * M;
+        const int blk = t / div_m, j = t - blk * M;
         const int e0 = blk * L + j;
         float2 *base;
         int es;
@@ -269,11 +345,13 @@ __device__ __forceinline__ void fft_pass_r(int R, float2 *S, const FftGeom &G, i
                                            const short *ku_of)
 {
     switch (R) {
-    case 2: fft_pass<2, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
     case 3: fft_pass<3, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
     case 4: fft_pass<4, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
     case 5: fft_pass<5, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
+    case 6: fft_pass<6, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
     case 8: fft_pass<8, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
+    case 10: fft_pass<10, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
+    case 12: fft_pass<12, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
     default: fft_pass<16, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
     }
 }
@@ -286,25 +364,23 @@ __device__ void fft_run(float2 *S, const FftGeom &G, int n_tr, int row0, int N, 
                         const float *Kf, const short *kv_of, const short *ku_of)
 {
     const Radices rd = radices_of(N);
-    int Ls[3];
-    int L = N;
-    for (int s = 0; s < rd.np; ++s) {
-        Ls[s] = L;
-        L /= rd.r[s];
-    }
+    const int r0 = rd.r[0], L1 = N / r0;
     if (!INV) {
-        for (int s = 0; s < rd.np; ++s) {
-            fft_pass_r<COLS, false, false>(rd.r[s], S, G, n_tr, row0, N, Ls[s], T, tmul, Kf, kv_of, ku_of);
+        fft_pass_r<COLS, false, false>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
+        __syncthreads();
+        if (rd.np > 1) {
+            fft_pass_r<COLS, false, false>(rd.r[1], S, G, n_tr, row0, N, L1, T, tmul, Kf, kv_of, ku_of);
             __syncthreads();
         }
     } else {
-        for (int s = rd.np - 1; s >= 0; --s) {
-            if (COLS && s == rd.np - 1)
-                fft_pass_r<COLS, true, true>(rd.r[s], S, G, n_tr, row0, N, Ls[s], T, tmul, Kf, kv_of, ku_of);
-            else
-                fft_pass_r<COLS, true, false>(rd.r[s], S, G, n_tr, row0, N, Ls[s], T, tmul, Kf, kv_of, ku_of);
+        if (rd.np > 1) {
+            fft_pass_r<COLS, true, COLS>(rd.r[1], S, G, n_tr, row0, N, L1, T, tmul, Kf, kv_of, ku_of);
             __syncthreads();
+            fft_pass_r<COLS, true, false>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
+        } else {
+            fft_pass_r<COLS, true, COLS>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
         }
+        __syncthreads();
     }
 }
 
@@ -347,9 +423,14 @@ int conv_fft_smem_bytes(int pmax)
     const int tw = 2 * pmax * 8;                               // Tu, Tv
     const int idx = (3 * pmax + 8) * 2;                         // pos_u, ku_of, kv_of (short)
     const int kf = (pmax / 2 + 1) * (hu + 1) * 4;               // Kf [kv'][ku]
-    const int s = pmax * (hu + 1) * 8;                          // S [pv][hu + 1] complex
+    const int ft = 4 * pmax * 8;                                // forward fill tables
+    // S [pv][hu + 1] complex; it also holds the kernel-spectrum scratch
+    // K, Cv, Cu, A for a kernel half-width up to pmax / 2 - 1
+    const int r1 = hu, w4 = ((hu + 1) + 3) & ~3;
+    const int scratch = (r1 * (r1 + 3 * w4) + 4) * 4;
+    const int s = std::max(pmax * (hu + 1) * 8, scratch);
     auto al = [](int x) { return (x + 15) & ~15; };
-    return 64 + al(tw) + al(idx) + al(kf) + al(s);
+    return 64 + al(tw) + al(idx) + al(kf) + ft + al(s);
 }
 
 template <bool ADJ>
@@ -375,6 +456,11 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
     p += al((3 * pmax + 8) * 2);
     float *Kf = reinterpret_cast<float *>(p);
     p += al((pmax / 2 + 1) * (hmax + 1) * 4);
+    int2 *fu_idx = reinterpret_cast<int2 *>(p);   // forward fill tables, [pmax] each
+    float2 *fu_w = reinterpret_cast<float2 *>(fu_idx + pmax);
+    int2 *fv_idx = reinterpret_cast<int2 *>(fu_w + pmax);
+    float2 *fv_w = reinterpret_cast<float2 *>(fv_idx + pmax);
+    p += 4 * pmax * 8;
     float2 *S = reinterpret_cast<float2 *>(p);
     float *scratch = reinterpret_cast<float *>(S);   // kernel rows and A before the fill
     const int tid = threadIdx.x;
@@ -427,12 +513,16 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
                 }
             }
         }
-        // kernel rows K(p, q), p, q in [0, R] (the expressions of the other
-        // convolution kernels), into the scratch
+        // Kernel spectrum.  Scratch in S: K(p, q) [R1][R1]; cosine tables
+        // Cv[q][kv'] = c_q cos(2 pi kv' q / pv) and Cu[p][ku] = c_p cos(2 pi ku p / pu)
+        // (rows padded to multiples of 4); A = K Cv [R1][nkv4]; then
+        // Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
         const int R1 = R + 1;
+        const int nkv = pv / 2 + 1, nkv4 = (nkv + 3) & ~3, hu4 = (hu + 1 + 3) & ~3;
         float *Kq = scratch;                   // [p][q]
-        float *A = scratch + R1 * R1;          // [p][kv'], kv' in [0, pv/2]
-        const int nkv = pv / 2 + 1;
+        float *Cv = Kq + ((R1 * R1 + 3) & ~3); // [q][kv'] (16-byte aligned rows)
+        float *Cu = Cv + R1 * nkv4;            // [p][ku]
+        float *A = Cu + R1 * hu4;              // [p][kv']
         for (int idx = tid; idx < R1 * R1; idx += kFftThreads) {
             const int pp = idx / R1, q = idx - pp * R1;
             const float pu_mm = pp * L.du, qv = q * L.dv;
@@ -446,29 +536,94 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
             s_sizes[0] = pu;
             s_sizes[1] = pv;
         }
-        // A(p, kv') = sum_q c_q K(p, q) cos(2 pi kv' q / pv)
-        for (int idx = tid; idx < R1 * nkv; idx += kFftThreads) {
-            const int pp = idx / nkv, kv = idx - pp * nkv;
-            float acc = Kq[pp * R1];
-            int e = kv;
-            for (int q = 1; q <= R; ++q, e += kv) {
-                if (e >= pv) e -= pv;
-                acc = fmaf(2.f * Kq[pp * R1 + q], Tv[e].x, acc);
+        {
+            const FastDiv dv = fast_div(pv), du = fast_div(pu), d4v = fast_div(nkv4), d4u = fast_div(hu4);
+            for (int idx = tid; idx < R1 * (nkv4 + hu4); idx += kFftThreads) {
+                if (idx < R1 * nkv4) {
+                    const int q = idx / d4v, kv = idx - q * nkv4;
+                    const int e = kv * q - ((kv * q) / dv) * pv;
+                    Cv[idx] = kv < nkv ? (q ? 2.f : 1.f) * Tv[e].x : 0.f;
+                } else {
+                    const int t = idx - R1 * nkv4;
+                    const int pp = t / d4u, ku = t - pp * hu4;
+                    const int e = ku * pp - ((ku * pp) / du) * pu;
+                    Cu[t] = ku <= hu ? (pp ? 2.f : 1.f) * Tu[e].x : 0.f;
+                }
             }
-            A[idx] = acc;
         }
         __syncthreads();
-        // Kf(ku, kv') = scale / (pu pv) sum_p c_p cos(2 pi ku p / pu) A(p, kv'), stored [kv'][ku]
-        const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
-        for (int idx = tid; idx < nkv * (hu + 1); idx += kFftThreads) {
-            const int kv = idx / (hu + 1), ku = idx - kv * (hu + 1);
-            float acc = A[kv];
-            int e = ku;
-            for (int pp = 1; pp <= R; ++pp, e += ku) {
-                if (e >= pu) e -= pu;
-                acc = fmaf(2.f * Tu[e].x, A[pp * nkv + kv], acc);
+        // A[p][4g .. 4g+3] per item: K row p (broadcast) against float4 of Cv
+        {
+            const int G4 = nkv4 / 4;
+            const FastDiv dg = fast_div(G4);
+            for (int idx = tid; idx < R1 * G4; idx += kFftThreads) {
+                const int pp = idx / dg, g = idx - pp * G4;
+                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float *kr = Kq + pp * R1;
+                const float4 *cv = reinterpret_cast<const float4 *>(Cv) + g;
+                for (int q = 0; q < R1; ++q) {
+                    const float k = kr[q];
+                    const float4 c = cv[q * G4];
+                    acc.x = fmaf(k, c.x, acc.x);
+                    acc.y = fmaf(k, c.y, acc.y);
+                    acc.z = fmaf(k, c.z, acc.z);
+                    acc.w = fmaf(k, c.w, acc.w);
+                }
+                reinterpret_cast<float4 *>(A)[pp * G4 + g] = acc;
             }
-            Kf[kv * G.pitch + ku] = acc * kscale;
+        }
+        __syncthreads();
+        // Kf for kv' in {2i, 2i+1} and ku in [4g, 4g+4) per item
+        {
+            const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
+            const int U4 = hu4 / 4, V2 = (nkv + 1) / 2;
+            const FastDiv du4 = fast_div(U4);
+            for (int idx = tid; idx < V2 * U4; idx += kFftThreads) {
+                const int i = idx / du4, g = idx - i * U4;
+                float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+                const float4 *cu = reinterpret_cast<const float4 *>(Cu) + g;
+                for (int pp = 0; pp < R1; ++pp) {
+                    const float2 av = *reinterpret_cast<const float2 *>(A + pp * nkv4 + 2 * i);
+                    const float4 c = cu[pp * U4];
+                    a0.x = fmaf(av.x, c.x, a0.x); a0.y = fmaf(av.x, c.y, a0.y);
+                    a0.z = fmaf(av.x, c.z, a0.z); a0.w = fmaf(av.x, c.w, a0.w);
+                    a1.x = fmaf(av.y, c.x, a1.x); a1.y = fmaf(av.y, c.y, a1.y);
+                    a1.z = fmaf(av.y, c.z, a1.z); a1.w = fmaf(av.y, c.w, a1.w);
+                }
+                const float r0[4] = {a0.x, a0.y, a0.z, a0.w}, r1[4] = {a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int ku = 4 * g + e;
+                    if (ku > hu) continue;
+                    Kf[(2 * i) * G.pitch + ku] = r0[e] * kscale;
+                    if (2 * i + 1 < nkv) Kf[(2 * i + 1) * G.pitch + ku] = r1[e] * kscale;
+                }
+            }
+        }
+        // fill tables (forward): per input column n the two fluence rows a
+        // of its bilinear stencil (clamped into the support box) with their
+        // weights (zero outside the box), likewise per input row j
+        if (!ADJ) {
+            const CpTab &ct = P.cptab[b];
+            for (int t = tid; t < wi + G.n_rows_in; t += kFftThreads) {
+                const bool col = t < wi;
+                const int lo = col ? ct.fa0 : ct.fc0, hi = col ? ct.fa1 : ct.fc1;
+                const int idx0 = col ? bx.in_i0 + t : bx.in_j0 + (t - wi);
+                const float f = col ? mag_coord(st.m, idx0, L.cu) : mag_coord(st.m, idx0, L.cv);
+                const float fl = floorf(f);
+                const int a0 = (int)fl;
+                const float tw = f - fl;
+                const bool ok0 = a0 >= lo && a0 < hi, ok1 = a0 + 1 >= lo && a0 + 1 < hi;
+                const int i0 = min(max(a0 - lo, 0), hi - lo - 1), i1 = min(max(a0 + 1 - lo, 0), hi - lo - 1);
+                const float w0 = ok0 ? 1.f - tw : 0.f, w1 = ok1 ? tw : 0.f;
+                if (col) {
+                    fu_idx[t] = make_int2(i0, i1);
+                    fu_w[t] = make_float2(w0, w1);
+                } else {
+                    fv_idx[t - wi] = make_int2(i0, i1);
+                    fv_w[t - wi] = make_float2(w0, w1);
+                }
+            }
         }
         __syncthreads();
 
@@ -476,32 +631,37 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
         // along u; rows past the input are zero
         {
             const int n_fill = pv * (hu + 1);
+            const FastDiv dp = fast_div(hu + 1);
             const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
-            const CpTab &ct = P.cptab[b];
-            const int fa0 = ct.fa0, fa1 = ct.fa1, fc0 = ct.fc0, fc1 = ct.fc1;
+            const int Fc = P.cptab[b].fc1 - P.cptab[b].fc0;
             const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
             const int h_w = st.oi1 - st.oi0;
             for (int idx = tid; idx < n_fill; idx += kFftThreads) {
-                const int j = idx / (hu + 1), m = idx - j * (hu + 1);
-                float x0 = 0.f, x1 = 0.f;
+                const int j = idx / dp, m = idx - j * (hu + 1);
+                float x[2] = {0.f, 0.f};
                 if (j < G.n_rows_in && m < hu) {
-                    const int v = bx.in_j0 + j;
+                    int2 ci;
+                    float2 cw;
+                    if (!ADJ) {
+                        ci = fv_idx[j];
+                        cw = fv_w[j];
+                    }
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
                         const int n = 2 * m + e;
                         if (n >= wi) continue;
-                        const int u = bx.in_i0 + n;
-                        float x;
                         if (ADJ) {
-                            x = hsrc[(long long)(v - st.oj0) * h_w + (u - st.oi0)];
+                            x[e] = hsrc[(long long)(bx.in_j0 + j - st.oj0) * h_w + (bx.in_i0 + n - st.oi0)];
                         } else {
-                            x = fluence_sample(fmap, fa0, fa1, fc0, fc1, mag_coord(st.m, u, L.cu),
-                                               mag_coord(st.m, v, L.cv));
+                            const int2 ai = fu_idx[n];
+                            const float2 aw = fu_w[n];
+                            const float *r0 = fmap + (long long)ai.x * Fc, *r1 = fmap + (long long)ai.y * Fc;
+                            x[e] = aw.x * (cw.x * __ldg(r0 + ci.x) + cw.y * __ldg(r0 + ci.y)) +
+                                   aw.y * (cw.x * __ldg(r1 + ci.x) + cw.y * __ldg(r1 + ci.y));
                         }
-                        if (e) x1 = x; else x0 = x;
                     }
                 }
-                S[idx] = make_float2(x0, x1);
+                S[idx] = make_float2(x[0], x[1]);
             }
         }
         __syncthreads();
