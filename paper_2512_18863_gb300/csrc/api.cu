@@ -476,6 +476,11 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     PLAN_TRY(dalloc(p, &P.counters, 4 * (size_t)n_cp + 2), "cudaMalloc(counters)");
     PLAN_TRY(dalloc(p, &P.fft_ctr, 4 * (size_t)n_cp + 4), "cudaMalloc(fft counters)");
     PLAN_TRY(dalloc(p, &P.fft_over, (size_t)chunk * L.nw), "cudaMalloc(fft overflow list)");
+    float *fcos = nullptr;
+    PLAN_TRY(dalloc(p, &fcos, (size_t)conv_fft_cos_floats(M.R)), "cudaMalloc(fft cosine table)");
+    P.fft_cos = fcos;
+    std::vector<float> hcos(conv_fft_cos_floats(M.R));
+    conv_fft_cos_table(M.R, hcos.data());
     P.leaf_bounds = lb;
     P.depth_dose = dd;
     P.cpgeo = dgeo;
@@ -493,6 +498,8 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
              "upload geometry");
     PLAN_TRY(cudaMemcpyAsync(dukr, ukr.data(), ukr.size() * sizeof(int2), cudaMemcpyHostToDevice, s),
              "upload slice ranges");
+    PLAN_TRY(cudaMemcpyAsync(fcos, hcos.data(), hcos.size() * sizeof(float), cudaMemcpyHostToDevice, s),
+             "upload fft cosine table");
     PLAN_TRY(cudaMemsetAsync(P.flags, 0, sizeof(unsigned), s), "clear flags");
     // host vectors go out of scope: wait for the copies
     PLAN_TRY(cudaStreamSynchronize(s), "plan upload sync");
@@ -528,8 +535,8 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
             const int pm = sizes[t];
             if (pm > want || pm < 2 * M.R + 2) continue;
             int cf = 0, ca = 0;
-            PLAN_TRY(conv_fft_ctas(pm, false, &cf), "fft convolution set-up");
-            PLAN_TRY(conv_fft_ctas(pm, true, &ca), "fft convolution set-up");
+            PLAN_TRY(conv_fft_ctas(pm, M.R, false, &cf), "fft convolution set-up");
+            PLAN_TRY(conv_fft_ctas(pm, M.R, true, &ca), "fft convolution set-up");
             if (cf > 0 && ca > 0) {
                 P.fft_pmax = pm;
                 p->fft_blocks[0] = cf * g->sm_count;
@@ -695,8 +702,8 @@ pdrt_status pdrt_plan_set_fft(pdrt_plan_t p, int32_t pmax)
         return fail(PDRT_EINVAL, "FFT size %d is below 2 R + 2 = %d for this kernel radius", pmax,
                     2 * p->dev.mach.R + 2);
     int cf = 0, ca = 0;
-    CU_TRY(conv_fft_ctas(pmax, false, &cf), "fft convolution set-up");
-    CU_TRY(conv_fft_ctas(pmax, true, &ca), "fft convolution set-up");
+    CU_TRY(conv_fft_ctas(pmax, p->dev.mach.R, false, &cf), "fft convolution set-up");
+    CU_TRY(conv_fft_ctas(pmax, p->dev.mach.R, true, &ca), "fft convolution set-up");
     if (cf <= 0 || ca <= 0) return fail(PDRT_EINVAL, "FFT size %d does not fit in shared memory", pmax);
     p->dev.fft_pmax = pmax;
     p->fft_blocks[0] = cf * p->grid->sm_count;
@@ -902,8 +909,8 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
         for (int pm : {32, 40, 48, 64, 80, 96, 120, 128, 160, 192}) {
             if (pm < 2 * R + 2) continue;
             int cf = 0, ca = 0;
-            CU_TRY(conv_fft_ctas(pm, false, &cf), "fft occupancy");
-            CU_TRY(conv_fft_ctas(pm, true, &ca), "fft occupancy");
+            CU_TRY(conv_fft_ctas(pm, R, false, &cf), "fft occupancy");
+            CU_TRY(conv_fft_ctas(pm, R, true, &ca), "fft occupancy");
             if (cf > 0 && ca > 0) fft_ok.push_back(pm);
         }
     auto apply = [&](const Sched &c) -> pdrt_status {
@@ -912,8 +919,8 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
         p->dev.fft_pmax = 0;
         if (c.fft && c.tc) {
             int cf = 0, ca = 0;
-            CU_TRY(conv_fft_ctas(c.fft, false, &cf), "fft occupancy");
-            CU_TRY(conv_fft_ctas(c.fft, true, &ca), "fft occupancy");
+            CU_TRY(conv_fft_ctas(c.fft, R, false, &cf), "fft occupancy");
+            CU_TRY(conv_fft_ctas(c.fft, R, true, &ca), "fft occupancy");
             p->dev.fft_pmax = c.fft;
             p->fft_blocks[0] = cf * sm;
             p->fft_blocks[1] = ca * sm;

@@ -34,6 +34,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "pdrt_impl.cuh"
 
@@ -42,6 +44,7 @@ namespace pdrt {
 namespace {
 
 constexpr int kFftThreads = 256;
+constexpr int kNumFftSizes = 10;
 
 struct Radices {
     int np;
@@ -283,11 +286,19 @@ __device__ __forceinline__ int operator/(int x, const FastDiv &f)
 // L is the pass's block size; the twiddle W_L^e = T[e (N / L) tmul] with T
 // the table of exp(-2 pi i t / (N tmul)).  MUL (first inverse column pass):
 // every element read is first multiplied by the kernel spectrum.
-template <int R, bool COLS, bool INV, bool MUL>
+// Output of the last inverse row pass, written straight to the region: real
+// sample n of row tr is output u = in_i0 + n (or n - pu) of output row tr.
+struct OutCtx {
+    float *dst;
+    int out_w, in_i0, out_i0, out_i1, pu;
+};
+
+template <int R, bool COLS, bool INV, bool MUL, bool OUT = false>
 __device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &G, int n_tr, int row0, int N,
                                          int L, const float2 *__restrict__ T, int tmul,
                                          const float *__restrict__ Kf, const short *__restrict__ kv_of,
-                                         const short *__restrict__ ku_of)
+                                         const short *__restrict__ ku_of, int valid = 1 << 30,
+                                         const OutCtx *oc = nullptr)
 {
     const int M = L / R;
     const int per_tr = N / R;
@@ -319,54 +330,75 @@ __device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &
         }
         float2 v[R];
 #pragma unroll
-        for (int m = 0; m < R; ++m) v[m] = base[(e0 + m * M) * es];
+        for (int m = 0; m < R; ++m)
+            v[m] = (e0 + m * M < valid) ? base[(e0 + m * M) * es] : make_float2(0.f, 0.f);
         if (MUL) {
-            const int ku = ku_of[tr];
+            const int ku = __ldg(ku_of + tr);
 #pragma unroll
-            for (int m = 0; m < R; ++m) v[m] = cscale(v[m], Kf[kv_of[e0 + m * M] * G.pitch + ku]);
+            for (int m = 0; m < R; ++m) v[m] = cscale(v[m], Kf[__ldg(kv_of + e0 + m * M) * G.pitch + ku]);
         }
         if (INV) {
 #pragma unroll
-            for (int m = 1; m < R; ++m) v[m] = cmul(v[m], cconj(T[j * m * tstep]));
+            for (int m = 1; m < R; ++m) v[m] = cmul(v[m], cconj(__ldg(T + j * m * tstep)));
             dft<R, 1>(v);
         } else {
             dft<R, -1>(v);
 #pragma unroll
-            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], T[j * q * tstep]);
+            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], __ldg(T + j * q * tstep));
         }
+        if (OUT) {
+            // natural order: complex element e0 + q M holds reals 2 (e0 + q M) and + 1
+            float *drow = oc->dst + (long long)tr * oc->out_w;
 #pragma unroll
-        for (int m = 0; m < R; ++m) base[(e0 + m * M) * es] = v[m];
+            for (int q = 0; q < R; ++q) {
+                int u = oc->in_i0 + 2 * (e0 + q * M);
+                if (u >= oc->out_i1) u -= oc->pu;
+                if (u >= oc->out_i0 && u < oc->out_i1) drow[u - oc->out_i0] = v[q].x;
+                int u1 = oc->in_i0 + 2 * (e0 + q * M) + 1;
+                if (u1 >= oc->out_i1) u1 -= oc->pu;
+                if (u1 >= oc->out_i0 && u1 < oc->out_i1) drow[u1 - oc->out_i0] = v[q].y;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < R; ++m) base[(e0 + m * M) * es] = v[m];
+        }
     }
 }
 
-template <bool COLS, bool INV, bool MUL>
+template <bool COLS, bool INV, bool MUL, bool OUT = false>
 __device__ __forceinline__ void fft_pass_r(int R, float2 *S, const FftGeom &G, int n_tr, int row0, int N, int L,
                                            const float2 *T, int tmul, const float *Kf, const short *kv_of,
-                                           const short *ku_of)
+                                           const short *ku_of, int valid = 1 << 30, const OutCtx *oc = nullptr)
 {
+#define PDRT_FFT_PASS(RR) \
+    fft_pass<RR, COLS, INV, MUL, OUT>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of, valid, oc)
     switch (R) {
-    case 3: fft_pass<3, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
-    case 4: fft_pass<4, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
-    case 5: fft_pass<5, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
-    case 6: fft_pass<6, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
-    case 8: fft_pass<8, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
-    case 10: fft_pass<10, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
-    case 12: fft_pass<12, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
-    default: fft_pass<16, COLS, INV, MUL>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of); break;
+    case 3: PDRT_FFT_PASS(3); break;
+    case 4: PDRT_FFT_PASS(4); break;
+    case 5: PDRT_FFT_PASS(5); break;
+    case 6: PDRT_FFT_PASS(6); break;
+    case 8: PDRT_FFT_PASS(8); break;
+    case 10: PDRT_FFT_PASS(10); break;
+    case 12: PDRT_FFT_PASS(12); break;
+    default: PDRT_FFT_PASS(16); break;
     }
+#undef PDRT_FFT_PASS
 }
 
 // Whole transform of length N over a batch: forward (DIF, natural in,
-// digit-reversed out) or inverse (DIT, digit-reversed in, natural out; the
-// first inverse column pass applies the kernel spectrum).
+// digit-reversed out; rows at or past `valid` of a column read as zero in the
+// first pass) or inverse (DIT, digit-reversed in, natural out; the first
+// inverse column pass applies the kernel spectrum; with an output context the
+// last inverse row pass writes the output box instead of S).
 template <bool COLS, bool INV>
 __device__ void fft_run(float2 *S, const FftGeom &G, int n_tr, int row0, int N, const float2 *T, int tmul,
-                        const float *Kf, const short *kv_of, const short *ku_of)
+                        const float *Kf, const short *kv_of, const short *ku_of, int valid = 1 << 30,
+                        const OutCtx *oc = nullptr)
 {
     const Radices rd = radices_of(N);
     const int r0 = rd.r[0], L1 = N / r0;
     if (!INV) {
-        fft_pass_r<COLS, false, false>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
+        fft_pass_r<COLS, false, false>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of, valid);
         __syncthreads();
         if (rd.np > 1) {
             fft_pass_r<COLS, false, false>(rd.r[1], S, G, n_tr, row0, N, L1, T, tmul, Kf, kv_of, ku_of);
@@ -376,6 +408,11 @@ __device__ void fft_run(float2 *S, const FftGeom &G, int n_tr, int row0, int N, 
         if (rd.np > 1) {
             fft_pass_r<COLS, true, COLS>(rd.r[1], S, G, n_tr, row0, N, L1, T, tmul, Kf, kv_of, ku_of);
             __syncthreads();
+        }
+        if (!COLS && oc) {
+            fft_pass_r<false, true, false, true>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of, 1 << 30,
+                                                 oc);
+        } else if (rd.np > 1) {
             fft_pass_r<COLS, true, false>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
         } else {
             fft_pass_r<COLS, true, COLS>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
@@ -386,7 +423,7 @@ __device__ void fft_run(float2 *S, const FftGeom &G, int n_tr, int row0, int N, 
 
 // position of frequency k in the forward (DIF) output of length N, and the
 // frequency held at position p
-__device__ __forceinline__ int dif_pos(int k, int N)
+__host__ __device__ inline int dif_pos(int k, int N)
 {
     const Radices rd = radices_of(N);
     int p = 0, L = N;
@@ -399,7 +436,7 @@ __device__ __forceinline__ int dif_pos(int k, int N)
     return p;
 }
 
-__device__ __forceinline__ int dif_freq(int p, int N)
+__host__ __device__ inline int dif_freq(int p, int N)
 {
     const Radices rd = radices_of(N);
     int k = 0, L = N, mul = 1;
@@ -413,24 +450,103 @@ __device__ __forceinline__ int dif_freq(int p, int N)
     return k;
 }
 
+// Tables of every supported padded size P, laid out one size after another:
+//   twiddles exp(-2 pi i t / P), t < P                          (sum P entries)
+//   pos: position of frequency k in the DIF of length P/2, k < P/2
+//   ku : frequency held at position c of that DIF (c < P/2), P/2 at c = P/2
+//   kv : min(f, P - f), f the frequency at position e of the DIF of length P
+// Constant, uploaded once per device (computed on the host in double).
+constexpr int kSizes[kNumFftSizes] = {32, 40, 48, 64, 80, 96, 120, 128, 160, 192};
+constexpr int kTwTotal = 960, kPosTotal = 480, kKuTotal = 490, kKvTotal = 960;
+__device__ float2 g_fft_tw[kTwTotal];
+__device__ short g_fft_pos[kPosTotal];
+__device__ short g_fft_ku[kKuTotal];
+__device__ short g_fft_kv[kKvTotal];
+
+struct SizeOff {
+    int tw, pos, ku, kv, cos;
+};
+
+// offsets of size P in the tables; cos: offset in the plan's cosine table
+// (rows of (P/2 + 1) rounded up to 4 floats, R + 1 rows per size)
+__host__ __device__ inline SizeOff size_offsets(int P, int R)
+{
+    const int sizes[kNumFftSizes] = {32, 40, 48, 64, 80, 96, 120, 128, 160, 192};
+    SizeOff o = {0, 0, 0, 0, 0};
+    for (int i = 0; i < kNumFftSizes && sizes[i] < P; ++i) {
+        const int q = sizes[i];
+        o.tw += q;
+        o.pos += q / 2;
+        o.ku += q / 2 + 1;
+        o.kv += q;
+        o.cos += (R + 1) * (((q / 2 + 1) + 3) & ~3);
+    }
+    return o;
+}
+
 }  // namespace
 
-// shared memory of k_conv_fft for a size limit pmax: header, twiddle tables,
-// index tables, kernel spectrum and the complex work array
-int conv_fft_smem_bytes(int pmax)
+int conv_fft_cos_floats(int R) { return size_offsets(1 << 20, R).cos; }
+
+// c_p cos(2 pi k p / P) for p <= R and k <= P/2 (0 in the row padding), c_0 = 1,
+// c_{p>0} = 2, every supported P: the cosine sums of the kernel spectrum
+void conv_fft_cos_table(int R, float *out)
 {
-    const int hu = pmax / 2;
-    const int tw = 2 * pmax * 8;                               // Tu, Tv
-    const int idx = (3 * pmax + 8) * 2;                         // pos_u, ku_of, kv_of (short)
+    for (int i = 0; i < kNumFftSizes; ++i) {
+        const int P = kSizes[i], w4 = ((P / 2 + 1) + 3) & ~3;
+        float *t = out + size_offsets(P, R).cos;
+        for (int pp = 0; pp <= R; ++pp)
+            for (int k = 0; k < w4; ++k) {
+                const long long e = ((long long)k * pp) % P;
+                t[pp * w4 + k] = k <= P / 2 ? (float)((pp ? 2.0 : 1.0) * cos(2.0 * M_PI * (double)e / P)) : 0.f;
+            }
+    }
+}
+
+// uploads the size tables to the current device (once per device)
+cudaError_t conv_fft_tables_upload()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    std::vector<float2> tw(kTwTotal);
+    std::vector<short> pos(kPosTotal), ku(kKuTotal), kv(kKvTotal);
+    for (int i = 0; i < kNumFftSizes; ++i) {
+        const int P = kSizes[i], H = P / 2;
+        const SizeOff o = size_offsets(P, 0);
+        for (int t = 0; t < P; ++t)
+            tw[o.tw + t] = make_float2((float)cos(2.0 * M_PI * t / P), (float)-sin(2.0 * M_PI * t / P));
+        for (int k = 0; k < H; ++k) pos[o.pos + k] = (short)dif_pos(k, H);
+        for (int c = 0; c <= H; ++c) ku[o.ku + c] = (short)(c == H ? H : dif_freq(c, H));
+        for (int q = 0; q < P; ++q) {
+            const int f = dif_freq(q, P);
+            kv[o.kv + q] = (short)std::min(f, P - f);
+        }
+    }
+    if ((e = cudaMemcpyToSymbol(g_fft_tw, tw.data(), sizeof(float2) * kTwTotal)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(g_fft_pos, pos.data(), sizeof(short) * kPosTotal)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(g_fft_ku, ku.data(), sizeof(short) * kKuTotal)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(g_fft_kv, kv.data(), sizeof(short) * kKvTotal)) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return cudaSuccess;
+}
+
+// shared memory of k_conv_fft for a size limit pmax and kernel half-width R:
+// header, kernel spectrum, forward fill tables and the complex work array
+// (which first holds the spectrum's scratch K [R+1][R+1] and A [R+1][P/2+1])
+int conv_fft_smem_bytes(int pmax, int R)
+{
+    const int hu = pmax / 2, r1 = R + 1, w4 = ((hu + 1) + 3) & ~3;
     const int kf = (pmax / 2 + 1) * (hu + 1) * 4;               // Kf [kv'][ku]
     const int ft = 4 * pmax * 8;                                // forward fill tables
-    // S [pv][hu + 1] complex; it also holds the kernel-spectrum scratch
-    // K, Cv, Cu, A for a kernel half-width up to pmax / 2 - 1
-    const int r1 = hu, w4 = ((hu + 1) + 3) & ~3;
-    const int scratch = (r1 * (r1 + 3 * w4) + 4) * 4;
-    const int s = std::max(pmax * (hu + 1) * 8, scratch);
+    const int scratch = (((r1 * r1 + 3) & ~3) + r1 * w4) * 4;
+    const int s = std::max(pmax * (hu + 1) * 8, scratch);       // S [pv][hu + 1] complex
     auto al = [](int x) { return (x + 15) & ~15; };
-    return 64 + al(tw) + al(idx) + al(kf) + ft + al(s);
+    return 64 + al(kf) + ft + al(s);
 }
 
 template <bool ADJ>
@@ -441,19 +557,11 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Lattice &L = P.lat;
-    const int R = P.mach.R;
+    const int R = P.mach.R, R1 = R + 1;
     const int hmax = pmax / 2;
     auto al = [](int x) { return (x + 15) & ~15; };
     int *s_item = reinterpret_cast<int *>(smem);
-    int *s_sizes = reinterpret_cast<int *>(smem + 16);   // current table sizes (pu, pv)
     unsigned char *p = smem + 64;
-    float2 *Tu = reinterpret_cast<float2 *>(p);
-    float2 *Tv = Tu + pmax;
-    p += al(2 * pmax * 8);
-    short *pos_u = reinterpret_cast<short *>(p);
-    short *ku_of = pos_u + hmax;
-    short *kv_of = ku_of + hmax + 4;
-    p += al((3 * pmax + 8) * 2);
     float *Kf = reinterpret_cast<float *>(p);
     p += al((pmax / 2 + 1) * (hmax + 1) * 4);
     int2 *fu_idx = reinterpret_cast<int2 *>(p);   // forward fill tables, [pmax] each
@@ -462,10 +570,11 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
     float2 *fv_w = reinterpret_cast<float2 *>(fv_idx + pmax);
     p += 4 * pmax * 8;
     float2 *S = reinterpret_cast<float2 *>(p);
-    float *scratch = reinterpret_cast<float *>(S);   // kernel rows and A before the fill
+    float *Kq = reinterpret_cast<float *>(S);        // spectrum scratch before the fill: [p][q]
+    float *A = Kq + ((R1 * R1 + 3) & ~3);            // [p][kv'] (16-byte aligned rows)
     const int tid = threadIdx.x;
     const int n_items = nb * L.nw;
-    if (tid == 0) s_sizes[0] = s_sizes[1] = 0;
+    const bool sym = L.du == L.dv;                   // K(p, q) = K(q, p)
 
     for (;;) {
         __syncthreads();
@@ -490,69 +599,26 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
         G.n_rows_out = bx.out_j1 - bx.out_j0;
         G.out_row0 = ((bx.out_j0 - bx.in_j0) % pv + pv) % pv;
         const int wi = bx.in_i1 - bx.in_i0;
-
-        // twiddle and index tables when the sizes change (all threads read
-        // s_sizes before any thread rewrites it: the barrier after the item)
-        const bool new_sizes = (s_sizes[0] != pu || s_sizes[1] != pv);
-        if (new_sizes) {
-            for (int t = tid; t < pu + pv; t += kFftThreads) {
-                const int n = t < pu ? pu : pv, e = t < pu ? t : t - pu;
-                float sn, cs;
-                sincospif(2.0f * (float)e / (float)n, &sn, &cs);
-                (t < pu ? Tu : Tv)[e] = make_float2(cs, -sn);
-            }
-            for (int t = tid; t < hu + 1 + pv + hu; t += kFftThreads) {
-                if (t < hu + 1) {
-                    ku_of[t] = (short)(t == hu ? hu : dif_freq(t, hu));
-                } else if (t < hu + 1 + pv) {
-                    const int e = t - hu - 1, kv = dif_freq(e, pv);
-                    kv_of[e] = (short)min(kv, pv - kv);
-                } else {
-                    const int e = t - hu - 1 - pv;
-                    pos_u[e] = (short)dif_pos(e, hu);
-                }
-            }
-        }
-        // Kernel spectrum.  Scratch in S: K(p, q) [R1][R1]; cosine tables
-        // Cv[q][kv'] = c_q cos(2 pi kv' q / pv) and Cu[p][ku] = c_p cos(2 pi ku p / pu)
-        // (rows padded to multiples of 4); A = K Cv [R1][nkv4]; then
-        // Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
-        const int R1 = R + 1;
+        const SizeOff ou = size_offsets(pu, R), ov = size_offsets(pv, R);
+        const float2 *Tu = g_fft_tw + ou.tw, *Tv = g_fft_tw + ov.tw;
+        const short *pos_u = g_fft_pos + ou.pos, *ku_of = g_fft_ku + ou.ku, *kv_of = g_fft_kv + ov.kv;
         const int nkv = pv / 2 + 1, nkv4 = (nkv + 3) & ~3, hu4 = (hu + 1 + 3) & ~3;
-        float *Kq = scratch;                   // [p][q]
-        float *Cv = Kq + ((R1 * R1 + 3) & ~3); // [q][kv'] (16-byte aligned rows)
-        float *Cu = Cv + R1 * nkv4;            // [p][ku]
-        float *A = Cu + R1 * hu4;              // [p][kv']
+        const float *Cv = P.fft_cos + ov.cos;        // [q][kv'], c_q folded in
+        const float *Cu = P.fft_cos + ou.cos;        // [p][ku], c_p folded in
+
+        // Kernel spectrum: K(p, q) (the expressions of the other convolution
+        // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv']
         for (int idx = tid; idx < R1 * R1; idx += kFftThreads) {
             const int pp = idx / R1, q = idx - pp * R1;
+            if (sym && pp > q) continue;
             const float pu_mm = pp * L.du, qv = q * L.dv;
             const float r = sqrtf(pu_mm * pu_mm + qv * qv);
-            Kq[idx] = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
-                      st.wn[2] * expf(-st.a[2] * r);
+            const float kv = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
+                             st.wn[2] * expf(-st.a[2] * r);
+            Kq[idx] = kv;
+            if (sym) Kq[q * R1 + pp] = kv;
         }
         __syncthreads();
-        // every thread has read s_sizes (before the barrier above)
-        if (tid == 0) {
-            s_sizes[0] = pu;
-            s_sizes[1] = pv;
-        }
-        {
-            const FastDiv dv = fast_div(pv), du = fast_div(pu), d4v = fast_div(nkv4), d4u = fast_div(hu4);
-            for (int idx = tid; idx < R1 * (nkv4 + hu4); idx += kFftThreads) {
-                if (idx < R1 * nkv4) {
-                    const int q = idx / d4v, kv = idx - q * nkv4;
-                    const int e = kv * q - ((kv * q) / dv) * pv;
-                    Cv[idx] = kv < nkv ? (q ? 2.f : 1.f) * Tv[e].x : 0.f;
-                } else {
-                    const int t = idx - R1 * nkv4;
-                    const int pp = t / d4u, ku = t - pp * hu4;
-                    const int e = ku * pp - ((ku * pp) / du) * pu;
-                    Cu[t] = ku <= hu ? (pp ? 2.f : 1.f) * Tu[e].x : 0.f;
-                }
-            }
-        }
-        __syncthreads();
-        // A[p][4g .. 4g+3] per item: K row p (broadcast) against float4 of Cv
         {
             const int G4 = nkv4 / 4;
             const FastDiv dg = fast_div(G4);
@@ -562,18 +628,17 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
                 const float *kr = Kq + pp * R1;
                 const float4 *cv = reinterpret_cast<const float4 *>(Cv) + g;
                 for (int q = 0; q < R1; ++q) {
-                    const float k = kr[q];
-                    const float4 c = cv[q * G4];
-                    acc.x = fmaf(k, c.x, acc.x);
-                    acc.y = fmaf(k, c.y, acc.y);
-                    acc.z = fmaf(k, c.z, acc.z);
-                    acc.w = fmaf(k, c.w, acc.w);
+                    const float kk = kr[q];
+                    const float4 c = __ldg(cv + q * G4);
+                    acc.x = fmaf(kk, c.x, acc.x);
+                    acc.y = fmaf(kk, c.y, acc.y);
+                    acc.z = fmaf(kk, c.z, acc.z);
+                    acc.w = fmaf(kk, c.w, acc.w);
                 }
                 reinterpret_cast<float4 *>(A)[pp * G4 + g] = acc;
             }
         }
         __syncthreads();
-        // Kf for kv' in {2i, 2i+1} and ku in [4g, 4g+4) per item
         {
             const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
             const int U4 = hu4 / 4, V2 = (nkv + 1) / 2;
@@ -584,7 +649,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
                 const float4 *cu = reinterpret_cast<const float4 *>(Cu) + g;
                 for (int pp = 0; pp < R1; ++pp) {
                     const float2 av = *reinterpret_cast<const float2 *>(A + pp * nkv4 + 2 * i);
-                    const float4 c = cu[pp * U4];
+                    const float4 c = __ldg(cu + pp * U4);
                     a0.x = fmaf(av.x, c.x, a0.x); a0.y = fmaf(av.x, c.y, a0.y);
                     a0.z = fmaf(av.x, c.z, a0.z); a0.w = fmaf(av.x, c.w, a0.w);
                     a1.x = fmaf(av.y, c.x, a1.x); a1.y = fmaf(av.y, c.y, a1.y);
@@ -600,8 +665,8 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
                 }
             }
         }
-        // fill tables (forward): per input column n the two fluence rows a
-        // of its bilinear stencil (clamped into the support box) with their
+        // fill tables (forward): per input column n the two fluence rows a of
+        // its bilinear stencil (clamped into the support box) with their
         // weights (zero outside the box), likewise per input row j
         if (!ADJ) {
             const CpTab &ct = P.cptab[b];
@@ -627,41 +692,40 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
         }
         __syncthreads();
 
-        // fill: row j = v offset from the input box, packed (x[2m], x[2m+1])
-        // along u; rows past the input are zero
+        // fill the input rows (j = v offset from the input box), packed
+        // (x[2m], x[2m+1]) along u; the rows past them are never written: the
+        // first column pass reads them as zero
         {
-            const int n_fill = pv * (hu + 1);
-            const FastDiv dp = fast_div(hu + 1);
+            const int n_fill = G.n_rows_in * hu;
+            const FastDiv dh = fast_div(hu);
             const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
             const int Fc = P.cptab[b].fc1 - P.cptab[b].fc0;
             const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
             const int h_w = st.oi1 - st.oi0;
             for (int idx = tid; idx < n_fill; idx += kFftThreads) {
-                const int j = idx / dp, m = idx - j * (hu + 1);
+                const int j = idx / dh, m = idx - j * hu;
                 float x[2] = {0.f, 0.f};
-                if (j < G.n_rows_in && m < hu) {
-                    int2 ci;
-                    float2 cw;
-                    if (!ADJ) {
-                        ci = fv_idx[j];
-                        cw = fv_w[j];
-                    }
+                int2 ci = make_int2(0, 0);
+                float2 cw = make_float2(0.f, 0.f);
+                if (!ADJ) {
+                    ci = fv_idx[j];
+                    cw = fv_w[j];
+                }
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int n = 2 * m + e;
-                        if (n >= wi) continue;
-                        if (ADJ) {
-                            x[e] = hsrc[(long long)(bx.in_j0 + j - st.oj0) * h_w + (bx.in_i0 + n - st.oi0)];
-                        } else {
-                            const int2 ai = fu_idx[n];
-                            const float2 aw = fu_w[n];
-                            const float *r0 = fmap + (long long)ai.x * Fc, *r1 = fmap + (long long)ai.y * Fc;
-                            x[e] = aw.x * (cw.x * __ldg(r0 + ci.x) + cw.y * __ldg(r0 + ci.y)) +
-                                   aw.y * (cw.x * __ldg(r1 + ci.x) + cw.y * __ldg(r1 + ci.y));
-                        }
+                for (int e = 0; e < 2; ++e) {
+                    const int n = 2 * m + e;
+                    if (n >= wi) continue;
+                    if (ADJ) {
+                        x[e] = hsrc[(long long)(bx.in_j0 + j - st.oj0) * h_w + (bx.in_i0 + n - st.oi0)];
+                    } else {
+                        const int2 ai = fu_idx[n];
+                        const float2 aw = fu_w[n];
+                        const float *r0 = fmap + (long long)ai.x * Fc, *r1 = fmap + (long long)ai.y * Fc;
+                        x[e] = aw.x * (cw.x * __ldg(r0 + ci.x) + cw.y * __ldg(r0 + ci.y)) +
+                               aw.y * (cw.x * __ldg(r1 + ci.x) + cw.y * __ldg(r1 + ci.y));
                     }
                 }
-                S[idx] = make_float2(x[0], x[1]);
+                S[j * G.pitch + m] = make_float2(x[0], x[1]);
             }
         }
         __syncthreads();
@@ -672,78 +736,78 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
         // W = exp(-2 pi i / pu); X[hu] goes to column hu
         {
             const int half = hu / 2 + 1;
+            const FastDiv dhf = fast_div(half);
             for (int idx = tid; idx < G.n_rows_in * half; idx += kFftThreads) {
-                const int j = idx / half, kk = idx - j * half;
+                const int j = idx / dhf, kk = idx - j * half;
                 float2 *row = S + j * G.pitch;
                 if (kk == 0) {
-                    const float2 z = row[pos_u[0]];
-                    row[pos_u[0]] = make_float2(z.x + z.y, 0.f);
+                    const int p0 = __ldg(pos_u);
+                    const float2 z = row[p0];
+                    row[p0] = make_float2(z.x + z.y, 0.f);
                     row[hu] = make_float2(z.x - z.y, 0.f);
                     continue;
                 }
-                const int pk = pos_u[kk], pc = pos_u[hu - kk];
+                const int pk = __ldg(pos_u + kk), pc = __ldg(pos_u + hu - kk);
                 const float2 zk = row[pk], zc = cconj(row[pc]);
                 const float2 E = cscale(cadd(zk, zc), 0.5f);
                 const float2 d = cscale(csub(zk, zc), 0.5f);
                 const float2 O = make_float2(d.y, -d.x);   // d / i
-                const float2 WO = cmul(Tu[kk], O);
+                const float2 WO = cmul(__ldg(Tu + kk), O);
                 row[pk] = cadd(E, WO);
                 if (pc != pk) row[pc] = cconj(csub(E, WO));
             }
         }
         __syncthreads();
-        // columns: forward FFT of length pv, then product and inverse
-        fft_run<true, false>(S, G, hu + 1, 0, pv, Tv, 1, Kf, kv_of, ku_of);
+        // columns: forward FFT of length pv (rows past the input read as
+        // zero), then product and inverse
+        fft_run<true, false>(S, G, hu + 1, 0, pv, Tv, 1, Kf, kv_of, ku_of, G.n_rows_in);
         fft_run<true, true>(S, G, hu + 1, 0, pv, Tv, 1, Kf, kv_of, ku_of);
         // inverse real FFT of the output rows: Z[k] = (X_k + conj X_{hu-k})
         // + i exp(2 pi i k / pu) (X_k - conj X_{hu-k}), stored at pos_u(k)
         {
             const int half = hu / 2 + 1;
+            const FastDiv dhf = fast_div(half);
             for (int idx = tid; idx < G.n_rows_out * half; idx += kFftThreads) {
-                const int rr = idx / half, kk = idx - rr * half;
+                const int rr = idx / dhf, kk = idx - rr * half;
                 int row_i = G.out_row0 + rr;
                 if (row_i >= pv) row_i -= pv;
                 float2 *row = S + row_i * G.pitch;
-                const int pk = pos_u[kk];
+                const int pk = __ldg(pos_u + kk);
+                const int pc = kk == 0 ? hu : __ldg(pos_u + hu - kk);
                 const float2 xk = row[pk];
-                const float2 xc = cconj(kk == 0 ? row[hu] : row[pos_u[hu - kk]]);
+                const float2 xc = cconj(row[pc]);
                 const float2 sum = cadd(xk, xc), dif = csub(xk, xc);
-                const float2 wd = cmul(cconj(Tu[kk]), dif);
+                const float2 w = __ldg(Tu + kk);
+                const float2 wd = cmul(cconj(w), dif);
                 row[pk] = make_float2(sum.x - wd.y, sum.y + wd.x);   // sum + i wd
                 if (kk > 0 && 2 * kk != hu) {
                     // Z[hu - k] = (X_{hu-k} + conj X_k) - i exp(-2 pi i k / pu) (X_{hu-k} - conj X_k)
                     const float2 yk = cconj(xc), yc = cconj(xk);   // X_{hu-k}, conj X_k
                     const float2 s2 = cadd(yk, yc), d2 = csub(yk, yc);
-                    const float2 w2 = cmul(Tu[kk], d2);
-                    row[pos_u[hu - kk]] = make_float2(s2.x + w2.y, s2.y - w2.x);   // s2 - i w2
+                    const float2 w2 = cmul(w, d2);
+                    row[pc] = make_float2(s2.x + w2.y, s2.y - w2.x);   // s2 - i w2
                 }
             }
         }
         __syncthreads();
-        fft_run<false, true>(S, G, G.n_rows_out, G.out_row0, hu, Tu, 2, Kf, kv_of, ku_of);
-        // output box: (u, v) reads real sample n = (u - in_i0) mod pu of row (v - in_j0) mod pv
-        {
-            float *dst = ADJ ? P.adjbuf + (long long)bl * P.cap_a + st.off_a
-                             : P.region + (long long)bl * P.cap_o + st.off_o;
-            const int out_w = bx.out_i1 - bx.out_i0;
-            const int n_out = out_w * G.n_rows_out;
-            for (int idx = tid; idx < n_out; idx += kFftThreads) {
-                const int rr = idx / out_w, uo = idx - rr * out_w;
-                int row_i = G.out_row0 + rr;
-                if (row_i >= pv) row_i -= pv;
-                int n = bx.out_i0 + uo - bx.in_i0;
-                if (n < 0) n += pu;
-                const float2 z = S[row_i * G.pitch + (n >> 1)];
-                dst[(long long)rr * out_w + uo] = (n & 1) ? z.y : z.x;
-            }
-        }
+        // inverse rows; the last pass writes the output box:
+        // (u, v) holds real sample (u - in_i0) mod pu of row (v - in_j0) mod pv
+        OutCtx oc;
+        oc.dst = ADJ ? P.adjbuf + (long long)bl * P.cap_a + st.off_a
+                     : P.region + (long long)bl * P.cap_o + st.off_o;
+        oc.out_w = bx.out_i1 - bx.out_i0;
+        oc.in_i0 = bx.in_i0;
+        oc.out_i0 = bx.out_i0;
+        oc.out_i1 = bx.out_i1;
+        oc.pu = pu;
+        fft_run<false, true>(S, G, G.n_rows_out, G.out_row0, hu, Tu, 2, Kf, kv_of, ku_of, 1 << 30, &oc);
     }
 }
 
 cudaError_t launch_conv_fft(const PlanDev &P, int b0, int nb, bool adjoint, int pmax, unsigned int *counter,
                             int *over_list, unsigned int *over_count, int grid_blocks, cudaStream_t s)
 {
-    const int smem = conv_fft_smem_bytes(pmax);
+    const int smem = conv_fft_smem_bytes(pmax, P.mach.R);
     if (adjoint)
         k_conv_fft<true><<<grid_blocks, kFftThreads, smem, s>>>(P, b0, nb, pmax, counter, over_list, over_count);
     else
@@ -751,12 +815,15 @@ cudaError_t launch_conv_fft(const PlanDev &P, int b0, int nb, bool adjoint, int 
     return cudaGetLastError();
 }
 
-// CTAs of one direction per SM at a size limit (shared memory, registers)
-cudaError_t conv_fft_ctas(int pmax, bool adjoint, int *ctas)
+// CTAs of one direction per SM at a size limit (shared memory, registers);
+// also uploads the size tables to the current device
+cudaError_t conv_fft_ctas(int pmax, int R, bool adjoint, int *ctas)
 {
     *ctas = 0;
-    if (!fft_size_for(pmax) || fft_size_for(pmax) != pmax) return cudaSuccess;
-    cudaError_t e = adjoint ? allow_full_smem(k_conv_fft<true>) : allow_full_smem(k_conv_fft<false>);
+    if (!fft_size_for(pmax) || fft_size_for(pmax) != pmax || pmax < 2 * R + 2) return cudaSuccess;
+    cudaError_t e = conv_fft_tables_upload();
+    if (e != cudaSuccess) return e;
+    e = adjoint ? allow_full_smem(k_conv_fft<true>) : allow_full_smem(k_conv_fft<false>);
     if (e != cudaSuccess) return e;
     int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, optin = 0;
     e = cudaGetDevice(&dev);
@@ -768,7 +835,7 @@ cudaError_t conv_fft_ctas(int pmax, bool adjoint, int *ctas)
     if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, adjoint ? (const void *)k_conv_fft<true>
                                                                   : (const void *)k_conv_fft<false>);
     if (e != cudaSuccess) return e;
-    const int smem = conv_fft_smem_bytes(pmax);
+    const int smem = conv_fft_smem_bytes(pmax, R);
     if (smem + (int)fa.sharedSizeBytes > optin) return cudaSuccess;
     const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + resv);
     const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;

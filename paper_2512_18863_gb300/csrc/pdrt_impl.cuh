@@ -130,6 +130,7 @@ struct PlanDev {
     int *fft_over;           // [chunk * nw] overflow list of one chunk launch (items)
     unsigned int *fft_ctr;   // [4 * n_cp]: per chunk {fwd counter, fwd overflow count,
                              // adj counter, adj overflow count}
+    const float *fft_cos;    // c_p cos(2 pi k p / P) per supported size P (conv_fft_cos_table)
 };
 
 // Same float expression in every kernel that samples or transposes the
@@ -337,9 +338,14 @@ cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsig
                            const unsigned int *list_n = nullptr);
 cudaError_t launch_conv_fft(const PlanDev &P, int b0, int nb, bool adjoint, int pmax, unsigned int *counter,
                             int *over_list, unsigned int *over_count, int grid_blocks, cudaStream_t s);
-int conv_fft_smem_bytes(int pmax);
-// CTAs per SM of k_conv_fft for a size limit (0 if it does not fit)
-cudaError_t conv_fft_ctas(int pmax, bool adjoint, int *ctas);
+int conv_fft_smem_bytes(int pmax, int R);
+// CTAs per SM of k_conv_fft for a size limit (0 if it does not fit or is
+// below 2 R + 2); uploads the constant size tables to the current device
+cudaError_t conv_fft_ctas(int pmax, int R, bool adjoint, int *ctas);
+// the plan's cosine table of the kernel spectrum: its length (floats) and
+// contents (host) for a kernel half-width R
+int conv_fft_cos_floats(int R);
+void conv_fft_cos_table(int R, float *out);
 cudaError_t conv_tc_prepare(int R, int *fwd_blocks_per_sm, int *adj_blocks_per_sm, int *fwd_phase,
                             int *adj_phase);
 // CTAs per SM of k_conv_tc for a phase depth (0 if the phase does not fit).
