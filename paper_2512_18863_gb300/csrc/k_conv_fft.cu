@@ -337,14 +337,30 @@ __device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &
 #pragma unroll
             for (int m = 0; m < R; ++m) v[m] = cscale(v[m], Kf[__ldg(kv_of + e0 + m * M) * G.pitch + ku]);
         }
+        // twiddles W_L^{j q}, q = 1..R-1, by recurrence from one table read
+        // (relative error grows by ~1 ulp per step: < 2e-6 at R = 16)
         if (INV) {
+            if (j) {
+                const float2 w1 = cconj(__ldg(T + j * tstep));
+                float2 w = w1;
 #pragma unroll
-            for (int m = 1; m < R; ++m) v[m] = cmul(v[m], cconj(__ldg(T + j * m * tstep)));
+                for (int m = 1; m < R; ++m) {
+                    v[m] = cmul(v[m], w);
+                    if (m + 1 < R) w = cmul(w, w1);
+                }
+            }
             dft<R, 1>(v);
         } else {
             dft<R, -1>(v);
+            if (j) {
+                const float2 w1 = __ldg(T + j * tstep);
+                float2 w = w1;
 #pragma unroll
-            for (int q = 1; q < R; ++q) v[q] = cmul(v[q], __ldg(T + j * q * tstep));
+                for (int q = 1; q < R; ++q) {
+                    v[q] = cmul(v[q], w);
+                    if (q + 1 < R) w = cmul(w, w1);
+                }
+            }
         }
         if (OUT) {
             // natural order: complex element e0 + q M holds reals 2 (e0 + q M) and + 1
@@ -543,7 +559,7 @@ int conv_fft_smem_bytes(int pmax, int R)
     const int hu = pmax / 2, r1 = R + 1, w4 = ((hu + 1) + 3) & ~3;
     const int kf = (pmax / 2 + 1) * (hu + 1) * 4;               // Kf [kv'][ku]
     const int ft = 4 * pmax * 8;                                // forward fill tables
-    const int scratch = (((r1 * r1 + 3) & ~3) + r1 * w4) * 4;
+    const int scratch = (r1 * ((r1 + 3) & ~3) + ((r1 + 3) & ~3) * w4) * 4;
     const int s = std::max(pmax * (hu + 1) * 8, scratch);       // S [pv][hu + 1] complex
     auto al = [](int x) { return (x + 15) & ~15; };
     return 64 + al(kf) + ft + al(s);
@@ -570,8 +586,9 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
     float2 *fv_w = reinterpret_cast<float2 *>(fv_idx + pmax);
     p += 4 * pmax * 8;
     float2 *S = reinterpret_cast<float2 *>(p);
-    float *Kq = reinterpret_cast<float *>(S);        // spectrum scratch before the fill: [p][q]
-    float *A = Kq + ((R1 * R1 + 3) & ~3);            // [p][kv'] (16-byte aligned rows)
+    const int R1p = (R1 + 3) & ~3;
+    float *KT = reinterpret_cast<float *>(S);        // spectrum scratch before the fill: [q][p]
+    float *A = KT + R1 * R1p;                        // [p][kv'] (16-byte aligned rows)
     const int tid = threadIdx.x;
     const int n_items = nb * L.nw;
     const bool sym = L.du == L.dv;                   // K(p, q) = K(q, p)
@@ -607,7 +624,9 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
         const float *Cu = P.fft_cos + ou.cos;        // [p][ku], c_p folded in
 
         // Kernel spectrum: K(p, q) (the expressions of the other convolution
-        // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv']
+        // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
+        // K is stored transposed, KT[q][p] (rows of R1p = R1 rounded up to 4),
+        // so that both products read 4-wide vectors of each operand.
         for (int idx = tid; idx < R1 * R1; idx += kFftThreads) {
             const int pp = idx / R1, q = idx - pp * R1;
             if (sym && pp > q) continue;
@@ -615,53 +634,75 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
             const float r = sqrtf(pu_mm * pu_mm + qv * qv);
             const float kv = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
                              st.wn[2] * expf(-st.a[2] * r);
-            Kq[idx] = kv;
-            if (sym) Kq[q * R1 + pp] = kv;
+            KT[q * R1p + pp] = kv;
+            if (sym) KT[pp * R1p + q] = kv;
+        }
+        for (int idx = tid; idx < R1 * (R1p - R1); idx += kFftThreads) {   // zero padding columns
+            const int q = idx / (R1p - R1);
+            KT[q * R1p + R1 + (idx - q * (R1p - R1))] = 0.f;
         }
         __syncthreads();
+        // A[4 p4 .. +3][4 g .. +3] per item
         {
-            const int G4 = nkv4 / 4;
+            const int G4 = nkv4 / 4, P4 = R1p / 4;
             const FastDiv dg = fast_div(G4);
-            for (int idx = tid; idx < R1 * G4; idx += kFftThreads) {
-                const int pp = idx / dg, g = idx - pp * G4;
-                float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float *kr = Kq + pp * R1;
+            for (int idx = tid; idx < P4 * G4; idx += kFftThreads) {
+                const int p4 = idx / dg, g = idx - p4 * G4;
+                float4 acc[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 *kt = reinterpret_cast<const float4 *>(KT) + p4;
                 const float4 *cv = reinterpret_cast<const float4 *>(Cv) + g;
                 for (int q = 0; q < R1; ++q) {
-                    const float kk = kr[q];
+                    const float4 kk = kt[q * P4];
                     const float4 c = __ldg(cv + q * G4);
-                    acc.x = fmaf(kk, c.x, acc.x);
-                    acc.y = fmaf(kk, c.y, acc.y);
-                    acc.z = fmaf(kk, c.z, acc.z);
-                    acc.w = fmaf(kk, c.w, acc.w);
+                    const float k4[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        acc[a].x = fmaf(k4[a], c.x, acc[a].x);
+                        acc[a].y = fmaf(k4[a], c.y, acc[a].y);
+                        acc[a].z = fmaf(k4[a], c.z, acc[a].z);
+                        acc[a].w = fmaf(k4[a], c.w, acc[a].w);
+                    }
                 }
-                reinterpret_cast<float4 *>(A)[pp * G4 + g] = acc;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    if (4 * p4 + a < R1) reinterpret_cast<float4 *>(A)[(4 * p4 + a) * G4 + g] = acc[a];
             }
         }
         __syncthreads();
+        // Kf[4 i4 .. +3][4 g .. +3] per item
         {
             const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
-            const int U4 = hu4 / 4, V2 = (nkv + 1) / 2;
+            const int U4 = hu4 / 4, V4 = nkv4 / 4;
             const FastDiv du4 = fast_div(U4);
-            for (int idx = tid; idx < V2 * U4; idx += kFftThreads) {
-                const int i = idx / du4, g = idx - i * U4;
-                float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+            for (int idx = tid; idx < V4 * U4; idx += kFftThreads) {
+                const int i4 = idx / du4, g = idx - i4 * U4;
+                float4 acc[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 *av = reinterpret_cast<const float4 *>(A) + i4;
                 const float4 *cu = reinterpret_cast<const float4 *>(Cu) + g;
                 for (int pp = 0; pp < R1; ++pp) {
-                    const float2 av = *reinterpret_cast<const float2 *>(A + pp * nkv4 + 2 * i);
+                    const float4 aa = av[pp * V4];
                     const float4 c = __ldg(cu + pp * U4);
-                    a0.x = fmaf(av.x, c.x, a0.x); a0.y = fmaf(av.x, c.y, a0.y);
-                    a0.z = fmaf(av.x, c.z, a0.z); a0.w = fmaf(av.x, c.w, a0.w);
-                    a1.x = fmaf(av.y, c.x, a1.x); a1.y = fmaf(av.y, c.y, a1.y);
-                    a1.z = fmaf(av.y, c.z, a1.z); a1.w = fmaf(av.y, c.w, a1.w);
-                }
-                const float r0[4] = {a0.x, a0.y, a0.z, a0.w}, r1[4] = {a1.x, a1.y, a1.z, a1.w};
+                    const float a4[4] = {aa.x, aa.y, aa.z, aa.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int ku = 4 * g + e;
-                    if (ku > hu) continue;
-                    Kf[(2 * i) * G.pitch + ku] = r0[e] * kscale;
-                    if (2 * i + 1 < nkv) Kf[(2 * i + 1) * G.pitch + ku] = r1[e] * kscale;
+                    for (int a = 0; a < 4; ++a) {
+                        acc[a].x = fmaf(a4[a], c.x, acc[a].x);
+                        acc[a].y = fmaf(a4[a], c.y, acc[a].y);
+                        acc[a].z = fmaf(a4[a], c.z, acc[a].z);
+                        acc[a].w = fmaf(a4[a], c.w, acc[a].w);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int kv = 4 * i4 + a;
+                    if (kv >= nkv) continue;
+                    const float r4[4] = {acc[a].x, acc[a].y, acc[a].z, acc[a].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (4 * g + e <= hu) Kf[kv * G.pitch + 4 * g + e] = r4[e] * kscale;
                 }
             }
         }
