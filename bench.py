@@ -61,6 +61,8 @@ def _args():
                     help="single steps timed after the run for median / p10 / p90 (0: skip)")
     ap.add_argument("--scratch-gb", type=float, default=24.0,
                     help="plan scratch budget in GB (0 = library default)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations and the 32-plan batch (extra keys)")
     return ap.parse_args()
 
 
@@ -292,13 +294,43 @@ def _reference(args):
         dist.destroy_process_group()
 
 
-# DRAM bytes (read + write) of the tensor-core convolution per fluence-support
-# point and pass, from a one-pass ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the 256x256x160 two-arc plan at R = 20 px: forward
-# 12.03 (output write), adjoint 18.27 (gathered-gradient read + output write).
-# Valid for that workload and this kernel version only (None: not captured
-# for the current kernel, reported as null).
-_TRAFFIC_B_PER_SUPPORT_POINT = {"workload": "pelvis256x256x160_2x178cp_R4cm", "fwd": 12.03, "adj": 18.27}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from a
+# one-pass ncu capture of the 256x256x160 two-arc plan at R = 20 px, 178
+# control points per launch (profiles/dram_pelvis256_2x178_R20.md).  Each
+# entry holds the SHA-256 prefixes of the sources the kernel is built from; a
+# figure is reported only while the sources and the workload match the
+# capture, else null.
+_CAPTURES = {
+    "workload": "pelvis256x256x160_2x178cp_R4cm",
+    "conv_forward_fft": {"src": ("csrc/k_conv_fft.cu", "csrc/pdrt_impl.cuh"),
+                         "sha": "9ec6d5fb65467cdc+db019f146a4840ad", "bytes": 1.2745e9},
+    "conv_adjoint_fft": {"src": ("csrc/k_conv_fft.cu", "csrc/pdrt_impl.cuh"),
+                         "sha": "9ec6d5fb65467cdc+db019f146a4840ad", "bytes": 1.6840e9},
+    "gather_accumulate": {"src": ("csrc/k_gather.cu", "csrc/pdrt_impl.cuh"),
+                          "sha": "2ade7527b14ad64d+db019f146a4840ad", "bytes": 1.5945e9},
+    "gather_transpose": {"src": ("csrc/k_gather.cu", "csrc/pdrt_impl.cuh"),
+                         "sha": "2ade7527b14ad64d+db019f146a4840ad", "bytes": 1.9821e9},
+    "mag_transpose": {"src": ("csrc/k_adjoint.cu", "csrc/pdrt_impl.cuh"),
+                      "sha": "7e30bff0a6f71a37+db019f146a4840ad", "bytes": 0.4235e9},
+}
+
+
+def _src_sha(paths):
+    import hashlib
+    out = []
+    for rel in paths:
+        with open(os.path.join(ROOT, "paper_2512_18863_gb300", rel), "rb") as f:
+            out.append(hashlib.sha256(f.read()).hexdigest()[:16])
+    return "+".join(out)
+
+
+def _captured_bytes(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the capture, or None when the
+    workload or the kernel's sources differ from the captured ones."""
+    c = _CAPTURES.get(kernel)
+    if not c or workload != _CAPTURES["workload"] or _src_sha(c["src"]) != c["sha"]:
+        return None
+    return c["bytes"]
 
 
 def _warm_start(n_cases):
@@ -382,31 +414,10 @@ def _gpu(args):
     arcs_per_step = w.plan.n_cp / CP_PER_ARC
     value = whole_job_value(arcs_per_step, args.steps, world, ms_max)
 
-    # roofline of the dominant kernel: the per-slice convolution (forward and
-    # adjoint), on the tensor cores, or FP32 SIMT when they are off
-    conv_keys = ("conv_forward", "conv_adjoint", "conv_forward_tc", "conv_adjoint_tc")
-    conv_ms = sum(prof[k]["total_ms"] for k in conv_keys if k in prof)
-    conv_launches = sum(prof[k]["launches"] for k in conv_keys if k in prof)
-    tc_ms = sum(prof[k]["total_ms"] for k in ("conv_forward_tc", "conv_adjoint_tc") if k in prof)
-    flops_total = 2.0 * work["conv_flops"] * args.steps          # two convolution passes per step
-    achieved = flops_total / (conv_ms / 1e3) / 1e12
-    peaks = _measured_peaks()
-    if tc_ms > 0.5 * conv_ms:
-        # the convolution is timed inside a long step: the sustained peak
-        bound, peak = "tensor", peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0))
-        peak_src = ("measured bf16 dense sustained (MEASURED_PEAKS.json)"
-                    if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s bf16 sustained")
-    else:
-        bound, peak = "alu", SMS * FP32_LANES * 2 * 2070.0e6 / 1e12
-        peak_src = "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"
-    mma_flops = work.get("mma_flops", 0.0) * args.steps          # tensor FLOPs issued in the timed steps
-    traffic = None
-    if (_TRAFFIC_B_PER_SUPPORT_POINT and w.name == _TRAFFIC_B_PER_SUPPORT_POINT["workload"]
-            and tc_ms > 0.5 * conv_ms):
-        per_point = _TRAFFIC_B_PER_SUPPORT_POINT["fwd"] + _TRAFFIC_B_PER_SUPPORT_POINT["adj"]
-        traffic = per_point * work["support_points"] * args.steps / max(conv_launches, 1)
+    roofline = _roofline(prof, work, args.steps, w.name)
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps}
                for k, v in prof.items() if not k.startswith("_") and v["launches"]}
+    kernel_hbm = _kernel_hbm(prof, w.name)
     # per-step distribution (after the timed region, outside it)
     step_ms = (_step_stats(eng, leaves, jaws, mu, g, dose, flush, args.step_stats)
                if args.step_stats > 0 else None)
@@ -463,6 +474,11 @@ def _gpu(args):
     warm = None
     if rank == 0 and world == 1 and args.warm_cases > 0:
         warm = _warm_start(args.warm_cases)
+    eng.close()
+    sweep = batch32 = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        sweep = _config_sweep(args, w.name)
+        batch32 = _batch32(args, steps=3, warmup=1, report=False)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -470,34 +486,177 @@ def _gpu(args):
                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded pelvis phantom and VMAT arcs)",
                "config": _config(w, world),
-               "roofline": {"bound": bound, "kernel": "convolution (forward + adjoint)",
-                            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak, "traffic": traffic,
-                            "traffic_source": ("ncu DRAM bytes per support point at this workload, "
-                                               "scaled to the launch" if traffic else None),
-                            "peak_source": peak_src,
-                            "flops": "algorithmic: 2 (2R+1)^2 per fluence-support point per pass",
-                            "flops_per_launch": flops_total / max(conv_launches, 1),
-                            "ms_per_launch": conv_ms / max(conv_launches, 1),
-                            "fp32_alu_frac": achieved / (SMS * FP32_LANES * 2 * 2070.0e6 / 1e12),
-                            "tensor_issued_tflops": (mma_flops / (tc_ms / 1e3) / 1e12) if tc_ms else None},
+               "precision": {"dose": "FP32 throughout; the convolution by FP32 FFTs, the slices "
+                                     "beyond the FFT size limit on the tensor cores with a BF16 hi/lo "
+                                     "split (three products, FP32 accumulation)",
+                             "parity_bar": "max |dD| <= 1e-4 max D, gradients 1e-3 relative "
+                                           "(tests against the FP64 oracle)"},
+               "roofline": roofline, "kernel_hbm": kernel_hbm,
                "kernels": kernels, "work": work, "gpu_launches": launches,
-               "launch": {"scratch_gb": args.scratch_gb, "tc_phase": info.get("tc_phase"),
+               "launch": {"scratch_gb": args.scratch_gb,
+                          "fft_pmax": info.get("fft_pmax"), "fft_ctas_per_sm": info.get("fft_ctas_per_sm"),
+                          "tc_phase": info.get("tc_phase"),
                           "tc_ctas_per_sm": info.get("tc_ctas_per_sm"),
                           "simt_ctas_per_sm": info.get("simt_ctas_per_sm"),
                           "chunk_cp": info.get("chunk_cp")},
+               "configs": sweep, "batch32": batch32,
                "hbm_literal": hbm, "warm_start": warm, "step_ms": step_ms,
                "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
         print(json.dumps(out), flush=True)
-    eng.close()
     if world > 1:
         dist.destroy_process_group()
 
 
+def _roofline(prof, work, steps, workload):
+    """Roofline of the dominant kernel.  With the FFT path on it is the FFT
+    convolution, bound by the FP32 pipes: achieved = its algorithmic FLOPs
+    (work.fft_flops: 2 x 2.5 N log2 N per slice and direction for the real
+    2-D transforms, N = Pu Pv, plus the kernel spectrum's cosine sums and the
+    product) over its CUDA-event time, peak = 152 SM x 128 FP32 lanes x 2 FLOP
+    x 2070 MHz.  Otherwise the tensor-core convolution against the measured
+    sustained BF16 peak, with the direct convolution's 2 (2R+1)^2 FLOP per
+    support point.  The direct-convolution-equivalent rate of all
+    convolution kernels is reported beside it."""
+    ms = lambda keys: sum(prof[k]["total_ms"] for k in keys if k in prof)
+    ln = lambda keys: sum(prof[k]["launches"] for k in keys if k in prof)
+    fft_k, tc_k, simt_k = (("conv_forward_fft", "conv_adjoint_fft"), ("conv_forward_tc", "conv_adjoint_tc"),
+                           ("conv_forward", "conv_adjoint"))
+    fft_ms, tc_ms, conv_ms = ms(fft_k), ms(tc_k), ms(fft_k + tc_k + simt_k)
+    alu_peak = SMS * FP32_LANES * 2 * 2070.0e6 / 1e12
+    peaks = _measured_peaks()
+    direct = 2.0 * work["conv_flops"] * steps / (conv_ms / 1e3) / 1e12 if conv_ms else None
+    if fft_ms > 0.5 * conv_ms:
+        flops = work["fft_flops"] * steps
+        achieved = flops / (fft_ms / 1e3) / 1e12
+        n = max(ln(fft_k), 1)
+        fb, ab = _captured_bytes("conv_forward_fft", workload), _captured_bytes("conv_adjoint_fft", workload)
+        traffic = 0.5 * (fb + ab) if fb and ab else None
+        return {"bound": "alu", "kernel": "k_conv_fft (FFT convolution, forward + adjoint)",
+                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                "traffic": traffic,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, one-pass "
+                                   "capture at this workload, mean of forward and adjoint" if traffic else None),
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 FLOP x 2070 MHz",
+                "flops": "algorithmic FFT: 2 x 2.5 N log2 N per slice and direction (N = Pu Pv) "
+                         "+ kernel spectrum + product",
+                "flops_per_launch": flops / n, "ms_per_launch": fft_ms / n,
+                "tc_overflow_ms_per_step": tc_ms / steps,
+                "direct_equivalent_tflops": direct}
+    if tc_ms > 0.5 * conv_ms:
+        flops = 2.0 * work["conv_flops"] * steps
+        achieved = flops / (tc_ms / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        n = max(ln(tc_k), 1)
+        return {"bound": "tensor", "kernel": "k_conv_tc (tensor-core convolution, forward + adjoint)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "traffic_source": None,
+                "peak_source": ("measured bf16 dense sustained (MEASURED_PEAKS.json)"
+                                if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s bf16 sustained"),
+                "flops": "algorithmic: 2 (2R+1)^2 per fluence-support point per pass",
+                "flops_per_launch": flops / n, "ms_per_launch": tc_ms / n,
+                "tensor_issued_tflops": work.get("mma_flops", 0.0) * steps / (tc_ms / 1e3) / 1e12}
+    flops = 2.0 * work["conv_flops"] * steps
+    achieved = flops / (conv_ms / 1e3) / 1e12
+    n = max(ln(simt_k), 1)
+    return {"bound": "alu", "kernel": "k_conv (FP32 SIMT convolution, forward + adjoint)",
+            "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+            "traffic": None, "traffic_source": None,
+            "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 FLOP x 2070 MHz",
+            "flops": "algorithmic: 2 (2R+1)^2 per fluence-support point per pass",
+            "flops_per_launch": flops / n, "ms_per_launch": conv_ms / n}
+
+
+def _kernel_hbm(prof, workload):
+    """Achieved DRAM bandwidth of the HBM-side kernels against the measured
+    copy bandwidth: captured DRAM bytes per launch over the CUDA-event time
+    per launch (null when no capture of the current sources exists)."""
+    peak = _measured_peaks().get("hbm_gbs", 6800.0)
+    out = {}
+    names = {"gather_accumulate": "gather_accumulate", "gather_transpose": "gather_transpose",
+             "mag_transpose": "mag_transpose_param_grad", "conv_forward_fft": "conv_forward_fft",
+             "conv_adjoint_fft": "conv_adjoint_fft"}
+    for key, pk in names.items():
+        if pk not in prof or not prof[pk]["launches"]:
+            continue
+        b = _captured_bytes(key, workload)
+        launches = prof[pk]["launches"]
+        if key == "mag_transpose":   # the parameter-gradient launch (one per call) shares the timer
+            launches = max(launches * 2 // 3, 1)
+        per = prof[pk]["total_ms"] / launches
+        gbs = b / (per / 1e3) / 1e9 if b else None
+        out[key] = {"bytes_per_launch": b, "ms_per_launch": per, "achieved_gbs": gbs, "peak_gbs": peak,
+                    "frac": gbs / peak if gbs else None}
+    return out
+
+
+def _timed_steps(eng, leaves, jaws, mu, g, dose, flush, n, adjoint):
+    """Median device time of n single steps (CUDA events, L2 flushed before each)."""
+    import torch
+    ev = []
+    for _ in range(n):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        eng.forward(leaves, jaws, mu, out=dose)
+        if adjoint:
+            eng.backward(leaves, jaws, mu, g)
+        b.record()
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+
+def _config_sweep(args, headline):
+    """The other dose configurations, each on its own plan: the two-arc plan
+    at the kernel radii 2 and 8 cm (forward and forward + adjoint), the
+    178-CP arc on 128x128x96 at 3 mm (forward) and the static 10 x 10 cm
+    field on 64^3 water (forward).  Median of 5 single steps after 2 warm-ups."""
+    import torch
+
+    from paper_2512_18863_gb300.engine import DoseEngine
+    cases = [("pelvis256", 2.0, True), ("pelvis256", 8.0, True), ("pelvis128", 4.0, False),
+             ("water64", 2.0, False)]
+    out = {}
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    for name, r_cm, adj in cases:
+        w = _workload(r_cm, name)
+        if w.name == headline:
+            continue
+        eng = DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso,
+                         scratch_budget_bytes=int(args.scratch_gb * 1e9))
+        dev = eng.device
+        t = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+        leaves, jaws, mu = t(w.plan.leaves), t(w.plan.jaws), t(w.plan.mu)
+        dose = eng.forward(leaves, jaws, mu)
+        masks = {k: torch.tensor(v, device=dev) for k, v in w.phantom.masks.items()}
+        g = _objective_grad(dose, masks, torch)
+        for _ in range(2):
+            eng.forward(leaves, jaws, mu, out=dose)
+            if adj:
+                eng.backward(leaves, jaws, mu, g)
+        row = {"n_cp": int(w.plan.n_cp), "kernel_radius_px": int(w.machine.r_px),
+               "forward_ms": _timed_steps(eng, leaves, jaws, mu, g, dose, flush, 5, False)}
+        arcs = w.plan.n_cp / CP_PER_ARC
+        row["forward_arc_evals_per_s"] = arcs / (row["forward_ms"] / 1e3)
+        if adj:
+            row["forward_adjoint_ms"] = _timed_steps(eng, leaves, jaws, mu, g, dose, flush, 5, True)
+            row["forward_adjoint_arc_evals_per_s"] = arcs / (row["forward_adjoint_ms"] / 1e3)
+        row["fft_pmax"] = eng.info.get("fft_pmax")
+        out[w.name] = row
+        eng.close()
+    return out
+
+
 def _gpu_batch(args):
+    _batch32(args, args.steps, args.warmup, report=True)
+
+
+def _batch32(args, steps, warmup, report):
     """32 plans of uneven grids (96..256 voxels per axis, 2-3 mm) and arcs
     (90-356 CPs): per-plan schedules from the autotuner, then forward +
-    adjoint of all plans per CUDA-graph launch."""
+    adjoint of all plans per CUDA-graph launch.  report: print its own JSON
+    line; else return the figures (extra keys of the headline line)."""
     import torch
 
     from paper_2512_18863_gb300 import synth
@@ -519,7 +678,7 @@ def _gpu_batch(args):
         grads.append(g)
     batch = DoseBatch(engines, [w.plan.leaves for w in ws], [w.plan.jaws for w in ws],
                       [w.plan.mu for w in ws], grads, n_branches=4)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.launch()
     torch.cuda.synchronize()
     lat = []
@@ -527,7 +686,7 @@ def _gpu_batch(args):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     total_ms = 0.0
-    for _ in range(args.steps):
+    for _ in range(steps):
         e0.record()
         batch.launch()
         e1.record()
@@ -536,11 +695,24 @@ def _gpu_batch(args):
     clk = clocks.stop()
     lat = np.concatenate(lat)
     n_cp = sum(w.plan.n_cp for w in ws)
+    if not report:
+        res = {"plans": len(ws), "control_points": n_cp, "steps": steps,
+               "plan_evals_per_s": len(ws) * steps / (total_ms / 1e3),
+               "arc_evals_per_s": n_cp / CP_PER_ARC * steps / (total_ms / 1e3),
+               "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                              "max": float(lat.max())},
+               "graph_launch_ms": total_ms / steps, "kernels_per_launch": batch.kernels,
+               "schedules": [{"fft_pmax": e.info["fft_pmax"], "tensor_cores": e.info["tensor_cores"],
+                              "chunk_cp": e.info["chunk_cp"]} for e in engines]}
+        batch.close()
+        for e in engines:
+            e.close()
+        return res
     if rank == 0:
         out = {"metric": "batched dose evals/sec fwd+adjoint (32 uneven plans, one CUDA-graph launch)",
-               "value": len(ws) * args.steps * world / (total_ms / 1e3), "unit": "plan evals/s",
-               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-               "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "value": len(ws) * steps * world / (total_ms / 1e3), "unit": "plan evals/s",
+               "n_gpus": world, "steps": steps, "warmup": warmup,
+               "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f32",
                "data": "synthetic (seeded pelvis phantoms, uneven grids and arcs)",
                "config": {"workload": "batch32_uneven", "plans": len(ws), "control_points": n_cp,
@@ -550,8 +722,8 @@ def _gpu_batch(args):
                                          "tc_ctas_per_sm": e.info["tc_ctas_per_sm"]} for e in engines]},
                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                               "max": float(lat.max())},
-               "arc_evals_per_s": n_cp / CP_PER_ARC * args.steps * world / (total_ms / 1e3),
-               "gpu_launches": batch.kernels * args.steps, "graph_launches": args.steps,
+               "arc_evals_per_s": n_cp / CP_PER_ARC * steps * world / (total_ms / 1e3),
+               "gpu_launches": batch.kernels * steps, "graph_launches": steps,
                "clocks": clk}
         print(json.dumps(out), flush=True)
     batch.close()
