@@ -293,53 +293,28 @@ struct OutCtx {
     int out_w, in_i0, out_i0, out_i1, pu;
 };
 
-// The transforms of a batch that one warp owns: [first, first + count),
-// balanced over the warps (the first n % W warps take one more).
-struct Owned {
-    int first, count;
-};
-__device__ __forceinline__ Owned owned(int n, int w, int W)
-{
-    const int base = n / W, extra = n - base * W;
-    return {w * base + min(w, extra), base + (w < extra ? 1 : 0)};
-}
-
-// One radix-R pass over the transforms a warp owns (the warp's lanes loop
-// over their butterflies; the caller separates passes with __syncwarp).
-//   COLS = false: transforms are S rows (row0 + t) % pv, t in the owned
-//                 range, length hu, elements contiguous;
-//   COLS = true : transforms are columns t of S, length pv, stride pitch.
-//   INV  = false: decimation in frequency (DFT then twiddle W_L^{jq});
-//   INV  = true : decimation in time (conjugate twiddle W_L^{-jm}, then DFT).
-// L is the pass's block size; the twiddle W_L^e = T[e (N / L) tmul] with T
-// the table of exp(-2 pi i t / (N tmul)).  Rows at or past `valid` of a
-// column read as zero (first forward column pass).  MUL (first inverse
-// column pass): every element read is first multiplied by the kernel
-// spectrum.  OUT (last inverse row pass): results go to the output box.
-template <int R, bool COLS, bool INV, bool MUL, bool OUT>
-__device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &G, Owned own, int row0, int N,
+template <int R, bool COLS, bool INV, bool MUL, bool OUT = false>
+__device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &G, int n_tr, int row0, int N,
                                          int L, const float2 *__restrict__ T, int tmul,
                                          const float *__restrict__ Kf, const short *__restrict__ kv_of,
-                                         const short *__restrict__ ku_of, int valid, const OutCtx *oc)
+                                         const short *__restrict__ ku_of, int valid = 1 << 30,
+                                         const OutCtx *oc = nullptr)
 {
-    if (own.count <= 0) return;
     const int M = L / R;
     const int per_tr = N / R;
-    const int total = own.count * per_tr;
+    const int total = n_tr * per_tr;
     const int tstep = (N / L) * tmul;
-    const FastDiv div_tr = fast_div(COLS ? own.count : per_tr), div_m = fast_div(M);
-    const int lane = threadIdx.x & 31;
-    for (int b = lane; b < total; b += 32) {
+    const FastDiv div_tr = fast_div(COLS ? n_tr : per_tr), div_m = fast_div(M);
+    for (int b = threadIdx.x; b < total; b += kFftThreads) {
         const int q0 = b / div_tr;
-        int tl, t;
+        int tr, t;
         if (COLS) {
             t = q0;
-            tl = b - q0 * own.count;
+            tr = b - q0 * n_tr;
         } else {
-            tl = q0;
+            tr = q0;
             t = b - q0 * per_tr;
         }
-        const int tr = own.first + tl;
         const int blk = t / div_m, j = t - blk * M;
         const int e0 = blk * L + j;
         float2 *base;
@@ -406,13 +381,13 @@ __device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &
     }
 }
 
-template <bool COLS, bool INV, bool MUL, bool OUT>
-__device__ __forceinline__ void fft_pass_r(int R, float2 *S, const FftGeom &G, Owned own, int row0, int N, int L,
+template <bool COLS, bool INV, bool MUL, bool OUT = false>
+__device__ __forceinline__ void fft_pass_r(int R, float2 *S, const FftGeom &G, int n_tr, int row0, int N, int L,
                                            const float2 *T, int tmul, const float *Kf, const short *kv_of,
-                                           const short *ku_of, int valid, const OutCtx *oc)
+                                           const short *ku_of, int valid = 1 << 30, const OutCtx *oc = nullptr)
 {
 #define PDRT_FFT_PASS(RR) \
-    fft_pass<RR, COLS, INV, MUL, OUT>(S, G, own, row0, N, L, T, tmul, Kf, kv_of, ku_of, valid, oc)
+    fft_pass<RR, COLS, INV, MUL, OUT>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of, valid, oc)
     switch (R) {
     case 3: PDRT_FFT_PASS(3); break;
     case 4: PDRT_FFT_PASS(4); break;
@@ -426,38 +401,39 @@ __device__ __forceinline__ void fft_pass_r(int R, float2 *S, const FftGeom &G, O
 #undef PDRT_FFT_PASS
 }
 
-// Whole transform of length N over the transforms a warp owns, passes
-// separated by __syncwarp: forward (DIF, natural in, digit-reversed out;
-// rows at or past `valid` of a column read as zero in the first pass) or
-// inverse (DIT, digit-reversed in, natural out; the first inverse column
-// pass applies the kernel spectrum; with an output context the last
-// inverse row pass writes the output box instead of S).
+// Whole transform of length N over a batch: forward (DIF, natural in,
+// digit-reversed out; rows at or past `valid` of a column read as zero in the
+// first pass) or inverse (DIT, digit-reversed in, natural out; the first
+// inverse column pass applies the kernel spectrum; with an output context the
+// last inverse row pass writes the output box instead of S).
 template <bool COLS, bool INV>
-__device__ __forceinline__ void fft_run(float2 *S, const FftGeom &G, Owned own, int row0, int N, const float2 *T,
-                                        int tmul, const float *Kf, const short *kv_of, const short *ku_of,
-                                        int valid = 1 << 30, const OutCtx *oc = nullptr)
+__device__ void fft_run(float2 *S, const FftGeom &G, int n_tr, int row0, int N, const float2 *T, int tmul,
+                        const float *Kf, const short *kv_of, const short *ku_of, int valid = 1 << 30,
+                        const OutCtx *oc = nullptr)
 {
     const Radices rd = radices_of(N);
     const int r0 = rd.r[0], L1 = N / r0;
     if (!INV) {
-        fft_pass_r<COLS, false, false, false>(r0, S, G, own, row0, N, N, T, tmul, Kf, kv_of, ku_of, valid, oc);
+        fft_pass_r<COLS, false, false>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of, valid);
+        __syncthreads();
         if (rd.np > 1) {
-            __syncwarp();
-            fft_pass_r<COLS, false, false, false>(rd.r[1], S, G, own, row0, N, L1, T, tmul, Kf, kv_of, ku_of,
-                                                  1 << 30, oc);
+            fft_pass_r<COLS, false, false>(rd.r[1], S, G, n_tr, row0, N, L1, T, tmul, Kf, kv_of, ku_of);
+            __syncthreads();
         }
     } else {
         if (rd.np > 1) {
-            fft_pass_r<COLS, true, COLS, false>(rd.r[1], S, G, own, row0, N, L1, T, tmul, Kf, kv_of, ku_of,
-                                                1 << 30, oc);
-            __syncwarp();
+            fft_pass_r<COLS, true, COLS>(rd.r[1], S, G, n_tr, row0, N, L1, T, tmul, Kf, kv_of, ku_of);
+            __syncthreads();
         }
-        if (!COLS && oc)
-            fft_pass_r<false, true, false, true>(r0, S, G, own, row0, N, N, T, tmul, Kf, kv_of, ku_of, 1 << 30, oc);
-        else if (rd.np > 1)
-            fft_pass_r<COLS, true, false, false>(r0, S, G, own, row0, N, N, T, tmul, Kf, kv_of, ku_of, 1 << 30, oc);
-        else
-            fft_pass_r<COLS, true, COLS, false>(r0, S, G, own, row0, N, N, T, tmul, Kf, kv_of, ku_of, 1 << 30, oc);
+        if (!COLS && oc) {
+            fft_pass_r<false, true, false, true>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of, 1 << 30,
+                                                 oc);
+        } else if (rd.np > 1) {
+            fft_pass_r<COLS, true, false>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
+        } else {
+            fft_pass_r<COLS, true, COLS>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
+        }
+        __syncthreads();
     }
 }
 
@@ -576,41 +552,29 @@ cudaError_t conv_fft_tables_upload()
 }
 
 // shared memory of k_conv_fft for a size limit pmax and kernel half-width R:
-// header, kernel spectrum Kf, forward fill tables, the spectrum's scratch
-// K^T [R+1][R1p] and A [R1p][P/2+1 rounded to 4], the complex work array
+// header, kernel spectrum, forward fill tables and the complex work array
+// (which first holds the spectrum's scratch K [R+1][R+1] and A [R+1][P/2+1])
 int conv_fft_smem_bytes(int pmax, int R)
 {
-    const int hu = pmax / 2, r1 = R + 1, r1p = (r1 + 3) & ~3, w4 = ((hu + 1) + 3) & ~3;
+    const int hu = pmax / 2, r1 = R + 1, w4 = ((hu + 1) + 3) & ~3;
     const int kf = (pmax / 2 + 1) * (hu + 1) * 4;               // Kf [kv'][ku]
     const int ft = 4 * pmax * 8;                                // forward fill tables
-    const int ka = (r1 * r1p + r1p * w4) * 4;                   // K^T and A
-    const int s = pmax * (hu + 1) * 8;                          // S [pv][hu + 1] complex
+    const int scratch = (r1 * ((r1 + 3) & ~3) + ((r1 + 3) & ~3) * w4) * 4;
+    const int s = std::max(pmax * (hu + 1) * 8, scratch);       // S [pv][hu + 1] complex
     auto al = [](int x) { return (x + 15) & ~15; };
-    return 64 + al(kf) + ft + al(ka) + al(s);
+    return 64 + al(kf) + ft + al(s);
 }
 
-// One CTA per slice at a time (persistent over a work counter), eight warps.
-// Five phases separated by block barriers; inside a phase every warp works
-// on the rows or columns it owns, its passes separated by __syncwarp:
-//   1. kernel values K^T and the fill tables (block-wide);
-//   2. A = K Cv (block-wide tiles); each warp fills its input rows, runs the
-//      row FFTs and the real-FFT split on them;
-//   3. Kf (block-wide tiles); each warp runs the forward column FFTs of its
-//      columns;
-//   4. each warp multiplies its columns by Kf and runs the inverse FFTs;
-//   5. each warp runs the inverse real FFT of its output rows and writes them.
 template <bool ADJ>
 __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, int nb, int pmax,
                                                             unsigned int *__restrict__ counter,
                                                             int *__restrict__ over_list,
                                                             unsigned int *__restrict__ over_count)
 {
-    constexpr int W = kFftThreads / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     const Lattice &L = P.lat;
     const int R = P.mach.R, R1 = R + 1;
-    const int R1p = (R1 + 3) & ~3;
-    const int hmax = pmax / 2, w4max = ((hmax + 1) + 3) & ~3;
+    const int hmax = pmax / 2;
     auto al = [](int x) { return (x + 15) & ~15; };
     int *s_item = reinterpret_cast<int *>(smem);
     unsigned char *p = smem + 64;
@@ -621,11 +585,11 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
     int2 *fv_idx = reinterpret_cast<int2 *>(fu_w + pmax);
     float2 *fv_w = reinterpret_cast<float2 *>(fv_idx + pmax);
     p += 4 * pmax * 8;
-    float *KT = reinterpret_cast<float *>(p);        // [q][p], rows of R1p
-    float *A = KT + R1 * R1p;                        // [p][kv'] (16-byte aligned rows)
-    p += al((R1 * R1p + R1p * w4max) * 4);
     float2 *S = reinterpret_cast<float2 *>(p);
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R1p = (R1 + 3) & ~3;
+    float *KT = reinterpret_cast<float *>(S);        // spectrum scratch before the fill: [q][p]
+    float *A = KT + R1 * R1p;                        // [p][kv'] (16-byte aligned rows)
+    const int tid = threadIdx.x;
     const int n_items = nb * L.nw;
     const bool sym = L.du == L.dv;                   // K(p, q) = K(q, p)
 
@@ -659,11 +623,10 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
         const float *Cv = P.fft_cos + ov.cos;        // [q][kv'], c_q folded in
         const float *Cu = P.fft_cos + ou.cos;        // [p][ku], c_p folded in
 
-        // ---- phase 1: kernel values K(p, q) (the expressions of the other
-        // convolution kernels), stored transposed with zero padding columns,
-        // and the forward fill tables: per input column n the two fluence rows
-        // of its bilinear stencil (clamped into the support box) with their
-        // weights (zero outside the box), likewise per input row
+        // Kernel spectrum: K(p, q) (the expressions of the other convolution
+        // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
+        // K is stored transposed, KT[q][p] (rows of R1p = R1 rounded up to 4),
+        // so that both products read 4-wide vectors of each operand.
         for (int idx = tid; idx < R1 * R1; idx += kFftThreads) {
             const int pp = idx / R1, q = idx - pp * R1;
             if (sym && pp > q) continue;
@@ -674,35 +637,12 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
             KT[q * R1p + pp] = kv;
             if (sym) KT[pp * R1p + q] = kv;
         }
-        for (int idx = tid; idx < R1 * (R1p - R1); idx += kFftThreads) {
+        for (int idx = tid; idx < R1 * (R1p - R1); idx += kFftThreads) {   // zero padding columns
             const int q = idx / (R1p - R1);
             KT[q * R1p + R1 + (idx - q * (R1p - R1))] = 0.f;
         }
-        if (!ADJ) {
-            const CpTab &ct = P.cptab[b];
-            for (int t = tid; t < wi + G.n_rows_in; t += kFftThreads) {
-                const bool col = t < wi;
-                const int lo = col ? ct.fa0 : ct.fc0, hi = col ? ct.fa1 : ct.fc1;
-                const int idx0 = col ? bx.in_i0 + t : bx.in_j0 + (t - wi);
-                const float f = col ? mag_coord(st.m, idx0, L.cu) : mag_coord(st.m, idx0, L.cv);
-                const float fl = floorf(f);
-                const int a0 = (int)fl;
-                const float tw = f - fl;
-                const bool ok0 = a0 >= lo && a0 < hi, ok1 = a0 + 1 >= lo && a0 + 1 < hi;
-                const int i0 = min(max(a0 - lo, 0), hi - lo - 1), i1 = min(max(a0 + 1 - lo, 0), hi - lo - 1);
-                const float w0 = ok0 ? 1.f - tw : 0.f, w1 = ok1 ? tw : 0.f;
-                if (col) {
-                    fu_idx[t] = make_int2(i0, i1);
-                    fu_w[t] = make_float2(w0, w1);
-                } else {
-                    fv_idx[t - wi] = make_int2(i0, i1);
-                    fv_w[t - wi] = make_float2(w0, w1);
-                }
-            }
-        }
         __syncthreads();
-
-        // ---- phase 2: A[4 p4 .. +3][4 g .. +3] per tile (A = K Cv)
+        // A[4 p4 .. +3][4 g .. +3] per item
         {
             const int G4 = nkv4 / 4, P4 = R1p / 4;
             const FastDiv dg = fast_div(G4);
@@ -730,79 +670,8 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
                     if (4 * p4 + a < R1) reinterpret_cast<float4 *>(A)[(4 * p4 + a) * G4 + g] = acc[a];
             }
         }
-        // each warp: its input rows (j = v offset from the input box), packed
-        // (x[2m], x[2m+1]) along u, row FFTs and the real-FFT split; the rows
-        // past the input are never written (the first column pass reads them
-        // as zero)
-        const Owned rows = owned(G.n_rows_in, warp, W);
-        {
-            const FastDiv dh = fast_div(hu);
-            const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
-            const int Fc = P.cptab[b].fc1 - P.cptab[b].fc0;
-            const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
-            const int h_w = st.oi1 - st.oi0;
-            for (int t = lane; t < rows.count * hu; t += 32) {
-                const int jl = t / dh, m = t - jl * hu, j = rows.first + jl;
-                float x[2] = {0.f, 0.f};
-                int2 ci = make_int2(0, 0);
-                float2 cw = make_float2(0.f, 0.f);
-                if (!ADJ) {
-                    ci = fv_idx[j];
-                    cw = fv_w[j];
-                }
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int n = 2 * m + e;
-                    if (n >= wi) continue;
-                    if (ADJ) {
-                        x[e] = hsrc[(long long)(bx.in_j0 + j - st.oj0) * h_w + (bx.in_i0 + n - st.oi0)];
-                    } else {
-                        const int2 ai = fu_idx[n];
-                        const float2 aw = fu_w[n];
-                        const float *r0 = fmap + (long long)ai.x * Fc, *r1 = fmap + (long long)ai.y * Fc;
-                        x[e] = aw.x * (cw.x * __ldg(r0 + ci.x) + cw.y * __ldg(r0 + ci.y)) +
-                               aw.y * (cw.x * __ldg(r1 + ci.x) + cw.y * __ldg(r1 + ci.y));
-                    }
-                }
-                S[j * G.pitch + m] = make_float2(x[0], x[1]);
-            }
-        }
-        __syncwarp();
-        fft_run<false, false>(S, G, rows, 0, hu, Tu, 2, Kf, kv_of, ku_of);
-        __syncwarp();
-        // real-FFT split: X[k] = E_k + W^k O_k and X[hu - k] = conj(E_k - W^k O_k),
-        // E_k = (Z_k + conj Z_{hu-k}) / 2, O_k = (Z_k - conj Z_{hu-k}) / (2i),
-        // W = exp(-2 pi i / pu); X[hu] goes to column hu
-        {
-            const int half = hu / 2 + 1;
-            const FastDiv dhf = fast_div(half);
-            for (int t = lane; t < rows.count * half; t += 32) {
-                const int jl = t / dhf, kk = t - jl * half;
-                float2 *row = S + (rows.first + jl) * G.pitch;
-                if (kk == 0) {
-                    const int p0 = __ldg(pos_u);
-                    const float2 z = row[p0];
-                    row[p0] = make_float2(z.x + z.y, 0.f);
-                    row[hu] = make_float2(z.x - z.y, 0.f);
-                    continue;
-                }
-                const int pk = __ldg(pos_u + kk), pc = __ldg(pos_u + hu - kk);
-                const float2 zk = row[pk], zc = cconj(row[pc]);
-                const float2 E = cscale(cadd(zk, zc), 0.5f);
-                const float2 d = cscale(csub(zk, zc), 0.5f);
-                const float2 O = make_float2(d.y, -d.x);   // d / i
-                const float2 WO = cmul(__ldg(Tu + kk), O);
-                row[pk] = cadd(E, WO);
-                if (pc != pk) row[pc] = cconj(csub(E, WO));
-            }
-        }
         __syncthreads();
-
-        // ---- phase 3: Kf[4 i4 .. +3][4 g .. +3] per tile (Kf = scale / (pu pv)
-        // Cu^T A), and each warp's forward column FFTs (rows past the input
-        // read as zero)
-        const Owned cols = owned(hu + 1, warp, W);
-        fft_run<true, false>(S, G, cols, 0, pv, Tv, 1, Kf, kv_of, ku_of, G.n_rows_in);
+        // Kf[4 i4 .. +3][4 g .. +3] per item
         {
             const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
             const int U4 = hu4 / 4, V4 = nkv4 / 4;
@@ -837,25 +706,111 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
                 }
             }
         }
+        // fill tables (forward): per input column n the two fluence rows a of
+        // its bilinear stencil (clamped into the support box) with their
+        // weights (zero outside the box), likewise per input row j
+        if (!ADJ) {
+            const CpTab &ct = P.cptab[b];
+            for (int t = tid; t < wi + G.n_rows_in; t += kFftThreads) {
+                const bool col = t < wi;
+                const int lo = col ? ct.fa0 : ct.fc0, hi = col ? ct.fa1 : ct.fc1;
+                const int idx0 = col ? bx.in_i0 + t : bx.in_j0 + (t - wi);
+                const float f = col ? mag_coord(st.m, idx0, L.cu) : mag_coord(st.m, idx0, L.cv);
+                const float fl = floorf(f);
+                const int a0 = (int)fl;
+                const float tw = f - fl;
+                const bool ok0 = a0 >= lo && a0 < hi, ok1 = a0 + 1 >= lo && a0 + 1 < hi;
+                const int i0 = min(max(a0 - lo, 0), hi - lo - 1), i1 = min(max(a0 + 1 - lo, 0), hi - lo - 1);
+                const float w0 = ok0 ? 1.f - tw : 0.f, w1 = ok1 ? tw : 0.f;
+                if (col) {
+                    fu_idx[t] = make_int2(i0, i1);
+                    fu_w[t] = make_float2(w0, w1);
+                } else {
+                    fv_idx[t - wi] = make_int2(i0, i1);
+                    fv_w[t - wi] = make_float2(w0, w1);
+                }
+            }
+        }
         __syncthreads();
 
-        // ---- phase 4: each warp's columns: product with Kf and inverse FFTs
-        __syncwarp();
-        fft_run<true, true>(S, G, cols, 0, pv, Tv, 1, Kf, kv_of, ku_of);
+        // fill the input rows (j = v offset from the input box), packed
+        // (x[2m], x[2m+1]) along u; the rows past them are never written: the
+        // first column pass reads them as zero
+        {
+            const int n_fill = G.n_rows_in * hu;
+            const FastDiv dh = fast_div(hu);
+            const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
+            const int Fc = P.cptab[b].fc1 - P.cptab[b].fc0;
+            const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
+            const int h_w = st.oi1 - st.oi0;
+            for (int idx = tid; idx < n_fill; idx += kFftThreads) {
+                const int j = idx / dh, m = idx - j * hu;
+                float x[2] = {0.f, 0.f};
+                int2 ci = make_int2(0, 0);
+                float2 cw = make_float2(0.f, 0.f);
+                if (!ADJ) {
+                    ci = fv_idx[j];
+                    cw = fv_w[j];
+                }
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int n = 2 * m + e;
+                    if (n >= wi) continue;
+                    if (ADJ) {
+                        x[e] = hsrc[(long long)(bx.in_j0 + j - st.oj0) * h_w + (bx.in_i0 + n - st.oi0)];
+                    } else {
+                        const int2 ai = fu_idx[n];
+                        const float2 aw = fu_w[n];
+                        const float *r0 = fmap + (long long)ai.x * Fc, *r1 = fmap + (long long)ai.y * Fc;
+                        x[e] = aw.x * (cw.x * __ldg(r0 + ci.x) + cw.y * __ldg(r0 + ci.y)) +
+                               aw.y * (cw.x * __ldg(r1 + ci.x) + cw.y * __ldg(r1 + ci.y));
+                    }
+                }
+                S[j * G.pitch + m] = make_float2(x[0], x[1]);
+            }
+        }
         __syncthreads();
-
-        // ---- phase 5: each warp's output rows: inverse real FFT
-        // Z[k] = (X_k + conj X_{hu-k}) + i exp(2 pi i k / pu) (X_k - conj X_{hu-k}),
-        // stored at pos_u(k), then the inverse row FFTs; the last pass writes
-        // the output box: (u, v) holds real sample (u - in_i0) mod pu of row
-        // (v - in_j0) mod pv
-        const Owned orows = owned(G.n_rows_out, warp, W);
+        // rows: complex FFT of length hu over the input rows
+        fft_run<false, false>(S, G, G.n_rows_in, 0, hu, Tu, 2, Kf, kv_of, ku_of);
+        // real-FFT split: X[k] = E_k + W^k O_k and X[hu - k] = conj(E_k - W^k O_k),
+        // E_k = (Z_k + conj Z_{hu-k}) / 2, O_k = (Z_k - conj Z_{hu-k}) / (2i),
+        // W = exp(-2 pi i / pu); X[hu] goes to column hu
         {
             const int half = hu / 2 + 1;
             const FastDiv dhf = fast_div(half);
-            for (int t = lane; t < orows.count * half; t += 32) {
-                const int rl = t / dhf, kk = t - rl * half;
-                int row_i = G.out_row0 + orows.first + rl;
+            for (int idx = tid; idx < G.n_rows_in * half; idx += kFftThreads) {
+                const int j = idx / dhf, kk = idx - j * half;
+                float2 *row = S + j * G.pitch;
+                if (kk == 0) {
+                    const int p0 = __ldg(pos_u);
+                    const float2 z = row[p0];
+                    row[p0] = make_float2(z.x + z.y, 0.f);
+                    row[hu] = make_float2(z.x - z.y, 0.f);
+                    continue;
+                }
+                const int pk = __ldg(pos_u + kk), pc = __ldg(pos_u + hu - kk);
+                const float2 zk = row[pk], zc = cconj(row[pc]);
+                const float2 E = cscale(cadd(zk, zc), 0.5f);
+                const float2 d = cscale(csub(zk, zc), 0.5f);
+                const float2 O = make_float2(d.y, -d.x);   // d / i
+                const float2 WO = cmul(__ldg(Tu + kk), O);
+                row[pk] = cadd(E, WO);
+                if (pc != pk) row[pc] = cconj(csub(E, WO));
+            }
+        }
+        __syncthreads();
+        // columns: forward FFT of length pv (rows past the input read as
+        // zero), then product and inverse
+        fft_run<true, false>(S, G, hu + 1, 0, pv, Tv, 1, Kf, kv_of, ku_of, G.n_rows_in);
+        fft_run<true, true>(S, G, hu + 1, 0, pv, Tv, 1, Kf, kv_of, ku_of);
+        // inverse real FFT of the output rows: Z[k] = (X_k + conj X_{hu-k})
+        // + i exp(2 pi i k / pu) (X_k - conj X_{hu-k}), stored at pos_u(k)
+        {
+            const int half = hu / 2 + 1;
+            const FastDiv dhf = fast_div(half);
+            for (int idx = tid; idx < G.n_rows_out * half; idx += kFftThreads) {
+                const int rr = idx / dhf, kk = idx - rr * half;
+                int row_i = G.out_row0 + rr;
                 if (row_i >= pv) row_i -= pv;
                 float2 *row = S + row_i * G.pitch;
                 const int pk = __ldg(pos_u + kk);
@@ -875,7 +830,9 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
+        // inverse rows; the last pass writes the output box:
+        // (u, v) holds real sample (u - in_i0) mod pu of row (v - in_j0) mod pv
         OutCtx oc;
         oc.dst = ADJ ? P.adjbuf + (long long)bl * P.cap_a + st.off_a
                      : P.region + (long long)bl * P.cap_o + st.off_o;
@@ -884,7 +841,7 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
         oc.out_i0 = bx.out_i0;
         oc.out_i1 = bx.out_i1;
         oc.pu = pu;
-        fft_run<false, true>(S, G, orows, G.out_row0, hu, Tu, 2, Kf, kv_of, ku_of, 1 << 30, &oc);
+        fft_run<false, true>(S, G, G.n_rows_out, G.out_row0, hu, Tu, 2, Kf, kv_of, ku_of, 1 << 30, &oc);
     }
 }
 
