@@ -565,8 +565,11 @@ int conv_fft_smem_bytes(int pmax, int R)
     return 64 + al(kf) + ft + al(s);
 }
 
-template <bool ADJ>
-__global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, int nb, int pmax,
+// MINB: resident CTAs per SM the register budget is sized for (launch
+// bounds); the launcher picks the instantiation that matches what the size
+// limit's shared memory allows (fewer resident CTAs leave more registers).
+template <bool ADJ, int MINB>
+__global__ void __launch_bounds__(kFftThreads, MINB) k_conv_fft(PlanDev P, int b0, int nb, int pmax,
                                                             unsigned int *__restrict__ counter,
                                                             int *__restrict__ over_list,
                                                             unsigned int *__restrict__ over_count)
@@ -845,43 +848,89 @@ __global__ void __launch_bounds__(kFftThreads, 3) k_conv_fft(PlanDev P, int b0, 
     }
 }
 
+namespace {
+
+// resident CTAs per SM that the shared memory of a size limit allows
+int fft_ctas_by_smem(int pmax, int R, int smem_sm, int resv)
+{
+    return smem_sm / (conv_fft_smem_bytes(pmax, R) + resv);
+}
+
+template <bool ADJ>
+const void *fft_kernel_for(int minb)
+{
+    if (minb >= 4) return (const void *)k_conv_fft<ADJ, 4>;
+    if (minb == 3) return (const void *)k_conv_fft<ADJ, 3>;
+    return (const void *)k_conv_fft<ADJ, 2>;
+}
+
+struct SmemLimits {
+    int smem_sm, resv, regs_sm, optin;
+};
+
+cudaError_t smem_limits(SmemLimits &l)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l.resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l.regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return e;
+}
+
+}  // namespace
+
 cudaError_t launch_conv_fft(const PlanDev &P, int b0, int nb, bool adjoint, int pmax, unsigned int *counter,
                             int *over_list, unsigned int *over_count, int grid_blocks, cudaStream_t s)
 {
     const int smem = conv_fft_smem_bytes(pmax, P.mach.R);
-    if (adjoint)
-        k_conv_fft<true><<<grid_blocks, kFftThreads, smem, s>>>(P, b0, nb, pmax, counter, over_list, over_count);
-    else
-        k_conv_fft<false><<<grid_blocks, kFftThreads, smem, s>>>(P, b0, nb, pmax, counter, over_list, over_count);
-    return cudaGetLastError();
+    // the grid is (CTAs per SM) x SMs; the instantiation for that many CTAs
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int minb = grid_blocks / (sms > 0 ? sms : 1);
+    const void *k = adjoint ? fft_kernel_for<true>(minb) : fft_kernel_for<false>(minb);
+    void *args[] = {(void *)&P, (void *)&b0, (void *)&nb, (void *)&pmax, (void *)&counter, (void *)&over_list,
+                    (void *)&over_count};
+    return cudaLaunchKernel(k, dim3(grid_blocks), dim3(kFftThreads), args, smem, s);
 }
 
-// CTAs of one direction per SM at a size limit (shared memory, registers);
-// also uploads the size tables to the current device
+// CTAs of one direction per SM at a size limit: the shared memory decides
+// how many fit, the register-bound instantiation for that count (2, 3 or 4)
+// must also fit; also uploads the size tables to the current device
 cudaError_t conv_fft_ctas(int pmax, int R, bool adjoint, int *ctas)
 {
     *ctas = 0;
     if (!fft_size_for(pmax) || fft_size_for(pmax) != pmax || pmax < 2 * R + 2) return cudaSuccess;
     cudaError_t e = conv_fft_tables_upload();
     if (e != cudaSuccess) return e;
-    e = adjoint ? allow_full_smem(k_conv_fft<true>) : allow_full_smem(k_conv_fft<false>);
-    if (e != cudaSuccess) return e;
-    int dev = 0, smem_sm = 0, resv = 0, regs_sm = 0, optin = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, adjoint ? (const void *)k_conv_fft<true>
-                                                                  : (const void *)k_conv_fft<false>);
-    if (e != cudaSuccess) return e;
+    SmemLimits l;
+    if ((e = smem_limits(l)) != cudaSuccess) return e;
     const int smem = conv_fft_smem_bytes(pmax, R);
-    if (smem + (int)fa.sharedSizeBytes > optin) return cudaSuccess;
-    const int by_smem = smem_sm / (smem + (int)fa.sharedSizeBytes + resv);
+    if (smem > l.optin) return cudaSuccess;
+    const int want = std::min(4, fft_ctas_by_smem(pmax, R, l.smem_sm, l.resv));
+    if (want < 1) return cudaSuccess;
+    // every instantiation may be launched (the launcher picks by CTAs per SM)
+    for (int mb = 2; mb <= 4 && e == cudaSuccess; ++mb) {
+        const void *km = adjoint ? fft_kernel_for<true>(mb) : fft_kernel_for<false>(mb);
+        cudaFuncAttributes fm;
+        e = cudaFuncGetAttributes(&fm, km);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(km, cudaFuncAttributeMaxDynamicSharedMemorySize, l.optin - (int)fm.sharedSizeBytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(km, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared);
+    }
+    if (e != cudaSuccess) return e;
+    const void *k = adjoint ? fft_kernel_for<true>(want) : fft_kernel_for<false>(want);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+    const int by_smem = l.smem_sm / (smem + (int)fa.sharedSizeBytes + l.resv);
     const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
-    const int by_regs = regs_sm / (regs_warp * (kFftThreads / 32));
-    *ctas = by_smem < by_regs ? by_smem : by_regs;
+    const int by_regs = l.regs_sm / (regs_warp * (kFftThreads / 32));
+    *ctas = std::max(1, std::min(want, std::min(by_smem, by_regs)));
     return cudaSuccess;
 }
 
