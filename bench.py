@@ -677,7 +677,7 @@ def _batch32(args, steps, warmup, report):
         engines.append(e)
         grads.append(g)
     batch = DoseBatch(engines, [w.plan.leaves for w in ws], [w.plan.jaws for w in ws],
-                      [w.plan.mu for w in ws], grads, n_branches=4)
+                      [w.plan.mu for w in ws], grads, n_branches=len(ws))   # one branch per plan
     for _ in range(warmup):
         batch.launch()
     torch.cuda.synchronize()

@@ -401,13 +401,21 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
 /*
  * Batched launch (Sec. 2.2: the beam sequence is organised for batched
  * operation).  Records the forward dose -- and the adjoint for every i with
- * dose_grad_dev[i] != NULL -- of n independent plans into ONE CUDA graph whose
- * n_branches parallel branches run the plans concurrently; pdrt_batch_launch
- * replays it with a single graph launch.  Every array argument has n entries
- * (device pointers as in pdrt_dose_forward / pdrt_dose_backward); a plan may
- * appear once per batch; the buffers must stay valid while the batch exists.
- * The recording calls no cudaMalloc.  Errors: EINVAL (NULL, n < 1, repeated
- * plan, mismatched grid), ECUDA.
+ * dose_grad_dev[i] != NULL -- of n independent plans into ONE CUDA graph;
+ * pdrt_batch_launch replays it with a single graph launch.  The graph runs in
+ * rounds, round c covering the c-th pass of control points of every plan:
+ * the FFT convolution of all FFT plans' (plan, control point, slice) items of
+ * the round is ONE persistent launch pulling items from one work counter, and
+ * the per-plan kernels (projection, tables, tensor-core overflow or
+ * convolution, gathers, gradients) run on n_branches parallel branches.
+ * Each plan keeps the pass size (pdrt_plan_set_chunk) it had at creation.
+ * Every array argument has n entries (device pointers as in pdrt_dose_forward
+ * / pdrt_dose_backward); a plan may appear once per batch; plans, grids and
+ * buffers must stay valid and unchanged while the batch exists.  Creation
+ * allocates the batch's small device tables (plan descriptors, round
+ * entries, counters), freed by pdrt_batch_destroy; a launch allocates
+ * nothing.  Errors: EINVAL (NULL, n < 1, repeated plan, mismatched grid),
+ * ECUDA.
  */
 typedef struct pdrt_batch_s *pdrt_batch_t;
 pdrt_status pdrt_batch_create(pdrt_batch_t *out, int32_t n, const pdrt_grid_t *grids,
@@ -423,6 +431,10 @@ pdrt_status pdrt_batch_launch(pdrt_batch_t b, pdrt_stream_t stream);
 pdrt_status pdrt_batch_plan_times(pdrt_batch_t b, pdrt_stream_t stream, float *ms_out);
 /* Number of kernel nodes in the batch's graph (kernels run per launch). */
 int64_t pdrt_batch_kernels(pdrt_batch_t b);
+/* Control points per pass of plan i in the batch (0 if b is NULL or i is out
+ * of range).  A plan's dose and gradients equal, bit for bit, those of
+ * pdrt_dose_forward / pdrt_dose_backward at this pass size. */
+int32_t pdrt_batch_pass_cp(pdrt_batch_t b, int32_t i);
 void pdrt_batch_destroy(pdrt_batch_t b);
 
 /* Number of kernels this library has launched since it was loaded. */

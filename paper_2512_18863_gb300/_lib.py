@@ -106,6 +106,7 @@ _SIG = {
     "pdrt_batch_launch": (C.c_int, [_VP, _VP]),
     "pdrt_batch_plan_times": (C.c_int, [_VP, _VP, C.POINTER(C.c_float)]),
     "pdrt_batch_kernels": (C.c_int64, [_VP]),
+    "pdrt_batch_pass_cp": (C.c_int32, [_VP, C.c_int32]),
     "pdrt_batch_destroy": (None, [_VP]),
     "pdrt_launch_count": (C.c_int64, []),
     "pdrt_last_error": (C.c_char_p, []),
@@ -314,6 +315,10 @@ def pdrt_batch_plan_times(batch, n, stream):
 
 def pdrt_batch_kernels(batch) -> int:
     return int(load().pdrt_batch_kernels(_VP(batch)))
+
+
+def pdrt_batch_pass_cp(batch, i) -> int:
+    return int(load().pdrt_batch_pass_cp(_VP(batch), int(i)))
 
 
 def pdrt_batch_destroy(batch):

@@ -6,6 +6,7 @@ recorded once into a single CUDA graph with parallel branches and replayed
 with one graph launch.  The batch owns the device buffers the graph reads and
 writes: set inputs with copy_() into `leaves[i]`, `jaws[i]`, `mu[i]`,
 `dose_grad[i]`; read `dose[i]`, `dleaves[i]`, `djaws[i]`, `dmu[i]`.
+A None gradient entry records the forward alone for that plan.
 """
 from __future__ import annotations
 
@@ -30,12 +31,14 @@ class DoseBatch:
         self.dose = [torch.empty(e.shape, dtype=torch.float32, device=dev) for e in self.engines]
         self.dose_grad = self.dleaves = self.djaws = self.dmu = None
         if dose_grad is not None:
+            # a None entry: forward only for that plan (its gradient entries stay None)
+            has = [dose_grad[i] is not None for i in range(n)]
             self.dose_grad = [torch.as_tensor(dose_grad[i], dtype=torch.float32, device=dev)
-                              .contiguous().clone() for i in range(n)]
-            self.dleaves = [torch.empty_like(t) for t in self.leaves]
-            self.djaws = [torch.empty_like(t) for t in self.jaws]
-            self.dmu = [torch.empty_like(t) for t in self.mu]
-        ptrs = lambda ts: None if ts is None else [t.data_ptr() for t in ts]
+                              .contiguous().clone() if has[i] else None for i in range(n)]
+            self.dleaves = [torch.empty_like(t) if h else None for t, h in zip(self.leaves, has)]
+            self.djaws = [torch.empty_like(t) if h else None for t, h in zip(self.jaws, has)]
+            self.dmu = [torch.empty_like(t) if h else None for t, h in zip(self.mu, has)]
+        ptrs = lambda ts: None if ts is None else [0 if t is None else t.data_ptr() for t in ts]
         self._batch = _lib.pdrt_batch_create(
             [e._grid for e in self.engines], [e._plan for e in self.engines], ptrs(self.leaves),
             ptrs(self.jaws), ptrs(self.mu), ptrs(self.dose), ptrs(self.dose_grad),
@@ -52,6 +55,12 @@ class DoseBatch:
     @property
     def kernels(self) -> int:
         return _lib.pdrt_batch_kernels(self._batch)
+
+    @property
+    def pass_cp(self) -> list:
+        """Control points per pass of each plan in the batch (a plan's dose
+        equals its engine's forward at that chunk size bit for bit)."""
+        return [_lib.pdrt_batch_pass_cp(self._batch, i) for i in range(self.n)]
 
     def close(self):
         if getattr(self, "_batch", None):

@@ -1045,10 +1045,12 @@ struct pdrt_batch_s {
     int n = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    std::vector<cudaStream_t> branches;
-    std::vector<cudaEvent_t> events;   // [0] = fork, [1 .. nbr] = branch joins (graph edges only)
-    std::vector<cudaEvent_t> marks;    // [0] = start, [1 .. n] = plan done (event-record nodes)
+    std::vector<cudaStream_t> branches;   // [0] origin (recording), [1 .. nbr] branches
+    std::vector<cudaEvent_t> events;      // [0] fork, [1 .. nbr] joins (graph edges only)
+    std::vector<cudaEvent_t> marks;       // [0] start, [1 .. n] plan done (event-record nodes)
     long long kernels = 0;
+    std::vector<int> pass_cp;             // control points per pass of each plan
+    unsigned int *d_ctr = nullptr;        // work counters of the batched FFT launches
 };
 
 static void batch_free(pdrt_batch_t b)
@@ -1059,6 +1061,7 @@ static void batch_free(pdrt_batch_t b)
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
     for (cudaEvent_t e : b->marks) cudaEventDestroy(e);
     for (cudaStream_t s : b->branches) cudaStreamDestroy(s);
+    cudaFree(b->d_ctr);
     delete b;
 }
 
@@ -1081,16 +1084,69 @@ pdrt_status pdrt_batch_create(pdrt_batch_t *out, int32_t n, const pdrt_grid_t *g
             return fail(PDRT_EINVAL, "plan %d missing or uploaded for another grid", i);
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return fail(PDRT_EINVAL, "plan %d appears twice", i);
+        if (!leaves_dev[i] || !jaws_dev[i] || !mu_dev[i] || !dose_dev[i])
+            return fail(PDRT_EINVAL, "a buffer of plan %d is NULL", i);
+        if (grids[i]->device != grids[0]->device) return fail(PDRT_EINVAL, "plans on different devices");
         if (dose_grad_dev && dose_grad_dev[i] &&
             (!dleaves_dev || !djaws_dev || !dmu_dev || !dleaves_dev[i] || !djaws_dev[i] || !dmu_dev[i]))
             return fail(PDRT_EINVAL, "adjoint outputs of plan %d are NULL", i);
     }
+    int dev = 0;
+    CU_TRY(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != grids[0]->device) return fail(PDRT_EINVAL, "current device differs from the plans' device");
     const int nbr = std::max(1, std::min<int>(n_branches, n));
+    const int sm = grids[0]->sm_count;
+    (void)stream;   // recording uses an internal origin stream (the caller's may be the legacy one)
+
+    // the shared FFT launch is sized for the largest size limit and kernel
+    // radius of the batch; if that does not fit in shared memory every FFT
+    // plan keeps its own launches
+    int pmax_l = 0, r_l = 0;
+    for (int i = 0; i < n; ++i)
+        if (plans[i]->dev.fft_pmax > 0) {
+            pmax_l = std::max(pmax_l, plans[i]->dev.fft_pmax);
+            r_l = std::max(r_l, plans[i]->dev.mach.R);
+        }
+    int fft_grid[2] = {0, 0};
+    if (pmax_l) {
+        CU_TRY(conv_fft_ctas(pmax_l, r_l, false, &fft_grid[0]), "fft convolution set-up");
+        CU_TRY(conv_fft_ctas(pmax_l, r_l, true, &fft_grid[1]), "fft convolution set-up");
+        if (fft_grid[0] <= 0 || fft_grid[1] <= 0) fft_grid[0] = fft_grid[1] = 0;
+    }
+    const int fft_smem = pmax_l ? conv_fft_smem_bytes(pmax_l, r_l) : 0;
+    std::vector<int> nch(n);
+    std::vector<bool> adj(n), shared(n);
+    int rounds = 0;
+    for (int i = 0; i < n; ++i) {
+        nch[i] = (plans[i]->n_cp + plans[i]->chunk - 1) / plans[i]->chunk;
+        adj[i] = dose_grad_dev && dose_grad_dev[i];
+        shared[i] = plans[i]->dev.fft_pmax > 0 && fft_grid[0] > 0;
+        rounds = std::max(rounds, nch[i]);
+    }
+    // entries of the shared FFT launch of round c, direction d: pass c of
+    // every FFT plan that has one; counters: one per launch group
+    std::vector<std::vector<FftPlan>> ent_p(2 * rounds);
+    std::vector<std::vector<int4>> ent_r(2 * rounds);
+    std::vector<int> ctr0(2 * rounds);
+    int n_ctr = 0;
+    for (int d = 0; d < 2; ++d)
+        for (int c = 0; c < rounds; ++c) {
+            const int r = d * rounds + c;
+            for (int i = 0; i < n; ++i) {
+                if (!shared[i] || c >= nch[i] || (d == 1 && !adj[i])) continue;
+                const int b0 = c * plans[i]->chunk, nb = std::min(plans[i]->chunk, plans[i]->n_cp - b0);
+                ent_p[r].push_back(fft_plan_of(plans[i]->dev));
+                ent_r[r].push_back(make_int4(b0, nb, 0, c));
+            }
+            ctr0[r] = n_ctr;
+            n_ctr += ((int)ent_p[r].size() + kFftBatchMax - 1) / kFftBatchMax;
+        }
     pdrt_batch_t b = new pdrt_batch_s();
     b->n = n;
-    (void)stream;   // recording uses an internal origin stream (the caller's may be the legacy one)
+    for (int i = 0; i < n; ++i) b->pass_cp.push_back(plans[i]->chunk);
+    cudaError_t e = cudaMalloc(&b->d_ctr, sizeof(unsigned) * std::max(n_ctr, 1));
     cudaStream_t s = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e == cudaSuccess) b->branches.push_back(s);
     for (int k = 0; k < nbr && e == cudaSuccess; ++k) {
         cudaStream_t bs;
@@ -1098,62 +1154,149 @@ pdrt_status pdrt_batch_create(pdrt_batch_t *out, int32_t n, const pdrt_grid_t *g
         if (e == cudaSuccess) b->branches.push_back(bs);
     }
     for (int k = 0; k < 1 + nbr && e == cudaSuccess; ++k) {
-        cudaEvent_t ev;
-        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) b->events.push_back(ev);
+        cudaEvent_t x;
+        e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+        if (e == cudaSuccess) b->events.push_back(x);
     }
     for (int k = 0; k < 1 + n && e == cudaSuccess; ++k) {
-        cudaEvent_t ev;
-        e = cudaEventCreate(&ev);
-        if (e == cudaSuccess) b->marks.push_back(ev);
+        cudaEvent_t x;
+        e = cudaEventCreate(&x);
+        if (e == cudaSuccess) b->marks.push_back(x);
     }
     if (e != cudaSuccess) {
         batch_free(b);
-        return cuda_fail(e, "batch streams/events");
+        return cuda_fail(e, "batch set-up");
     }
-    // balance branches by a work estimate (control points x grid voxels)
-    std::vector<int> order(n), owner(n);
-    std::vector<double> load(nbr, 0.0);
-    for (int i = 0; i < n; ++i) order[i] = i;
-    auto cost = [&](int i) {
-        return (double)plans[i]->n_cp * grids[i]->nx * grids[i]->ny * grids[i]->nz;
-    };
-    std::sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
-    for (int i : order) {
-        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        owner[i] = k;
-        load[k] += cost(i);
+    // plans to branches, balanced by a work estimate (control points x voxels)
+    std::vector<int> owner(n);
+    {
+        std::vector<int> order(n);
+        std::vector<double> load(nbr, 0.0);
+        for (int i = 0; i < n; ++i) order[i] = i;
+        auto cost = [&](int i) { return (double)plans[i]->n_cp * grids[i]->nx * grids[i]->ny * grids[i]->nz; };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+        for (int i : order) {
+            const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            owner[i] = k;
+            load[k] += cost(i);
+        }
     }
     std::vector<bool> prof(n);
     for (int i = 0; i < n; ++i) {
         prof[i] = plans[i]->profiling;
         plans[i]->profiling = false;
     }
-    pdrt_status rst = PDRT_OK;
-    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        // timing marks become event-record nodes; the fork/join events only add edges
-        cudaEventRecordWithFlags(b->marks[0], s, cudaEventRecordExternal);
+    auto chk = [&](cudaError_t x) {
+        if (x != cudaSuccess && e == cudaSuccess) e = x;
+    };
+    auto bstream = [&](int i) { return b->branches[1 + owner[i]]; };
+    auto fork = [&]() {
         cudaEventRecord(b->events[0], s);
         for (int k = 0; k < nbr; ++k) cudaStreamWaitEvent(b->branches[1 + k], b->events[0], 0);
-        for (int i = 0; i < n && rst == PDRT_OK; ++i) {
-            pdrt_stream_t bs = (pdrt_stream_t)b->branches[1 + owner[i]];
-            rst = pdrt_dose_forward(grids[i], plans[i], leaves_dev[i], jaws_dev[i], mu_dev[i], dose_dev[i], bs);
-            if (rst == PDRT_OK && dose_grad_dev && dose_grad_dev[i])
-                rst = pdrt_dose_backward(grids[i], plans[i], leaves_dev[i], jaws_dev[i], mu_dev[i],
-                                         dose_grad_dev[i], dleaves_dev[i], djaws_dev[i], dmu_dev[i], bs);
-            cudaEventRecordWithFlags(b->marks[1 + i], b->branches[1 + owner[i]], cudaEventRecordExternal);
-        }
+    };
+    auto join = [&]() {
         for (int k = 0; k < nbr; ++k) {
             cudaEventRecord(b->events[1 + k], b->branches[1 + k]);
             cudaStreamWaitEvent(s, b->events[1 + k], 0);
         }
+    };
+    // the convolution of pass c of plan i beside the shared FFT launch: the
+    // tensor-core pass over its overflow list, or (a plan off the shared
+    // launch) its own FFT + overflow, tensor-core or SIMT convolution
+    auto conv_rest = [&](int i, int c, bool ad) -> cudaError_t {
+        pdrt_plan_t p = plans[i];
+        const PlanDev &P = p->dev;
+        const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0), nc = nch[i];
+        cudaStream_t bs = bstream(i);
+        unsigned int *fc = P.fft_ctr + 4 * c + (ad ? 2 : 0);
+        if (P.fft_pmax && !shared[i]) {
+            const cudaError_t x = launch_conv_fft(P, b0, nb, ad, P.fft_pmax, fc, P.fft_over, fc + 1,
+                                                  p->fft_blocks[ad ? 1 : 0], bs);
+            if (x != cudaSuccess) return x;
+        }
+        if (P.fft_pmax)
+            return launch_conv_tc(P, b0, nb, ad, P.counters + (ad ? 3 : 2) * nc + c,
+                                  ad ? p->tc_blocks_adj : p->tc_blocks, bs, P.fft_over, fc + 1);
+        if (P.tc_enabled)
+            return launch_conv_tc(P, b0, nb, ad, P.counters + (ad ? 3 : 2) * nc + c,
+                                  ad ? p->tc_blocks_adj : p->tc_blocks, bs);
+        return launch_conv(P, b0, nb, ad, P.counters + (ad ? nc : 0) + c,
+                           ad ? p->conv_blocks_adj : p->conv_blocks_fwd, bs);
+    };
+    auto fft_round = [&](int d, int c) {
+        const int r = d * rounds + c;
+        if (!ent_p[r].empty())
+            chk(launch_conv_fft_multi(ent_p[r].data(), ent_r[r].data(), (int)ent_p[r].size(), pmax_l, fft_smem,
+                                      fft_grid[d] * sm, d == 1, b->d_ctr + ctr0[r], s));
+    };
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecordWithFlags(b->marks[0], s, cudaEventRecordExternal);
+        cudaMemsetAsync(b->d_ctr, 0, sizeof(unsigned) * std::max(n_ctr, 1), s);
+        // counters, projection, fluence and slice tables of every plan (the
+        // adjoint of the same parameters reuses them)
+        fork();
+        for (int i = 0; i < n; ++i) {
+            const PlanDev &P = plans[i]->dev;
+            cudaMemsetAsync(P.counters, 0, sizeof(unsigned) * 4 * nch[i], bstream(i));
+            cudaMemsetAsync(P.fft_ctr, 0, sizeof(unsigned) * 4 * nch[i], bstream(i));
+            chk(launch_raster(P, leaves_dev[i], jaws_dev[i], mu_dev[i], bstream(i)));
+            chk(launch_tables(P, bstream(i)));
+        }
+        join();
+        // forward: per round the shared FFT launch over pass c of every FFT
+        // plan, then per plan on its branch the rest of its convolution and
+        // its gather
+        for (int c = 0; c < rounds; ++c) {
+            fft_round(0, c);
+            fork();
+            for (int i = 0; i < n; ++i) {
+                if (c >= nch[i]) continue;
+                pdrt_plan_t p = plans[i];
+                const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
+                chk(conv_rest(i, c, false));
+                chk(launch_gather(p->dev, b0, nb, dose_dev[i], c == 0, bstream(i)));
+                if (c == nch[i] - 1 && !adj[i])
+                    cudaEventRecordWithFlags(b->marks[1 + i], bstream(i), cudaEventRecordExternal);
+            }
+            join();
+        }
+        // adjoint in the same rounds: gradient gathers, shared FFT launch,
+        // overflow and transposed magnification
+        for (int c = 0; c < rounds; ++c) {
+            fork();
+            for (int i = 0; i < n; ++i) {
+                if (!adj[i] || c >= nch[i]) continue;
+                pdrt_plan_t p = plans[i];
+                const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
+                chk(launch_gather_T(p->dev, b0, nb, dose_grad_dev[i], bstream(i)));
+            }
+            join();
+            fft_round(1, c);
+            fork();
+            for (int i = 0; i < n; ++i) {
+                if (!adj[i] || c >= nch[i]) continue;
+                pdrt_plan_t p = plans[i];
+                const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
+                chk(conv_rest(i, c, true));
+                chk(launch_mag_T(p->dev, b0, nb, bstream(i)));
+            }
+            join();
+        }
+        fork();
+        for (int i = 0; i < n; ++i) {
+            if (!adj[i]) continue;
+            chk(launch_param_grad(plans[i]->dev, leaves_dev[i], jaws_dev[i], mu_dev[i], dleaves_dev[i],
+                                  djaws_dev[i], dmu_dev[i], bstream(i)));
+            cudaEventRecordWithFlags(b->marks[1 + i], bstream(i), cudaEventRecordExternal);
+        }
+        join();
         cudaError_t e2 = cudaStreamEndCapture(s, &b->graph);
         if (e == cudaSuccess) e = e2;
     }
     for (int i = 0; i < n; ++i) plans[i]->profiling = prof[i];
-    if (rst == PDRT_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
-    if (rst == PDRT_OK && e == cudaSuccess) {
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e == cudaSuccess) {
         size_t nn = 0;
         e = cudaGraphGetNodes(b->graph, nullptr, &nn);
         std::vector<cudaGraphNode_t> nodes(nn);
@@ -1164,11 +1307,9 @@ pdrt_status pdrt_batch_create(pdrt_batch_t *out, int32_t n, const pdrt_grid_t *g
                 ++b->kernels;
         }
     }
-    if (rst != PDRT_OK || e != cudaSuccess) {
-        std::string msg = g_last_error;
+    if (e != cudaSuccess) {
         batch_free(b);
-        if (rst != PDRT_OK) return fail(rst, "batch recording failed: %s", msg.c_str());
-        return cuda_fail(e, "batch graph capture");
+        return cuda_fail(e, "batch graph recording");
     }
     *out = b;
     return PDRT_OK;
@@ -1194,6 +1335,11 @@ pdrt_status pdrt_batch_plan_times(pdrt_batch_t b, pdrt_stream_t stream, float *m
 }
 
 int64_t pdrt_batch_kernels(pdrt_batch_t b) { return b ? b->kernels : 0; }
+
+int32_t pdrt_batch_pass_cp(pdrt_batch_t b, int32_t i)
+{
+    return b && i >= 0 && i < b->n ? b->pass_cp[i] : 0;
+}
 
 void pdrt_batch_destroy(pdrt_batch_t b) { batch_free(b); }
 

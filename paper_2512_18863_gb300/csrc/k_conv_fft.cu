@@ -568,6 +568,302 @@ int conv_fft_smem_bytes(int pmax, int R)
 // MINB: resident CTAs per SM the register budget is sized for (launch
 // bounds); the launcher picks the instantiation that matches what the size
 // limit's shared memory allows (fewer resident CTAs leave more registers).
+// Shared-memory carve-up of k_conv_fft for a size limit pmax: the kernel
+// spectrum, the forward fill tables and the complex work array (which also
+// holds the spectrum's scratch before the fill).
+struct FftSmem {
+    float *Kf;
+    int2 *fu_idx;
+    float2 *fu_w;
+    int2 *fv_idx;
+    float2 *fv_w;
+    float2 *S;
+};
+
+__device__ __forceinline__ FftSmem fft_smem(unsigned char *smem, int pmax)
+{
+    auto al = [](int x) { return (x + 15) & ~15; };
+    const int hmax = pmax / 2;
+    FftSmem m;
+    unsigned char *p = smem + 64;
+    m.Kf = reinterpret_cast<float *>(p);
+    p += al((pmax / 2 + 1) * (hmax + 1) * 4);
+    m.fu_idx = reinterpret_cast<int2 *>(p);
+    m.fu_w = reinterpret_cast<float2 *>(m.fu_idx + pmax);
+    m.fv_idx = reinterpret_cast<int2 *>(m.fu_w + pmax);
+    m.fv_w = reinterpret_cast<float2 *>(m.fv_idx + pmax);
+    p += 4 * pmax * 8;
+    m.S = reinterpret_cast<float2 *>(p);
+    return m;
+}
+
+// Convolution of one (control point, slice) item of the chunk starting at
+// control point b0, by the whole CTA; a slice beyond the size limit pmax is
+// appended to the overflow list instead.  Every thread calls it with the
+// same arguments; it starts and ends between barriers.
+template <bool ADJ, class PL>
+__device__ __forceinline__ void fft_slice(const PL &P, int R, int b0, int item, int pmax,
+                                          int *__restrict__ over_list, unsigned int *__restrict__ over_count,
+                                          const FftSmem &sm)
+{
+    const Lattice &L = P.lat;
+    const int R1 = R + 1;
+    float *Kf = sm.Kf;
+    int2 *fu_idx = sm.fu_idx;
+    float2 *fu_w = sm.fu_w;
+    int2 *fv_idx = sm.fv_idx;
+    float2 *fv_w = sm.fv_w;
+    float2 *S = sm.S;
+    const int R1p = (R1 + 3) & ~3;
+    float *KT = reinterpret_cast<float *>(S);        // spectrum scratch before the fill: [q][p]
+    float *A = KT + R1 * R1p;                        // [p][kv'] (16-byte aligned rows)
+    const int tid = threadIdx.x;
+    const bool sym = L.du == L.dv;                   // K(p, q) = K(q, p)
+    const int bl = item / L.nw, k = item - bl * L.nw, b = b0 + bl;
+    const SliceTab st = P.slices[(long long)b * L.nw + k];
+    int pu, pv;
+    fft_slice_sizes(st, ADJ, R, pu, pv);
+    if (pu == 0) return;                     // no work in this slice
+    if (pu > pmax || pv > pmax) {              // too large: the tensor-core kernel takes it
+        if (tid == 0) over_list[atomicAdd(over_count, 1u)] = item;
+        return;
+    }
+    const TcBoxes bx = tc_boxes(st, ADJ, R);
+    const int hu = pu / 2;
+    FftGeom G;
+    G.pu = pu; G.pv = pv; G.hu = hu; G.pitch = hu + 1;
+    G.n_rows_in = bx.in_j1 - bx.in_j0;
+    G.n_rows_out = bx.out_j1 - bx.out_j0;
+    G.out_row0 = ((bx.out_j0 - bx.in_j0) % pv + pv) % pv;
+    const int wi = bx.in_i1 - bx.in_i0;
+    const SizeOff ou = size_offsets(pu, R), ov = size_offsets(pv, R);
+    const float2 *Tu = g_fft_tw + ou.tw, *Tv = g_fft_tw + ov.tw;
+    const short *pos_u = g_fft_pos + ou.pos, *ku_of = g_fft_ku + ou.ku, *kv_of = g_fft_kv + ov.kv;
+    const int nkv = pv / 2 + 1, nkv4 = (nkv + 3) & ~3, hu4 = (hu + 1 + 3) & ~3;
+    const float *Cv = P.fft_cos + ov.cos;        // [q][kv'], c_q folded in
+    const float *Cu = P.fft_cos + ou.cos;        // [p][ku], c_p folded in
+
+    // Kernel spectrum: K(p, q) (the expressions of the other convolution
+    // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
+    // K is stored transposed, KT[q][p] (rows of R1p = R1 rounded up to 4),
+    // so that both products read 4-wide vectors of each operand.
+    for (int idx = tid; idx < R1 * R1; idx += kFftThreads) {
+        const int pp = idx / R1, q = idx - pp * R1;
+        if (sym && pp > q) continue;
+        const float pu_mm = pp * L.du, qv = q * L.dv;
+        const float r = sqrtf(pu_mm * pu_mm + qv * qv);
+        const float kv = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
+                         st.wn[2] * expf(-st.a[2] * r);
+        KT[q * R1p + pp] = kv;
+        if (sym) KT[pp * R1p + q] = kv;
+    }
+    for (int idx = tid; idx < R1 * (R1p - R1); idx += kFftThreads) {   // zero padding columns
+        const int q = idx / (R1p - R1);
+        KT[q * R1p + R1 + (idx - q * (R1p - R1))] = 0.f;
+    }
+    __syncthreads();
+    // A[4 p4 .. +3][4 g .. +3] per item
+    {
+        const int G4 = nkv4 / 4, P4 = R1p / 4;
+        const FastDiv dg = fast_div(G4);
+        for (int idx = tid; idx < P4 * G4; idx += kFftThreads) {
+            const int p4 = idx / dg, g = idx - p4 * G4;
+            float4 acc[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 *kt = reinterpret_cast<const float4 *>(KT) + p4;
+            const float4 *cv = reinterpret_cast<const float4 *>(Cv) + g;
+            for (int q = 0; q < R1; ++q) {
+                const float4 kk = kt[q * P4];
+                const float4 c = __ldg(cv + q * G4);
+                const float k4[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    acc[a].x = fmaf(k4[a], c.x, acc[a].x);
+                    acc[a].y = fmaf(k4[a], c.y, acc[a].y);
+                    acc[a].z = fmaf(k4[a], c.z, acc[a].z);
+                    acc[a].w = fmaf(k4[a], c.w, acc[a].w);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (4 * p4 + a < R1) reinterpret_cast<float4 *>(A)[(4 * p4 + a) * G4 + g] = acc[a];
+        }
+    }
+    __syncthreads();
+    // Kf[4 i4 .. +3][4 g .. +3] per item
+    {
+        const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
+        const int U4 = hu4 / 4, V4 = nkv4 / 4;
+        const FastDiv du4 = fast_div(U4);
+        for (int idx = tid; idx < V4 * U4; idx += kFftThreads) {
+            const int i4 = idx / du4, g = idx - i4 * U4;
+            float4 acc[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 *av = reinterpret_cast<const float4 *>(A) + i4;
+            const float4 *cu = reinterpret_cast<const float4 *>(Cu) + g;
+            for (int pp = 0; pp < R1; ++pp) {
+                const float4 aa = av[pp * V4];
+                const float4 c = __ldg(cu + pp * U4);
+                const float a4[4] = {aa.x, aa.y, aa.z, aa.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    acc[a].x = fmaf(a4[a], c.x, acc[a].x);
+                    acc[a].y = fmaf(a4[a], c.y, acc[a].y);
+                    acc[a].z = fmaf(a4[a], c.z, acc[a].z);
+                    acc[a].w = fmaf(a4[a], c.w, acc[a].w);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int kv = 4 * i4 + a;
+                if (kv >= nkv) continue;
+                const float r4[4] = {acc[a].x, acc[a].y, acc[a].z, acc[a].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * g + e <= hu) Kf[kv * G.pitch + 4 * g + e] = r4[e] * kscale;
+            }
+        }
+    }
+    // fill tables (forward): per input column n the two fluence rows a of
+    // its bilinear stencil (clamped into the support box) with their
+    // weights (zero outside the box), likewise per input row j
+    if (!ADJ) {
+        const CpTab &ct = P.cptab[b];
+        for (int t = tid; t < wi + G.n_rows_in; t += kFftThreads) {
+            const bool col = t < wi;
+            const int lo = col ? ct.fa0 : ct.fc0, hi = col ? ct.fa1 : ct.fc1;
+            const int idx0 = col ? bx.in_i0 + t : bx.in_j0 + (t - wi);
+            const float f = col ? mag_coord(st.m, idx0, L.cu) : mag_coord(st.m, idx0, L.cv);
+            const float fl = floorf(f);
+            const int a0 = (int)fl;
+            const float tw = f - fl;
+            const bool ok0 = a0 >= lo && a0 < hi, ok1 = a0 + 1 >= lo && a0 + 1 < hi;
+            const int i0 = min(max(a0 - lo, 0), hi - lo - 1), i1 = min(max(a0 + 1 - lo, 0), hi - lo - 1);
+            const float w0 = ok0 ? 1.f - tw : 0.f, w1 = ok1 ? tw : 0.f;
+            if (col) {
+                fu_idx[t] = make_int2(i0, i1);
+                fu_w[t] = make_float2(w0, w1);
+            } else {
+                fv_idx[t - wi] = make_int2(i0, i1);
+                fv_w[t - wi] = make_float2(w0, w1);
+            }
+        }
+    }
+    __syncthreads();
+
+    // fill the input rows (j = v offset from the input box), packed
+    // (x[2m], x[2m+1]) along u; the rows past them are never written: the
+    // first column pass reads them as zero
+    {
+        const int n_fill = G.n_rows_in * hu;
+        const FastDiv dh = fast_div(hu);
+        const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
+        const int Fc = P.cptab[b].fc1 - P.cptab[b].fc0;
+        const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
+        const int h_w = st.oi1 - st.oi0;
+        for (int idx = tid; idx < n_fill; idx += kFftThreads) {
+            const int j = idx / dh, m = idx - j * hu;
+            float x[2] = {0.f, 0.f};
+            int2 ci = make_int2(0, 0);
+            float2 cw = make_float2(0.f, 0.f);
+            if (!ADJ) {
+                ci = fv_idx[j];
+                cw = fv_w[j];
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int n = 2 * m + e;
+                if (n >= wi) continue;
+                if (ADJ) {
+                    x[e] = hsrc[(long long)(bx.in_j0 + j - st.oj0) * h_w + (bx.in_i0 + n - st.oi0)];
+                } else {
+                    const int2 ai = fu_idx[n];
+                    const float2 aw = fu_w[n];
+                    const float *r0 = fmap + (long long)ai.x * Fc, *r1 = fmap + (long long)ai.y * Fc;
+                    x[e] = aw.x * (cw.x * __ldg(r0 + ci.x) + cw.y * __ldg(r0 + ci.y)) +
+                           aw.y * (cw.x * __ldg(r1 + ci.x) + cw.y * __ldg(r1 + ci.y));
+                }
+            }
+            S[j * G.pitch + m] = make_float2(x[0], x[1]);
+        }
+    }
+    __syncthreads();
+    // rows: complex FFT of length hu over the input rows
+    fft_run<false, false>(S, G, G.n_rows_in, 0, hu, Tu, 2, Kf, kv_of, ku_of);
+    // real-FFT split: X[k] = E_k + W^k O_k and X[hu - k] = conj(E_k - W^k O_k),
+    // E_k = (Z_k + conj Z_{hu-k}) / 2, O_k = (Z_k - conj Z_{hu-k}) / (2i),
+    // W = exp(-2 pi i / pu); X[hu] goes to column hu
+    {
+        const int half = hu / 2 + 1;
+        const FastDiv dhf = fast_div(half);
+        for (int idx = tid; idx < G.n_rows_in * half; idx += kFftThreads) {
+            const int j = idx / dhf, kk = idx - j * half;
+            float2 *row = S + j * G.pitch;
+            if (kk == 0) {
+                const int p0 = __ldg(pos_u);
+                const float2 z = row[p0];
+                row[p0] = make_float2(z.x + z.y, 0.f);
+                row[hu] = make_float2(z.x - z.y, 0.f);
+                continue;
+            }
+            const int pk = __ldg(pos_u + kk), pc = __ldg(pos_u + hu - kk);
+            const float2 zk = row[pk], zc = cconj(row[pc]);
+            const float2 E = cscale(cadd(zk, zc), 0.5f);
+            const float2 d = cscale(csub(zk, zc), 0.5f);
+            const float2 O = make_float2(d.y, -d.x);   // d / i
+            const float2 WO = cmul(__ldg(Tu + kk), O);
+            row[pk] = cadd(E, WO);
+            if (pc != pk) row[pc] = cconj(csub(E, WO));
+        }
+    }
+    __syncthreads();
+    // columns: forward FFT of length pv (rows past the input read as
+    // zero), then product and inverse
+    fft_run<true, false>(S, G, hu + 1, 0, pv, Tv, 1, Kf, kv_of, ku_of, G.n_rows_in);
+    fft_run<true, true>(S, G, hu + 1, 0, pv, Tv, 1, Kf, kv_of, ku_of);
+    // inverse real FFT of the output rows: Z[k] = (X_k + conj X_{hu-k})
+    // + i exp(2 pi i k / pu) (X_k - conj X_{hu-k}), stored at pos_u(k)
+    {
+        const int half = hu / 2 + 1;
+        const FastDiv dhf = fast_div(half);
+        for (int idx = tid; idx < G.n_rows_out * half; idx += kFftThreads) {
+            const int rr = idx / dhf, kk = idx - rr * half;
+            int row_i = G.out_row0 + rr;
+            if (row_i >= pv) row_i -= pv;
+            float2 *row = S + row_i * G.pitch;
+            const int pk = __ldg(pos_u + kk);
+            const int pc = kk == 0 ? hu : __ldg(pos_u + hu - kk);
+            const float2 xk = row[pk];
+            const float2 xc = cconj(row[pc]);
+            const float2 sum = cadd(xk, xc), dif = csub(xk, xc);
+            const float2 w = __ldg(Tu + kk);
+            const float2 wd = cmul(cconj(w), dif);
+            row[pk] = make_float2(sum.x - wd.y, sum.y + wd.x);   // sum + i wd
+            if (kk > 0 && 2 * kk != hu) {
+                // Z[hu - k] = (X_{hu-k} + conj X_k) - i exp(-2 pi i k / pu) (X_{hu-k} - conj X_k)
+                const float2 yk = cconj(xc), yc = cconj(xk);   // X_{hu-k}, conj X_k
+                const float2 s2 = cadd(yk, yc), d2 = csub(yk, yc);
+                const float2 w2 = cmul(w, d2);
+                row[pc] = make_float2(s2.x + w2.y, s2.y - w2.x);   // s2 - i w2
+            }
+        }
+    }
+    __syncthreads();
+    // inverse rows; the last pass writes the output box:
+    // (u, v) holds real sample (u - in_i0) mod pu of row (v - in_j0) mod pv
+    OutCtx oc;
+    oc.dst = ADJ ? P.adjbuf + (long long)bl * P.cap_a + st.off_a
+                 : P.region + (long long)bl * P.cap_o + st.off_o;
+    oc.out_w = bx.out_i1 - bx.out_i0;
+    oc.in_i0 = bx.in_i0;
+    oc.out_i0 = bx.out_i0;
+    oc.out_i1 = bx.out_i1;
+    oc.pu = pu;
+    fft_run<false, true>(S, G, G.n_rows_out, G.out_row0, hu, Tu, 2, Kf, kv_of, ku_of, 1 << 30, &oc);
+}
+
 template <bool ADJ, int MINB>
 __global__ void __launch_bounds__(kFftThreads, MINB) k_conv_fft(PlanDev P, int b0, int nb, int pmax,
                                                             unsigned int *__restrict__ counter,
@@ -575,276 +871,52 @@ __global__ void __launch_bounds__(kFftThreads, MINB) k_conv_fft(PlanDev P, int b
                                                             unsigned int *__restrict__ over_count)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const Lattice &L = P.lat;
-    const int R = P.mach.R, R1 = R + 1;
-    const int hmax = pmax / 2;
-    auto al = [](int x) { return (x + 15) & ~15; };
     int *s_item = reinterpret_cast<int *>(smem);
-    unsigned char *p = smem + 64;
-    float *Kf = reinterpret_cast<float *>(p);
-    p += al((pmax / 2 + 1) * (hmax + 1) * 4);
-    int2 *fu_idx = reinterpret_cast<int2 *>(p);   // forward fill tables, [pmax] each
-    float2 *fu_w = reinterpret_cast<float2 *>(fu_idx + pmax);
-    int2 *fv_idx = reinterpret_cast<int2 *>(fu_w + pmax);
-    float2 *fv_w = reinterpret_cast<float2 *>(fv_idx + pmax);
-    p += 4 * pmax * 8;
-    float2 *S = reinterpret_cast<float2 *>(p);
-    const int R1p = (R1 + 3) & ~3;
-    float *KT = reinterpret_cast<float *>(S);        // spectrum scratch before the fill: [q][p]
-    float *A = KT + R1 * R1p;                        // [p][kv'] (16-byte aligned rows)
-    const int tid = threadIdx.x;
-    const int n_items = nb * L.nw;
-    const bool sym = L.du == L.dv;                   // K(p, q) = K(q, p)
-
+    const FftSmem sm = fft_smem(smem, pmax);
+    const int n_items = nb * P.lat.nw;
     for (;;) {
         __syncthreads();
-        if (tid == 0) *s_item = (int)atomicAdd(counter, 1u);
+        if (threadIdx.x == 0) *s_item = (int)atomicAdd(counter, 1u);
         __syncthreads();
         const int item = *s_item;
         if (item >= n_items) break;
-        const int bl = item / L.nw, k = item - bl * L.nw, b = b0 + bl;
-        const SliceTab st = P.slices[(long long)b * L.nw + k];
-        int pu, pv;
-        fft_slice_sizes(st, ADJ, R, pu, pv);
-        if (pu == 0) continue;                     // no work in this slice
-        if (pu > pmax || pv > pmax) {              // too large: the tensor-core kernel takes it
-            if (tid == 0) over_list[atomicAdd(over_count, 1u)] = item;
-            continue;
-        }
-        const TcBoxes bx = tc_boxes(st, ADJ, R);
-        const int hu = pu / 2;
-        FftGeom G;
-        G.pu = pu; G.pv = pv; G.hu = hu; G.pitch = hu + 1;
-        G.n_rows_in = bx.in_j1 - bx.in_j0;
-        G.n_rows_out = bx.out_j1 - bx.out_j0;
-        G.out_row0 = ((bx.out_j0 - bx.in_j0) % pv + pv) % pv;
-        const int wi = bx.in_i1 - bx.in_i0;
-        const SizeOff ou = size_offsets(pu, R), ov = size_offsets(pv, R);
-        const float2 *Tu = g_fft_tw + ou.tw, *Tv = g_fft_tw + ov.tw;
-        const short *pos_u = g_fft_pos + ou.pos, *ku_of = g_fft_ku + ou.ku, *kv_of = g_fft_kv + ov.kv;
-        const int nkv = pv / 2 + 1, nkv4 = (nkv + 3) & ~3, hu4 = (hu + 1 + 3) & ~3;
-        const float *Cv = P.fft_cos + ov.cos;        // [q][kv'], c_q folded in
-        const float *Cu = P.fft_cos + ou.cos;        // [p][ku], c_p folded in
+        fft_slice<ADJ>(P, P.mach.R, b0, item, pmax, over_list, over_count, sm);
+    }
+}
 
-        // Kernel spectrum: K(p, q) (the expressions of the other convolution
-        // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
-        // K is stored transposed, KT[q][p] (rows of R1p = R1 rounded up to 4),
-        // so that both products read 4-wide vectors of each operand.
-        for (int idx = tid; idx < R1 * R1; idx += kFftThreads) {
-            const int pp = idx / R1, q = idx - pp * R1;
-            if (sym && pp > q) continue;
-            const float pu_mm = pp * L.du, qv = q * L.dv;
-            const float r = sqrtf(pu_mm * pu_mm + qv * qv);
-            const float kv = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
-                             st.wn[2] * expf(-st.a[2] * r);
-            KT[q * R1p + pp] = kv;
-            if (sym) KT[pp * R1p + q] = kv;
-        }
-        for (int idx = tid; idx < R1 * (R1p - R1); idx += kFftThreads) {   // zero padding columns
-            const int q = idx / (R1p - R1);
-            KT[q * R1p + R1 + (idx - q * (R1p - R1))] = 0.f;
-        }
-        __syncthreads();
-        // A[4 p4 .. +3][4 g .. +3] per item
-        {
-            const int G4 = nkv4 / 4, P4 = R1p / 4;
-            const FastDiv dg = fast_div(G4);
-            for (int idx = tid; idx < P4 * G4; idx += kFftThreads) {
-                const int p4 = idx / dg, g = idx - p4 * G4;
-                float4 acc[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 *kt = reinterpret_cast<const float4 *>(KT) + p4;
-                const float4 *cv = reinterpret_cast<const float4 *>(Cv) + g;
-                for (int q = 0; q < R1; ++q) {
-                    const float4 kk = kt[q * P4];
-                    const float4 c = __ldg(cv + q * G4);
-                    const float k4[4] = {kk.x, kk.y, kk.z, kk.w};
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        acc[a].x = fmaf(k4[a], c.x, acc[a].x);
-                        acc[a].y = fmaf(k4[a], c.y, acc[a].y);
-                        acc[a].z = fmaf(k4[a], c.z, acc[a].z);
-                        acc[a].w = fmaf(k4[a], c.w, acc[a].w);
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-                    if (4 * p4 + a < R1) reinterpret_cast<float4 *>(A)[(4 * p4 + a) * G4 + g] = acc[a];
-            }
-        }
-        __syncthreads();
-        // Kf[4 i4 .. +3][4 g .. +3] per item
-        {
-            const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
-            const int U4 = hu4 / 4, V4 = nkv4 / 4;
-            const FastDiv du4 = fast_div(U4);
-            for (int idx = tid; idx < V4 * U4; idx += kFftThreads) {
-                const int i4 = idx / du4, g = idx - i4 * U4;
-                float4 acc[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 *av = reinterpret_cast<const float4 *>(A) + i4;
-                const float4 *cu = reinterpret_cast<const float4 *>(Cu) + g;
-                for (int pp = 0; pp < R1; ++pp) {
-                    const float4 aa = av[pp * V4];
-                    const float4 c = __ldg(cu + pp * U4);
-                    const float a4[4] = {aa.x, aa.y, aa.z, aa.w};
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        acc[a].x = fmaf(a4[a], c.x, acc[a].x);
-                        acc[a].y = fmaf(a4[a], c.y, acc[a].y);
-                        acc[a].z = fmaf(a4[a], c.z, acc[a].z);
-                        acc[a].w = fmaf(a4[a], c.w, acc[a].w);
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const int kv = 4 * i4 + a;
-                    if (kv >= nkv) continue;
-                    const float r4[4] = {acc[a].x, acc[a].y, acc[a].z, acc[a].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (4 * g + e <= hu) Kf[kv * G.pitch + 4 * g + e] = r4[e] * kscale;
-                }
-            }
-        }
-        // fill tables (forward): per input column n the two fluence rows a of
-        // its bilinear stencil (clamped into the support box) with their
-        // weights (zero outside the box), likewise per input row j
-        if (!ADJ) {
-            const CpTab &ct = P.cptab[b];
-            for (int t = tid; t < wi + G.n_rows_in; t += kFftThreads) {
-                const bool col = t < wi;
-                const int lo = col ? ct.fa0 : ct.fc0, hi = col ? ct.fa1 : ct.fc1;
-                const int idx0 = col ? bx.in_i0 + t : bx.in_j0 + (t - wi);
-                const float f = col ? mag_coord(st.m, idx0, L.cu) : mag_coord(st.m, idx0, L.cv);
-                const float fl = floorf(f);
-                const int a0 = (int)fl;
-                const float tw = f - fl;
-                const bool ok0 = a0 >= lo && a0 < hi, ok1 = a0 + 1 >= lo && a0 + 1 < hi;
-                const int i0 = min(max(a0 - lo, 0), hi - lo - 1), i1 = min(max(a0 + 1 - lo, 0), hi - lo - 1);
-                const float w0 = ok0 ? 1.f - tw : 0.f, w1 = ok1 ? tw : 0.f;
-                if (col) {
-                    fu_idx[t] = make_int2(i0, i1);
-                    fu_w[t] = make_float2(w0, w1);
-                } else {
-                    fv_idx[t - wi] = make_int2(i0, i1);
-                    fv_w[t - wi] = make_float2(w0, w1);
-                }
-            }
-        }
-        __syncthreads();
+// Batched form: one persistent launch over the items of several plans'
+// passes.  Entry e is pass round[e].w (control points round[e].x ..
+// + round[e].y) of plan plan[e]; its items follow those of the entries
+// before it.  Each slice goes by its own plan's size limit and overflow list;
+// the shared memory is laid out for the largest limit pmax.  The entries sit
+// in the kernel parameters (grid constant), so an entry's fields are read
+// through the constant cache as in k_conv_fft.
+struct FftBatchArgs {
+    FftPlan plan[kFftBatchMax];
+    int4 round[kFftBatchMax];   // {b0, nb, first item, pass}
+    int n_ent, n_items;
+};
+static_assert(sizeof(FftBatchArgs) + 2 * sizeof(void *) <= 32764, "kernel parameters above 32 KB");
 
-        // fill the input rows (j = v offset from the input box), packed
-        // (x[2m], x[2m+1]) along u; the rows past them are never written: the
-        // first column pass reads them as zero
-        {
-            const int n_fill = G.n_rows_in * hu;
-            const FastDiv dh = fast_div(hu);
-            const float *fmap = P.fbuf + (long long)b * L.nu * L.nv;
-            const int Fc = P.cptab[b].fc1 - P.cptab[b].fc0;
-            const float *hsrc = P.region + (long long)bl * P.cap_o + st.off_o;
-            const int h_w = st.oi1 - st.oi0;
-            for (int idx = tid; idx < n_fill; idx += kFftThreads) {
-                const int j = idx / dh, m = idx - j * hu;
-                float x[2] = {0.f, 0.f};
-                int2 ci = make_int2(0, 0);
-                float2 cw = make_float2(0.f, 0.f);
-                if (!ADJ) {
-                    ci = fv_idx[j];
-                    cw = fv_w[j];
-                }
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int n = 2 * m + e;
-                    if (n >= wi) continue;
-                    if (ADJ) {
-                        x[e] = hsrc[(long long)(bx.in_j0 + j - st.oj0) * h_w + (bx.in_i0 + n - st.oi0)];
-                    } else {
-                        const int2 ai = fu_idx[n];
-                        const float2 aw = fu_w[n];
-                        const float *r0 = fmap + (long long)ai.x * Fc, *r1 = fmap + (long long)ai.y * Fc;
-                        x[e] = aw.x * (cw.x * __ldg(r0 + ci.x) + cw.y * __ldg(r0 + ci.y)) +
-                               aw.y * (cw.x * __ldg(r1 + ci.x) + cw.y * __ldg(r1 + ci.y));
-                    }
-                }
-                S[j * G.pitch + m] = make_float2(x[0], x[1]);
-            }
-        }
+template <bool ADJ, int MINB>
+__global__ void __launch_bounds__(kFftThreads, MINB)
+k_conv_fft_multi(const __grid_constant__ FftBatchArgs A, int pmax, unsigned int *__restrict__ counter)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *s_item = reinterpret_cast<int *>(smem);
+    const FftSmem sm = fft_smem(smem, pmax);
+    for (;;) {
         __syncthreads();
-        // rows: complex FFT of length hu over the input rows
-        fft_run<false, false>(S, G, G.n_rows_in, 0, hu, Tu, 2, Kf, kv_of, ku_of);
-        // real-FFT split: X[k] = E_k + W^k O_k and X[hu - k] = conj(E_k - W^k O_k),
-        // E_k = (Z_k + conj Z_{hu-k}) / 2, O_k = (Z_k - conj Z_{hu-k}) / (2i),
-        // W = exp(-2 pi i / pu); X[hu] goes to column hu
-        {
-            const int half = hu / 2 + 1;
-            const FastDiv dhf = fast_div(half);
-            for (int idx = tid; idx < G.n_rows_in * half; idx += kFftThreads) {
-                const int j = idx / dhf, kk = idx - j * half;
-                float2 *row = S + j * G.pitch;
-                if (kk == 0) {
-                    const int p0 = __ldg(pos_u);
-                    const float2 z = row[p0];
-                    row[p0] = make_float2(z.x + z.y, 0.f);
-                    row[hu] = make_float2(z.x - z.y, 0.f);
-                    continue;
-                }
-                const int pk = __ldg(pos_u + kk), pc = __ldg(pos_u + hu - kk);
-                const float2 zk = row[pk], zc = cconj(row[pc]);
-                const float2 E = cscale(cadd(zk, zc), 0.5f);
-                const float2 d = cscale(csub(zk, zc), 0.5f);
-                const float2 O = make_float2(d.y, -d.x);   // d / i
-                const float2 WO = cmul(__ldg(Tu + kk), O);
-                row[pk] = cadd(E, WO);
-                if (pc != pk) row[pc] = cconj(csub(E, WO));
-            }
-        }
+        if (threadIdx.x == 0) *s_item = (int)atomicAdd(counter, 1u);
         __syncthreads();
-        // columns: forward FFT of length pv (rows past the input read as
-        // zero), then product and inverse
-        fft_run<true, false>(S, G, hu + 1, 0, pv, Tv, 1, Kf, kv_of, ku_of, G.n_rows_in);
-        fft_run<true, true>(S, G, hu + 1, 0, pv, Tv, 1, Kf, kv_of, ku_of);
-        // inverse real FFT of the output rows: Z[k] = (X_k + conj X_{hu-k})
-        // + i exp(2 pi i k / pu) (X_k - conj X_{hu-k}), stored at pos_u(k)
-        {
-            const int half = hu / 2 + 1;
-            const FastDiv dhf = fast_div(half);
-            for (int idx = tid; idx < G.n_rows_out * half; idx += kFftThreads) {
-                const int rr = idx / dhf, kk = idx - rr * half;
-                int row_i = G.out_row0 + rr;
-                if (row_i >= pv) row_i -= pv;
-                float2 *row = S + row_i * G.pitch;
-                const int pk = __ldg(pos_u + kk);
-                const int pc = kk == 0 ? hu : __ldg(pos_u + hu - kk);
-                const float2 xk = row[pk];
-                const float2 xc = cconj(row[pc]);
-                const float2 sum = cadd(xk, xc), dif = csub(xk, xc);
-                const float2 w = __ldg(Tu + kk);
-                const float2 wd = cmul(cconj(w), dif);
-                row[pk] = make_float2(sum.x - wd.y, sum.y + wd.x);   // sum + i wd
-                if (kk > 0 && 2 * kk != hu) {
-                    // Z[hu - k] = (X_{hu-k} + conj X_k) - i exp(-2 pi i k / pu) (X_{hu-k} - conj X_k)
-                    const float2 yk = cconj(xc), yc = cconj(xk);   // X_{hu-k}, conj X_k
-                    const float2 s2 = cadd(yk, yc), d2 = csub(yk, yc);
-                    const float2 w2 = cmul(w, d2);
-                    row[pc] = make_float2(s2.x + w2.y, s2.y - w2.x);   // s2 - i w2
-                }
-            }
-        }
-        __syncthreads();
-        // inverse rows; the last pass writes the output box:
-        // (u, v) holds real sample (u - in_i0) mod pu of row (v - in_j0) mod pv
-        OutCtx oc;
-        oc.dst = ADJ ? P.adjbuf + (long long)bl * P.cap_a + st.off_a
-                     : P.region + (long long)bl * P.cap_o + st.off_o;
-        oc.out_w = bx.out_i1 - bx.out_i0;
-        oc.in_i0 = bx.in_i0;
-        oc.out_i0 = bx.out_i0;
-        oc.out_i1 = bx.out_i1;
-        oc.pu = pu;
-        fft_run<false, true>(S, G, G.n_rows_out, G.out_row0, hu, Tu, 2, Kf, kv_of, ku_of, 1 << 30, &oc);
+        const int item = *s_item;
+        if (item >= A.n_items) break;
+        int e = 0;
+        while (e + 1 < A.n_ent && A.round[e + 1].z <= item) ++e;
+        const FftPlan &P = A.plan[e];
+        const int4 r = A.round[e];
+        unsigned int *ctr = P.fft_ctr + 4 * r.w + (ADJ ? 2 : 0);
+        fft_slice<ADJ>(P, P.R, r.x, item - r.z, P.fft_pmax, P.fft_over, ctr + 1, sm);
     }
 }
 
@@ -862,6 +934,14 @@ const void *fft_kernel_for(int minb)
     if (minb >= 4) return (const void *)k_conv_fft<ADJ, 4>;
     if (minb == 3) return (const void *)k_conv_fft<ADJ, 3>;
     return (const void *)k_conv_fft<ADJ, 2>;
+}
+
+template <bool ADJ>
+const void *fft_multi_kernel_for(int minb)
+{
+    if (minb >= 4) return (const void *)k_conv_fft_multi<ADJ, 4>;
+    if (minb == 3) return (const void *)k_conv_fft_multi<ADJ, 3>;
+    return (const void *)k_conv_fft_multi<ADJ, 2>;
 }
 
 struct SmemLimits {
@@ -896,6 +976,32 @@ cudaError_t launch_conv_fft(const PlanDev &P, int b0, int nb, bool adjoint, int 
     return cudaLaunchKernel(k, dim3(grid_blocks), dim3(kFftThreads), args, smem, s);
 }
 
+cudaError_t launch_conv_fft_multi(const FftPlan *plans, const int4 *round, int n_ent, int pmax, int smem,
+                                  int grid_blocks, bool adjoint, unsigned int *counters, cudaStream_t s)
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int minb = grid_blocks / (sms > 0 ? sms : 1);
+    const void *k = adjoint ? fft_multi_kernel_for<true>(minb) : fft_multi_kernel_for<false>(minb);
+    static thread_local FftBatchArgs A;   // 22 KB: not on the stack
+    for (int g = 0; g * kFftBatchMax < n_ent; ++g) {
+        const int e0 = g * kFftBatchMax, ne = std::min(kFftBatchMax, n_ent - e0);
+        A.n_ent = ne;
+        A.n_items = 0;
+        for (int e = 0; e < ne; ++e) {
+            A.plan[e] = plans[e0 + e];
+            A.round[e] = make_int4(round[e0 + e].x, round[e0 + e].y, A.n_items, round[e0 + e].w);
+            A.n_items += round[e0 + e].y * plans[e0 + e].lat.nw;
+        }
+        unsigned int *ctr = counters + g;
+        void *args[] = {(void *)&A, (void *)&pmax, (void *)&ctr};
+        const cudaError_t e = cudaLaunchKernel(k, dim3(grid_blocks), dim3(kFftThreads), args, smem, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // CTAs of one direction per SM at a size limit: the shared memory decides
 // how many fit, the register-bound instantiation for that count (2, 3 or 4)
 // must also fit; also uploads the size tables to the current device
@@ -911,9 +1017,11 @@ cudaError_t conv_fft_ctas(int pmax, int R, bool adjoint, int *ctas)
     if (smem > l.optin) return cudaSuccess;
     const int want = std::min(4, fft_ctas_by_smem(pmax, R, l.smem_sm, l.resv));
     if (want < 1) return cudaSuccess;
-    // every instantiation may be launched (the launcher picks by CTAs per SM)
-    for (int mb = 2; mb <= 4 && e == cudaSuccess; ++mb) {
-        const void *km = adjoint ? fft_kernel_for<true>(mb) : fft_kernel_for<false>(mb);
+    // every instantiation may be launched (the launchers pick by CTAs per SM)
+    for (int q = 0; q < 6 && e == cudaSuccess; ++q) {
+        const int mb = 2 + q % 3;
+        const void *km = q < 3 ? (adjoint ? fft_kernel_for<true>(mb) : fft_kernel_for<false>(mb))
+                               : (adjoint ? fft_multi_kernel_for<true>(mb) : fft_multi_kernel_for<false>(mb));
         cudaFuncAttributes fm;
         e = cudaFuncGetAttributes(&fm, km);
         if (e == cudaSuccess)

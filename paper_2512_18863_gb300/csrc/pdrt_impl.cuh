@@ -339,6 +339,48 @@ cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsig
 cudaError_t launch_conv_fft(const PlanDev &P, int b0, int nb, bool adjoint, int pmax, unsigned int *counter,
                             int *over_list, unsigned int *over_count, int grid_blocks, cudaStream_t s);
 int conv_fft_smem_bytes(int pmax, int R);
+// What the FFT convolution reads of a plan: the batched launch carries one
+// of these per entry in its kernel parameters.
+struct FftPlan {
+    Lattice lat;
+    const SliceTab *slices;
+    const CpTab *cptab;
+    const float *fbuf;
+    float *region, *adjbuf;
+    const float *fft_cos;
+    int *fft_over;
+    unsigned int *fft_ctr;
+    long long cap_o, cap_a;
+    int R, fft_pmax;
+};
+inline FftPlan fft_plan_of(const PlanDev &P)
+{
+    FftPlan f;
+    f.lat = P.lat;
+    f.slices = P.slices;
+    f.cptab = P.cptab;
+    f.fbuf = P.fbuf;
+    f.region = P.region;
+    f.adjbuf = P.adjbuf;
+    f.fft_cos = P.fft_cos;
+    f.fft_over = P.fft_over;
+    f.fft_ctr = P.fft_ctr;
+    f.cap_o = P.cap_o;
+    f.cap_a = P.cap_a;
+    f.R = P.mach.R;
+    f.fft_pmax = P.fft_pmax;
+    return f;
+}
+// entries of one batched FFT launch (its kernel parameters stay under the
+// 32 KB limit)
+constexpr int kFftBatchMax = 160;
+// one persistent FFT launch per group of up to kFftBatchMax entries (plan
+// passes): plans[e] with round[e] = {b0, nb, -, pass index} for e < n_ent;
+// counters[g] is the work counter of group g (zeroed beforehand); smem for
+// the largest size limit and kernel radius among them, grid = CTAs per SM x
+// SMs.  Groups: (n_ent + kFftBatchMax - 1) / kFftBatchMax.
+cudaError_t launch_conv_fft_multi(const FftPlan *plans, const int4 *round, int n_ent, int pmax, int smem,
+                                  int grid_blocks, bool adjoint, unsigned int *counters, cudaStream_t s);
 // CTAs per SM of k_conv_fft for a size limit (0 if it does not fit or is
 // below 2 R + 2); uploads the constant size tables to the current device
 cudaError_t conv_fft_ctas(int pmax, int R, bool adjoint, int *ctas);

@@ -30,6 +30,11 @@ def test_batch_matches_individual_calls_and_oracle():
     assert t.shape == (4,) and np.all(t > 0)
     assert b.kernels > 0
     for i, (w, e) in enumerate(zip(ws, engines)):
+        full = e.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).clone()
+        # the pass size only regroups the sum over control points
+        assert torch.allclose(b.dose[i], full, rtol=0, atol=1e-6 * float(full.max()))
+        assert 1 <= b.pass_cp[i] <= e.info["chunk_cp"]
+        e.set_chunk(b.pass_cp[i])
         d = e.forward(w.plan.leaves, w.plan.jaws, w.plan.mu)
         dl, dj, dm = e.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, grads[i])
         assert torch.equal(b.dose[i], d)
@@ -37,6 +42,37 @@ def test_batch_matches_individual_calls_and_oracle():
     ref = O.Model(ws[2].phantom, ws[2].machine, ws[2].plan).dose()
     got = b.dose[2].cpu().numpy().astype(np.float64)
     assert np.abs(got - ref).max() <= 1e-4 * ref.max()
+    b.close()
+    for e in engines:
+        e.close()
+
+
+def test_batch_mixes_convolution_paths_and_fft_size_limits():
+    """One batched FFT launch per round serves plans with different size
+    limits (a small limit sends slices to the tensor-core overflow pass) while
+    tensor-core and SIMT plans run their own kernels on their branches; every
+    result equals the plan's individual call at the batch's pass size bit for
+    bit."""
+    ws = _plans()
+    paths = [("fft", 32), ("tc", None), ("fft", None), ("simt", None)]
+    engines = [DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso, conv=c, fft_pmax=pm)
+               for w, (c, pm) in zip(ws, paths)]
+    assert engines[0].info["fft_pmax"] == 32 and engines[1].info["fft_pmax"] == 0
+    rng = np.random.default_rng(2)
+    grads = [rng.standard_normal(w.phantom.shape).astype(np.float32) for w in ws]
+    grads[1] = None                         # forward only for one plan
+    b = DoseBatch(engines, [w.plan.leaves for w in ws], [w.plan.jaws for w in ws],
+                  [w.plan.mu for w in ws], grads, n_branches=2)
+    b.launch()
+    b.launch()
+    b.plan_times_ms()
+    for i, (w, e) in enumerate(zip(ws, engines)):
+        e.set_chunk(b.pass_cp[i])
+        d = e.forward(w.plan.leaves, w.plan.jaws, w.plan.mu)
+        assert torch.equal(b.dose[i], d), i
+        if grads[i] is not None:
+            dl, dj, dm = e.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, grads[i])
+            assert torch.equal(b.dleaves[i], dl) and torch.equal(b.djaws[i], dj) and torch.equal(b.dmu[i], dm), i
     b.close()
     for e in engines:
         e.close()
