@@ -260,21 +260,50 @@ struct FftGeom {
 // Division by a small positive divisor d (< 2^16) of x < 2^16 by a multiply
 // high: with m = ceil(2^32 / d), floor(x m / 2^32) = floor(x / d) because the
 // error term x (m - 2^32 / d) / 2^32 < 2^-16 < 1 / d cannot reach the next
-// integer.
+// integer.  The multipliers of d <= kFdivMax (every divisor of the
+// transforms: lengths, counts and strides of at most 97) come from a
+// constant table, so a divisor costs one broadcast load instead of a
+// division per thread.
 struct FastDiv {
     unsigned m;
     int d;
 };
+constexpr int kFdivMax = 255;
+__constant__ unsigned g_fft_mh[kFdivMax + 1];   // m(d) = floor((2^32 - 1) / d) + 1, m(0) = m(1) = 0
+__host__ __device__ inline unsigned fast_div_mult(int d)
+{
+    return d > 1 ? (unsigned)(0xFFFFFFFFull / (unsigned)d) + 1u : 0u;
+}
 __device__ __forceinline__ FastDiv fast_div(int d)
 {
     FastDiv f;
     f.d = d;
-    f.m = d > 1 ? (unsigned)(0xFFFFFFFFull / (unsigned)d) + 1u : 0u;
+    f.m = d <= kFdivMax ? g_fft_mh[d] : fast_div_mult(d);
     return f;
 }
 __device__ __forceinline__ int operator/(int x, const FastDiv &f)
 {
     return f.d == 1 ? x : (int)__umulhi((unsigned)x, f.m);
+}
+
+// v[q] *= w^q for q = 1 .. R-1, the powers by a balanced product tree
+// (w^q = w^h w^(q-h), h the largest power of two below q; w^(2h) = (w^h)^2):
+// depth log2 R instead of the R - 2 steps of a recurrence, so the
+// butterfly's critical path is short and the rounding error grows with the
+// depth (<= 4 products) only
+template <int R>
+__device__ __forceinline__ void twiddle_powers(float2 *v, float2 w)
+{
+    float2 p[R];
+    p[1] = w;
+#pragma unroll
+    for (int q = 2; q < R; ++q) {
+        int h = 1;
+        while (2 * h < q) h *= 2;
+        p[q] = (2 * h == q) ? cmul(p[h], p[h]) : cmul(p[h], p[q - h]);
+    }
+#pragma unroll
+    for (int q = 1; q < R; ++q) v[q] = cmul(v[q], p[q]);
 }
 
 // One radix-R pass over a batch of transforms.
@@ -283,8 +312,8 @@ __device__ __forceinline__ int operator/(int x, const FastDiv &f)
 //   COLS = true : transforms are the hu + 1 columns, length pv, stride pitch.
 //   INV  = false: decimation in frequency (DFT then twiddle W_L^{jq});
 //   INV  = true : decimation in time (conjugate twiddle W_L^{-jm}, then DFT).
-// L is the pass's block size; the twiddle W_L^e = T[e (N / L) tmul] with T
-// the table of exp(-2 pi i t / (N tmul)).  MUL (first inverse column pass):
+// L is the pass's block size and nl = N / L; the twiddle W_L^e =
+// T[e nl tmul] with T the table of exp(-2 pi i t / (N tmul)).  MUL (first inverse column pass):
 // every element read is first multiplied by the kernel spectrum.
 // Output of the last inverse row pass, written straight to the region: real
 // sample n of row tr is output u = in_i0 + n (or n - pu) of output row tr.
@@ -295,7 +324,7 @@ struct OutCtx {
 
 template <int R, bool COLS, bool INV, bool MUL, bool OUT = false>
 __device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &G, int n_tr, int row0, int N,
-                                         int L, const float2 *__restrict__ T, int tmul,
+                                         int L, int nl, const float2 *__restrict__ T, int tmul,
                                          const float *__restrict__ Kf, const short *__restrict__ kv_of,
                                          const short *__restrict__ ku_of, int valid = 1 << 30,
                                          const OutCtx *oc = nullptr)
@@ -303,7 +332,7 @@ __device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &
     const int M = L / R;
     const int per_tr = N / R;
     const int total = n_tr * per_tr;
-    const int tstep = (N / L) * tmul;
+    const int tstep = nl * tmul;
     const FastDiv div_tr = fast_div(COLS ? n_tr : per_tr), div_m = fast_div(M);
     for (int b = threadIdx.x; b < total; b += kFftThreads) {
         const int q0 = b / div_tr;
@@ -337,30 +366,13 @@ __device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &
 #pragma unroll
             for (int m = 0; m < R; ++m) v[m] = cscale(v[m], Kf[__ldg(kv_of + e0 + m * M) * G.pitch + ku]);
         }
-        // twiddles W_L^{j q}, q = 1..R-1, by recurrence from one table read
-        // (relative error grows by ~1 ulp per step: < 2e-6 at R = 16)
+        // twiddles W_L^{j q}, q = 1..R-1, from one table read
         if (INV) {
-            if (j) {
-                const float2 w1 = cconj(__ldg(T + j * tstep));
-                float2 w = w1;
-#pragma unroll
-                for (int m = 1; m < R; ++m) {
-                    v[m] = cmul(v[m], w);
-                    if (m + 1 < R) w = cmul(w, w1);
-                }
-            }
+            if (j) twiddle_powers<R>(v, cconj(__ldg(T + j * tstep)));
             dft<R, 1>(v);
         } else {
             dft<R, -1>(v);
-            if (j) {
-                const float2 w1 = __ldg(T + j * tstep);
-                float2 w = w1;
-#pragma unroll
-                for (int q = 1; q < R; ++q) {
-                    v[q] = cmul(v[q], w);
-                    if (q + 1 < R) w = cmul(w, w1);
-                }
-            }
+            if (j) twiddle_powers<R>(v, __ldg(T + j * tstep));
         }
         if (OUT) {
             // natural order: complex element e0 + q M holds reals 2 (e0 + q M) and + 1
@@ -383,11 +395,11 @@ __device__ __forceinline__ void fft_pass(float2 *__restrict__ S, const FftGeom &
 
 template <bool COLS, bool INV, bool MUL, bool OUT = false>
 __device__ __forceinline__ void fft_pass_r(int R, float2 *S, const FftGeom &G, int n_tr, int row0, int N, int L,
-                                           const float2 *T, int tmul, const float *Kf, const short *kv_of,
+                                           int nl, const float2 *T, int tmul, const float *Kf, const short *kv_of,
                                            const short *ku_of, int valid = 1 << 30, const OutCtx *oc = nullptr)
 {
 #define PDRT_FFT_PASS(RR) \
-    fft_pass<RR, COLS, INV, MUL, OUT>(S, G, n_tr, row0, N, L, T, tmul, Kf, kv_of, ku_of, valid, oc)
+    fft_pass<RR, COLS, INV, MUL, OUT>(S, G, n_tr, row0, N, L, nl, T, tmul, Kf, kv_of, ku_of, valid, oc)
     switch (R) {
     case 3: PDRT_FFT_PASS(3); break;
     case 4: PDRT_FFT_PASS(4); break;
@@ -414,24 +426,24 @@ __device__ void fft_run(float2 *S, const FftGeom &G, int n_tr, int row0, int N, 
     const Radices rd = radices_of(N);
     const int r0 = rd.r[0], L1 = N / r0;
     if (!INV) {
-        fft_pass_r<COLS, false, false>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of, valid);
+        fft_pass_r<COLS, false, false>(r0, S, G, n_tr, row0, N, N, 1, T, tmul, Kf, kv_of, ku_of, valid);
         __syncthreads();
         if (rd.np > 1) {
-            fft_pass_r<COLS, false, false>(rd.r[1], S, G, n_tr, row0, N, L1, T, tmul, Kf, kv_of, ku_of);
+            fft_pass_r<COLS, false, false>(rd.r[1], S, G, n_tr, row0, N, L1, r0, T, tmul, Kf, kv_of, ku_of);
             __syncthreads();
         }
     } else {
         if (rd.np > 1) {
-            fft_pass_r<COLS, true, COLS>(rd.r[1], S, G, n_tr, row0, N, L1, T, tmul, Kf, kv_of, ku_of);
+            fft_pass_r<COLS, true, COLS>(rd.r[1], S, G, n_tr, row0, N, L1, r0, T, tmul, Kf, kv_of, ku_of);
             __syncthreads();
         }
         if (!COLS && oc) {
-            fft_pass_r<false, true, false, true>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of, 1 << 30,
+            fft_pass_r<false, true, false, true>(r0, S, G, n_tr, row0, N, N, 1, T, tmul, Kf, kv_of, ku_of, 1 << 30,
                                                  oc);
         } else if (rd.np > 1) {
-            fft_pass_r<COLS, true, false>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
+            fft_pass_r<COLS, true, false>(r0, S, G, n_tr, row0, N, N, 1, T, tmul, Kf, kv_of, ku_of);
         } else {
-            fft_pass_r<COLS, true, COLS>(r0, S, G, n_tr, row0, N, N, T, tmul, Kf, kv_of, ku_of);
+            fft_pass_r<COLS, true, COLS>(r0, S, G, n_tr, row0, N, N, 1, T, tmul, Kf, kv_of, ku_of);
         }
         __syncthreads();
     }
@@ -547,6 +559,9 @@ cudaError_t conv_fft_tables_upload()
     if ((e = cudaMemcpyToSymbol(g_fft_pos, pos.data(), sizeof(short) * kPosTotal)) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(g_fft_ku, ku.data(), sizeof(short) * kKuTotal)) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(g_fft_kv, kv.data(), sizeof(short) * kKvTotal)) != cudaSuccess) return e;
+    unsigned mh[kFdivMax + 1];
+    for (int d = 0; d <= kFdivMax; ++d) mh[d] = fast_div_mult(d);
+    if ((e = cudaMemcpyToSymbol(g_fft_mh, mh, sizeof(mh))) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = true;
     return cudaSuccess;
 }
