@@ -524,24 +524,32 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
         }
     }
     // FFT convolution: default size limit from the kernel radius (inputs up
-    // to ~48 pixels wide fit; wider slices take the tensor-core path), needs
-    // the tensor-core kernel for the overflow
+    // to ~48 pixels wide fit; wider slices take the tensor-core path), raised
+    // to the largest size with as many CTAs per SM (a larger limit only
+    // changes the shared-memory layout, not a slice's work); needs the
+    // tensor-core kernel for the overflow
     P.fft_pmax = 0;
     p->fft_blocks[0] = p->fft_blocks[1] = 0;
     if (P.tc_enabled) {
         const int want = fft_size_for(2 * M.R + 48) ? fft_size_for(2 * M.R + 48) : 192;
-        const int sizes[10] = {192, 160, 128, 120, 96, 80, 64, 48, 40, 32};
-        for (int t = 0; t < 10 && !P.fft_pmax; ++t) {
+        const int sizes[11] = {192, 160, 144, 128, 120, 96, 80, 64, 48, 40, 32};
+        int base_f = 0, base_a = 0;
+        for (int t = 0; t < 11 && !P.fft_pmax; ++t) {   // the base limit
             const int pm = sizes[t];
             if (pm > want || pm < 2 * M.R + 2) continue;
+            PLAN_TRY(conv_fft_ctas(pm, M.R, false, &base_f), "fft convolution set-up");
+            PLAN_TRY(conv_fft_ctas(pm, M.R, true, &base_a), "fft convolution set-up");
+            if (base_f > 0 && base_a > 0) P.fft_pmax = pm;
+        }
+        for (int t = 0; t < 11 && P.fft_pmax && sizes[t] > P.fft_pmax; ++t) {   // as many CTAs
             int cf = 0, ca = 0;
-            PLAN_TRY(conv_fft_ctas(pm, M.R, false, &cf), "fft convolution set-up");
-            PLAN_TRY(conv_fft_ctas(pm, M.R, true, &ca), "fft convolution set-up");
-            if (cf > 0 && ca > 0) {
-                P.fft_pmax = pm;
-                p->fft_blocks[0] = cf * g->sm_count;
-                p->fft_blocks[1] = ca * g->sm_count;
-            }
+            PLAN_TRY(conv_fft_ctas(sizes[t], M.R, false, &cf), "fft convolution set-up");
+            PLAN_TRY(conv_fft_ctas(sizes[t], M.R, true, &ca), "fft convolution set-up");
+            if (cf == base_f && ca == base_a) P.fft_pmax = sizes[t];
+        }
+        if (P.fft_pmax) {
+            p->fft_blocks[0] = base_f * g->sm_count;
+            p->fft_blocks[1] = base_a * g->sm_count;
         }
     }
 #undef PLAN_TRY
@@ -697,7 +705,7 @@ pdrt_status pdrt_plan_set_fft(pdrt_plan_t p, int32_t pmax)
     if (!p->dev.tc_enabled)
         return fail(PDRT_EINVAL, "the FFT convolution needs the tensor-core path for its overflow");
     if (pmax < 0 || fft_size_for(pmax) != pmax)
-        return fail(PDRT_EINVAL, "unsupported FFT size %d (32, 40, 48, 64, 80, 96, 120, 128, 160, 192)", pmax);
+        return fail(PDRT_EINVAL, "unsupported FFT size %d (32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192)", pmax);
     if (pmax < 2 * p->dev.mach.R + 2)
         return fail(PDRT_EINVAL, "FFT size %d is below 2 R + 2 = %d for this kernel radius", pmax,
                     2 * p->dev.mach.R + 2);
@@ -906,7 +914,7 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
     // FFT size limits that fit (each with its CTAs per SM)
     std::vector<int> fft_ok;
     if (tc_ok)
-        for (int pm : {32, 40, 48, 64, 80, 96, 120, 128, 160, 192}) {
+        for (int pm : {32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192}) {
             if (pm < 2 * R + 2) continue;
             int cf = 0, ca = 0;
             CU_TRY(conv_fft_ctas(pm, R, false, &cf), "fft occupancy");

@@ -22,7 +22,7 @@
 //   4. product with Kf, inverse FFT along v, inverse real FFT along u of the
 //      output rows, and the output box written out.
 // The complex FFTs are in place in shared memory: mixed-radix (2, 3, 4, 5,
-// 8, 16) decimation in frequency forward, leaving the spectrum in
+// 8, 9, 16) decimation in frequency forward, leaving the spectrum in
 // digit-reversed order, and decimation in time backward, which takes that
 // order and returns natural order, so no reordering pass exists; every
 // element belongs to one butterfly per pass and one barrier separates the
@@ -44,7 +44,7 @@ namespace pdrt {
 namespace {
 
 constexpr int kFftThreads = 256;
-constexpr int kNumFftSizes = 10;
+constexpr int kNumFftSizes = 11;
 
 struct Radices {
     int np;
@@ -64,10 +64,12 @@ __host__ __device__ inline Radices radices_of(int n)
     case 48: return {2, {16, 3, 1}};
     case 60: return {2, {12, 5, 1}};
     case 64: return {2, {8, 8, 1}};
+    case 72: return {2, {8, 9, 1}};
     case 80: return {2, {16, 5, 1}};
     case 96: return {2, {16, 6, 1}};
     case 120: return {2, {12, 10, 1}};
     case 128: return {2, {16, 8, 1}};
+    case 144: return {2, {16, 9, 1}};
     case 160: return {2, {16, 10, 1}};
     case 192: return {2, {16, 12, 1}};
     default: return {0, {1, 1, 1}};
@@ -231,6 +233,16 @@ __device__ __forceinline__ void dft(float2 *v)
                                {1.f, 0.f}, {-0.5f, 0.86602540378443865f}};
         dft_ct<2, 3, S>(v, w);
     } else if constexpr (R == 8) dft8<S>(v);
+    else if constexpr (R == 9) {
+        // A = 3, B = 3: twiddles 2 pi n2 k1 / 9
+        const float c40 = 0.76604444311897804f, s40 = 0.64278760968653933f;
+        const float c80 = 0.17364817766693035f, s80 = 0.98480775301220806f;
+        const float c160 = -0.93969262078590838f, s160 = 0.34202014332566873f;
+        const float w[9][2] = {{1.f, 0.f}, {1.f, 0.f}, {1.f, 0.f},
+                               {1.f, 0.f}, {c40, s40}, {c80, s80},
+                               {1.f, 0.f}, {c80, s80}, {c160, s160}};
+        dft_ct<3, 3, S>(v, w);
+    }
     else if constexpr (R == 10) {
         // A = 2, B = 5: twiddles 2 pi n2 / 10 for k1 = 1
         const float w[10][2] = {{1.f, 0.f}, {1.f, 0.f},
@@ -406,6 +418,7 @@ __device__ __forceinline__ void fft_pass_r(int R, float2 *S, const FftGeom &G, i
     case 5: PDRT_FFT_PASS(5); break;
     case 6: PDRT_FFT_PASS(6); break;
     case 8: PDRT_FFT_PASS(8); break;
+    case 9: PDRT_FFT_PASS(9); break;
     case 10: PDRT_FFT_PASS(10); break;
     case 12: PDRT_FFT_PASS(12); break;
     default: PDRT_FFT_PASS(16); break;
@@ -484,8 +497,8 @@ __host__ __device__ inline int dif_freq(int p, int N)
 //   ku : frequency held at position c of that DIF (c < P/2), P/2 at c = P/2
 //   kv : min(f, P - f), f the frequency at position e of the DIF of length P
 // Constant, uploaded once per device (computed on the host in double).
-constexpr int kSizes[kNumFftSizes] = {32, 40, 48, 64, 80, 96, 120, 128, 160, 192};
-constexpr int kTwTotal = 960, kPosTotal = 480, kKuTotal = 490, kKvTotal = 960;
+constexpr int kSizes[kNumFftSizes] = {32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192};
+constexpr int kTwTotal = 1104, kPosTotal = 552, kKuTotal = 563, kKvTotal = 1104;
 __device__ float2 g_fft_tw[kTwTotal];
 __device__ short g_fft_pos[kPosTotal];
 __device__ short g_fft_ku[kKuTotal];
@@ -499,7 +512,7 @@ struct SizeOff {
 // (rows of (P/2 + 1) rounded up to 4 floats, R + 1 rows per size)
 __host__ __device__ inline SizeOff size_offsets(int P, int R)
 {
-    const int sizes[kNumFftSizes] = {32, 40, 48, 64, 80, 96, 120, 128, 160, 192};
+    const int sizes[kNumFftSizes] = {32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192};
     SizeOff o = {0, 0, 0, 0, 0};
     for (int i = 0; i < kNumFftSizes && sizes[i] < P; ++i) {
         const int q = sizes[i];

@@ -256,7 +256,7 @@ def test_tensor_and_simt_paths_match_oracle_on_arc_subset():
         _assert_dose(d.astype(np.float64), ref)
 
 
-@pytest.mark.parametrize("pmax", [32, 48, 64, 80, 96, 120, 128, 160, 192])
+@pytest.mark.parametrize("pmax", [32, 48, 64, 80, 96, 120, 128, 144, 160, 192])
 def test_fft_size_limits_and_overflow_match_oracle(pmax):
     """The FFT convolution at every supported size limit: slices whose padded
     sizes exceed it go to the tensor cores through the overflow list (at the
@@ -283,6 +283,36 @@ def test_fft_size_limits_and_overflow_match_oracle(pmax):
     _assert_grad(dl, rl, "leaves")
     _assert_grad(dj, rj, "jaws")
     _assert_grad(dm, rm, "mu")
+
+
+def test_fft_size_144_radix9_matches_oracle():
+    """Slices whose padded u size falls in (128, 144]: with the size limit at
+    128 they overflow to the tensor cores, at 144 they go by FFT (rows of
+    72 = 8 x 9, the radix-9 passes; the wider ones stay on the tensor cores);
+    dose and gradients of both against the oracle."""
+    w = S.small_pelvis(seed=29, n=(16, 160, 160), spacing=2.0, n_cp=2, r_px=44,
+                       ptv_radii=(46.0, 40.0, 12.0))
+    g = np.random.default_rng(144).standard_normal(w.phantom.shape).astype(np.float32)
+    out = {}
+    for pmax in (128, 144):
+        eng = _engine(w, conv="fft", fft_pmax=pmax)
+        assert eng.info["fft_pmax"] == pmax
+        d = eng.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).cpu().numpy().astype(np.float64)
+        grads = [t.cpu().numpy().astype(np.float64)
+                 for t in eng.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, g)]
+        out[pmax] = (d, grads, eng.work())
+        assert eng.status_flags() == 0
+        eng.close()
+    assert out[144][2]["tc_slices"] < out[128][2]["tc_slices"]
+    assert out[144][2]["fft_slices"] > out[128][2]["fft_slices"]
+    mod = O.Model(w.phantom, w.machine, w.plan)
+    ref = mod.dose()
+    rgrads = mod.dose_grad(g.astype(np.float64))
+    for pmax in (128, 144):
+        d, grads, _ = out[pmax]
+        _assert_dose(d, ref)
+        for gg, rr, name in zip(grads, rgrads, ("leaves", "jaws", "mu")):
+            _assert_grad(gg, rr, name)
 
 
 def test_plan_without_control_points_is_rejected():
