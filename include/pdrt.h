@@ -283,8 +283,8 @@ pdrt_status pdrt_plan_set_tensor_cores(pdrt_plan_t p, int32_t enable);
  * FFT convolution (Sec. 2.2.6 computed by FP32 FFTs in shared memory, the
  * default): slices whose padded transform sizes are at most pmax are
  * convolved by FFT, the others by the tensor-core kernel.  pmax = 0 turns it
- * off; otherwise one of 32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192 (sets the
- * shared memory per CTA and so the CTAs per SM).  The upload picks the
+ * off; otherwise one of 32, 40, 48, 60, 64, 72, 80, 90, 96, 100, 108, 120,
+ * 128, 144, 160, 192 (sets the shared memory per CTA and so the CTAs per SM).  The upload picks the
  * smallest size that holds a 48-pixel input plus the kernel's 2R margin,
  * raised to the largest size that keeps as many CTAs per SM.
  * Host only.  Errors: EINVAL (NULL plan, unsupported size, size below

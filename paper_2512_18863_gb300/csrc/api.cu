@@ -532,16 +532,16 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     p->fft_blocks[0] = p->fft_blocks[1] = 0;
     if (P.tc_enabled) {
         const int want = fft_size_for(2 * M.R + 48) ? fft_size_for(2 * M.R + 48) : 192;
-        const int sizes[11] = {192, 160, 144, 128, 120, 96, 80, 64, 48, 40, 32};
+        const int sizes[16] = {192, 160, 144, 128, 120, 108, 100, 96, 90, 80, 72, 64, 60, 48, 40, 32};
         int base_f = 0, base_a = 0;
-        for (int t = 0; t < 11 && !P.fft_pmax; ++t) {   // the base limit
+        for (int t = 0; t < 16 && !P.fft_pmax; ++t) {   // the base limit
             const int pm = sizes[t];
             if (pm > want || pm < 2 * M.R + 2) continue;
             PLAN_TRY(conv_fft_ctas(pm, M.R, false, &base_f), "fft convolution set-up");
             PLAN_TRY(conv_fft_ctas(pm, M.R, true, &base_a), "fft convolution set-up");
             if (base_f > 0 && base_a > 0) P.fft_pmax = pm;
         }
-        for (int t = 0; t < 11 && P.fft_pmax && sizes[t] > P.fft_pmax; ++t) {   // as many CTAs
+        for (int t = 0; t < 16 && P.fft_pmax && sizes[t] > P.fft_pmax; ++t) {   // as many CTAs
             int cf = 0, ca = 0;
             PLAN_TRY(conv_fft_ctas(sizes[t], M.R, false, &cf), "fft convolution set-up");
             PLAN_TRY(conv_fft_ctas(sizes[t], M.R, true, &ca), "fft convolution set-up");
@@ -705,7 +705,7 @@ pdrt_status pdrt_plan_set_fft(pdrt_plan_t p, int32_t pmax)
     if (!p->dev.tc_enabled)
         return fail(PDRT_EINVAL, "the FFT convolution needs the tensor-core path for its overflow");
     if (pmax < 0 || fft_size_for(pmax) != pmax)
-        return fail(PDRT_EINVAL, "unsupported FFT size %d (32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192)", pmax);
+        return fail(PDRT_EINVAL, "unsupported FFT size %d (32, 40, 48, 60, 64, 72, 80, 90, 96, 100, 108, 120, 128, 144, 160, 192)", pmax);
     if (pmax < 2 * p->dev.mach.R + 2)
         return fail(PDRT_EINVAL, "FFT size %d is below 2 R + 2 = %d for this kernel radius", pmax,
                     2 * p->dev.mach.R + 2);
@@ -914,7 +914,7 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
     // FFT size limits that fit (each with its CTAs per SM)
     std::vector<int> fft_ok;
     if (tc_ok)
-        for (int pm : {32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192}) {
+        for (int pm : {32, 40, 48, 60, 64, 72, 80, 90, 96, 100, 108, 120, 128, 144, 160, 192}) {
             if (pm < 2 * R + 2) continue;
             int cf = 0, ca = 0;
             CU_TRY(conv_fft_ctas(pm, R, false, &cf), "fft occupancy");

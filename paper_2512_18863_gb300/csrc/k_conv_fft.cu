@@ -44,7 +44,7 @@ namespace pdrt {
 namespace {
 
 constexpr int kFftThreads = 256;
-constexpr int kNumFftSizes = 11;
+constexpr int kNumFftSizes = 16;
 
 struct Radices {
     int np;
@@ -59,14 +59,22 @@ __host__ __device__ inline Radices radices_of(int n)
     case 16: return {1, {16, 1, 1}};
     case 20: return {2, {4, 5, 1}};
     case 24: return {2, {8, 3, 1}};
+    case 30: return {2, {6, 5, 1}};
     case 32: return {2, {8, 4, 1}};
+    case 36: return {2, {6, 6, 1}};
     case 40: return {2, {8, 5, 1}};
+    case 45: return {2, {9, 5, 1}};
     case 48: return {2, {16, 3, 1}};
+    case 50: return {2, {10, 5, 1}};
+    case 54: return {2, {6, 9, 1}};
     case 60: return {2, {12, 5, 1}};
     case 64: return {2, {8, 8, 1}};
     case 72: return {2, {8, 9, 1}};
     case 80: return {2, {16, 5, 1}};
+    case 90: return {2, {10, 9, 1}};
     case 96: return {2, {16, 6, 1}};
+    case 100: return {2, {10, 10, 1}};
+    case 108: return {2, {12, 9, 1}};
     case 120: return {2, {12, 10, 1}};
     case 128: return {2, {16, 8, 1}};
     case 144: return {2, {16, 9, 1}};
@@ -497,8 +505,8 @@ __host__ __device__ inline int dif_freq(int p, int N)
 //   ku : frequency held at position c of that DIF (c < P/2), P/2 at c = P/2
 //   kv : min(f, P - f), f the frequency at position e of the DIF of length P
 // Constant, uploaded once per device (computed on the host in double).
-constexpr int kSizes[kNumFftSizes] = {32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192};
-constexpr int kTwTotal = 1104, kPosTotal = 552, kKuTotal = 563, kKvTotal = 1104;
+constexpr int kSizes[kNumFftSizes] = {32, 40, 48, 60, 64, 72, 80, 90, 96, 100, 108, 120, 128, 144, 160, 192};
+constexpr int kTwTotal = 1534, kPosTotal = 767, kKuTotal = 783, kKvTotal = 1534;
 __device__ float2 g_fft_tw[kTwTotal];
 __device__ short g_fft_pos[kPosTotal];
 __device__ short g_fft_ku[kKuTotal];
@@ -512,7 +520,7 @@ struct SizeOff {
 // (rows of (P/2 + 1) rounded up to 4 floats, R + 1 rows per size)
 __host__ __device__ inline SizeOff size_offsets(int P, int R)
 {
-    const int sizes[kNumFftSizes] = {32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192};
+    const int sizes[kNumFftSizes] = {32, 40, 48, 60, 64, 72, 80, 90, 96, 100, 108, 120, 128, 144, 160, 192};
     SizeOff o = {0, 0, 0, 0, 0};
     for (int i = 0; i < kNumFftSizes && sizes[i] < P; ++i) {
         const int q = sizes[i];

@@ -224,8 +224,8 @@ __device__ __forceinline__ float fluence_sample(const float *__restrict__ F, int
 // lengths (P along v, P / 2 along u) have radix plans in k_conv_fft.
 __host__ __device__ inline int fft_size_for(int n)
 {
-    const int sizes[11] = {32, 40, 48, 64, 80, 96, 120, 128, 144, 160, 192};
-    for (int t = 0; t < 11; ++t)
+    const int sizes[16] = {32, 40, 48, 60, 64, 72, 80, 90, 96, 100, 108, 120, 128, 144, 160, 192};
+    for (int t = 0; t < 16; ++t)
         if (sizes[t] >= n) return sizes[t];
     return 0;
 }

@@ -256,7 +256,7 @@ def test_tensor_and_simt_paths_match_oracle_on_arc_subset():
         _assert_dose(d.astype(np.float64), ref)
 
 
-@pytest.mark.parametrize("pmax", [32, 48, 64, 80, 96, 120, 128, 144, 160, 192])
+@pytest.mark.parametrize("pmax", [32, 48, 60, 64, 72, 80, 90, 96, 100, 108, 120, 128, 144, 160, 192])
 def test_fft_size_limits_and_overflow_match_oracle(pmax):
     """The FFT convolution at every supported size limit: slices whose padded
     sizes exceed it go to the tensor cores through the overflow list (at the
