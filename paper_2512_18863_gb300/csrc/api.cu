@@ -1253,33 +1253,42 @@ pdrt_status pdrt_batch_create(pdrt_batch_t *out, int32_t n, const pdrt_grid_t *g
         }
         join();
         // forward: per round the shared FFT launch over pass c of every FFT
-        // plan, then per plan on its branch the rest of its convolution and
-        // its gather
+        // plan, then per plan on its branch the rest of its convolution, then
+        // one shared gather launch over pass c of every plan
+        std::vector<GatherEntry> gents;
+        auto gather_round = [&](int c, bool transpose) {
+            gents.clear();
+            for (int i = 0; i < n; ++i) {
+                if (c >= nch[i] || (transpose && !adj[i])) continue;
+                pdrt_plan_t p = plans[i];
+                GatherEntry E;
+                memset(&E, 0, sizeof(E));
+                E.p = gather_plan_of(p->dev);
+                E.b0 = c * p->chunk;
+                E.nb = std::min(p->chunk, p->n_cp - E.b0);
+                E.first = c == 0;
+                E.dose = dose_dev[i];
+                E.gd = transpose ? dose_grad_dev[i] : nullptr;
+                gents.push_back(E);
+            }
+            if (!gents.empty()) chk(launch_gather_multi(gents.data(), (int)gents.size(), transpose, s));
+        };
         for (int c = 0; c < rounds; ++c) {
             fft_round(0, c);
             fork();
             for (int i = 0; i < n; ++i) {
                 if (c >= nch[i]) continue;
-                pdrt_plan_t p = plans[i];
-                const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
                 chk(conv_rest(i, c, false));
-                chk(launch_gather(p->dev, b0, nb, dose_dev[i], c == 0, bstream(i)));
-                if (c == nch[i] - 1 && !adj[i])
-                    cudaEventRecordWithFlags(b->marks[1 + i], bstream(i), cudaEventRecordExternal);
             }
             join();
+            gather_round(c, false);
+            for (int i = 0; i < n; ++i)
+                if (c == nch[i] - 1 && !adj[i]) cudaEventRecordWithFlags(b->marks[1 + i], s, cudaEventRecordExternal);
         }
-        // adjoint in the same rounds: gradient gathers, shared FFT launch,
-        // overflow and transposed magnification
+        // adjoint in the same rounds: shared gradient-gather launch, shared
+        // FFT launch, overflow and transposed magnification per plan
         for (int c = 0; c < rounds; ++c) {
-            fork();
-            for (int i = 0; i < n; ++i) {
-                if (!adj[i] || c >= nch[i]) continue;
-                pdrt_plan_t p = plans[i];
-                const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
-                chk(launch_gather_T(p->dev, b0, nb, dose_grad_dev[i], bstream(i)));
-            }
-            join();
+            gather_round(c, true);
             fft_round(1, c);
             fork();
             for (int i = 0; i < n; ++i) {

@@ -31,7 +31,8 @@ namespace pdrt {
 // outside the slices' output boxes and the lattice; the coordinate and
 // slice-record work is shared by the two planes.  The voxel's beam
 // coordinates (fu, fw) use the same float expression as voxel_to_beam.
-__device__ __forceinline__ void sample_cp2(const PlanDev &P, int bl, int b, float fu, float fw, int iz,
+template <class PL>
+__device__ __forceinline__ void sample_cp2(const PL &P, int bl, int b, float fu, float fw, int iz,
                                            float &va, float &vb)
 {
     const Lattice &L = P.lat;
@@ -65,19 +66,22 @@ __device__ __forceinline__ void sample_cp2(const PlanDev &P, int bl, int b, floa
     }
 }
 
-__global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float *__restrict__ dose,
-                                                int first)
+// CTA (tx, ty, tz) of one plan's gather: voxel columns 32 tx .. + 31,
+// 8 ty .. + 7 of planes 2 tz and 2 tz + 1
+template <class PL>
+__device__ __forceinline__ void gather_block(const PL &P, int b0, int nb, float *__restrict__ dose, int first,
+                                             int tx, int ty, int tz)
 {
     // warp w covers voxels 8 x 4 (x, y) of the CTA's 32 x 8: whatever the
     // gantry angle, a warp's samples then fall in few beam slices and rows
     const int wq = threadIdx.x >> 5, lq = threadIdx.x & 31;
-    const int ix = blockIdx.x * 32 + (wq & 3) * 8 + (lq & 7);
-    const int iy = blockIdx.y * 8 + (wq >> 2) * 4 + (lq >> 3);
-    const int iz = 2 * blockIdx.z;          // planes iz and iz + 1 (if inside)
+    const int ix = tx * 32 + (wq & 3) * 8 + (lq & 7);
+    const int iy = ty * 8 + (wq >> 2) * 4 + (lq >> 3);
+    const int iz = 2 * tz;                  // planes iz and iz + 1 (if inside)
     const bool has1 = iz + 1 < P.nz;
     const bool inside = ix < P.nx && iy < P.ny;
-    const float bx0 = (float)(blockIdx.x * 32), bx1 = (float)min((int)blockIdx.x * 32 + 31, P.nx - 1);
-    const float by0 = (float)(blockIdx.y * 8), by1 = (float)min((int)blockIdx.y * 8 + 7, P.ny - 1);
+    const float bx0 = (float)(tx * 32), bx1 = (float)min(tx * 32 + 31, P.nx - 1);
+    const float by0 = (float)(ty * 8), by1 = (float)min(ty * 8 + 7, P.ny - 1);
     __shared__ int s_list[kMaxCpPerChunk];
     __shared__ int s_wcnt[8];
     __shared__ float4 s_geo[kMaxCpPerChunk];    // au, bu, cu0, cal * MU
@@ -169,6 +173,12 @@ __global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float
     }
 }
 
+__global__ void __launch_bounds__(256) k_gather(PlanDev P, int b0, int nb, float *__restrict__ dose,
+                                                int first)
+{
+    gather_block(P, b0, nb, dose, first, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 cudaError_t launch_gather(const PlanDev &P, int b0, int nb, float *dose, bool first, cudaStream_t s)
 {
     dim3 grid((P.nx + 31) / 32, (P.ny + 7) / 8, (P.nz + 1) / 2);
@@ -188,10 +198,11 @@ constexpr int kGtCols = 8 * kGtW;    // lattice columns per pass of a CTA (8 war
 // fall in few cache lines at any gantry angle.  Each thread builds its
 // column's taps once (they do not depend on the plane) and sweeps its
 // slice's planes two at a time.
-__global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
+template <class PL>
+__device__ __forceinline__ void gather_t_block(const PL &P, int b0, const float *__restrict__ gd, int tg, int bl)
 {
     const Lattice &L = P.lat;
-    const int kg = blockIdx.x * kGtS, bl = blockIdx.y, b = b0 + bl;
+    const int kg = tg * kGtS, b = b0 + bl;
     const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
     const int sl = lane / kGtW, cl = lane % kGtW;   // slice and column of this lane
     const int k = kg + sl;
@@ -241,11 +252,92 @@ __global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float
     }
 }
 
+__global__ void __launch_bounds__(256) k_gather_T(PlanDev P, int b0, const float *__restrict__ gd)
+{
+    gather_t_block(P, b0, gd, blockIdx.x, blockIdx.y);
+}
+
 cudaError_t launch_gather_T(const PlanDev &P, int b0, int nb, const float *g, cudaStream_t s)
 {
     dim3 grid((P.lat.nw + kGtS - 1) / kGtS, nb);
     k_gather_T<<<grid, 256, 0, s>>>(P, b0, g);
     return cudaGetLastError();
+}
+
+// Batched forms: one launch over the CTAs of several plans' passes (the
+// gather of a round of the batched graph, or its transpose).  Entry e owns
+// CTAs A.ent[e].blk0 .. A.ent[e + 1].blk0 - 1 of the one-dimensional grid,
+// in the order of its plan's own grid (x fastest); its plan view, pass
+// and buffers sit in the kernel parameters (grid constant), read through
+// the constant cache.  Each CTA does exactly what the per-plan kernel's CTA
+// of the same coordinates does, so the results are the per-plan ones bit
+// for bit.
+struct GatherBatchArgs {
+    GatherEntry ent[kGatherBatchMax];
+    int n_ent, n_blk;
+};
+static_assert(sizeof(GatherBatchArgs) <= 32000, "kernel parameters above 32 KB");
+
+__device__ __forceinline__ int gather_entry_of(const GatherBatchArgs &A, int blk)
+{
+    int e = 0;
+    while (e + 1 < A.n_ent && A.ent[e + 1].blk0 <= blk) ++e;
+    return e;
+}
+
+__global__ void __launch_bounds__(256) k_gather_multi(const __grid_constant__ GatherBatchArgs A)
+{
+    const int e = gather_entry_of(A, (int)blockIdx.x);
+    const GatherEntry &E = A.ent[e];
+    const int t = (int)blockIdx.x - E.blk0;
+    const int tx = t % E.gx, r = t / E.gx;
+    gather_block(E.p, E.b0, E.nb, E.dose, E.first, tx, r % E.gy, r / E.gy);
+}
+
+__global__ void __launch_bounds__(256) k_gather_T_multi(const __grid_constant__ GatherBatchArgs A)
+{
+    const int e = gather_entry_of(A, (int)blockIdx.x);
+    const GatherEntry &E = A.ent[e];
+    const int t = (int)blockIdx.x - E.blk0;
+    gather_t_block(E.p, E.b0, E.gd, t % E.gx, t / E.gx);
+}
+
+cudaError_t launch_gather_multi(const GatherEntry *ents, int n, bool transpose, cudaStream_t s)
+{
+    static thread_local GatherBatchArgs A;   // ~20 KB: not on the stack
+    for (int g0 = 0; g0 < n; g0 += kGatherBatchMax) {
+        const int ne = n - g0 < kGatherBatchMax ? n - g0 : kGatherBatchMax;
+        A.n_ent = ne;
+        long long blk = 0;
+        for (int e = 0; e < ne; ++e) {
+            GatherEntry E = ents[g0 + e];
+            const GatherPlan &P = E.p;
+            if (transpose) {
+                if (!E.gd) return cudaErrorInvalidValue;
+                E.gx = (P.lat.nw + kGtS - 1) / kGtS;
+                E.gy = E.nb;
+            } else {
+                if (!E.dose) return cudaErrorInvalidValue;
+                E.gx = (P.nx + 31) / 32;
+                E.gy = (P.ny + 7) / 8;
+            }
+            const long long nblk = transpose ? (long long)E.gx * E.gy
+                                             : (long long)E.gx * E.gy * ((P.nz + 1) / 2);
+            E.blk0 = (int)blk;
+            blk += nblk;
+            A.ent[e] = E;
+        }
+        if (blk >= (1LL << 31)) return cudaErrorInvalidValue;
+        A.n_blk = (int)blk;
+        if (!blk) continue;
+        if (transpose)
+            k_gather_T_multi<<<(unsigned)blk, 256, 0, s>>>(A);
+        else
+            k_gather_multi<<<(unsigned)blk, 256, 0, s>>>(A);
+        const cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace pdrt

@@ -324,6 +324,47 @@ cudaError_t launch_conv(const PlanDev &P, int b0, int nb, bool adjoint, unsigned
 cudaError_t launch_gather(const PlanDev &P, int b0, int nb, float *dose, bool first,
                           cudaStream_t s);
 cudaError_t launch_gather_T(const PlanDev &P, int b0, int nb, const float *g, cudaStream_t s);
+// What the gather and its transpose read of a plan: the batched launches
+// carry one of these per entry in their kernel parameters.
+struct GatherPlan {
+    Lattice lat;
+    int nx, ny, nz;
+    const CpTab *cptab;
+    const CpGeo *cpgeo;
+    const SliceTab *slices;
+    const int4 *gbox;
+    float *region;
+    long long cap_o;
+};
+inline GatherPlan gather_plan_of(const PlanDev &P)
+{
+    GatherPlan g;
+    g.lat = P.lat;
+    g.nx = P.nx;
+    g.ny = P.ny;
+    g.nz = P.nz;
+    g.cptab = P.cptab;
+    g.cpgeo = P.cpgeo;
+    g.slices = P.slices;
+    g.gbox = P.gbox;
+    g.region = P.region;
+    g.cap_o = P.cap_o;
+    return g;
+}
+// one plan's pass in a batched gather (dose, first) or gather transpose (gd)
+struct GatherEntry {
+    GatherPlan p;
+    float *dose;
+    const float *gd;
+    int b0, nb, first;
+    int blk0, gx, gy;        // set by the launcher
+};
+constexpr int kGatherBatchMax = 128;
+// one launch per group of up to kGatherBatchMax entries: the gathers
+// (transpose = false: accumulate pass b0 .. b0 + nb - 1 into dose, first =
+// overwrite) or the gather transposes (transpose = true: h of the pass from
+// gd) of several plans, each CTA as in the per-plan launch
+cudaError_t launch_gather_multi(const GatherEntry *ents, int n, bool transpose, cudaStream_t s);
 cudaError_t launch_mag_T(const PlanDev &P, int b0, int nb, cudaStream_t s);
 cudaError_t launch_param_grad(const PlanDev &P, const float *leaves, const float *jaws,
                               const float *mu, float *dleaves, float *djaws, float *dmu,

@@ -47,6 +47,47 @@ def test_batch_matches_individual_calls_and_oracle():
         e.close()
 
 
+def test_uneven_eight_plan_batch_in_rounds_matches_individual_calls_and_oracle():
+    """Eight uneven plans cut into 1-4 passes each: the batch runs in rounds
+    (round c holds pass c of every plan that has one, so plans drop out of the
+    later rounds), each round one shared FFT launch and one shared gather
+    launch per direction over the plans still in it. Every plan equals its
+    own calls with the same pass size bit for bit (dose and gradients); two
+    plans match the oracle."""
+    shapes = [((20, 32, 36), 3.0, 9, 5, 3), ((16, 28, 28), 4.0, 3, 4, 3), ((24, 40, 40), 3.0, 12, 6, 3),
+              ((18, 30, 26), 3.0, 5, 8, 2), ((22, 36, 30), 3.0, 8, 5, 8), ((16, 24, 40), 3.5, 6, 3, 2),
+              ((20, 34, 34), 3.0, 10, 7, 4), ((14, 26, 30), 4.0, 4, 4, 1)]
+    ws = [S.small_pelvis(seed=70 + q, n=n, spacing=sp, n_cp=c, r_px=r)
+          for q, (n, sp, c, r, _) in enumerate(shapes)]
+    engines = [DoseEngine(w.phantom, w.machine, w.plan.gantry_deg, w.plan.iso) for w in ws]
+    for e, sh in zip(engines, shapes):
+        e.set_chunk(sh[4])
+    rng = np.random.default_rng(8)
+    grads = [rng.standard_normal(w.phantom.shape).astype(np.float32) for w in ws]
+    b = DoseBatch(engines, [w.plan.leaves for w in ws], [w.plan.jaws for w in ws],
+                  [w.plan.mu for w in ws], grads, n_branches=4)
+    b.launch()
+    b.launch()
+    passes = [-(-w.plan.n_cp // pc) for w, pc in zip(ws, b.pass_cp)]
+    assert b.pass_cp == [sh[4] for sh in shapes] and min(passes) == 1 and max(passes) == 4
+    for i, (w, e) in enumerate(zip(ws, engines)):
+        d = e.forward(w.plan.leaves, w.plan.jaws, w.plan.mu)
+        dl, dj, dm = e.backward(w.plan.leaves, w.plan.jaws, w.plan.mu, grads[i])
+        assert torch.equal(b.dose[i], d), i
+        assert torch.equal(b.dleaves[i], dl) and torch.equal(b.djaws[i], dj) and torch.equal(b.dmu[i], dm), i
+    for i in (0, 6):
+        mod = O.Model(ws[i].phantom, ws[i].machine, ws[i].plan)
+        ref = mod.dose()
+        got = b.dose[i].cpu().numpy().astype(np.float64)
+        assert np.abs(got - ref).max() <= 1e-4 * ref.max()
+        for gg, rr in zip((b.dleaves[i], b.djaws[i], b.dmu[i]), mod.dose_grad(grads[i].astype(np.float64))):
+            gg = gg.cpu().numpy().astype(np.float64)
+            assert np.abs(gg - rr).max() <= 1e-3 * np.abs(rr).max()
+    b.close()
+    for e in engines:
+        e.close()
+
+
 def test_batch_mixes_convolution_paths_and_fft_size_limits():
     """One batched FFT launch per round serves plans with different size
     limits (a small limit sends slices to the tensor-core overflow pass) while
