@@ -406,9 +406,11 @@ pdrt_status pdrt_plan_autotune(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
  * pdrt_batch_launch replays it with a single graph launch.  The graph runs in
  * rounds, round c covering the c-th pass of control points of every plan:
  * the FFT convolution of all FFT plans' (plan, control point, slice) items of
- * the round is ONE persistent launch pulling items from one work counter, and
- * the per-plan kernels (projection, tables, tensor-core overflow or
- * convolution, gathers, gradients) run on n_branches parallel branches.
+ * the round is ONE persistent launch pulling items from one work counter, the
+ * gather (forward) and its transpose (adjoint) of every plan's pass are one
+ * launch each, and the remaining per-plan kernels (projection, tables,
+ * tensor-core overflow or convolution, magnification transpose, gradients)
+ * run on n_branches parallel branches.
  * Each plan keeps the pass size (pdrt_plan_set_chunk) it had at creation.
  * Every array argument has n entries (device pointers as in pdrt_dose_forward
  * / pdrt_dose_backward); a plan may appear once per batch; plans, grids and
