@@ -209,6 +209,14 @@ def _cpu_model():
     return platform.machine()
 
 
+def _memo_reset(eng):
+    """Forget the plan's memoised kernel spectra: every timed step then
+    computes the spectra of its slices once (in the forward; its adjoint
+    takes them), so no work is carried from one step into the next."""
+    if eng.info.get("spectrum_memo_bytes"):
+        eng.reset_spectrum_memo()
+
+
 def _step_stats(eng, leaves, jaws, mu, g, dose, flush, n):
     """Device time of single steps (CUDA events around each, L2 flushed
     before it): median, p10 and p90 of n forward-only and of n forward +
@@ -222,6 +230,7 @@ def _step_stats(eng, leaves, jaws, mu, g, dose, flush, n):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record()
+            _memo_reset(eng)
             eng.forward(leaves, jaws, mu, out=dose)
             if adj:
                 eng.backward(leaves, jaws, mu, g)
@@ -381,6 +390,7 @@ def _gpu(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     def step():
+        _memo_reset(eng)
         eng.forward(leaves, jaws, mu, out=dose)
         eng.backward(leaves, jaws, mu, g)
         flush.zero_()
@@ -418,6 +428,29 @@ def _gpu(args):
     kernels = {k: {"launches": v["launches"], "ms_per_step": v["total_ms"] / args.steps}
                for k, v in prof.items() if not k.startswith("_") and v["launches"]}
     kernel_hbm = _kernel_hbm(prof, w.name)
+    # the same step with the spectra kept from step to step (outside the
+    # timed region; the headline resets them before every step)
+    memo = None
+    if eng.info.get("spectrum_memo_bytes"):
+        def warm_step():
+            eng.forward(leaves, jaws, mu, out=dose)
+            eng.backward(leaves, jaws, mu, g)
+            flush.zero_()
+        for _ in range(2):
+            warm_step()
+        w0 = torch.cuda.Event(enable_timing=True)
+        w1 = torch.cuda.Event(enable_timing=True)
+        w0.record()
+        for _ in range(args.steps):
+            warm_step()
+        w1.record()
+        torch.cuda.synchronize()
+        warm_ms = w0.elapsed_time(w1) / args.steps
+        memo = {"headline": "memo reset before every timed step: each step computes its kernel spectra "
+                            "once (forward) and its adjoint takes them",
+                "bytes": int(eng.info["spectrum_memo_bytes"]), "pmax": int(eng.info["spectrum_memo_pmax"]),
+                "kept_across_steps": {"ms_per_step": warm_ms,
+                                      "value": arcs_per_step / (warm_ms / 1e3) * world}}
     # per-step distribution (after the timed region, outside it)
     step_ms = (_step_stats(eng, leaves, jaws, mu, g, dose, flush, args.step_stats)
                if args.step_stats > 0 else None)
@@ -432,17 +465,33 @@ def _gpu(args):
                             for t in (leaves, jaws, mu))
         d_l, d_j, d_m, d_g = (torch.empty_like(t) for t in (leaves, jaws, mu, g))
 
+        # the 42 MB copies overlap the compute that does not need them: the
+        # dose gradient's upload runs beside the forward, the dose's download
+        # beside the adjoint (copy stream + events; both inside every step)
+        cs = torch.cuda.Stream(device=dev)
+        ev_g, ev_f = torch.cuda.Event(), torch.cuda.Event()
+
         def e2e_step():
+            main = torch.cuda.current_stream(dev)
+            _memo_reset(eng)
             d_l.copy_(h_leaves, non_blocking=True)
             d_j.copy_(h_jaws, non_blocking=True)
             d_m.copy_(h_mu, non_blocking=True)
-            d_g.copy_(h_g, non_blocking=True)
+            cs.wait_stream(main)          # the previous adjoint has read d_g
+            with torch.cuda.stream(cs):
+                d_g.copy_(h_g, non_blocking=True)
+                ev_g.record(cs)
             eng.forward(d_l, d_j, d_m, out=dose)
+            ev_f.record(main)
+            cs.wait_event(ev_f)
+            with torch.cuda.stream(cs):
+                h_dose.copy_(dose, non_blocking=True)
+            main.wait_event(ev_g)
             dl, dj, dm = eng.backward(d_l, d_j, d_m, d_g)
-            h_dose.copy_(dose, non_blocking=True)
             h_dl.copy_(dl, non_blocking=True)
             h_dj.copy_(dj, non_blocking=True)
             h_dm.copy_(dm, non_blocking=True)
+            main.wait_stream(cs)          # the dose has left before the next forward
             flush.zero_()
 
         for _ in range(2):
@@ -501,7 +550,7 @@ def _gpu(args):
                           "chunk_cp": info.get("chunk_cp")},
                "configs": sweep, "batch32": batch32,
                "hbm_literal": hbm, "warm_start": warm, "step_ms": step_ms,
-               "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+               "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "spectrum_memo": memo}
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -598,6 +647,7 @@ def _timed_steps(eng, leaves, jaws, mu, g, dose, flush, n, adjoint):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
+        _memo_reset(eng)
         eng.forward(leaves, jaws, mu, out=dose)
         if adjoint:
             eng.backward(leaves, jaws, mu, g)
@@ -679,6 +729,8 @@ def _batch32(args, steps, warmup, report):
     batch = DoseBatch(engines, [w.plan.leaves for w in ws], [w.plan.jaws for w in ws],
                       [w.plan.mu for w in ws], grads, n_branches=len(ws))   # one branch per plan
     for _ in range(warmup):
+        for e in engines:
+            _memo_reset(e)
         batch.launch()
     torch.cuda.synchronize()
     lat = []
@@ -688,6 +740,8 @@ def _batch32(args, steps, warmup, report):
     total_ms = 0.0
     for _ in range(steps):
         e0.record()
+        for e in engines:
+            _memo_reset(e)
         batch.launch()
         e1.record()
         lat.append(batch.plan_times_ms())     # synchronises

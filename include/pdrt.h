@@ -145,7 +145,33 @@ typedef struct {
     int32_t fft_pmax;            /* > 0: FFT convolution for slices whose padded sizes are at most
                                     this, tensor cores for the rest; 0: FFT off */
     int32_t fft_ctas_per_sm[2];  /* FFT convolution CTAs per SM (forward, adjoint) */
+    int32_t spectrum_memo_pmax;  /* kernel-spectrum memo: largest padded size memoised (0: off) */
+    size_t spectrum_memo_bytes;  /* device memory of the memo (not part of scratch_bytes) */
 } pdrt_plan_info;
+
+/*
+ * Kernel-spectrum memo of the FFT convolution (Sec. 2.2.6).  The spectrum
+ * of slice k of control point b -- the DFT of the kernel K(z_k), scaled by
+ * T(z_k) C(d_k) -- depends only on what the plan fixes (the slice's WEPL
+ * depth, kernel parameters and magnification) and on the slice's padded
+ * transform sizes (pu, pv), which follow from the fluence support of the
+ * call.  With the memo on, the FFT convolution stores each spectrum it
+ * computes, tagged with (pu, pv), and takes it from the memo while the sizes
+ * stay the same: the adjoint of a call takes what its forward computed (the
+ * two directions pad a slice to the same sizes), later calls take what
+ * earlier ones computed.  The stored spectra are bit-identical to
+ * recomputed ones, so every result is the same with the memo on or off.
+ * The upload turns it on for its default size limit when the memory
+ * (n_cp x nw x (pmax/2 + 1)^2 floats, pdrt_plan_info.spectrum_memo_bytes)
+ * can be allocated; slices padded beyond that limit are not memoised.
+ * pdrt_plan_set_spectrum_memo: enable = 0 frees it, 1 allocates it for the
+ * current FFT size limit (host, synchronous).  pdrt_plan_reset_spectrum_memo
+ * forgets every stored spectrum (asynchronous on stream; the next call
+ * computes them again).  Errors: EINVAL (NULL plan; enable with the FFT
+ * convolution off), ECUDA (allocation).
+ */
+pdrt_status pdrt_plan_set_spectrum_memo(pdrt_plan_t p, int32_t enable);
+pdrt_status pdrt_plan_reset_spectrum_memo(pdrt_plan_t p, pdrt_stream_t stream);
 
 /* Work counters of the last forward/backward call (for roofline accounting). */
 typedef struct {

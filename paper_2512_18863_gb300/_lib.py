@@ -51,7 +51,8 @@ class pdrt_plan_info(C.Structure):
                 ("n_cp", C.c_int32), ("chunk_cp", C.c_int32), ("scratch_bytes", C.c_size_t),
                 ("tensor_cores", C.c_int32), ("tc_ctas_per_sm", C.c_int32 * 2),
                 ("simt_ctas_per_sm", C.c_int32 * 2), ("tc_phase", C.c_int32 * 2),
-                ("fft_pmax", C.c_int32), ("fft_ctas_per_sm", C.c_int32 * 2)]
+                ("fft_pmax", C.c_int32), ("fft_ctas_per_sm", C.c_int32 * 2),
+                ("spectrum_memo_pmax", C.c_int32), ("spectrum_memo_bytes", C.c_size_t)]
 
 
 class pdrt_work(C.Structure):
@@ -84,6 +85,8 @@ _SIG = {
     "pdrt_dose_forward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "pdrt_dose_backward": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "pdrt_plan_get_info": (C.c_int, [_VP, C.POINTER(pdrt_plan_info)]),
+    "pdrt_plan_set_spectrum_memo": (C.c_int, [_VP, C.c_int32]),
+    "pdrt_plan_reset_spectrum_memo": (C.c_int, [_VP, _VP]),
     "pdrt_plan_set_tensor_cores": (C.c_int, [_VP, C.c_int32]),
     "pdrt_plan_status": (C.c_int, [_VP, _VP, C.POINTER(C.c_uint32)]),
     "pdrt_plan_work": (C.c_int, [_VP, _VP, C.POINTER(pdrt_work)]),
@@ -430,6 +433,14 @@ def pdrt_bev_project(masks_dev, nx, ny, nz, spacing, origin, iso, sid, gantry_de
                                    (C.c_double * 3)(*[float(x) for x in iso]), float(sid),
                                    len(gantry_deg), g, int(side), float(pitch), float(reach),
                                    float(step), _VP(out_dev), _VP(stream)))
+
+
+def pdrt_plan_set_spectrum_memo(plan, enable):
+    _check(load().pdrt_plan_set_spectrum_memo(_VP(plan), 1 if enable else 0))
+
+
+def pdrt_plan_reset_spectrum_memo(plan, stream):
+    _check(load().pdrt_plan_reset_spectrum_memo(_VP(plan), _VP(stream)))
 
 
 def pdrt_plan_set_fft(plan, pmax):

@@ -72,6 +72,7 @@ struct pdrt_plan_s {
     PlanDev dev;
     size_t scratch_bytes;
     std::vector<void *> allocs;
+    size_t memo_bytes = 0;    // kernel-spectrum memo (dev.kf_memo, dev.kf_tag), held apart from allocs
     // profiling
     bool profiling = false;
     std::vector<cudaEvent_t> events;
@@ -272,9 +273,51 @@ void pdrt_grid_destroy(pdrt_grid_t g)
     delete g;
 }
 
+namespace {
+
+void memo_free(pdrt_plan_t p)
+{
+    cudaFree(p->dev.kf_memo);
+    cudaFree(p->dev.kf_tag);
+    p->dev.kf_memo = nullptr;
+    p->dev.kf_tag = nullptr;
+    p->dev.kf_pmax = 0;
+    p->dev.kf_stride = 0;
+    p->memo_bytes = 0;
+}
+
+// kernel-spectrum memo for slices of padded sizes up to pmax: one entry of
+// (pmax/2 + 1)^2 floats (rounded up to 4) per (control point, slice), tags
+// cleared (synchronously)
+cudaError_t memo_alloc(pdrt_plan_t p, int pmax)
+{
+    memo_free(p);
+    const long long entries = (long long)p->n_cp * p->dev.lat.nw;
+    const long long stride = (((long long)(pmax / 2 + 1) * (pmax / 2 + 1)) + 3) & ~3LL;
+    float *memo = nullptr;
+    int *tag = nullptr;
+    cudaError_t e = cudaMalloc(&memo, sizeof(float) * (size_t)(entries * stride));
+    if (e == cudaSuccess) e = cudaMalloc(&tag, sizeof(int) * (size_t)entries);
+    if (e == cudaSuccess) e = cudaMemset(tag, 0, sizeof(int) * (size_t)entries);
+    if (e != cudaSuccess) {
+        cudaFree(memo);
+        cudaFree(tag);
+        return e;
+    }
+    p->dev.kf_memo = memo;
+    p->dev.kf_tag = tag;
+    p->dev.kf_pmax = pmax;
+    p->dev.kf_stride = stride;
+    p->memo_bytes = sizeof(float) * (size_t)(entries * stride) + sizeof(int) * (size_t)entries;
+    return cudaSuccess;
+}
+
+}  // namespace
+
 void pdrt_plan_destroy(pdrt_plan_t p)
 {
     if (!p) return;
+    memo_free(p);
     for (void *q : p->allocs) cudaFree(q);
     for (cudaEvent_t e : p->events) cudaEventDestroy(e);
     delete p;
@@ -552,6 +595,9 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
             p->fft_blocks[1] = base_a * g->sm_count;
         }
     }
+    // the kernel-spectrum memo for the default size limit (off if it does
+    // not fit in device memory: the FFT then computes every spectrum)
+    if (P.fft_pmax && memo_alloc(p, P.fft_pmax) != cudaSuccess) cudaGetLastError();
 #undef PLAN_TRY
     *out = p;
     return PDRT_OK;
@@ -739,6 +785,34 @@ pdrt_status pdrt_plan_get_info(pdrt_plan_t p, pdrt_plan_info *out)
     out->fft_pmax = p->dev.fft_pmax;
     out->fft_ctas_per_sm[0] = p->dev.fft_pmax && p->grid->sm_count > 0 ? p->fft_blocks[0] / p->grid->sm_count : 0;
     out->fft_ctas_per_sm[1] = p->dev.fft_pmax && p->grid->sm_count > 0 ? p->fft_blocks[1] / p->grid->sm_count : 0;
+    out->spectrum_memo_pmax = p->dev.kf_pmax;
+    out->spectrum_memo_bytes = p->memo_bytes;
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_plan_set_spectrum_memo(pdrt_plan_t p, int32_t enable)
+{
+    g_last_error.clear();
+    if (!p) return fail(PDRT_EINVAL, "NULL plan");
+    if (!enable) {
+        memo_free(p);
+        return PDRT_OK;
+    }
+    if (p->dev.kf_memo) return PDRT_OK;
+    const int pmax = p->dev.fft_pmax ? p->dev.fft_pmax : 0;
+    if (!pmax) return fail(PDRT_EINVAL, "the FFT convolution is off: no spectra to memoise");
+    CU_TRY(memo_alloc(p, pmax), "cudaMalloc(spectrum memo)");
+    return PDRT_OK;
+}
+
+pdrt_status pdrt_plan_reset_spectrum_memo(pdrt_plan_t p, pdrt_stream_t stream)
+{
+    g_last_error.clear();
+    if (!p) return fail(PDRT_EINVAL, "NULL plan");
+    if (!p->dev.kf_tag) return PDRT_OK;
+    CU_TRY(cudaMemsetAsync(p->dev.kf_tag, 0, sizeof(int) * (size_t)p->n_cp * p->dev.lat.nw,
+                           (cudaStream_t)stream),
+           "clear spectrum memo");
     return PDRT_OK;
 }
 

@@ -678,89 +678,104 @@ __device__ __forceinline__ void fft_slice(const PL &P, int R, int b0, int item, 
     const int nkv = pv / 2 + 1, nkv4 = (nkv + 3) & ~3, hu4 = (hu + 1 + 3) & ~3;
     const float *Cv = P.fft_cos + ov.cos;        // [q][kv'], c_q folded in
     const float *Cu = P.fft_cos + ou.cos;        // [p][ku], c_p folded in
+    // memoised spectrum of this slice: it depends on the slice's depth,
+    // kernel and magnification (fixed by the plan) and on (pu, pv) only, so
+    // an entry tagged with the same sizes holds exactly what the three steps
+    // below would compute (every thread reads the same tag: no CTA of this
+    // launch writes it)
+    const long long ce = (long long)b * L.nw + k;
+    const bool memo = P.kf_memo != nullptr && pu <= P.kf_pmax && pv <= P.kf_pmax;
+    const int ktag = (pu << 16) | pv;
+    const bool hit = memo && P.kf_tag[ce] == ktag;
+    const int nkf4 = (nkv * G.pitch + 3) >> 2;   // Kf as float4 (the rows are contiguous)
+    float4 *memo4 = memo ? reinterpret_cast<float4 *>(P.kf_memo + ce * P.kf_stride) : nullptr;
 
-    // Kernel spectrum: K(p, q) (the expressions of the other convolution
-    // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
-    // K is stored transposed, KT[q][p] (rows of R1p = R1 rounded up to 4),
-    // so that both products read 4-wide vectors of each operand.
-    for (int idx = tid; idx < R1 * R1; idx += kFftThreads) {
-        const int pp = idx / R1, q = idx - pp * R1;
-        if (sym && pp > q) continue;
-        const float pu_mm = pp * L.du, qv = q * L.dv;
-        const float r = sqrtf(pu_mm * pu_mm + qv * qv);
-        const float kv = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
-                         st.wn[2] * expf(-st.a[2] * r);
-        KT[q * R1p + pp] = kv;
-        if (sym) KT[pp * R1p + q] = kv;
-    }
-    for (int idx = tid; idx < R1 * (R1p - R1); idx += kFftThreads) {   // zero padding columns
-        const int q = idx / (R1p - R1);
-        KT[q * R1p + R1 + (idx - q * (R1p - R1))] = 0.f;
-    }
-    __syncthreads();
-    // A[4 p4 .. +3][4 g .. +3] per item
-    {
-        const int G4 = nkv4 / 4, P4 = R1p / 4;
-        const FastDiv dg = fast_div(G4);
-        for (int idx = tid; idx < P4 * G4; idx += kFftThreads) {
-            const int p4 = idx / dg, g = idx - p4 * G4;
-            float4 acc[4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 *kt = reinterpret_cast<const float4 *>(KT) + p4;
-            const float4 *cv = reinterpret_cast<const float4 *>(Cv) + g;
-            for (int q = 0; q < R1; ++q) {
-                const float4 kk = kt[q * P4];
-                const float4 c = __ldg(cv + q * G4);
-                const float k4[4] = {kk.x, kk.y, kk.z, kk.w};
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    acc[a].x = fmaf(k4[a], c.x, acc[a].x);
-                    acc[a].y = fmaf(k4[a], c.y, acc[a].y);
-                    acc[a].z = fmaf(k4[a], c.z, acc[a].z);
-                    acc[a].w = fmaf(k4[a], c.w, acc[a].w);
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-                if (4 * p4 + a < R1) reinterpret_cast<float4 *>(A)[(4 * p4 + a) * G4 + g] = acc[a];
+    if (!hit) {
+        // Kernel spectrum: K(p, q) (the expressions of the other convolution
+        // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
+        // K is stored transposed, KT[q][p] (rows of R1p = R1 rounded up to 4),
+        // so that both products read 4-wide vectors of each operand.
+        for (int idx = tid; idx < R1 * R1; idx += kFftThreads) {
+            const int pp = idx / R1, q = idx - pp * R1;
+            if (sym && pp > q) continue;
+            const float pu_mm = pp * L.du, qv = q * L.dv;
+            const float r = sqrtf(pu_mm * pu_mm + qv * qv);
+            const float kv = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
+                             st.wn[2] * expf(-st.a[2] * r);
+            KT[q * R1p + pp] = kv;
+            if (sym) KT[pp * R1p + q] = kv;
         }
-    }
-    __syncthreads();
-    // Kf[4 i4 .. +3][4 g .. +3] per item
-    {
-        const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
-        const int U4 = hu4 / 4, V4 = nkv4 / 4;
-        const FastDiv du4 = fast_div(U4);
-        for (int idx = tid; idx < V4 * U4; idx += kFftThreads) {
-            const int i4 = idx / du4, g = idx - i4 * U4;
-            float4 acc[4];
+        for (int idx = tid; idx < R1 * (R1p - R1); idx += kFftThreads) {   // zero padding columns
+            const int q = idx / (R1p - R1);
+            KT[q * R1p + R1 + (idx - q * (R1p - R1))] = 0.f;
+        }
+        __syncthreads();
+        // A[4 p4 .. +3][4 g .. +3] per item
+        {
+            const int G4 = nkv4 / 4, P4 = R1p / 4;
+            const FastDiv dg = fast_div(G4);
+            for (int idx = tid; idx < P4 * G4; idx += kFftThreads) {
+                const int p4 = idx / dg, g = idx - p4 * G4;
+                float4 acc[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 *av = reinterpret_cast<const float4 *>(A) + i4;
-            const float4 *cu = reinterpret_cast<const float4 *>(Cu) + g;
-            for (int pp = 0; pp < R1; ++pp) {
-                const float4 aa = av[pp * V4];
-                const float4 c = __ldg(cu + pp * U4);
-                const float a4[4] = {aa.x, aa.y, aa.z, aa.w};
+                for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 *kt = reinterpret_cast<const float4 *>(KT) + p4;
+                const float4 *cv = reinterpret_cast<const float4 *>(Cv) + g;
+                for (int q = 0; q < R1; ++q) {
+                    const float4 kk = kt[q * P4];
+                    const float4 c = __ldg(cv + q * G4);
+                    const float k4[4] = {kk.x, kk.y, kk.z, kk.w};
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    acc[a].x = fmaf(a4[a], c.x, acc[a].x);
-                    acc[a].y = fmaf(a4[a], c.y, acc[a].y);
-                    acc[a].z = fmaf(a4[a], c.z, acc[a].z);
-                    acc[a].w = fmaf(a4[a], c.w, acc[a].w);
+                    for (int a = 0; a < 4; ++a) {
+                        acc[a].x = fmaf(k4[a], c.x, acc[a].x);
+                        acc[a].y = fmaf(k4[a], c.y, acc[a].y);
+                        acc[a].z = fmaf(k4[a], c.z, acc[a].z);
+                        acc[a].w = fmaf(k4[a], c.w, acc[a].w);
+                    }
                 }
-            }
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int kv = 4 * i4 + a;
-                if (kv >= nkv) continue;
-                const float r4[4] = {acc[a].x, acc[a].y, acc[a].z, acc[a].w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (4 * g + e <= hu) Kf[kv * G.pitch + 4 * g + e] = r4[e] * kscale;
+                for (int a = 0; a < 4; ++a)
+                    if (4 * p4 + a < R1) reinterpret_cast<float4 *>(A)[(4 * p4 + a) * G4 + g] = acc[a];
             }
         }
+        __syncthreads();
+        // Kf[4 i4 .. +3][4 g .. +3] per item
+        {
+            const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
+            const int U4 = hu4 / 4, V4 = nkv4 / 4;
+            const FastDiv du4 = fast_div(U4);
+            for (int idx = tid; idx < V4 * U4; idx += kFftThreads) {
+                const int i4 = idx / du4, g = idx - i4 * U4;
+                float4 acc[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 *av = reinterpret_cast<const float4 *>(A) + i4;
+                const float4 *cu = reinterpret_cast<const float4 *>(Cu) + g;
+                for (int pp = 0; pp < R1; ++pp) {
+                    const float4 aa = av[pp * V4];
+                    const float4 c = __ldg(cu + pp * U4);
+                    const float a4[4] = {aa.x, aa.y, aa.z, aa.w};
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        acc[a].x = fmaf(a4[a], c.x, acc[a].x);
+                        acc[a].y = fmaf(a4[a], c.y, acc[a].y);
+                        acc[a].z = fmaf(a4[a], c.z, acc[a].z);
+                        acc[a].w = fmaf(a4[a], c.w, acc[a].w);
+                    }
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const int kv = 4 * i4 + a;
+                    if (kv >= nkv) continue;
+                    const float r4[4] = {acc[a].x, acc[a].y, acc[a].z, acc[a].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (4 * g + e <= hu) Kf[kv * G.pitch + 4 * g + e] = r4[e] * kscale;
+                }
+            }
+        }
+    } else {
+        for (int t = tid; t < nkf4; t += kFftThreads) reinterpret_cast<float4 *>(Kf)[t] = __ldg(memo4 + t);
     }
     // fill tables (forward): per input column n the two fluence rows a of
     // its bilinear stencil (clamped into the support box) with their
@@ -824,6 +839,10 @@ __device__ __forceinline__ void fft_slice(const PL &P, int R, int b0, int item, 
             }
             S[j * G.pitch + m] = make_float2(x[0], x[1]);
         }
+    }
+    if (memo && !hit) {   // store the spectrum just computed
+        for (int t = tid; t < nkf4; t += kFftThreads) memo4[t] = reinterpret_cast<const float4 *>(Kf)[t];
+        if (tid == 0) P.kf_tag[ce] = ktag;
     }
     __syncthreads();
     // rows: complex FFT of length hu over the input rows

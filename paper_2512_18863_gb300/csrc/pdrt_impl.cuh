@@ -131,6 +131,14 @@ struct PlanDev {
     unsigned int *fft_ctr;   // [4 * n_cp]: per chunk {fwd counter, fwd overflow count,
                              // adj counter, adj overflow count}
     const float *fft_cos;    // c_p cos(2 pi k p / P) per supported size P (conv_fft_cos_table)
+    // kernel-spectrum memo of the FFT convolution: entry b * nw + k holds the
+    // spectrum Kf of slice k of control point b ([kv'][ku], nkv rows of pu/2
+    // + 1) as the FFT kernel computed it, tagged kf_tag = (pu << 16) | pv (0:
+    // empty); slices with sizes above kf_pmax are not memoised; NULL: off
+    float *kf_memo;
+    int *kf_tag;
+    int kf_pmax;
+    long long kf_stride;     // floats per entry (16-byte multiple)
 };
 
 // Same float expression in every kernel that samples or transposes the
@@ -393,6 +401,10 @@ struct FftPlan {
     unsigned int *fft_ctr;
     long long cap_o, cap_a;
     int R, fft_pmax;
+    float *kf_memo;
+    int *kf_tag;
+    int kf_pmax;
+    long long kf_stride;
 };
 inline FftPlan fft_plan_of(const PlanDev &P)
 {
@@ -410,6 +422,10 @@ inline FftPlan fft_plan_of(const PlanDev &P)
     f.cap_a = P.cap_a;
     f.R = P.mach.R;
     f.fft_pmax = P.fft_pmax;
+    f.kf_memo = P.kf_memo;
+    f.kf_tag = P.kf_tag;
+    f.kf_pmax = P.kf_pmax;
+    f.kf_stride = P.kf_stride;
     return f;
 }
 // entries of one batched FFT launch (its kernel parameters stay under the

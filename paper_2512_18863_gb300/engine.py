@@ -129,6 +129,16 @@ class DoseEngine:
         _lib.pdrt_plan_set_tensor_cores(self._plan, enable)
         self.info = _lib.pdrt_plan_get_info(self._plan)
 
+    def set_spectrum_memo(self, enable: bool):
+        """Kernel-spectrum memo of the FFT convolution on (allocated for the
+        current FFT size limit) or off (freed); results do not depend on it."""
+        _lib.pdrt_plan_set_spectrum_memo(self._plan, enable)
+        self.info = _lib.pdrt_plan_get_info(self._plan)
+
+    def reset_spectrum_memo(self):
+        """Forget every memoised spectrum (stream-ordered on the current stream)."""
+        _lib.pdrt_plan_reset_spectrum_memo(self._plan, _stream_ptr())
+
     def set_chunk(self, chunk_cp: int):
         """Control points per pass (1 .. the count the scratch was sized for)."""
         _lib.pdrt_plan_set_chunk(self._plan, chunk_cp)

@@ -315,6 +315,39 @@ def test_fft_size_144_radix9_matches_oracle():
             _assert_grad(gg, rr, name)
 
 
+def test_spectrum_memo_changes_no_result():
+    """The kernel-spectrum memo: a plan with it (the default) and one without
+    give bit-identical doses and gradients over a call sequence that fills it
+    (forward), takes from it (adjoint, repeated calls), meets other padded
+    sizes (wider jaws: those slices are computed again and stored) and is
+    reset."""
+    w = S.small_pelvis(seed=31, n=(20, 36, 36), n_cp=5, r_px=6)
+    on, off = _engine(w), _engine(w)
+    off.set_spectrum_memo(False)
+    assert on.info["spectrum_memo_bytes"] > 0 and on.info["spectrum_memo_pmax"] == on.info["fft_pmax"]
+    assert off.info["spectrum_memo_bytes"] == 0
+    g = np.random.default_rng(31).standard_normal(w.phantom.shape).astype(np.float32)
+    wide = w.plan.jaws.copy()
+    wide[:, 0] -= 12.0
+    wide[:, 1] += 12.0
+    seq = [w.plan.jaws, w.plan.jaws, wide, w.plan.jaws, None, w.plan.jaws]
+    for jaws in seq:
+        if jaws is None:
+            on.reset_spectrum_memo()
+            continue
+        d1 = on.forward(w.plan.leaves, jaws, w.plan.mu).clone()
+        d0 = off.forward(w.plan.leaves, jaws, w.plan.mu).clone()
+        assert torch.equal(d1, d0)
+        for a, b in zip(on.backward(w.plan.leaves, jaws, w.plan.mu, g),
+                        off.backward(w.plan.leaves, jaws, w.plan.mu, g)):
+            assert torch.equal(a, b)
+    assert on.status_flags() == 0
+    ref = O.Model(w.phantom, w.machine, w.plan).dose()
+    _assert_dose(on.forward(w.plan.leaves, w.plan.jaws, w.plan.mu).cpu().numpy().astype(np.float64), ref)
+    on.close()
+    off.close()
+
+
 def test_plan_without_control_points_is_rejected():
     """An arc with no control points is a shape error of the upload (ESHAPE),
     not an empty dose."""
