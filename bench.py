@@ -312,15 +312,15 @@ def _reference(args):
 _CAPTURES = {
     "workload": "pelvis256x256x160_2x178cp_R4cm",
     "conv_forward_fft": {"src": ("csrc/k_conv_fft.cu", "csrc/pdrt_impl.cuh"),
-                         "sha": "9916d9906b76030a+263847ddcf162b97", "bytes": 1.2949e9},
+                         "sha": "f3a8b103c6fefc7a+9bcd876871eb1683", "bytes": 1.7514e9},
     "conv_adjoint_fft": {"src": ("csrc/k_conv_fft.cu", "csrc/pdrt_impl.cuh"),
-                         "sha": "9916d9906b76030a+263847ddcf162b97", "bytes": 1.7100e9},
+                         "sha": "f3a8b103c6fefc7a+9bcd876871eb1683", "bytes": 2.1382e9},
     "gather_accumulate": {"src": ("csrc/k_gather.cu", "csrc/pdrt_impl.cuh"),
-                          "sha": "2ade7527b14ad64d+263847ddcf162b97", "bytes": 1.5951e9},
+                          "sha": "f9d6a140dfd9f8d7+9bcd876871eb1683", "bytes": 1.6050e9},
     "gather_transpose": {"src": ("csrc/k_gather.cu", "csrc/pdrt_impl.cuh"),
-                         "sha": "2ade7527b14ad64d+263847ddcf162b97", "bytes": 1.9822e9},
+                         "sha": "f9d6a140dfd9f8d7+9bcd876871eb1683", "bytes": 1.9869e9},
     "mag_transpose": {"src": ("csrc/k_adjoint.cu", "csrc/pdrt_impl.cuh"),
-                      "sha": "7e30bff0a6f71a37+263847ddcf162b97", "bytes": 0.4231e9},
+                      "sha": "7e30bff0a6f71a37+9bcd876871eb1683", "bytes": 0.4229e9},
 }
 
 
