@@ -226,8 +226,11 @@ void pdrt_grid_destroy(pdrt_grid_t g);
  *   m                beam model (host, copied).
  *   scratch_budget_bytes  upper bound on the device scratch the plan may own
  *                    (0 = library default: a quarter of the free device
- *                    memory, between 1 and 32 GiB); it sets how many control
- *                    points one pass processes (passes are balanced).
+ *                    memory, between 1 and 4 GiB); it sets how many control
+ *                    points one pass processes (passes are balanced).  Fewer,
+ *                    longer passes are faster (a 256x256x160 two-arc plan
+ *                    runs 2 passes at 24 GB and is ~15 % slower at 4 GB);
+ *                    the kernel-spectrum memo is allocated beside it.
  * The plan owns all device scratch the forward and backward passes need.
  * Errors: ESHAPE (n_cp < 1: an arc needs a control point), EINVAL (bad
  * values; kernel radius above PDRT_MAX_RADIUS_PX; SID not larger than the

@@ -475,10 +475,10 @@ pdrt_status pdrt_plan_upload(pdrt_plan_t *out, pdrt_grid_t g, int32_t n_cp,
     const size_t fixed = sizeof(float) * (M.corr ? 3 : 2) * (size_t)n_cp * L.nu * L.nv +
                          sizeof(SliceTab) * (size_t)n_cp * L.nw;
     size_t budget = scratch_budget_bytes;
-    if (!budget) {   // default: a quarter of the free device memory, 1..32 GiB
+    if (!budget) {   // default: a quarter of the free device memory, 1..4 GiB
         size_t free_b = 0, total_b = 0;
         CU_TRY(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
-        budget = std::min<size_t>(std::max<size_t>(free_b / 4, (size_t)1 << 30), (size_t)32 << 30);
+        budget = std::min<size_t>(std::max<size_t>(free_b / 4, (size_t)1 << 30), (size_t)4 << 30);
     }
     const size_t per_cp = sizeof(float) * (size_t)(cap_o + cap_a);
     long long chunk = budget > fixed ? (long long)((budget - fixed) / per_cp) : 1;
