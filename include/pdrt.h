@@ -167,7 +167,9 @@ typedef struct {
  * pdrt_plan_set_spectrum_memo: enable = 0 frees it, 1 allocates it for the
  * current FFT size limit (host, synchronous).  pdrt_plan_reset_spectrum_memo
  * forgets every stored spectrum (asynchronous on stream; the next call
- * computes them again).  Errors: EINVAL (NULL plan; enable with the FFT
+ * computes them again).  A batch (pdrt_batch_create) records the memo of
+ * each of its plans: do not turn a plan's memo on or off while a batch
+ * holds the plan.  Errors: EINVAL (NULL plan; enable with the FFT
  * convolution off), ECUDA (allocation).
  */
 pdrt_status pdrt_plan_set_spectrum_memo(pdrt_plan_t p, int32_t enable);
