@@ -333,8 +333,9 @@ __device__ __forceinline__ void twiddle_powers(float2 *v, float2 w)
 //   INV  = false: decimation in frequency (DFT then twiddle W_L^{jq});
 //   INV  = true : decimation in time (conjugate twiddle W_L^{-jm}, then DFT).
 // L is the pass's block size and nl = N / L; the twiddle W_L^e =
-// T[e nl tmul] with T the table of exp(-2 pi i t / (N tmul)).  MUL (first inverse column pass):
-// every element read is first multiplied by the kernel spectrum.
+// T[e nl tmul] with T the table of exp(-2 pi i t / (N tmul)).  MUL (first
+// inverse column pass): every element read is first multiplied by the
+// kernel spectrum.
 // Output of the last inverse row pass, written straight to the region: real
 // sample n of row tr is output u = in_i0 + n (or n - pu) of output row tr.
 struct OutCtx {
