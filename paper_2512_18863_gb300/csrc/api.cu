@@ -288,7 +288,7 @@ void memo_free(pdrt_plan_t p)
 
 // kernel-spectrum memo for slices of padded sizes up to pmax: one entry of
 // (pmax/2 + 1)^2 floats (rounded up to 4) per (control point, slice), tags
-// cleared (synchronously)
+// cleared before it returns
 cudaError_t memo_alloc(pdrt_plan_t p, int pmax)
 {
     memo_free(p);
@@ -299,6 +299,10 @@ cudaError_t memo_alloc(pdrt_plan_t p, int pmax)
     cudaError_t e = cudaMalloc(&memo, sizeof(float) * (size_t)(entries * stride));
     if (e == cudaSuccess) e = cudaMalloc(&tag, sizeof(int) * (size_t)entries);
     if (e == cudaSuccess) e = cudaMemset(tag, 0, sizeof(int) * (size_t)entries);
+    // the tags must be clear before any stream (non-blocking ones included)
+    // runs a convolution of the plan: a stale tag would read as a stored
+    // spectrum
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) {
         cudaFree(memo);
         cudaFree(tag);
