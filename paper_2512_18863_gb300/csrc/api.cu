@@ -637,11 +637,14 @@ pdrt_status pdrt_dose_forward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves_
     for (int c = 0; c < n_chunks; ++c) {
         const int b0 = c * p->chunk, nb = std::min(p->chunk, p->n_cp - b0);
         if (P.fft_pmax) {
-            // FFT for the slices within the size limit, tensor cores for the
-            // overflow list it leaves
+            // FFT for the slices within the size limit (their kernel spectra
+            // first, into the memo), tensor cores for the overflow list it
+            // leaves
             unsigned int *fc = P.fft_ctr + 4 * c;
             CU_TRY(timed(p, K_CONV_FFT_FWD, s,
                          [&] {
+                             const cudaError_t x = launch_spectrum(P, b0, nb, false, P.fft_pmax, s);
+                             if (x != cudaSuccess) return x;
                              return launch_conv_fft(P, b0, nb, false, P.fft_pmax, fc, P.fft_over, fc + 1,
                                                     p->fft_blocks[0], s);
                          }),
@@ -700,6 +703,8 @@ pdrt_status pdrt_dose_backward(pdrt_grid_t g, pdrt_plan_t p, const float *leaves
             unsigned int *fc = P.fft_ctr + 4 * c + 2;
             CU_TRY(timed(p, K_CONV_FFT_ADJ, s,
                          [&] {
+                             const cudaError_t x = launch_spectrum(P, b0, nb, true, P.fft_pmax, s);
+                             if (x != cudaSuccess) return x;
                              return launch_conv_fft(P, b0, nb, true, P.fft_pmax, fc, P.fft_over, fc + 1,
                                                     p->fft_blocks[1], s);
                          }),

@@ -634,6 +634,109 @@ __device__ __forceinline__ FftSmem fft_smem(unsigned char *smem, int pmax)
     return m;
 }
 
+// Kernel spectrum of one slice into Kf[kv'][ku] (kv' < pv/2 + 1, ku <= pu/2,
+// rows of pitch floats; shared or global memory) by the NT threads of the
+// CTA: K(p, q) (the expressions of the other convolution kernels), A = K Cv,
+// Kf = scale / (pu pv) Cu^T A.  KT and A are shared scratch ([R1][R1p] and
+// [R1][nkv4] floats).  Starts between barriers; ends after the Kf stores,
+// before the barrier that must follow them.
+template <int NT, class PL>
+__device__ __forceinline__ void slice_spectrum(const PL &P, const SliceTab &st, int R, int pu, int pv,
+                                               float *__restrict__ KT, float *__restrict__ A,
+                                               float *__restrict__ Kf, int pitch)
+{
+    const Lattice &L = P.lat;
+    const int R1 = R + 1, R1p = (R1 + 3) & ~3, tid = threadIdx.x;
+    const bool sym = L.du == L.dv;                   // K(p, q) = K(q, p)
+    const int hu = pu / 2, nkv = pv / 2 + 1, nkv4 = (nkv + 3) & ~3, hu4 = (hu + 1 + 3) & ~3;
+    const SizeOff ou = size_offsets(pu, R), ov = size_offsets(pv, R);
+    const float *Cv = P.fft_cos + ov.cos;        // [q][kv'], c_q folded in
+    const float *Cu = P.fft_cos + ou.cos;        // [p][ku], c_p folded in
+    // Kernel spectrum: K(p, q) (the expressions of the other convolution
+    // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
+    // K is stored transposed, KT[q][p] (rows of R1p = R1 rounded up to 4),
+    // so that both products read 4-wide vectors of each operand.
+    for (int idx = tid; idx < R1 * R1; idx += NT) {
+        const int pp = idx / R1, q = idx - pp * R1;
+        if (sym && pp > q) continue;
+        const float pu_mm = pp * L.du, qv = q * L.dv;
+        const float r = sqrtf(pu_mm * pu_mm + qv * qv);
+        const float kv = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
+                         st.wn[2] * expf(-st.a[2] * r);
+        KT[q * R1p + pp] = kv;
+        if (sym) KT[pp * R1p + q] = kv;
+    }
+    for (int idx = tid; idx < R1 * (R1p - R1); idx += NT) {   // zero padding columns
+        const int q = idx / (R1p - R1);
+        KT[q * R1p + R1 + (idx - q * (R1p - R1))] = 0.f;
+    }
+    __syncthreads();
+    // A[4 p4 .. +3][4 g .. +3] per item
+    {
+        const int G4 = nkv4 / 4, P4 = R1p / 4;
+        const FastDiv dg = fast_div(G4);
+        for (int idx = tid; idx < P4 * G4; idx += NT) {
+            const int p4 = idx / dg, g = idx - p4 * G4;
+            float4 acc[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 *kt = reinterpret_cast<const float4 *>(KT) + p4;
+            const float4 *cv = reinterpret_cast<const float4 *>(Cv) + g;
+            for (int q = 0; q < R1; ++q) {
+                const float4 kk = kt[q * P4];
+                const float4 c = __ldg(cv + q * G4);
+                const float k4[4] = {kk.x, kk.y, kk.z, kk.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    acc[a].x = fmaf(k4[a], c.x, acc[a].x);
+                    acc[a].y = fmaf(k4[a], c.y, acc[a].y);
+                    acc[a].z = fmaf(k4[a], c.z, acc[a].z);
+                    acc[a].w = fmaf(k4[a], c.w, acc[a].w);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+                if (4 * p4 + a < R1) reinterpret_cast<float4 *>(A)[(4 * p4 + a) * G4 + g] = acc[a];
+        }
+    }
+    __syncthreads();
+    // Kf[4 i4 .. +3][4 g .. +3] per item
+    {
+        const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
+        const int U4 = hu4 / 4, V4 = nkv4 / 4;
+        const FastDiv du4 = fast_div(U4);
+        for (int idx = tid; idx < V4 * U4; idx += NT) {
+            const int i4 = idx / du4, g = idx - i4 * U4;
+            float4 acc[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 *av = reinterpret_cast<const float4 *>(A) + i4;
+            const float4 *cu = reinterpret_cast<const float4 *>(Cu) + g;
+            for (int pp = 0; pp < R1; ++pp) {
+                const float4 aa = av[pp * V4];
+                const float4 c = __ldg(cu + pp * U4);
+                const float a4[4] = {aa.x, aa.y, aa.z, aa.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    acc[a].x = fmaf(a4[a], c.x, acc[a].x);
+                    acc[a].y = fmaf(a4[a], c.y, acc[a].y);
+                    acc[a].z = fmaf(a4[a], c.z, acc[a].z);
+                    acc[a].w = fmaf(a4[a], c.w, acc[a].w);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int kv = 4 * i4 + a;
+                if (kv >= nkv) continue;
+                const float r4[4] = {acc[a].x, acc[a].y, acc[a].z, acc[a].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * g + e <= hu) Kf[kv * pitch + 4 * g + e] = r4[e] * kscale;
+            }
+        }
+    }
+}
+
 // Convolution of one (control point, slice) item of the chunk starting at
 // control point b0, by the whole CTA; a slice beyond the size limit pmax is
 // appended to the overflow list instead.  Every thread calls it with the
@@ -655,7 +758,6 @@ __device__ __forceinline__ void fft_slice(const PL &P, int R, int b0, int item, 
     float *KT = reinterpret_cast<float *>(S);        // spectrum scratch before the fill: [q][p]
     float *A = KT + R1 * R1p;                        // [p][kv'] (16-byte aligned rows)
     const int tid = threadIdx.x;
-    const bool sym = L.du == L.dv;                   // K(p, q) = K(q, p)
     const int bl = item / L.nw, k = item - bl * L.nw, b = b0 + bl;
     const SliceTab st = P.slices[(long long)b * L.nw + k];
     int pu, pv;
@@ -676,14 +778,12 @@ __device__ __forceinline__ void fft_slice(const PL &P, int R, int b0, int item, 
     const SizeOff ou = size_offsets(pu, R), ov = size_offsets(pv, R);
     const float2 *Tu = g_fft_tw + ou.tw, *Tv = g_fft_tw + ov.tw;
     const short *pos_u = g_fft_pos + ou.pos, *ku_of = g_fft_ku + ou.ku, *kv_of = g_fft_kv + ov.kv;
-    const int nkv = pv / 2 + 1, nkv4 = (nkv + 3) & ~3, hu4 = (hu + 1 + 3) & ~3;
-    const float *Cv = P.fft_cos + ov.cos;        // [q][kv'], c_q folded in
-    const float *Cu = P.fft_cos + ou.cos;        // [p][ku], c_p folded in
+    const int nkv = pv / 2 + 1;
     // memoised spectrum of this slice: it depends on the slice's depth,
     // kernel and magnification (fixed by the plan) and on (pu, pv) only, so
-    // an entry tagged with the same sizes holds exactly what the three steps
-    // below would compute (every thread reads the same tag: no CTA of this
-    // launch writes it)
+    // an entry tagged with the same sizes holds exactly what slice_spectrum
+    // would compute (every thread reads the same tag: no CTA of this launch
+    // writes it)
     const long long ce = (long long)b * L.nw + k;
     const bool memo = P.kf_memo != nullptr && pu <= P.kf_pmax && pv <= P.kf_pmax;
     const int ktag = (pu << 16) | pv;
@@ -692,89 +792,7 @@ __device__ __forceinline__ void fft_slice(const PL &P, int R, int b0, int item, 
     float4 *memo4 = memo ? reinterpret_cast<float4 *>(P.kf_memo + ce * P.kf_stride) : nullptr;
 
     if (!hit) {
-        // Kernel spectrum: K(p, q) (the expressions of the other convolution
-        // kernels), A = K Cv, Kf[kv'][ku] = scale / (pu pv) sum_p Cu[p][ku] A[p][kv'].
-        // K is stored transposed, KT[q][p] (rows of R1p = R1 rounded up to 4),
-        // so that both products read 4-wide vectors of each operand.
-        for (int idx = tid; idx < R1 * R1; idx += kFftThreads) {
-            const int pp = idx / R1, q = idx - pp * R1;
-            if (sym && pp > q) continue;
-            const float pu_mm = pp * L.du, qv = q * L.dv;
-            const float r = sqrtf(pu_mm * pu_mm + qv * qv);
-            const float kv = st.wn[0] * expf(-st.a[0] * r) + st.wn[1] * expf(-st.a[1] * r) +
-                             st.wn[2] * expf(-st.a[2] * r);
-            KT[q * R1p + pp] = kv;
-            if (sym) KT[pp * R1p + q] = kv;
-        }
-        for (int idx = tid; idx < R1 * (R1p - R1); idx += kFftThreads) {   // zero padding columns
-            const int q = idx / (R1p - R1);
-            KT[q * R1p + R1 + (idx - q * (R1p - R1))] = 0.f;
-        }
-        __syncthreads();
-        // A[4 p4 .. +3][4 g .. +3] per item
-        {
-            const int G4 = nkv4 / 4, P4 = R1p / 4;
-            const FastDiv dg = fast_div(G4);
-            for (int idx = tid; idx < P4 * G4; idx += kFftThreads) {
-                const int p4 = idx / dg, g = idx - p4 * G4;
-                float4 acc[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 *kt = reinterpret_cast<const float4 *>(KT) + p4;
-                const float4 *cv = reinterpret_cast<const float4 *>(Cv) + g;
-                for (int q = 0; q < R1; ++q) {
-                    const float4 kk = kt[q * P4];
-                    const float4 c = __ldg(cv + q * G4);
-                    const float k4[4] = {kk.x, kk.y, kk.z, kk.w};
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        acc[a].x = fmaf(k4[a], c.x, acc[a].x);
-                        acc[a].y = fmaf(k4[a], c.y, acc[a].y);
-                        acc[a].z = fmaf(k4[a], c.z, acc[a].z);
-                        acc[a].w = fmaf(k4[a], c.w, acc[a].w);
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-                    if (4 * p4 + a < R1) reinterpret_cast<float4 *>(A)[(4 * p4 + a) * G4 + g] = acc[a];
-            }
-        }
-        __syncthreads();
-        // Kf[4 i4 .. +3][4 g .. +3] per item
-        {
-            const float kscale = st.tdd * st.c2 / ((float)pu * (float)pv);
-            const int U4 = hu4 / 4, V4 = nkv4 / 4;
-            const FastDiv du4 = fast_div(U4);
-            for (int idx = tid; idx < V4 * U4; idx += kFftThreads) {
-                const int i4 = idx / du4, g = idx - i4 * U4;
-                float4 acc[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) acc[a] = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 *av = reinterpret_cast<const float4 *>(A) + i4;
-                const float4 *cu = reinterpret_cast<const float4 *>(Cu) + g;
-                for (int pp = 0; pp < R1; ++pp) {
-                    const float4 aa = av[pp * V4];
-                    const float4 c = __ldg(cu + pp * U4);
-                    const float a4[4] = {aa.x, aa.y, aa.z, aa.w};
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        acc[a].x = fmaf(a4[a], c.x, acc[a].x);
-                        acc[a].y = fmaf(a4[a], c.y, acc[a].y);
-                        acc[a].z = fmaf(a4[a], c.z, acc[a].z);
-                        acc[a].w = fmaf(a4[a], c.w, acc[a].w);
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    const int kv = 4 * i4 + a;
-                    if (kv >= nkv) continue;
-                    const float r4[4] = {acc[a].x, acc[a].y, acc[a].z, acc[a].w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (4 * g + e <= hu) Kf[kv * G.pitch + 4 * g + e] = r4[e] * kscale;
-                }
-            }
-        }
+        slice_spectrum<kFftThreads>(P, st, R, pu, pv, KT, A, Kf, G.pitch);
     } else {
         for (int t = tid; t < nkf4; t += kFftThreads) reinterpret_cast<float4 *>(Kf)[t] = __ldg(memo4 + t);
     }
@@ -974,6 +992,45 @@ k_conv_fft_multi(const __grid_constant__ FftBatchArgs A, int pmax, unsigned int 
         unsigned int *ctr = P.fft_ctr + 4 * r.w + (ADJ ? 2 : 0);
         fft_slice<ADJ>(P, P.R, r.x, item - r.z, P.fft_pmax, P.fft_over, ctr + 1, sm);
     }
+}
+
+// Spectra of one pass's slices into the kernel-spectrum memo, ahead of the
+// FFT convolution (which then takes them from the memo): one CTA of
+// kSpecThreads per (control point, slice) item; items without FFT work, with
+// sizes beyond the memo or the size limit, or whose entry already holds
+// their sizes, return at once.  The spectrum is the FFT kernel's own
+// (slice_spectrum), so the memo holds the same bytes either way.
+constexpr int kSpecThreads = 128;
+
+__global__ void __launch_bounds__(kSpecThreads) k_spectrum(PlanDev P, int b0, int nb, int pmax, int adjoint)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Lattice &L = P.lat;
+    const int bl = (int)blockIdx.x / L.nw, k = (int)blockIdx.x - bl * L.nw, b = b0 + bl;
+    if (bl >= nb) return;
+    const int R = P.mach.R;
+    const SliceTab st = P.slices[(long long)b * L.nw + k];
+    int pu, pv;
+    fft_slice_sizes(st, adjoint != 0, R, pu, pv);
+    if (pu == 0 || pu > pmax || pv > pmax || pu > P.kf_pmax || pv > P.kf_pmax) return;
+    const long long ce = (long long)b * L.nw + k;
+    const int ktag = (pu << 16) | pv;
+    if (P.kf_tag[ce] == ktag) return;
+    const int R1 = R + 1, R1p = (R1 + 3) & ~3;
+    float *KT = reinterpret_cast<float *>(smem);
+    float *A = KT + R1 * R1p;
+    slice_spectrum<kSpecThreads>(P, st, R, pu, pv, KT, A, P.kf_memo + ce * P.kf_stride, pu / 2 + 1);
+    if (threadIdx.x == 0) P.kf_tag[ce] = ktag;
+}
+
+cudaError_t launch_spectrum(const PlanDev &P, int b0, int nb, bool adjoint, int pmax, cudaStream_t s)
+{
+    if (!P.kf_memo || !pmax || nb < 1) return cudaSuccess;
+    const int R1 = P.mach.R + 1, R1p = (R1 + 3) & ~3, w4 = ((P.kf_pmax / 2 + 1) + 3) & ~3;
+    const int smem = (R1 * R1p + R1 * w4) * (int)sizeof(float);
+    k_spectrum<<<(unsigned)(nb * P.lat.nw), kSpecThreads, smem, s>>>(P, b0, nb, pmax, adjoint ? 1 : 0);
+    internal_count_launch();
+    return cudaGetLastError();
 }
 
 namespace {

@@ -388,6 +388,10 @@ cudaError_t launch_conv_tc(const PlanDev &P, int b0, int nb, bool adjoint, unsig
 cudaError_t launch_conv_fft(const PlanDev &P, int b0, int nb, bool adjoint, int pmax, unsigned int *counter,
                             int *over_list, unsigned int *over_count, int grid_blocks, cudaStream_t s);
 int conv_fft_smem_bytes(int pmax, int R);
+// the kernel spectra of pass b0 .. b0 + nb - 1 into the plan's memo, for the
+// padded sizes of one direction (a no-op without a memo); the FFT
+// convolution of the pass then takes them from it
+cudaError_t launch_spectrum(const PlanDev &P, int b0, int nb, bool adjoint, int pmax, cudaStream_t s);
 // What the FFT convolution reads of a plan: the batched launch carries one
 // of these per entry in its kernel parameters.
 struct FftPlan {
