@@ -560,8 +560,10 @@ def _roofline(prof, work, steps, workload):
     """Roofline of the dominant kernel.  With the FFT path on it is the FFT
     convolution, bound by the FP32 pipes: achieved = its algorithmic FLOPs
     (work.fft_flops: 2 x 2.5 N log2 N per slice and direction for the real
-    2-D transforms, N = Pu Pv, plus the kernel spectrum's cosine sums and the
-    product) over its CUDA-event time, peak = 152 SM x 128 FP32 lanes x 2 FLOP
+    2-D transforms, N = Pu Pv, plus the product, plus the kernel spectrum's
+    cosine sums once per slice and padded size: the adjoint takes the
+    forward's from the memo) over its CUDA-event time (the spectrum kernel's
+    included), peak = 152 SM x 128 FP32 lanes x 2 FLOP
     x 2070 MHz.  Otherwise the tensor-core convolution against the measured
     sustained BF16 peak, with the direct convolution's 2 (2R+1)^2 FLOP per
     support point.  The direct-convolution-equivalent rate of all
@@ -587,7 +589,7 @@ def _roofline(prof, work, steps, workload):
                                    "capture at this workload, mean of forward and adjoint" if traffic else None),
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 FLOP x 2070 MHz",
                 "flops": "algorithmic FFT: 2 x 2.5 N log2 N per slice and direction (N = Pu Pv) "
-                         "+ kernel spectrum + product",
+                         "+ product + kernel spectrum once per slice and padded size",
                 "flops_per_launch": flops / n, "ms_per_launch": fft_ms / n,
                 "tc_overflow_ms_per_step": tc_ms / steps,
                 "direct_equivalent_tflops": direct}

@@ -188,9 +188,11 @@ typedef struct {
     double fft_flops;            /* FP32 FLOPs of the FFT convolution of one forward + one
                                     adjoint pass on the slices it takes: per slice and direction
                                     2 x 2.5 N log2 N for the forward and inverse real 2-D FFTs
-                                    (N = Pu Pv), the kernel spectrum's cosine sums
-                                    2 (R+1)^2 (Pv/2+1) + 2 (R+1)(Pv/2+1)(Pu/2+1) and the
-                                    product 2 Pv (Pu/2+1) */
+                                    (N = Pu Pv) and the product 2 Pv (Pu/2+1); the kernel
+                                    spectrum's cosine sums 2 (R+1)^2 (Pv/2+1) +
+                                    2 (R+1)(Pv/2+1)(Pu/2+1) per slice in the forward, and in
+                                    the adjoint where the spectrum memo does not hold its
+                                    sizes */
     int64_t fft_slices;          /* (slice, direction) pairs the FFT convolution takes */
     int64_t tc_slices;           /* (slice, direction) pairs left to the tensor cores */
 } pdrt_work;

@@ -867,6 +867,8 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
         CU_TRY(cudaMemcpy(sl.data(), p->dev.slices, sizeof(SliceTab) * sl.size(), cudaMemcpyDeviceToHost),
                "read slice tables");
         for (const SliceTab &st : sl) {
+            int fpu = 0, fpv = 0;   // the forward's padded sizes (its spectrum)
+            fft_slice_sizes(st, false, R, fpu, fpv);
             for (int adj = 0; adj < 2; ++adj) {
                 if (p->dev.fft_pmax) {
                     int pu = 0, pv = 0;
@@ -874,8 +876,13 @@ pdrt_status pdrt_plan_work(pdrt_plan_t p, pdrt_stream_t stream, pdrt_work *out)
                     if (pu == 0) continue;
                     if (pu <= p->dev.fft_pmax && pv <= p->dev.fft_pmax) {
                         const double n = (double)pu * pv, hu1 = pu / 2 + 1, kv1 = pv / 2 + 1;
-                        out->fft_flops += 2.0 * 2.5 * n * log2(n) + 2.0 * (R + 1) * (R + 1) * kv1 +
-                                          2.0 * (R + 1) * kv1 * hu1 + 2.0 * pv * hu1;
+                        // the spectrum once per call and size: the adjoint
+                        // takes the forward's from the memo when it pads alike
+                        const bool memo_hit = adj && p->dev.kf_memo && pu == fpu && pv == fpv &&
+                                              pu <= p->dev.kf_pmax && pv <= p->dev.kf_pmax;
+                        out->fft_flops += 2.0 * 2.5 * n * log2(n) + 2.0 * pv * hu1;
+                        if (!memo_hit)
+                            out->fft_flops += 2.0 * (R + 1) * (R + 1) * kv1 + 2.0 * (R + 1) * kv1 * hu1;
                         out->fft_slices += 1;
                         continue;
                     }
