@@ -305,22 +305,23 @@ def _reference(args):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch from a
 # one-pass ncu capture of the 256x256x160 two-arc plan at R = 20 px, 178
-# control points per launch (profiles/dram_pelvis256_2x178_R20.md).  Each
-# entry holds the SHA-256 prefixes of the sources the kernel is built from; a
-# figure is reported only while the sources and the workload match the
-# capture, else null.
+# control points per launch (profiles/dram_pelvis256_2x178_R20.md); the FFT
+# entries add the spectrum kernel launched (and timed) with each FFT pass.
+# Each entry holds the SHA-256 prefixes of the sources the kernel is built
+# from; a figure is reported only while the sources and the workload match
+# the capture, else null.
 _CAPTURES = {
     "workload": "pelvis256x256x160_2x178cp_R4cm",
     "conv_forward_fft": {"src": ("csrc/k_conv_fft.cu", "csrc/pdrt_impl.cuh"),
-                         "sha": "bf95b5dcc3b68b36+9bcd876871eb1683", "bytes": 1.7514e9},
+                         "sha": "bb152f6734abf8a1+635819d77a80519b", "bytes": 2.1025e9},
     "conv_adjoint_fft": {"src": ("csrc/k_conv_fft.cu", "csrc/pdrt_impl.cuh"),
-                         "sha": "bf95b5dcc3b68b36+9bcd876871eb1683", "bytes": 2.1382e9},
+                         "sha": "bb152f6734abf8a1+635819d77a80519b", "bytes": 2.1461e9},
     "gather_accumulate": {"src": ("csrc/k_gather.cu", "csrc/pdrt_impl.cuh"),
-                          "sha": "f9d6a140dfd9f8d7+9bcd876871eb1683", "bytes": 1.6050e9},
+                          "sha": "f9d6a140dfd9f8d7+635819d77a80519b", "bytes": 1.6072e9},
     "gather_transpose": {"src": ("csrc/k_gather.cu", "csrc/pdrt_impl.cuh"),
-                         "sha": "f9d6a140dfd9f8d7+9bcd876871eb1683", "bytes": 1.9869e9},
+                         "sha": "f9d6a140dfd9f8d7+635819d77a80519b", "bytes": 1.9807e9},
     "mag_transpose": {"src": ("csrc/k_adjoint.cu", "csrc/pdrt_impl.cuh"),
-                      "sha": "7e30bff0a6f71a37+9bcd876871eb1683", "bytes": 0.4229e9},
+                      "sha": "7e30bff0a6f71a37+635819d77a80519b", "bytes": 0.4359e9},
 }
 
 
