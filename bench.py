@@ -252,14 +252,34 @@ def _cpu_baseline(w, n_cps):
     rng = np.random.default_rng(0)
     g = rng.standard_normal(sub.phantom.shape)
     t0 = time.perf_counter()
-    mod.dose()
-    mod.dose_grad(g)
+    dose = mod.dose()
+    grads = mod.dose_grad(g)
     dt = time.perf_counter() - t0
-    return {"value": (n_cps / CP_PER_ARC) / dt, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle", "cpu_model": _cpu_model(),
-            "sample": f"{n_cps} of {w.plan.n_cp} control points (fwd+adjoint) on the full "
-                      f"{'x'.join(str(s) for s in w.phantom.shape[::-1])} grid, FP64, OpenMP; "
-                      f"{dt:.1f} s"}
+    out = {"value": (n_cps / CP_PER_ARC) / dt, "unit": UNIT, "cores": oracle.num_threads(),
+           "kind": "oracle", "cpu_model": _cpu_model(),
+           "sample": f"{n_cps} of {w.plan.n_cp} control points (fwd+adjoint) on the full "
+                     f"{'x'.join(str(s) for s in w.phantom.shape[::-1])} grid, FP64, OpenMP; "
+                     f"{dt:.1f} s"}
+    return out, (sub, g, dose, grads)
+
+
+def _accuracy(sample):
+    """The engine on the CPU baseline's sample of control points against the
+    oracle's results (outside any timed region): the largest dose deviation
+    relative to the maximum dose and the largest gradient deviation relative
+    to each class's largest gradient (the parity bars are 1e-4 and 1e-3)."""
+    from paper_2512_18863_gb300.engine import DoseEngine
+    sub, g, dose_ref, grads_ref = sample
+    eng = DoseEngine(sub.phantom, sub.machine, sub.plan.gantry_deg, sub.plan.iso)
+    d = eng.forward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu).cpu().numpy().astype(np.float64)
+    grads = [t.cpu().numpy().astype(np.float64)
+             for t in eng.backward(sub.plan.leaves, sub.plan.jaws, sub.plan.mu, g.astype(np.float32))]
+    eng.close()
+    rel = lambda a, r: float(np.abs(a - r).max() / max(float(np.abs(r).max()), 1e-300))
+    return {"sample": f"the CPU baseline's {sub.plan.n_cp} control points, full grid, same kernel radius",
+            "dose_max_err_rel_max": rel(d, dose_ref),
+            "grad_max_err_rel_max": {n: rel(a, r) for n, a, r in zip(("leaves", "jaws", "mu"), grads, grads_ref)},
+            "bars": {"dose": 1e-4, "grad": 1e-3}}
 
 
 def _reference(args):
@@ -508,9 +528,10 @@ def _gpu(args):
                "h2d_bytes_per_step": el([h_leaves, h_jaws, h_mu, h_g]),
                "d2h_bytes_per_step": el([h_dose, h_dl, h_dj, h_dm])}
 
-    cpu = None
+    cpu = accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = _cpu_baseline(w, args.cpu_sample_cps)
+        cpu, sample = _cpu_baseline(w, args.cpu_sample_cps)
+        accuracy = _accuracy(sample)
     info = eng.info
     # the literal "vs HBM roofline" figure: bytes the method must move per
     # step (dose written, its gradient read, parameters and gradients) over
@@ -540,7 +561,9 @@ def _gpu(args):
                                      "beyond the FFT size limit on the tensor cores with a BF16 hi/lo "
                                      "split (three products, FP32 accumulation)",
                              "parity_bar": "max |dD| <= 1e-4 max D, gradients 1e-3 relative "
-                                           "(tests against the FP64 oracle)"},
+                                           "(tests against the FP64 oracle)",
+                             "measured": "the line's accuracy key: this run's engine against the oracle "
+                                         "on the CPU baseline's control points"},
                "roofline": roofline, "kernel_hbm": kernel_hbm,
                "kernels": kernels, "work": work, "gpu_launches": launches,
                "launch": {"scratch_gb": args.scratch_gb,
@@ -551,7 +574,8 @@ def _gpu(args):
                           "chunk_cp": info.get("chunk_cp")},
                "configs": sweep, "batch32": batch32,
                "hbm_literal": hbm, "warm_start": warm, "step_ms": step_ms,
-               "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "spectrum_memo": memo}
+               "clocks": clk, "e2e": e2e, "cpu_baseline": cpu, "accuracy": accuracy,
+               "spectrum_memo": memo}
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
