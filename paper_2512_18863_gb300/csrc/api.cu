@@ -1340,6 +1340,9 @@ pdrt_status pdrt_batch_create(pdrt_batch_t *out, int32_t n, const pdrt_grid_t *g
             cudaMemsetAsync(P.fft_ctr, 0, sizeof(unsigned) * 4 * nch[i], bstream(i));
             chk(launch_raster(P, leaves_dev[i], jaws_dev[i], mu_dev[i], bstream(i)));
             chk(launch_tables(P, bstream(i)));
+            // the forward's kernel spectra of every control point into the
+            // plan's memo (no-op without one): the FFT rounds take them
+            if (P.fft_pmax) chk(launch_spectrum(P, 0, plans[i]->n_cp, false, P.fft_pmax, bstream(i)));
         }
         join();
         // forward: per round the shared FFT launch over pass c of every FFT
