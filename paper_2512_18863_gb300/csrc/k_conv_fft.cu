@@ -742,7 +742,7 @@ __device__ __forceinline__ void slice_spectrum(const PL &P, const SliceTab &st, 
 // appended to the overflow list instead.  Every thread calls it with the
 // same arguments; it starts and ends between barriers.
 template <bool ADJ, class PL>
-__device__ __forceinline__ void fft_slice(const PL &P, int R, int b0, int item, int pmax,
+__device__ __forceinline__ void fft_slice(const PL &P, int R, int b0, int nb, int item, int pmax,
                                           int *__restrict__ over_list, unsigned int *__restrict__ over_count,
                                           const FftSmem &sm)
 {
@@ -758,13 +758,15 @@ __device__ __forceinline__ void fft_slice(const PL &P, int R, int b0, int item, 
     float *KT = reinterpret_cast<float *>(S);        // spectrum scratch before the fill: [q][p]
     float *A = KT + R1 * R1p;                        // [p][kv'] (16-byte aligned rows)
     const int tid = threadIdx.x;
-    const int bl = item / L.nw, k = item - bl * L.nw, b = b0 + bl;
+    // items in slice-major order: the CTAs in flight work on neighbouring
+    // depths of every control point, whose padded sizes mostly agree
+    const int k = item / nb, bl = item - k * nb, b = b0 + bl;
     const SliceTab st = P.slices[(long long)b * L.nw + k];
     int pu, pv;
     fft_slice_sizes(st, ADJ, R, pu, pv);
     if (pu == 0) return;                     // no work in this slice
     if (pu > pmax || pv > pmax) {              // too large: the tensor-core kernel takes it
-        if (tid == 0) over_list[atomicAdd(over_count, 1u)] = item;
+        if (tid == 0) over_list[atomicAdd(over_count, 1u)] = bl * L.nw + k;   // control-point-major
         return;
     }
     const TcBoxes bx = tc_boxes(st, ADJ, R);
@@ -954,7 +956,7 @@ __global__ void __launch_bounds__(kFftThreads, MINB) k_conv_fft(PlanDev P, int b
         __syncthreads();
         const int item = *s_item;
         if (item >= n_items) break;
-        fft_slice<ADJ>(P, P.mach.R, b0, item, pmax, over_list, over_count, sm);
+        fft_slice<ADJ>(P, P.mach.R, b0, nb, item, pmax, over_list, over_count, sm);
     }
 }
 
@@ -990,7 +992,7 @@ k_conv_fft_multi(const __grid_constant__ FftBatchArgs A, int pmax, unsigned int 
         const FftPlan &P = A.plan[e];
         const int4 r = A.round[e];
         unsigned int *ctr = P.fft_ctr + 4 * r.w + (ADJ ? 2 : 0);
-        fft_slice<ADJ>(P, P.R, r.x, item - r.z, P.fft_pmax, P.fft_over, ctr + 1, sm);
+        fft_slice<ADJ>(P, P.R, r.x, r.y, item - r.z, P.fft_pmax, P.fft_over, ctr + 1, sm);
     }
 }
 
