@@ -65,6 +65,9 @@ def test_null_handles_rejected():
     assert lib.pdrt_plan_upload(C.byref(out), None, 1, None, None, C.byref(m), 0, None) == 1
     info = _lib.pdrt_plan_info()
     assert lib.pdrt_plan_get_info(None, C.byref(info)) == 1
+    assert lib.pdrt_plan_set_spectrum_memo(None, 1) == 1
+    assert lib.pdrt_plan_set_spectrum_memo(None, 0) == 1
+    assert lib.pdrt_plan_reset_spectrum_memo(None, None) == 1
 
 
 def test_struct_layouts_match_the_header(tmp_path):
